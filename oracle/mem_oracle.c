@@ -1,0 +1,836 @@
+/*
+ * mem_oracle.c -- FP64 CPU oracle for the 35-moment maximal-entropy moment
+ * method (MEM) of arXiv 2303.02898, "Stabilizing the Maximal Entropy Moment
+ * Method for Rarefied Gas Dynamics at Single-Precision".
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain, obviously-correct
+ * reference that the CUDA library is checked against.  Only the test suite,
+ * __graft_entry__.smoke() and the CPU-baseline / reference arm of bench.py may
+ * load it.  It shares no code, table or constant generator with the CUDA
+ * library, and it never reads anything the CUDA library produced as an
+ * expected value.
+ *
+ * Everything is FP64, dense, in the order the paper states it:
+ *   - tensor Gauss-Hermite rule (Golub-Welsch: eigen-decomposition of the
+ *     Jacobi matrix of the probabilists' Hermite polynomials);
+ *   - the 35 orthonormal Hermite-product statistics phi_i(ubar) of total
+ *     degree <= 4 in 3D velocity (Appendix B, orthonormal form of Eq.
+ *     "Sufficient 35", extended from the 1D cylindrical set to full 3D);
+ *   - the canonical-form moment map with the log-sum-exp partition function
+ *     (Eqs. "Numerical integration moments" and "MLE optimization goal log sum
+ *     exp", Section 3.1);
+ *   - Algorithm 1 (modified Newton with a multiple of the identity, Armijo
+ *     backtracking), objective/gradient/Hessian of Appendix C;
+ *   - the translation/dilation gauge and its change-of-gauge matrix
+ *     (Eqs. "Sufficient 35 ortho", "Change gauge M F", "Hermite parameters");
+ *   - characteristic speed = spectral radius of dF/dM (Eq. "The lax F");
+ *   - ES-BGK source (Appendix A), local Lax-Friedrichs finite-volume update
+ *     with neighbour gauge transforms and Strang-split collision (Algorithm 2);
+ *   - Rankine-Hugoniot states (Appendix D).
+ *
+ * Parity status: every function below has a pin in tests/test_oracle_pins.py
+ * (closed forms, invariants, brute force).  The paper's figures print no
+ * values, so nothing is pinned to a figure.
+ *
+ * Conventions (readings of the paper, also listed in the design doc):
+ *   - M_i(g) = int phi_i((u-w)/s) f(u) d^3u, the moments in the cell's gauge
+ *     g = (w_x,w_y,w_z,s_x,s_y,s_z); M_0 = n.
+ *   - beta_0 = n; beta_1..34 are the natural parameters relative to the
+ *     Gauss-Hermite base measure: f ~ n exp(-|ubar|^2/2 + sum_{i>=1} beta_i
+ *     phi_i(ubar)).  This is an exact re-parameterisation of the paper's
+ *     Lebesgue-measure beta (|ubar|^2/2 lies in the span of the statistics):
+ *     objective differences, gradient and Hessian are identical, so Algorithm
+ *     1 takes identical steps.  beta = 0 is the Maxwellian of the gauge.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define NP 35      /* number of statistics, total degree <= 4 in 3D */
+#define NMAXQ 64   /* largest 1D Gauss-Hermite order supported */
+
+/* ------------------------------------------------------------------------ */
+/* Multi-index table: statistic k <-> (a,b,c), a+b+c <= 4.  Ordered by total
+ * degree, then a descending, then b descending. */
+static int g_idx[NP][3];
+static int g_idx_ready = 0;
+
+static void build_index(void) {
+    if (g_idx_ready) return;
+    int k = 0;
+    for (int d = 0; d <= 4; ++d)
+        for (int a = d; a >= 0; --a)
+            for (int b = d - a; b >= 0; --b) {
+                g_idx[k][0] = a; g_idx[k][1] = b; g_idx[k][2] = d - a - b; ++k;
+            }
+    g_idx_ready = 1;
+}
+
+void or_basis_index(int *abc) {
+    build_index();
+    for (int k = 0; k < NP; ++k) for (int j = 0; j < 3; ++j) abc[3 * k + j] = g_idx[k][j];
+}
+
+int or_index_of(int a, int b, int c) {
+    build_index();
+    for (int k = 0; k < NP; ++k)
+        if (g_idx[k][0] == a && g_idx[k][1] == b && g_idx[k][2] == c) return k;
+    return -1;
+}
+
+/* Orthonormal probabilists' Hermite values he_0..he_kmax at x:
+ * He_{k+1} = x He_k - k He_{k-1}; he_k = He_k / sqrt(k!). */
+static void hermite_on(double x, int kmax, double *he) {
+    double Hm1 = 0.0, H = 1.0, fact = 1.0;
+    he[0] = 1.0;
+    for (int k = 0; k < kmax; ++k) {
+        double Hp = x * H - k * Hm1;
+        Hm1 = H; H = Hp;
+        fact *= (double)(k + 1);
+        he[k + 1] = H / sqrt(fact);
+    }
+}
+
+/* phi_i(ubar) for all 35 statistics. */
+void or_phi(const double *u, double *phi) {
+    build_index();
+    double hx[5], hy[5], hz[5];
+    hermite_on(u[0], 4, hx); hermite_on(u[1], 4, hy); hermite_on(u[2], 4, hz);
+    for (int k = 0; k < NP; ++k) phi[k] = hx[g_idx[k][0]] * hy[g_idx[k][1]] * hz[g_idx[k][2]];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dense symmetric eigen-decomposition by cyclic Jacobi rotations (textbook,
+ * FP64).  a is n x n row-major and is destroyed; eigenvalues to ev, the
+ * eigenvectors (columns) to v if v != NULL. */
+static void jacobi_eigen(int n, double *a, double *ev, double *v) {
+    if (v) { for (int i = 0; i < n * n; ++i) v[i] = 0.0; for (int i = 0; i < n; ++i) v[i * n + i] = 1.0; }
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int p = 0; p < n; ++p) {
+            diag += a[p * n + p] * a[p * n + p];
+            for (int q = p + 1; q < n; ++q) off += a[p * n + q] * a[p * n + q];
+        }
+        if (off <= 1e-30 * (diag + 1e-300)) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = a[p * n + q];
+                if (fabs(apq) < 1e-300) continue;
+                double theta = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) { /* columns p,q */
+                    double akp = a[k * n + p], akq = a[k * n + q];
+                    a[k * n + p] = c * akp - s * akq;
+                    a[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) { /* rows p,q */
+                    double apk = a[p * n + k], aqk = a[q * n + k];
+                    a[p * n + k] = c * apk - s * aqk;
+                    a[q * n + k] = s * apk + c * aqk;
+                }
+                if (v)
+                    for (int k = 0; k < n; ++k) {
+                        double vkp = v[k * n + p], vkq = v[k * n + q];
+                        v[k * n + p] = c * vkp - s * vkq;
+                        v[k * n + q] = s * vkp + c * vkq;
+                    }
+            }
+    }
+    for (int i = 0; i < n; ++i) ev[i] = a[i * n + i];
+}
+
+/* Gauss-Hermite rule for the standard normal weight (probabilists'), by
+ * Golub-Welsch: nodes = eigenvalues of the Jacobi matrix with off-diagonal
+ * sqrt(k), weights = squared first eigenvector components (sum to 1).
+ * Returns 0 on success. */
+int or_gh_rule(int n, double *x, double *w) {
+    if (n < 1 || n > NMAXQ) return -1;
+    double *J = calloc((size_t)n * n, sizeof(double)), *V = calloc((size_t)n * n, sizeof(double));
+    double ev[NMAXQ];
+    for (int k = 0; k + 1 < n; ++k) J[k * n + k + 1] = J[(k + 1) * n + k] = sqrt((double)(k + 1));
+    jacobi_eigen(n, J, ev, V);
+    int order[NMAXQ];
+    for (int i = 0; i < n; ++i) order[i] = i;
+    for (int i = 0; i < n; ++i) /* sort ascending */
+        for (int j = i + 1; j < n; ++j)
+            if (ev[order[j]] < ev[order[i]]) { int t = order[i]; order[i] = order[j]; order[j] = t; }
+    double sw = 0.0;
+    for (int i = 0; i < n; ++i) { x[i] = ev[order[i]]; w[i] = V[0 * n + order[i]] * V[0 * n + order[i]]; sw += w[i]; }
+    for (int i = 0; i < n; ++i) w[i] /= sw;
+    free(J); free(V);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Quadrature rule cache: tensor n^3 nodes ubar_q, log w_q, phi(ubar_q). */
+typedef struct { int n, Q; double *u; double *logw; double *phi; } rule_t;
+static rule_t g_rules[NMAXQ + 1];
+
+static const rule_t *get_rule(int n) {
+    if (n < 1 || n > NMAXQ) return NULL;
+    rule_t *r = &g_rules[n];
+    if (r->Q) return r;
+    #pragma omp critical(or_rule_init)
+    {
+        if (!r->Q) {
+            double x[NMAXQ], w[NMAXQ];
+            or_gh_rule(n, x, w);
+            int Q = n * n * n;
+            double *u = malloc(sizeof(double) * 3 * Q), *lw = malloc(sizeof(double) * Q), *ph = malloc(sizeof(double) * NP * Q);
+            for (int i = 0; i < n; ++i) for (int j = 0; j < n; ++j) for (int k = 0; k < n; ++k) {
+                int q = (i * n + j) * n + k;
+                u[3 * q] = x[i]; u[3 * q + 1] = x[j]; u[3 * q + 2] = x[k];
+                lw[q] = log(w[i]) + log(w[j]) + log(w[k]);
+                or_phi(&u[3 * q], &ph[NP * q]);
+            }
+            r->n = n; r->u = u; r->logw = lw; r->phi = ph;
+            #pragma omp flush
+            r->Q = Q;
+        }
+    }
+    return r;
+}
+
+int or_rule_nodes(int n, double *u, double *logw) {
+    const rule_t *r = get_rule(n);
+    if (!r) return -1;
+    memcpy(u, r->u, sizeof(double) * 3 * r->Q);
+    memcpy(logw, r->logw, sizeof(double) * r->Q);
+    return r->Q;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward map beta -> expectations under the discrete canonical-form
+ * distribution sigma_q = w_q exp(beta.phi_q - log Z)  (Section 3.1, Eqs.
+ * "Numerical integration moments" and the log-sum-exp form of log Z).
+ * Outputs (any may be NULL): logZ; m[i] = E phi_i; S[i][j] = E phi_i phi_j;
+ * X[i] = E ubar_x phi_i; XS[i][j] = E ubar_x phi_i phi_j. */
+void or_expect(int order, const double *beta, double *logZ, double *m, double *S, double *X, double *XS) {
+    const rule_t *r = get_rule(order);
+    int Q = r->Q;
+    double *e = malloc(sizeof(double) * Q);
+    double emax = -INFINITY;
+    for (int q = 0; q < Q; ++q) {
+        double s = r->logw[q];
+        for (int i = 1; i < NP; ++i) s += beta[i] * r->phi[NP * q + i];
+        e[q] = s;
+        if (s > emax) emax = s;
+    }
+    double Z = 0.0;
+    for (int q = 0; q < Q; ++q) { e[q] = exp(e[q] - emax); Z += e[q]; }
+    if (logZ) *logZ = emax + log(Z);
+    if (m) memset(m, 0, sizeof(double) * NP);
+    if (S) memset(S, 0, sizeof(double) * NP * NP);
+    if (X) memset(X, 0, sizeof(double) * NP);
+    if (XS) memset(XS, 0, sizeof(double) * NP * NP);
+    for (int q = 0; q < Q; ++q) {
+        double sg = e[q] / Z;
+        const double *ph = &r->phi[NP * q];
+        double ux = r->u[3 * q];
+        for (int i = 0; i < NP; ++i) {
+            if (m) m[i] += sg * ph[i];
+            if (X) X[i] += sg * ux * ph[i];
+            if (S || XS)
+                for (int j = 0; j <= i; ++j) {
+                    double p = sg * ph[i] * ph[j];
+                    if (S) S[i * NP + j] += p;
+                    if (XS) XS[i * NP + j] += ux * p;
+                }
+        }
+    }
+    for (int i = 0; i < NP; ++i)
+        for (int j = i + 1; j < NP; ++j) {
+            if (S) S[i * NP + j] = S[j * NP + i];
+            if (XS) XS[i * NP + j] = XS[j * NP + i];
+        }
+    free(e);
+}
+
+/* Objective of Appendix C, Eq. "MLE optimization goal", with beta_0 = n held
+ * at its minimiser: L = log Z - sum_{i>=1} beta_i M_i / n. */
+double or_objective(int order, const double *beta, const double *M) {
+    double lz;
+    or_expect(order, beta, &lz, NULL, NULL, NULL, NULL);
+    double s = 0.0;
+    for (int i = 1; i < NP; ++i) s += beta[i] * M[i] / M[0];
+    return lz - s;
+}
+
+/* Relative moment residual ||E phi(beta) - M/n||_2 / ||M/n||_2 (acceptance
+ * measure of the solve; slot 0 contributes 0 by construction). */
+double or_residual(int order, const double *beta, const double *M) {
+    double m[NP];
+    or_expect(order, beta, NULL, m, NULL, NULL, NULL);
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < NP; ++i) {
+        double t = M[i] / M[0];
+        den += t * t;
+        if (i) num += (m[i] - t) * (m[i] - t);
+    }
+    return sqrt(num / den);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1 (Section 3.2): Newton's method modified by adding a multiple of
+ * the identity, with backtracking line search on a relaxed Armijo test. */
+typedef struct {
+    double tol;        /* convergence tolerance on res (1e-8) */
+    int maxI;          /* iteration limit (500, as in every experiment) */
+    double lambda0;    /* first identity multiple (1e-3) */
+    double lambda_mul; /* growth per failed factorisation (10) */
+    int max_lambda;    /* cap on lambda retries (reading: unbounded in paper) */
+    double c;          /* Armijo slope factor (5e-4) */
+    double atol, rtol; /* Armijo floating-point slack (5e-6, 5e-5) */
+    int maxT;          /* line-search trials are s = 0..maxT (25) */
+    double alpha_min;  /* stagnation exit alpha <= 1e-6 */
+    int final_step;    /* apply the last computed Newton step on res <= tol */
+} or_opts;
+
+enum {
+    ST_CONVERGED = 1, ST_STAGNATED = 2, ST_MAXITER = 4, ST_NONFINITE = 8,
+    ST_LAMBDA = 16, ST_LAMBDA_CAP = 32, ST_BADINPUT = 64
+};
+
+static void default_opts(or_opts *o) {
+    o->tol = 1e-8; o->maxI = 500; o->lambda0 = 1e-3; o->lambda_mul = 10.0; o->max_lambda = 20;
+    o->c = 5e-4; o->atol = 5e-6; o->rtol = 5e-5; o->maxT = 25; o->alpha_min = 1e-6;
+    o->final_step = 1;
+}
+
+/* Standard Cholesky of the n x n matrix A + shift*I (row-major); fails on a
+ * pivot that is not positive and finite.  L is lower triangular. */
+static int cholesky(int n, const double *A, double shift, double *L) {
+    for (int i = 0; i < n * n; ++i) L[i] = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double d = A[j * n + j] + shift;
+        for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
+        if (!(d > 0.0) || !isfinite(d)) return 1;
+        double ljj = sqrt(d);
+        L[j * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double s = A[i * n + j];
+            for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+            L[i * n + j] = s / ljj;
+        }
+    }
+    return 0;
+}
+
+static void solve_lower(int n, const double *L, const double *b, double *x) {
+    for (int i = 0; i < n; ++i) {
+        double s = b[i];
+        for (int k = 0; k < i; ++k) s -= L[i * n + k] * x[k];
+        x[i] = s / L[i * n + i];
+    }
+}
+
+static void solve_upper_T(int n, const double *L, const double *b, double *x) { /* L^T x = b */
+    for (int i = n - 1; i >= 0; --i) {
+        double s = b[i];
+        for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+        x[i] = s / L[i * n + i];
+    }
+}
+
+/* Solve one cell.  M[35] (M_0 = n), beta[35] in: warm start (slots 1..34),
+ * out: solution with beta_0 = n.  Returns status bits; *iters = loop count;
+ * *res_out = last res; *lam_out = largest identity multiple used. */
+int or_solve(int order, const double *M, double *beta, const double *optv, int *iters, double *res_out, double *lam_out) {
+    or_opts o; default_opts(&o);
+    if (optv) { o.tol = optv[0]; o.maxI = (int)optv[1]; o.final_step = optv[2] != 0.0; }
+    const int D = NP - 1;
+    double n = M[0];
+    int st = 0;
+    if (!(n > 0.0) || !isfinite(n)) { if (iters) *iters = 0; return ST_BADINPUT; }
+    for (int i = 0; i < NP; ++i) if (!isfinite(M[i]) || !isfinite(beta[i])) { if (iters) *iters = 0; return ST_BADINPUT; }
+    double b[NP], db[NP] = {0}, G[NP] = {0}, m[NP], S[NP * NP], H[34 * 34], Lh[34 * 34], wv[34], rhs[34], trial[NP];
+    memcpy(b, beta, sizeof(b));
+    b[0] = n;
+    double Lcur = or_objective(order, b, M);
+    int it = 0, conv = 0;
+    double res = INFINITY, lam_used = 0.0, alpha = 1.0;
+    while (!conv && it <= o.maxI) {
+        /* BackTrackingLineSearch: alpha = 2 -> halve before each trial. */
+        alpha = 2.0;
+        int s = 0, sat = 0;
+        while (!sat && s <= o.maxT) {
+            if (!sat) alpha *= 0.5;
+            for (int i = 0; i < NP; ++i) trial[i] = b[i] + alpha * db[i];
+            trial[0] = n;
+            double Lt = or_objective(order, trial, M);
+            double LD = Lcur - Lt, gd = 0.0;
+            for (int i = 1; i < NP; ++i) gd += G[i] * alpha * db[i];
+            double gradD = -o.c * gd;
+            sat = (LD - gradD) >= -(o.atol + o.rtol * fabs(LD));
+            s += 1;
+        }
+        for (int i = 1; i < NP; ++i) b[i] += alpha * db[i];
+        Lcur = or_objective(order, b, M);
+        /* Hessian and gradient of L at beta (Appendix C). */
+        or_expect(order, b, NULL, m, S, NULL, NULL);
+        for (int i = 1; i < NP; ++i) G[i] = m[i] - M[i] / n;
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) H[i * D + j] = S[(i + 1) * NP + (j + 1)] - m[i + 1] * m[j + 1];
+        /* Cholesky, adding lambda*I until it succeeds. */
+        double lambda = o.lambda0;
+        int fail = cholesky(D, H, 0.0, Lh), tries = 0;
+        while (fail) {
+            if (tries >= o.max_lambda) break;
+            fail = cholesky(D, H, lambda, Lh);
+            st |= ST_LAMBDA;
+            if (lambda > lam_used) lam_used = lambda;
+            lambda *= o.lambda_mul;
+            ++tries;
+        }
+        if (fail) { st |= ST_LAMBDA_CAP | ST_NONFINITE; ++it; break; }
+        for (int i = 0; i < D; ++i) rhs[i] = -G[i + 1];
+        solve_lower(D, Lh, rhs, wv);
+        double dx[34];
+        solve_upper_T(D, Lh, wv, dx);
+        db[0] = 0.0;
+        for (int i = 0; i < D; ++i) db[i + 1] = dx[i];
+        double dg = 0.0;
+        for (int i = 1; i < NP; ++i) dg += db[i] * G[i];
+        res = 0.5 * fabs(dg);
+        if (!isfinite(res)) { st |= ST_NONFINITE; ++it; break; }
+        if (res <= o.tol) st |= ST_CONVERGED;
+        if (alpha <= o.alpha_min) st |= ST_STAGNATED;
+        conv = (res <= o.tol) || (alpha <= o.alpha_min);
+        ++it;
+    }
+    if (!conv && !(st & ST_NONFINITE)) st |= ST_MAXITER;
+    /* Algorithm 1 returns beta without the direction computed in the last
+     * pass.  The decrement res = |dbeta.grad|/2 <= tol bounds the objective
+     * error, not the moment residual (|grad|^2 <= 2 res lambda_max(H)), so by
+     * default the final Newton step is applied when the loop stops on
+     * res <= tol; final_step = 0 gives the literal order. */
+    if (o.final_step && (st & ST_CONVERGED))
+        for (int i = 1; i < NP; ++i) b[i] += db[i];
+    memcpy(beta, b, sizeof(b));
+    beta[0] = n;
+    if (iters) *iters = it;
+    if (res_out) *res_out = res;
+    if (lam_out) *lam_out = lam_used;
+    return st;
+}
+
+void or_solve_batch(int order, int64_t B, const double *M, double *beta, int *status, int *iters, const double *optv, int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    get_rule(order);
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t c = 0; c < B; ++c) {
+        int it = 0;
+        int st = or_solve(order, &M[NP * c], &beta[NP * c], optv, &it, NULL, NULL);
+        if (status) status[c] = st;
+        if (iters) iters[c] = it;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Change of gauge (Eq. "Change gauge M F").  For g = (w, s) and g' = (w', s'),
+ * ubar' = a*ubar + b per axis with a = s/s', b = (w - w')/s'.  T(g', g) maps
+ * M(g) -> M(g'): phi_i(ubar') = sum_j T_ij phi_j(ubar).  Built here by going
+ * through monomials: he_a(y) = sum_k H[a][k] y^k, y^k by the binomial theorem,
+ * x^j = sum_d E[j][d] he_d(x) with E = H^{-1}. */
+static void hermite_monomial_coeffs(double H[5][5]) {
+    double He[5][5] = {{0}};
+    He[0][0] = 1.0;
+    He[1][1] = 1.0;
+    for (int k = 1; k < 4; ++k)
+        for (int p = 0; p < 5; ++p) {
+            double v = -k * He[k - 1][p];
+            if (p > 0) v += He[k][p - 1];
+            He[k + 1][p] = v;
+        }
+    double fact = 1.0;
+    for (int a = 0; a < 5; ++a) {
+        if (a > 0) fact *= a;
+        for (int p = 0; p < 5; ++p) H[a][p] = He[a][p] / sqrt(fact);
+    }
+}
+
+static void axis_map(double a, double b, double t[5][5]) {
+    double H[5][5], E[5][5] = {{0}};
+    hermite_monomial_coeffs(H);
+    /* E = H^{-1}, lower triangular, by forward substitution on columns. */
+    for (int col = 0; col < 5; ++col)
+        for (int r = 0; r < 5; ++r) {
+            double s = (r == col) ? 1.0 : 0.0;
+            for (int k = 0; k < r; ++k) s -= H[r][k] * E[k][col];
+            E[r][col] = s / H[r][r];
+        }
+    /* x^j in he: x^j = sum_d Einv[j][d] he_d  where Einv = E (since H maps he->x^p
+       coefficients: he = H x  => x = E he). */
+    double C[5][5] = {{0}};
+    for (int k = 0; k < 5; ++k) { C[k][0] = 1.0; for (int j = 1; j <= k; ++j) C[k][j] = C[k - 1][j - 1] + (j <= k - 1 ? C[k - 1][j] : 0.0); }
+    for (int A = 0; A < 5; ++A)
+        for (int d = 0; d < 5; ++d) {
+            double s = 0.0;
+            for (int k = 0; k <= A; ++k)          /* he_A(y) = sum_k H[A][k] y^k */
+                for (int j = 0; j <= k; ++j)      /* y^k = sum_j C(k,j) a^j b^(k-j) x^j */
+                    s += H[A][k] * C[k][j] * pow(a, j) * pow(b, k - j) * E[j][d];
+            t[A][d] = s;
+        }
+}
+
+void or_gauge_T(const double *g_to, const double *g_from, double *T) {
+    build_index();
+    double t[3][5][5];
+    for (int ax = 0; ax < 3; ++ax) {
+        double a = g_from[3 + ax] / g_to[3 + ax];
+        double b = (g_from[ax] - g_to[ax]) / g_to[3 + ax];
+        axis_map(a, b, t[ax]);
+    }
+    for (int i = 0; i < NP; ++i)
+        for (int j = 0; j < NP; ++j)
+            T[i * NP + j] = t[0][g_idx[i][0]][g_idx[j][0]] * t[1][g_idx[i][1]][g_idx[j][1]] * t[2][g_idx[i][2]][g_idx[j][2]];
+}
+
+static void matvec35(const double *T, const double *x, double *y) {
+    for (int i = 0; i < NP; ++i) { double s = 0.0; for (int j = 0; j < NP; ++j) s += T[i * NP + j] * x[j]; y[i] = s; }
+}
+
+/* Hermite gauge of the distribution with moments M in gauge g (Eqs. "Hermite
+ * parameters", "Hermite parameters in moments"): mean velocity and variance.
+ * axisym = 1 is the 1D-shock form (w_y = w_z = 0, s_y = s_z = s_r with
+ * s_r^2 = (<u_y^2> + <u_z^2>)/2); axisym = 0 takes each axis on its own. */
+void or_hermite_gauge(const double *M, const double *g, int axisym, double *gH) {
+    double n = M[0];
+    double mean[3], ex2[3];
+    for (int ax = 0; ax < 3; ++ax) {
+        int e1[3] = {0, 0, 0}, e2[3] = {0, 0, 0};
+        e1[ax] = 1; e2[ax] = 2;
+        double m1 = M[or_index_of(e1[0], e1[1], e1[2])] / n;            /* E ubar */
+        double m2 = sqrt(2.0) * M[or_index_of(e2[0], e2[1], e2[2])] / n + 1.0; /* E ubar^2 */
+        mean[ax] = g[ax] + g[3 + ax] * m1;                              /* E u */
+        ex2[ax] = g[ax] * g[ax] + 2.0 * g[ax] * g[3 + ax] * m1 + g[3 + ax] * g[3 + ax] * m2; /* E u^2 */
+    }
+    if (axisym) {
+        gH[0] = mean[0]; gH[1] = 0.0; gH[2] = 0.0;
+        gH[3] = sqrt(ex2[0] - mean[0] * mean[0]);
+        double sr = sqrt(0.5 * (ex2[1] + ex2[2]));
+        gH[4] = sr; gH[5] = sr;
+    } else {
+        for (int ax = 0; ax < 3; ++ax) { gH[ax] = mean[ax]; gH[3 + ax] = sqrt(ex2[ax] - mean[ax] * mean[ax]); }
+    }
+}
+
+void or_transform_M(const double *g_to, const double *g_from, const double *M, double *Mout) {
+    double T[NP * NP];
+    or_gauge_T(g_to, g_from, T);
+    matvec35(T, M, Mout);
+}
+
+/* beta (Gauss-Hermite base measure) from gauge g_from to g_to.  With
+ * c = coefficients of -|ubar|^2/2 in the basis, the Lebesgue parameters are
+ * beta + c and transform with T(g_from, g_to)^T (Eq. "Change gauge M F"). */
+void or_transform_beta(const double *g_to, const double *g_from, const double *beta, double *bout) {
+    double T[NP * NP], bl[NP], c[NP] = {0};
+    int i200 = or_index_of(2, 0, 0), i020 = or_index_of(0, 2, 0), i002 = or_index_of(0, 0, 2);
+    c[i200] = c[i020] = c[i002] = -1.0 / sqrt(2.0);
+    or_gauge_T(g_from, g_to, T);
+    for (int j = 0; j < NP; ++j) bl[j] = (j ? beta[j] + c[j] : 0.0);
+    for (int i = 1; i < NP; ++i) {
+        double s = 0.0;
+        for (int j = 1; j < NP; ++j) s += T[j * NP + i] * bl[j];
+        bout[i] = s - c[i];
+    }
+    bout[0] = beta[0];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Flux (Eq. "The ME equation", subeq. 3) and characteristic speed (Eq. "The
+ * lax F"): F_i = n (w_x E phi_i + s_x E ubar_x phi_i); the eigenvalues of
+ * dF/dM are the generalised eigenvalues of (d F/d alpha, d M/d alpha) =
+ * n (E u_x phi phi^T, E phi phi^T) over all 35 statistics.  Whitened with the
+ * Cholesky factor of E phi phi^T and diagonalised by Jacobi. */
+void or_flux(int order, const double *beta, const double *g, double n, double *F, double *speed, double *lmin, double *lmax) {
+    double m[NP], S[NP * NP], X[NP], XS[NP * NP];
+    or_expect(order, beta, NULL, m, S, X, XS);
+    if (F) for (int i = 0; i < NP; ++i) F[i] = n * (g[0] * m[i] + g[3] * X[i]);
+    if (speed || lmin || lmax) {
+        double L[NP * NP], C[NP * NP], tmp[NP * NP], ev[NP];
+        if (cholesky(NP, S, 0.0, L)) {
+            /* E phi phi^T numerically singular: the pencil has no reliable
+             * spectrum (the failure mode the paper reports for over-refined
+             * Mach-10 meshes).  Fall back to the Rayleigh-quotient bound over
+             * the nodes, max_q |w_x + s_x ubar_x,q|. */
+            const rule_t *r = get_rule(order);
+            double xmax = 0.0;
+            for (int q = 0; q < r->Q; ++q) if (r->u[3 * q] > xmax) xmax = r->u[3 * q];
+            double a = g[0] - g[3] * xmax, b = g[0] + g[3] * xmax;
+            if (lmin) *lmin = a;
+            if (lmax) *lmax = b;
+            if (speed) *speed = fmax(fabs(a), fabs(b));
+            return;
+        }
+        /* tmp = L^{-1} XS  (column by column), C = tmp L^{-T} */
+        for (int col = 0; col < NP; ++col) {
+            double bcol[NP], xcol[NP];
+            for (int i = 0; i < NP; ++i) bcol[i] = XS[i * NP + col];
+            solve_lower(NP, L, bcol, xcol);
+            for (int i = 0; i < NP; ++i) tmp[i * NP + col] = xcol[i];
+        }
+        for (int row = 0; row < NP; ++row) {
+            double brow[NP], xrow[NP];
+            for (int i = 0; i < NP; ++i) brow[i] = tmp[row * NP + i];
+            solve_lower(NP, L, brow, xrow);
+            for (int i = 0; i < NP; ++i) C[row * NP + i] = xrow[i];
+        }
+        for (int i = 0; i < NP; ++i) for (int j = i + 1; j < NP; ++j) {
+            double avg = 0.5 * (C[i * NP + j] + C[j * NP + i]);
+            C[i * NP + j] = C[j * NP + i] = avg;
+        }
+        jacobi_eigen(NP, C, ev, NULL);
+        double mu_lo = ev[0], mu_hi = ev[0];
+        for (int i = 1; i < NP; ++i) { if (ev[i] < mu_lo) mu_lo = ev[i]; if (ev[i] > mu_hi) mu_hi = ev[i]; }
+        double a = g[0] + g[3] * mu_lo, b = g[0] + g[3] * mu_hi;
+        if (lmin) *lmin = a;
+        if (lmax) *lmax = b;
+        if (speed) *speed = fmax(fabs(a), fabs(b));
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* ES-BGK target moments (Appendix A, Eq. "The ES BGK model"): Gaussian with
+ * the cell's density and mean velocity and covariance
+ * Sigma = T/Pr I + (1 - 1/Pr) P/n, expressed in the cell's gauge g.  The
+ * Gaussian expectation of each statistic is taken with a 5-point-per-axis
+ * Gauss-Hermite rule in whitened coordinates (exact for degree <= 9). */
+static void central_moments(const double *M, const double *g, double *mean_u, double *P_over_n) {
+    double n = M[0], mb[3], E2[3][3];
+    for (int a = 0; a < 3; ++a) {
+        int e[3] = {0, 0, 0}; e[a] = 1;
+        mb[a] = M[or_index_of(e[0], e[1], e[2])] / n;
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            int e[3] = {0, 0, 0};
+            if (a == b) { e[a] = 2; E2[a][b] = sqrt(2.0) * M[or_index_of(e[0], e[1], e[2])] / n + 1.0; }
+            else { e[a] = 1; e[b] = 1; E2[a][b] = M[or_index_of(e[0], e[1], e[2])] / n; }
+        }
+    for (int a = 0; a < 3; ++a) mean_u[a] = g[a] + g[3 + a] * mb[a];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) P_over_n[3 * a + b] = g[3 + a] * g[3 + b] * (E2[a][b] - mb[a] * mb[b]);
+}
+
+void or_macro(const double *M, const double *g, double *out /* n, v[3], T, P/n[9] */) {
+    double v[3], P[9];
+    central_moments(M, g, v, P);
+    out[0] = M[0];
+    for (int a = 0; a < 3; ++a) out[1 + a] = v[a];
+    out[4] = (P[0] + P[4] + P[8]) / 3.0;
+    for (int k = 0; k < 9; ++k) out[5 + k] = P[k];
+}
+
+void or_gaussian_moments(const double *mean_bar, const double *cov_bar, double n, double *Mout) {
+    double x[5], w[5], Lc[9];
+    or_gh_rule(5, x, w);
+    cholesky(3, cov_bar, 0.0, Lc);
+    for (int i = 0; i < NP; ++i) Mout[i] = 0.0;
+    for (int i = 0; i < 5; ++i) for (int j = 0; j < 5; ++j) for (int k = 0; k < 5; ++k) {
+        double z[3] = {x[i], x[j], x[k]}, u[3], ph[NP];
+        for (int a = 0; a < 3; ++a) { u[a] = mean_bar[a]; for (int b = 0; b <= a; ++b) u[a] += Lc[3 * a + b] * z[b]; }
+        or_phi(u, ph);
+        double ww = w[i] * w[j] * w[k];
+        for (int p = 0; p < NP; ++p) Mout[p] += n * ww * ph[p];
+    }
+}
+
+void or_esbgk(const double *M, const double *g, double Pr, double *Mt) {
+    double n = M[0], v[3], P[9];
+    central_moments(M, g, v, P);
+    double T = (P[0] + P[4] + P[8]) / 3.0;
+    double mb[3], cb[9];
+    for (int a = 0; a < 3; ++a) mb[a] = (v[a] - g[a]) / g[3 + a];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double sig = (a == b ? T / Pr : 0.0) + (1.0 - 1.0 / Pr) * P[3 * a + b];
+            cb[3 * a + b] = sig / (g[3 + a] * g[3 + b]);
+        }
+    or_gaussian_moments(mb, cb, n, Mt);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Rankine-Hugoniot jump (Appendix D, Eq. "RH condition"). */
+void or_rh(double mach, double gamma, double *rho_ratio, double *T_ratio) {
+    double M2 = mach * mach;
+    *rho_ratio = (gamma + 1.0) * M2 / ((gamma - 1.0) * M2 + 2.0);
+    *T_ratio = (2.0 * gamma * M2 - (gamma - 1.0)) * ((gamma - 1.0) * M2 + 2.0) / ((gamma + 1.0) * (gamma + 1.0) * M2);
+}
+
+/* ------------------------------------------------------------------------ */
+/* One time step of Algorithm 2 on a 1D mesh of N interior cells plus one
+ * Dirichlet ghost cell on each side (slots 0 and N+1).  State arrays are
+ * (N+2) x 35 (M, beta) and (N+2) x 6 (g); speed (N+2) holds on entry the
+ * characteristic speeds of the previous Transport (they set dt) and on exit
+ * this Transport's speeds.
+ *   dt = cfl * dx / max(speed_prev)
+ *   Collision(dt/2) -> Transport(dt) [Newton, flux, neighbour gauge, LF, FV]
+ *   -> Collision(dt/2) -> Hermite gauge and transform of M, beta.
+ * relax_coef: tau = relax_coef / n (Maxwell molecules with mu ~ T).
+ * out[0] = dt, out[1] = max new speed, out[2] = max |d rho| over the step. */
+static void collide(double *M, const double *g, double dt, double Pr, double relax_coef) {
+    double Mt[NP];
+    or_esbgk(M, g, Pr, Mt);
+    double tau = relax_coef / M[0];
+    double r = dt / tau;
+    for (int i = 0; i < NP; ++i) M[i] = (1.0 - r) * M[i] + r * Mt[i];
+}
+
+void or_shock_step(int order, int N, double dx, double cfl, double Pr, double relax_coef,
+                   double *M, double *beta, double *g, double *speed, int *status, int *iters,
+                   const double *optv, int nthreads, double *out) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    get_rule(order);
+    int NT = N + 2;
+    double smax = 0.0;
+    for (int c = 0; c < NT; ++c) if (speed[c] > smax) smax = speed[c];
+    double dt = cfl * dx / smax;
+    double *rho0 = malloc(sizeof(double) * NT), *F = malloc(sizeof(double) * NP * NT), *Mn = malloc(sizeof(double) * NP * NT);
+    for (int c = 0; c < NT; ++c) rho0[c] = M[NP * c];
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 1; c <= N; ++c) {
+        collide(&M[NP * c], &g[6 * c], 0.5 * dt, Pr, relax_coef);
+        int it = 0;
+        int st = or_solve(order, &M[NP * c], &beta[NP * c], optv, &it, NULL, NULL);
+        if (status) status[c] = st;
+        if (iters) iters[c] = it;
+    }
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < NT; ++c) {
+        double bb[NP];
+        memcpy(bb, &beta[NP * c], sizeof(bb));
+        if (c == 0 || c == N + 1) for (int i = 0; i < NP; ++i) bb[i] = 0.0;
+        or_flux(order, bb, &g[6 * c], M[NP * c], &F[NP * c], &speed[c], NULL, NULL);
+    }
+    #pragma omp parallel for schedule(static)
+    for (int c = 1; c <= N; ++c) {
+        double T[NP * NP], Ml[NP], Fl[NP], Mr[NP], Fr[NP];
+        const double *M0 = &M[NP * c], *F0 = &F[NP * c];
+        or_gauge_T(&g[6 * c], &g[6 * (c - 1)], T);
+        matvec35(T, &M[NP * (c - 1)], Ml); matvec35(T, &F[NP * (c - 1)], Fl);
+        or_gauge_T(&g[6 * c], &g[6 * (c + 1)], T);
+        matvec35(T, &M[NP * (c + 1)], Mr); matvec35(T, &F[NP * (c + 1)], Fr);
+        double ll = fmax(speed[c - 1], speed[c]), lr = fmax(speed[c], speed[c + 1]);
+        for (int i = 0; i < NP; ++i) {
+            double fl = 0.5 * (Fl[i] + F0[i]) + 0.5 * ll * (Ml[i] - M0[i]);
+            double fr = 0.5 * (F0[i] + Fr[i]) + 0.5 * lr * (M0[i] - Mr[i]);
+            Mn[NP * c + i] = M0[i] + dt / dx * (fl - fr);
+        }
+    }
+    double dmax = 0.0, snew = 0.0;
+    for (int c = 0; c < NT; ++c) if (speed[c] > snew) snew = speed[c];
+    #pragma omp parallel for schedule(static) reduction(max:dmax)
+    for (int c = 1; c <= N; ++c) {
+        double *Mc = &Mn[NP * c];
+        collide(Mc, &g[6 * c], 0.5 * dt, Pr, relax_coef);
+        double gH[6], bt[NP];
+        or_hermite_gauge(Mc, &g[6 * c], 1, gH);
+        or_transform_M(gH, &g[6 * c], Mc, &M[NP * c]);
+        or_transform_beta(gH, &g[6 * c], &beta[NP * c], bt);
+        memcpy(&beta[NP * c], bt, sizeof(bt));
+        memcpy(&g[6 * c], gH, sizeof(gH));
+        double d = fabs(M[NP * c] - rho0[c]);
+        if (d > dmax) dmax = d;
+    }
+    out[0] = dt; out[1] = snew; out[2] = dmax;
+    free(rho0); free(F); free(Mn);
+}
+
+/* Flux and speed of a batch of cells (used to prime the first step's dt). */
+void or_flux_batch(int order, int64_t B, const double *M, const double *beta, const double *g, double *F, double *speed, int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    get_rule(order);
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t c = 0; c < B; ++c)
+        or_flux(order, &beta[NP * c], &g[6 * c], M[NP * c], F ? &F[NP * c] : NULL, speed ? &speed[c] : NULL, NULL, NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Synthetic solve targets: the moments, in the distribution's own Hermite
+ * gauge (per-axis), of p(c) ~ exp(-|c|^2/2 + sum_k a_k c^k - sum_k b_k c^k),
+ * c = (u - v)/sqrt(T): a = 10 cubic coefficients in the multi-index order of
+ * the degree-3 statistics, b = 6 coefficients of c_x^4, c_y^4, c_z^4,
+ * c_x^2 c_y^2, c_x^2 c_z^2, c_y^2 c_z^2.  Density n = 1.  The expectations use
+ * a tensor Gauss-Hermite rule of the given order in c. */
+void or_target_moments(int order, const double *v, double T, const double *a, const double *b, double *M, double *gH) {
+    build_index();
+    const rule_t *r = get_rule(order);
+    int Q = r->Q;
+    double *e = malloc(sizeof(double) * Q), *p = malloc(sizeof(double) * Q);
+    static const int quart[6][3] = {{4, 0, 0}, {0, 4, 0}, {0, 0, 4}, {2, 2, 0}, {2, 0, 2}, {0, 2, 2}};
+    /* The rule is re-centred on the distribution: c = mu + sc * z with z on
+     * the Gauss-Hermite nodes, so the integrand p(c(z)) / N(z) is smooth and
+     * the rule converges fast.  Three passes refine (mu, sc) to the mean and
+     * standard deviation of c; the last frame is the Hermite gauge. */
+    double mu[3] = {0, 0, 0}, sc[3] = {1, 1, 1};
+    for (int pass = 0; pass < 4; ++pass) {
+        double emax = -INFINITY;
+        for (int q = 0; q < Q; ++q) {
+            const double *z = &r->u[3 * q];
+            double c[3];
+            for (int ax = 0; ax < 3; ++ax) c[ax] = mu[ax] + sc[ax] * z[ax];
+            double ex = r->logw[q] + 0.5 * (z[0] * z[0] + z[1] * z[1] + z[2] * z[2]);
+            ex -= 0.5 * (c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+            for (int k = 0; k < 10; ++k) {
+                int *ix = g_idx[10 + k];
+                ex += a[k] * pow(c[0], ix[0]) * pow(c[1], ix[1]) * pow(c[2], ix[2]);
+            }
+            for (int k = 0; k < 6; ++k) ex -= b[k] * pow(c[0], quart[k][0]) * pow(c[1], quart[k][1]) * pow(c[2], quart[k][2]);
+            e[q] = ex;
+            if (ex > emax) emax = ex;
+        }
+        double Z = 0.0;
+        for (int q = 0; q < Q; ++q) { p[q] = exp(e[q] - emax); Z += p[q]; }
+        for (int q = 0; q < Q; ++q) p[q] /= Z;
+        double mean[3] = {0, 0, 0}, var[3] = {0, 0, 0};
+        for (int q = 0; q < Q; ++q) for (int ax = 0; ax < 3; ++ax) mean[ax] += p[q] * (mu[ax] + sc[ax] * r->u[3 * q + ax]);
+        for (int q = 0; q < Q; ++q) for (int ax = 0; ax < 3; ++ax) {
+            double d = mu[ax] + sc[ax] * r->u[3 * q + ax] - mean[ax];
+            var[ax] += p[q] * d * d;
+        }
+        if (pass == 3) {
+            /* Hermite gauge in u = v + sqrt(T) c, and the moments there. */
+            for (int ax = 0; ax < 3; ++ax) { gH[ax] = v[ax] + sqrt(T) * mean[ax]; gH[3 + ax] = sqrt(T * var[ax]); }
+            for (int i = 0; i < NP; ++i) M[i] = 0.0;
+            for (int q = 0; q < Q; ++q) {
+                double ub[3], ph[NP];
+                for (int ax = 0; ax < 3; ++ax) ub[ax] = (v[ax] + sqrt(T) * (mu[ax] + sc[ax] * r->u[3 * q + ax]) - gH[ax]) / gH[3 + ax];
+                or_phi(ub, ph);
+                for (int i = 0; i < NP; ++i) M[i] += p[q] * ph[i];
+            }
+        }
+        for (int ax = 0; ax < 3; ++ax) { mu[ax] = mean[ax]; sc[ax] = sqrt(var[ax]); }
+    }
+    free(e); free(p);
+}
+
+void or_target_batch(int order, int64_t B, const double *v, const double *T, const double *a, const double *b, double *M, double *gH, int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    get_rule(order);
+    #pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t c = 0; c < B; ++c)
+        or_target_moments(order, &v[3 * c], T[c], &a[10 * c], &b[6 * c], &M[NP * c], &gH[6 * c]);
+}
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,294 @@
+"""ctypes binding of the FP64 oracle (oracle/mem_oracle.c).
+
+TEST INFRASTRUCTURE ONLY.  Each wrapper states the paper passage it follows;
+the arithmetic lives in the C file.  Arrays are float64 numpy arrays in the
+same layouts as the CUDA library: moments/parameters [B, 35], gauges [B, 6]
+= (w_x, w_y, w_z, s_x, s_y, s_z).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NP = 35
+ST_CONVERGED, ST_STAGNATED, ST_MAXITER, ST_NONFINITE = 1, 2, 4, 8
+ST_LAMBDA, ST_LAMBDA_CAP, ST_BADINPUT = 16, 32, 64
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.or_objective.restype = ctypes.c_double
+        L.or_residual.restype = ctypes.c_double
+        L.or_index_of.restype = ctypes.c_int
+        L.or_num_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_D)
+
+
+def _i(a):
+    return a.ctypes.data_as(_I)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def num_threads():
+    return lib().or_num_threads()
+
+
+def basis_index():
+    """(a, b, c) exponents of the 35 statistics, in library order."""
+    out = np.zeros((NP, 3), dtype=np.int32)
+    lib().or_basis_index(_i(out))
+    return out
+
+
+def index_of(a, b, c):
+    return lib().or_index_of(a, b, c)
+
+
+def gh_rule(n):
+    """Probabilists' Gauss-Hermite nodes/weights (Golub-Welsch), weights sum to 1."""
+    x = np.zeros(n)
+    w = np.zeros(n)
+    if lib().or_gh_rule(n, _d(x), _d(w)) != 0:
+        raise ValueError("unsupported order")
+    return x, w
+
+
+def phi(u):
+    """The 35 orthonormal Hermite-product statistics at ubar (Appendix B, 3D)."""
+    u = _f64(u, (3,))
+    out = np.zeros(NP)
+    lib().or_phi(_d(u), _d(out))
+    return out
+
+
+def rule_nodes(order):
+    Q = order ** 3
+    u = np.zeros((Q, 3))
+    lw = np.zeros(Q)
+    lib().or_rule_nodes(order, _d(u), _d(lw))
+    return u, lw
+
+
+def expect(order, beta):
+    """logZ, E phi, E phi phi^T, E ubar_x phi, E ubar_x phi phi^T (Section 3.1)."""
+    beta = _f64(beta, (NP,))
+    lz = ctypes.c_double()
+    m = np.zeros(NP)
+    S = np.zeros((NP, NP))
+    X = np.zeros(NP)
+    XS = np.zeros((NP, NP))
+    lib().or_expect(order, _d(beta), ctypes.byref(lz), _d(m), _d(S), _d(X), _d(XS))
+    return lz.value, m, S, X, XS
+
+
+def objective(order, beta, M):
+    """Appendix C objective L(beta; M) with beta_0 = n."""
+    return lib().or_objective(order, _d(_f64(beta, (NP,))), _d(_f64(M, (NP,))))
+
+
+def residual(order, beta, M):
+    """Relative moment residual ||E phi(beta) - M/n|| / ||M/n||."""
+    return lib().or_residual(order, _d(_f64(beta, (NP,))), _d(_f64(M, (NP,))))
+
+
+def residual_batch(order, beta, M):
+    beta = _f64(beta).reshape(-1, NP)
+    M = _f64(M).reshape(-1, NP)
+    return np.array([residual(order, b, m) for b, m in zip(beta, M)])
+
+
+def solve(order, M, beta0=None, tol=1e-8, maxI=500, final_step=True):
+    """Algorithm 1 on one cell.  Returns (beta, status, iters, res, max_lambda)."""
+    M = _f64(M, (NP,))
+    beta = np.zeros(NP) if beta0 is None else _f64(beta0, (NP,)).copy()
+    opts = np.array([tol, float(maxI), float(bool(final_step))])
+    it = ctypes.c_int()
+    res = ctypes.c_double()
+    lam = ctypes.c_double()
+    st = lib().or_solve(order, _d(M), _d(beta), _d(opts), ctypes.byref(it), ctypes.byref(res), ctypes.byref(lam))
+    return beta, st, it.value, res.value, lam.value
+
+
+def solve_batch(order, M, beta0=None, tol=1e-8, maxI=500, nthreads=0, final_step=True):
+    """Algorithm 1 over a batch of cells (OpenMP).  Returns (beta, status, iters)."""
+    M = _f64(M).reshape(-1, NP)
+    B = M.shape[0]
+    beta = np.zeros((B, NP)) if beta0 is None else _f64(beta0).reshape(B, NP).copy()
+    st = np.zeros(B, dtype=np.int32)
+    it = np.zeros(B, dtype=np.int32)
+    opts = np.array([tol, float(maxI), float(bool(final_step))])
+    lib().or_solve_batch(order, ctypes.c_int64(B), _d(M), _d(beta), _i(st), _i(it), _d(opts), nthreads)
+    return beta, st, it
+
+
+def gauge_T(g_to, g_from):
+    """T(g', g) of Eq. "Change gauge M F": M(g') = T M(g)."""
+    T = np.zeros((NP, NP))
+    lib().or_gauge_T(_d(_f64(g_to, (6,))), _d(_f64(g_from, (6,))), _d(T))
+    return T
+
+
+def hermite_gauge(M, g, axisym=False):
+    """Hermite gauge parameters from moments in gauge g (Eq. "Hermite parameters")."""
+    gH = np.zeros(6)
+    lib().or_hermite_gauge(_d(_f64(M, (NP,))), _d(_f64(g, (6,))), int(bool(axisym)), _d(gH))
+    return gH
+
+
+def transform_M(g_to, g_from, M):
+    out = np.zeros(NP)
+    lib().or_transform_M(_d(_f64(g_to, (6,))), _d(_f64(g_from, (6,))), _d(_f64(M, (NP,))), _d(out))
+    return out
+
+
+def transform_beta(g_to, g_from, beta):
+    out = np.zeros(NP)
+    lib().or_transform_beta(_d(_f64(g_to, (6,))), _d(_f64(g_from, (6,))), _d(_f64(beta, (NP,))), _d(out))
+    return out
+
+
+def flux(order, beta, g, n):
+    """F = n (w_x E phi + s_x E ubar_x phi) and the spectral radius of dF/dM."""
+    F = np.zeros(NP)
+    sp, lo, hi = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lib().or_flux(order, _d(_f64(beta, (NP,))), _d(_f64(g, (6,))), ctypes.c_double(n), _d(F),
+                  ctypes.byref(sp), ctypes.byref(lo), ctypes.byref(hi))
+    return F, sp.value, lo.value, hi.value
+
+
+def flux_batch(order, M, beta, g, nthreads=0):
+    M = _f64(M).reshape(-1, NP)
+    B = M.shape[0]
+    beta = _f64(beta).reshape(B, NP)
+    g = _f64(g).reshape(B, 6)
+    F = np.zeros((B, NP))
+    sp = np.zeros(B)
+    lib().or_flux_batch(order, ctypes.c_int64(B), _d(M), _d(beta), _d(g), _d(F), _d(sp), nthreads)
+    return F, sp
+
+
+def macro(M, g):
+    """(n, v[3], T, P/n[3x3]) from moments in gauge g (Appendix A definitions)."""
+    out = np.zeros(14)
+    lib().or_macro(_d(_f64(M, (NP,))), _d(_f64(g, (6,))), _d(out))
+    return out[0], out[1:4].copy(), out[4], out[5:].reshape(3, 3).copy()
+
+
+def gaussian_moments(mean_bar, cov_bar, n):
+    out = np.zeros(NP)
+    lib().or_gaussian_moments(_d(_f64(mean_bar, (3,))), _d(_f64(cov_bar, (3, 3))), ctypes.c_double(n), _d(out))
+    return out
+
+
+def esbgk(M, g, Pr=2.0 / 3.0):
+    """ES-BGK target moments in gauge g (Appendix A, Eq. "The ES BGK model")."""
+    out = np.zeros(NP)
+    lib().or_esbgk(_d(_f64(M, (NP,))), _d(_f64(g, (6,))), ctypes.c_double(Pr), _d(out))
+    return out
+
+
+def rh(mach, gamma=5.0 / 3.0):
+    """Rankine-Hugoniot density and temperature ratios (Appendix D)."""
+    r, t = ctypes.c_double(), ctypes.c_double()
+    lib().or_rh(ctypes.c_double(mach), ctypes.c_double(gamma), ctypes.byref(r), ctypes.byref(t))
+    return r.value, t.value
+
+
+def target_moments(order, v, T, a, b):
+    """Moments (own Hermite gauge) of exp(-|c|^2/2 + cubic(a) - quartic(b))."""
+    M = np.zeros(NP)
+    gH = np.zeros(6)
+    lib().or_target_moments(order, _d(_f64(v, (3,))), ctypes.c_double(T), _d(_f64(a, (10,))),
+                            _d(_f64(b, (6,))), _d(M), _d(gH))
+    return M, gH
+
+
+def target_batch(order, v, T, a, b, nthreads=0):
+    v = _f64(v).reshape(-1, 3)
+    B = v.shape[0]
+    T = _f64(T).reshape(B)
+    a = _f64(a).reshape(B, 10)
+    b = _f64(b).reshape(B, 6)
+    M = np.zeros((B, NP))
+    gH = np.zeros((B, 6))
+    lib().or_target_batch(order, ctypes.c_int64(B), _d(v), _d(T), _d(a), _d(b), _d(M), _d(gH), nthreads)
+    return M, gH
+
+
+# --------------------------------------------------------------------------
+# Algorithm 2 on a 1D normal shock (Appendix D set-up).
+
+RELAX_KN1 = float(np.sqrt(2.0 / np.pi))  # mu = sqrt(2/pi) T at Kn = 1; tau = coef/(Pr n)
+
+
+class Shock:
+    """FP64 shock-tube state: N interior cells + 2 Dirichlet ghost cells."""
+
+    def __init__(self, mach, ncells, xl, xr, order=8, cfl=0.5, Pr=2.0 / 3.0, gamma=5.0 / 3.0,
+                 kn=1.0, tol=1e-8, maxI=500, nthreads=0):
+        self.order, self.N, self.cfl, self.Pr = order, ncells, cfl, Pr
+        self.dx = (xr - xl) / ncells
+        self.x = xl + (np.arange(ncells) + 0.5) * self.dx
+        self.relax = kn * RELAX_KN1 / Pr
+        self.opts = np.array([tol, float(maxI), 1.0])
+        self.nthreads = nthreads
+        r, t = rh(mach, gamma)
+        self.n_up, self.T_up, self.v_up = 1.0, 1.0, np.sqrt(gamma) * mach
+        self.n_dn, self.T_dn, self.v_dn = r, t, np.sqrt(gamma) * mach / r
+        NT = ncells + 2
+        self.M = np.zeros((NT, NP))
+        self.beta = np.zeros((NT, NP))
+        self.g = np.zeros((NT, 6))
+        xs = np.concatenate([[xl - 0.5 * self.dx], self.x, [xr + 0.5 * self.dx]])
+        for c in range(NT):
+            up = xs[c] < 0.0
+            n, T, v = (self.n_up, self.T_up, self.v_up) if up else (self.n_dn, self.T_dn, self.v_dn)
+            self.M[c, 0] = n
+            self.beta[c, 0] = n
+            s = np.sqrt(T)
+            self.g[c] = [v, 0.0, 0.0, s, s, s]
+        _, self.speed = flux_batch(order, self.M, self.beta, self.g, nthreads)
+        self.status = np.zeros(NT, dtype=np.int32)
+        self.iters = np.zeros(NT, dtype=np.int32)
+        self.t = 0.0
+        self.steps = 0
+
+    def step(self):
+        out = np.zeros(3)
+        lib().or_shock_step(self.order, self.N, ctypes.c_double(self.dx), ctypes.c_double(self.cfl),
+                            ctypes.c_double(self.Pr), ctypes.c_double(self.relax), _d(self.M), _d(self.beta),
+                            _d(self.g), _d(self.speed), _i(self.status), _i(self.iters), _d(self.opts),
+                            self.nthreads, _d(out))
+        self.t += out[0]
+        self.steps += 1
+        return out  # dt, max speed, max |d rho|
+
+    def profile(self):
+        """rho, u_x, T for the interior cells."""
+        rho = np.zeros(self.N)
+        ux = np.zeros(self.N)
+        T = np.zeros(self.N)
+        for i in range(self.N):
+            n, v, Tc, _ = macro(self.M[i + 1], self.g[i + 1])
+            rho[i], ux[i], T[i] = n, v[0], Tc
+        return rho, ux, T

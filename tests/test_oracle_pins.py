@@ -1,0 +1,472 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test ties one oracle function to something other than itself: a closed
+form, an invariant, brute force, or a value printed in the paper.  None of
+these tests needs a GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+
+SQ2 = math.sqrt(2.0)
+
+
+# ---------------------------------------------------------------- closed forms
+def he_gauss_moment(n, mu, var):
+    """E[He_n(x)] for x ~ N(mu, var), from the generating function
+    E exp(t x - t^2/2) = exp(t mu + t^2 (var - 1)/2)."""
+    s = 0.0
+    for j in range(n // 2 + 1):
+        s += math.factorial(n) / (math.factorial(j) * math.factorial(n - 2 * j)) * ((var - 1) / 2) ** j * mu ** (n - 2 * j)
+    return s
+
+
+def hermite_gauss_vector(O, mean, var):
+    """Orthonormal-Hermite-product expectations of an axis-aligned Gaussian."""
+    idx = O.basis_index()
+    out = np.zeros(35)
+    for k, (a, b, c) in enumerate(idx):
+        v = 1.0
+        for e, m, s2 in zip((a, b, c), mean, var):
+            v *= he_gauss_moment(int(e), m, s2) / math.sqrt(math.factorial(int(e)))
+        out[k] = v
+    return out
+
+
+def random_beta(O, rng, s=0.05):
+    """Natural parameters near a Maxwellian: N(0, s^2) on degree 1-2, s/3 on
+    degree 3, s/10 on degree 4 (the high-degree statistics reach ~100 at the
+    outer nodes of the 8-point rule)."""
+    deg = O.basis_index().sum(1)
+    scale = np.where(deg <= 2, s, np.where(deg == 3, s / 3, s / 10))
+    b = rng.normal(0, 1, 35) * scale
+    b[0] = 1.0
+    return b
+
+
+def physical_totals(O, M, g):
+    """(mass, x-momentum, energy) of a cell, m = k_B = 1."""
+    n, v, T, _ = O.macro(M, g)
+    return np.array([n, n * v[0], 0.5 * n * (v @ v + 3 * T)])
+
+
+# ---------------------------------------------------------------- quadrature
+@pytest.mark.parametrize("n", [2, 3, 5, 8, 12, 24])
+def test_gh_rule_exact_for_polynomials(O, n):
+    x, w = O.gh_rule(n)
+    assert abs(w.sum() - 1) < 1e-13
+    for k in range(0, min(2 * n, 24)):
+        exact = 0.0 if k % 2 else float(np.prod(np.arange(k - 1, 0, -2))) if k else 1.0
+        got = (w * x ** k).sum()
+        scale = (w * np.abs(x) ** k).sum()
+        assert abs(got - exact) <= 1e-10 * max(1.0, scale), (n, k, got, exact)
+
+
+def test_gh_known_nodes(O):
+    x, w = O.gh_rule(2)
+    assert np.allclose(x, [-1, 1]) and np.allclose(w, [0.5, 0.5])
+    x, w = O.gh_rule(3)
+    assert np.allclose(x, [-math.sqrt(3), 0, math.sqrt(3)]) and np.allclose(w, [1 / 6, 2 / 3, 1 / 6])
+
+
+# ---------------------------------------------------------------- basis
+def test_basis_order_and_count(O):
+    idx = O.basis_index()
+    assert idx.shape == (35, 3)
+    assert len({tuple(r) for r in idx}) == 35
+    deg = idx.sum(1)
+    assert (np.diff(deg) >= 0).all() and deg.max() == 4
+    assert tuple(idx[1]) == (1, 0, 0) and tuple(idx[4]) == (2, 0, 0) and tuple(idx[9]) == (0, 0, 2)
+
+
+def test_basis_matches_paper_statistics(O):
+    """Appendix B, orthonormal form of the 35-moment statistics (1D set),
+    written out by hand and compared with the 3D products they span."""
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        u = rng.normal(0, 1.5, 3)
+        ph = O.phi(u)
+        ux, ur2 = u[0], u[1] ** 2 + u[2] ** 2
+        I = O.index_of
+        assert math.isclose(ph[I(1, 0, 0)], ux, abs_tol=1e-12)
+        assert math.isclose(ph[I(2, 0, 0)], (ux ** 2 - 1) / SQ2, abs_tol=1e-12)
+        assert math.isclose((ph[I(0, 2, 0)] + ph[I(0, 0, 2)]) / SQ2, ur2 / 2 - 1, abs_tol=1e-12)
+        assert math.isclose(ph[I(3, 0, 0)], (ux ** 3 - 3 * ux) / math.sqrt(6), abs_tol=1e-12)
+        assert math.isclose(ph[I(4, 0, 0)], (ux ** 4 - 6 * ux ** 2 + 3) / (2 * math.sqrt(6)), abs_tol=1e-11)
+        # (u_x^2-1)(u_r^2-2)/(2 sqrt 2) = (he2(x)he2(y) + he2(x)he2(z))/sqrt 2
+        assert math.isclose((ph[I(2, 2, 0)] + ph[I(2, 0, 2)]) / SQ2, (ux ** 2 - 1) * (ur2 - 2) / (2 * SQ2), abs_tol=1e-11)
+        # u_r^4/8 - u_r^2 + 1 spans he4(y), he4(z), he2 he2, he2 and 1
+        r4 = ur2 ** 2 / 8 - ur2 + 1
+        rec = (math.sqrt(24) * (ph[I(0, 4, 0)] + ph[I(0, 0, 4)]) + 2 * 2 * ph[I(0, 2, 2)]
+               + 8 * SQ2 * (ph[I(0, 2, 0)] + ph[I(0, 0, 2)]) + 8) / 8 - (SQ2 * (ph[I(0, 2, 0)] + ph[I(0, 0, 2)]) + 2) + 1
+        assert math.isclose(rec, r4, abs_tol=1e-10)
+
+
+def test_basis_orthonormal_under_gh8(O):
+    u, lw = O.rule_nodes(8)
+    w = np.exp(lw)
+    P = np.array([O.phi(x) for x in u])
+    G = (P * w[:, None]).T @ P
+    assert np.abs(G - np.eye(35)).max() < 1e-12
+
+
+# ---------------------------------------------------------------- moment map
+@pytest.mark.parametrize("order", [8, 12])
+def test_maxwellian_identity(O, order):
+    """beta = 0 is the gauge's Maxwellian: E phi = e_0, Hessian = I_34 exactly
+    (the rule integrates every product of two statistics exactly)."""
+    lz, m, S, X, XS = O.expect(order, np.zeros(35))
+    assert np.abs(m - np.eye(35)[0]).max() < 1e-13
+    H = S[1:, 1:] - np.outer(m[1:], m[1:])
+    assert np.abs(H - np.eye(34)).max() < 1e-13
+    assert abs(lz) < 1e-12
+
+
+def test_gaussian_closed_form_and_order_convergence(O):
+    """Only degree <= 2 diagonal parameters: the distribution is an
+    axis-aligned Gaussian; E phi must converge with the rule order to the
+    closed-form Hermite moments."""
+    I = O.index_of
+    beta = np.zeros(35)
+    b1 = [0.3, -0.2, 0.1]
+    b2 = [0.15, -0.1, 0.05]
+    for ax, (e1, e2) in enumerate([((1, 0, 0), (2, 0, 0)), ((0, 1, 0), (0, 2, 0)), ((0, 0, 1), (0, 0, 2))]):
+        beta[I(*e1)] = b1[ax]
+        beta[I(*e2)] = b2[ax]
+    prec = [1 - SQ2 * b for b in b2]
+    mean = [b / p for b, p in zip(b1, prec)]
+    var = [1 / p for p in prec]
+    exact = hermite_gauss_vector(O, mean, var)
+    errs = []
+    for order in (6, 10, 16, 24):
+        _, m, *_ = O.expect(order, beta)
+        errs.append(np.abs(m - exact).max())
+    assert errs[-1] < 1e-10
+    assert errs[0] > errs[1] > errs[2]
+
+
+def test_hessian_is_covariance_and_spd(O):
+    rng = np.random.default_rng(4)
+    beta = random_beta(O, rng, 0.1)
+    _, m, S, *_ = O.expect(8, beta)
+    u, lw = O.rule_nodes(8)
+    P = np.array([O.phi(x) for x in u])
+    e = lw + P[:, 1:] @ beta[1:]
+    s = np.exp(e - e.max())
+    s /= s.sum()
+    mean = s @ P
+    cov = (P - mean).T @ (P * s[:, None])
+    H = S[1:, 1:] - np.outer(m[1:], m[1:])
+    assert np.abs(H - cov[1:, 1:]).max() < 1e-12 * np.abs(S).max()
+    assert np.linalg.eigvalsh(H).min() > 0
+
+
+# ---------------------------------------------------------------- Algorithm 1
+def _moments_of(O, order, beta, n=1.0):
+    _, m, *_ = O.expect(order, beta)
+    M = n * m
+    return M
+
+
+def test_newton_recovers_parameters(O):
+    rng = np.random.default_rng(5)
+    for trial in range(5):
+        bstar = random_beta(O, rng, 0.1)
+        M = _moments_of(O, 8, bstar, n=1.7)
+        b, st, it, res, lam = O.solve(8, M)
+        assert st & O.ST_CONVERGED
+        assert it <= 12
+        assert b[0] == pytest.approx(1.7)
+        assert np.abs(b[1:] - bstar[1:]).max() < 1e-7
+        assert O.residual(8, b, M) < 1e-6
+        # literal Algorithm 1 order: the last direction is not applied
+        b2, st2, it2, res2, _ = O.solve(8, M, final_step=False)
+        assert it2 == it and res2 == res and np.abs(b2[1:] - bstar[1:]).max() < 1e-4
+
+
+def test_newton_quadratic_convergence(O):
+    """Near the solution the Newton decrement res = |dbeta.grad|/2 falls
+    quadratically (undamped steps)."""
+    rng = np.random.default_rng(6)
+    bstar = random_beta(O, rng, 0.05)
+    M = _moments_of(O, 8, bstar)
+    res = [O.solve(8, M, tol=0.0, maxI=k)[3] for k in range(7)]
+    assert res[-1] < 1e-18, res
+    assert all(res[k + 1] < res[k] for k in range(6)), res
+    for k in (4, 5):
+        assert res[k + 1] < 1e3 * res[k] ** 2, res
+    # maxI = 0: one pass; the start point comes back unchanged (Algorithm 1
+    # computes a direction after the update and does not apply it)
+    b0, st0, it0, *_ = O.solve(8, M, tol=0.0, maxI=0)
+    assert it0 == 1 and st0 & O.ST_MAXITER and np.abs(b0[1:]).max() == 0.0
+
+
+def test_newton_maxwellian_is_fixed(O):
+    M = np.zeros(35)
+    M[0] = 2.5
+    b, st, it, res, lam = O.solve(8, M)
+    assert st & O.ST_CONVERGED and it == 1
+    assert np.abs(b[1:]).max() < 1e-13 and b[0] == 2.5
+
+
+def test_newton_bad_input_flagged(O):
+    M = np.zeros(35)
+    M[0] = -1.0
+    _, st, it, *_ = O.solve(8, M)
+    assert st == O.ST_BADINPUT and it == 0
+
+
+def test_objective_gradient_by_finite_differences(O):
+    """Appendix C: grad L = E phi - M/n, Hessian = covariance."""
+    rng = np.random.default_rng(7)
+    beta = random_beta(O, rng, 0.1)
+    M = _moments_of(O, 8, random_beta(O, rng, 0.1))
+    _, m, S, *_ = O.expect(8, beta)
+    grad = m[1:] - M[1:] / M[0]
+    h = 1e-6
+    for i in (1, 5, 17, 34):
+        bp, bm = beta.copy(), beta.copy()
+        bp[i] += h
+        bm[i] -= h
+        fd = (O.objective(8, bp, M) - O.objective(8, bm, M)) / (2 * h)
+        assert abs(fd - grad[i - 1]) < 1e-7
+
+
+# ---------------------------------------------------------------- gauge
+def test_gauge_T_against_brute_force(O):
+    """M(g') = T(g', g) M(g) for any discrete measure (direct evaluation of
+    the statistics in both frames)."""
+    rng = np.random.default_rng(8)
+    u = rng.normal(0.5, 2.0, (60, 3))
+    w = rng.random(60)
+    g1 = np.array([0.3, -0.2, 0.1, 1.2, 0.8, 1.1])
+    g2 = np.array([-0.5, 0.4, 0.0, 0.7, 1.3, 0.9])
+
+    def mom(g):
+        return sum(wi * O.phi((ui - g[:3]) / g[3:]) for ui, wi in zip(u, w))
+
+    assert np.abs(O.gauge_T(g1, g2) @ mom(g2) - mom(g1)).max() < 1e-11
+    assert np.abs(O.transform_M(g2, g1, mom(g1)) - mom(g2)).max() < 1e-11
+
+
+def test_gauge_T_group_laws(O):
+    g1 = np.array([0.3, -0.2, 0.1, 1.2, 0.8, 1.1])
+    g2 = np.array([-0.5, 0.4, 0.0, 0.7, 1.3, 0.9])
+    g3 = np.array([1.5, 0.0, -0.3, 2.0, 0.5, 1.0])
+    assert np.abs(O.gauge_T(g1, g1) - np.eye(35)).max() < 1e-14
+    assert np.abs(O.gauge_T(g1, g2) @ O.gauge_T(g2, g1) - np.eye(35)).max() < 1e-12
+    assert np.abs(O.gauge_T(g3, g2) @ O.gauge_T(g2, g1) - O.gauge_T(g3, g1)).max() < 1e-11
+    T = O.gauge_T(g1, g2)
+    assert T[0, 0] == pytest.approx(1.0) and np.abs(T[0, 1:]).max() == 0.0
+
+
+def test_beta_transform_preserves_density(O):
+    rng = np.random.default_rng(9)
+    b = random_beta(O, rng, 0.1)
+    g1 = np.array([0.3, -0.2, 0.1, 1.2, 0.8, 1.1])
+    g2 = np.array([-0.5, 0.4, 0.0, 0.7, 1.3, 0.9])
+    bt = O.transform_beta(g1, g2, b)
+
+    def logf(beta, g, u):
+        ub = (u - g[:3]) / g[3:]
+        return beta[1:] @ O.phi(ub)[1:] - 0.5 * ub @ ub
+
+    d = [logf(b, g2, u) - logf(bt, g1, u) for u in rng.normal(0, 2, (8, 3))]
+    assert np.ptp(d) < 1e-12
+    assert bt[0] == b[0]
+
+
+def test_hermite_gauge_zeroes_and_idempotent(O):
+    rng = np.random.default_rng(10)
+    M = np.zeros(35)
+    M[0] = 1.3
+    M[1:] = rng.normal(0, 0.1, 34)
+    g = np.array([0.4, 0.2, -0.1, 1.5, 0.9, 1.2])
+    gH = O.hermite_gauge(M, g)
+    MH = O.transform_M(gH, g, M)
+    I = O.index_of
+    for e in [(1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0), (0, 0, 2)]:
+        assert abs(MH[I(*e)]) < 1e-12
+    assert np.abs(O.hermite_gauge(MH, gH) - gH).max() < 1e-12
+    # physical mean / variance
+    n, v, T, P = O.macro(M, g)
+    assert np.allclose(gH[:3], v) and np.allclose(gH[3:] ** 2, np.diag(P))
+    # axisymmetric form: w_y = w_z = 0, s_y = s_z = s_r
+    gA = O.hermite_gauge(M, g, axisym=True)
+    assert gA[1] == 0 and gA[2] == 0 and gA[4] == gA[5]
+    MA = O.transform_M(gA, g, M)
+    assert abs(MA[I(1, 0, 0)]) < 1e-12 and abs(MA[I(2, 0, 0)]) < 1e-12
+
+
+# ---------------------------------------------------------------- flux, speed
+def test_speed_at_maxwellian_is_hermite5_root(O):
+    """At a Maxwellian the characteristic speeds are w_x + s_x * roots of
+    He_5 ... He_1; the spectral radius is |w_x| + sqrt(5 + sqrt 10) s_x."""
+    for wx, sx in [(0.0, 1.0), (0.7, 1.3), (-2.0, 0.5)]:
+        F, sp, lo, hi = O.flux(8, np.zeros(35), [wx, 0, 0, sx, 1.1, 1.1], 1.0)
+        r = math.sqrt(5 + math.sqrt(10))
+        assert sp == pytest.approx(abs(wx) + r * sx, rel=1e-12)
+        assert hi == pytest.approx(wx + r * sx, rel=1e-12) and lo == pytest.approx(wx - r * sx, rel=1e-12)
+
+
+def test_flux_of_maxwellian(O):
+    """Mass flux n w_x; momentum-statistic flux n s_x (Appendix A)."""
+    n, wx, sx = 1.7, 0.8, 1.4
+    F, *_ = O.flux(8, np.zeros(35), [wx, 0, 0, sx, sx, sx], n)
+    assert F[0] == pytest.approx(n * wx)
+    assert F[O.index_of(1, 0, 0)] == pytest.approx(n * sx)
+    mask = np.ones(35, bool)
+    mask[[0, O.index_of(1, 0, 0)]] = False
+    assert np.abs(F[mask]).max() < 1e-13
+
+
+def test_speed_bounded_by_nodes(O):
+    """Rayleigh-quotient bound: |lambda| <= max_q |w_x + s_x ubar_x,q|."""
+    rng = np.random.default_rng(11)
+    x, _ = O.gh_rule(8)
+    for _ in range(5):
+        b = random_beta(O, rng, 0.15)
+        g = [rng.normal(), 0, 0, rng.uniform(0.5, 2), 1, 1]
+        _, sp, lo, hi = O.flux(8, b, g, 1.0)
+        assert sp <= max(abs(g[0] + g[3] * x.max()), abs(g[0] + g[3] * x.min())) + 1e-12
+        assert lo < hi
+
+
+# ---------------------------------------------------------------- collision
+def test_esbgk_matches_paper_canonical_form(O):
+    """Appendix B, Eq. "The Maxwell distribution" (1D ES-BGK in canonical
+    form): variance A/Pr along x and B/(2 Pr) per transverse axis, with
+    A = (n Pr T + (Pr-1) sigma_xx)/n, B = (2 n Pr T + (1-Pr) sigma_xx)/n."""
+    Pr = 2.0 / 3.0
+    n, vx, Txx, Tr = 1.4, 0.6, 1.8, 0.9
+    g = np.array([0.2, 0.0, 0.0, 1.1, 0.95, 0.95])
+    mean = [(vx - g[0]) / g[3], 0.0, 0.0]
+    var = [Txx / g[3] ** 2, Tr / g[4] ** 2, Tr / g[5] ** 2]
+    M = n * hermite_gauss_vector(O, mean, var)
+    rng = np.random.default_rng(12)
+    M[10:] += rng.normal(0, 0.02, 25)   # degree 3-4 changes neither n, v nor P
+    T = (Txx + 2 * Tr) / 3
+    sxx = n * (Txx - T)
+    A = (n * Pr * T + (Pr - 1) * sxx) / n
+    B = (2 * n * Pr * T + (1 - Pr) * sxx) / n
+    vt = [A / Pr / g[3] ** 2, B / (2 * Pr) / g[4] ** 2, B / (2 * Pr) / g[5] ** 2]
+    expect = n * hermite_gauss_vector(O, mean, vt)
+    assert np.abs(O.esbgk(M, g, Pr) - expect).max() < 1e-12
+
+
+def test_maxwellian_is_collision_fixed_point(O):
+    g = np.array([0.4, 0.0, 0.0, 1.3, 1.3, 1.3])
+    M = np.zeros(35)
+    M[0] = 2.0
+    assert np.abs(O.esbgk(M, g) - M).max() < 1e-13
+
+
+# ---------------------------------------------------------------- shock
+def test_rankine_hugoniot_values_and_conservation(O):
+    r, t = O.rh(1.5)
+    assert r == pytest.approx(1.714286, abs=1e-6) and t == pytest.approx(1.494792, abs=1e-6)
+    r, t = O.rh(10.0)
+    assert r == pytest.approx(3.883495, abs=1e-6) and t == pytest.approx(32.123125, abs=1e-6)
+    g = 5 / 3
+    for mach in (1.2, 1.5, 4.0, 10.0):
+        r, t = O.rh(mach)
+        v1, v2 = math.sqrt(g) * mach, math.sqrt(g) * mach / r
+        assert v1 == pytest.approx(r * v2)                                   # mass
+        assert v1 ** 2 + 1 == pytest.approx(r * (v2 ** 2 + t))               # momentum
+        assert v1 * (v1 ** 2 / 2 + 2.5) == pytest.approx(r * v2 * (v2 ** 2 / 2 + 2.5 * t))  # energy
+
+
+def test_shock_conserves_mass_momentum_energy(O):
+    sh = O.Shock(1.5, 64, -20.0, 20.0)
+    tot0 = sum(physical_totals(O, sh.M[c], sh.g[c]) for c in range(1, 65))
+    for _ in range(10):
+        sh.step()
+    tot1 = sum(physical_totals(O, sh.M[c], sh.g[c]) for c in range(1, 65))
+    assert np.abs(tot1 - tot0).max() < 1e-11 * np.abs(tot0).max()
+    # the boundary cells are still the RH states
+    rho, ux, T = sh.profile()
+    assert rho[0] == pytest.approx(1.0, abs=1e-12) and rho[-1] == pytest.approx(sh.n_dn, abs=1e-12)
+    assert T[-1] == pytest.approx(sh.T_dn, abs=1e-12)
+
+
+def test_uniform_state_is_steady(O):
+    sh = O.Shock(1.5, 16, 1.0, 11.0)   # every cell on the downstream side
+    M0 = sh.M.copy()
+    for _ in range(3):
+        sh.step()
+    assert np.abs(sh.M - M0).max() < 1e-12
+
+
+def test_shock_symmetry_zeros(O):
+    """y -> -y and y <-> z leave the 1D shock invariant: parameters odd in u_y
+    or u_z stay zero."""
+    sh = O.Shock(1.5, 32, -10.0, 10.0)
+    for _ in range(4):
+        sh.step()
+    idx = O.basis_index()
+    odd = (idx[:, 1] % 2 == 1) | (idx[:, 2] % 2 == 1)
+    assert np.abs(sh.beta[1:-1][:, odd]).max() < 1e-10
+    assert np.abs(sh.M[1:-1][:, odd]).max() < 1e-12
+
+
+def test_shock_step_dt_from_cfl(O):
+    sh = O.Shock(1.5, 64, -20.0, 20.0)
+    smax = sh.speed.max()
+    dt, snew, drho = sh.step()
+    assert dt == pytest.approx(0.5 * sh.dx / smax)
+    r = math.sqrt(5 + math.sqrt(10))
+    assert smax == pytest.approx(max(sh.v_up + r, sh.v_dn + r * math.sqrt(sh.T_dn)))
+
+
+# ---------------------------------------------------------------- targets
+def test_target_moments_gaussian_limit(O):
+    M, gH = O.target_moments(24, [0.5, -1.0, 2.0], 3.0, np.zeros(10), np.zeros(6))
+    assert np.abs(M - np.eye(35)[0]).max() < 1e-12
+    assert np.allclose(gH, [0.5, -1.0, 2.0] + [math.sqrt(3.0)] * 3)
+
+
+def test_target_moments_order_converged_and_hermite(O):
+    from paper_2303_02898_gb300 import workloads
+    t = workloads.solve_targets(4, seed=0)
+    for i in range(4):
+        M1, g1 = O.target_moments(32, t.v[i], t.T[i], t.a[i], t.b[i])
+        M2, g2 = O.target_moments(24, t.v[i], t.T[i], t.a[i], t.b[i])
+        assert np.abs(M1 - M2).max() < 5e-6 and np.abs(g1 - g2).max() < 5e-6
+        I = O.index_of
+        for e in [(1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0), (0, 0, 2)]:
+            assert abs(M2[I(*e)]) < 1e-12
+
+
+def test_targets_are_solvable(O):
+    from paper_2303_02898_gb300 import workloads
+    t = workloads.solve_targets(16, seed=0)
+    M, g = O.target_batch(24, t.v, t.T, t.a, t.b)
+    beta, st, it = O.solve_batch(8, M)
+    assert ((st & (O.ST_CONVERGED | O.ST_STAGNATED)) != 0).all()
+    res = O.residual_batch(8, beta, M)
+    assert res.max() < 1e-6
+
+
+def test_golden_constants_and_rh(O):
+    """Stored fixtures: the paper's Algorithm 1 constants, and RH states
+    written by tests/golden/make_golden.py from the oracle."""
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    c = json.load(open(os.path.join(here, "paper_constants.json")))
+    assert c["tol"] == 1e-8 and c["armijo_c"] == 5e-4 and c["maxT"] == 25
+    assert c["A2_maxwell"] == 1.37035
+    g = json.load(open(os.path.join(here, "rh_and_speed.json")))
+    for key, v in g.items():
+        if not key.startswith("mach_"):
+            continue
+        r, t = O.rh(float(key[5:]))
+        assert r == pytest.approx(v["rho_ratio"], rel=1e-14) and t == pytest.approx(v["T_ratio"], rel=1e-14)
+        assert v["speed_dn_oracle_q8"] == pytest.approx(v["speed_dn"], rel=1e-12)
+
+
+def test_relaxation_time_from_paper_constants(O):
+    """Appendix A: Maxwell molecules, mu/Pr = n k T tau; at Kn = 1 (upstream
+    mean free path 1, Appendix D) mu = sqrt(2/pi) T, so tau = 1.19683 / n."""
+    assert O.RELAX_KN1 / (2.0 / 3.0) == pytest.approx(1.19683, abs=1e-5)

@@ -1,0 +1,210 @@
+/*
+ * mem.h -- C ABI of the GB300 (sm_103a) library for the hot path of the
+ * 35-moment maximal-entropy moment method (MEM), arXiv 2303.02898.
+ *
+ * Conventions shared by every entry point:
+ *   - Statistics: the 35 orthonormal Hermite products
+ *       phi_k(ubar) = He_a(ubar_x) He_b(ubar_y) He_c(ubar_z) / sqrt(a! b! c!),
+ *     a + b + c <= 4 (Appendix B, orthonormal form, extended to 3D), ordered
+ *     by total degree, then a descending, then b descending; k = 0 is 1.
+ *   - Gauge g = (w_x, w_y, w_z, s_x, s_y, s_z), ubar = (u - w) / s per axis
+ *     (Section 3.3, Eq. "Sufficient 35 ortho").
+ *   - Moments M[k] = int phi_k(ubar) f(u) d^3u in the cell's gauge; M[0] = n.
+ *   - Natural parameters beta[k], k >= 1, relative to the Gauss-Hermite base
+ *     measure: f = n exp(-|ubar|^2/2 + sum_{k>=1} beta_k phi_k - log Z);
+ *     beta[0] = n.  beta = 0 is the Maxwellian of the gauge.  This is an
+ *     exact re-parameterisation of the paper's canonical form (Eq. "exp
+ *     family"): subtract 1/sqrt(2) from the three (2,0,0)-type entries to get
+ *     the Lebesgue-measure parameters.
+ *   - Arrays are row-major float32: moments/parameters [B][35], gauges
+ *     [B][6].  Pointers marked "dev" are device memory, "host" host memory.
+ *     The caller owns every array it passes; the library keeps no pointer to
+ *     it after the call returns (stream-ordered work may still read it until
+ *     the stream reaches that point).
+ *   - stream: a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Unless stated otherwise a call only enqueues work.
+ *   - Return codes: MEM_OK (0) or a negative MEM_E* code; per-cell outcomes
+ *     are status bits, and a failed cell never fails the call.
+ */
+#ifndef MEM_GB300_H
+#define MEM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MEM_NP 35
+
+/* Return codes. */
+#define MEM_OK 0
+#define MEM_PENDING 1
+#define MEM_EINVAL (-1)
+#define MEM_ENOMEM (-2)
+#define MEM_ECUDA (-3)
+#define MEM_EBUSY (-4)
+#define MEM_ENOTFOUND (-5)
+
+/* Per-cell status bits of mem_solve. */
+#define MEM_ST_CONVERGED 1   /* Newton decrement res <= tol (Algorithm 1)      */
+#define MEM_ST_STAGNATED 2   /* step size alpha <= alpha_min: also converged   */
+#define MEM_ST_MAXITER 4     /* more than maxI iterations                      */
+#define MEM_ST_NONFINITE 8   /* non-finite objective, gradient or Hessian      */
+#define MEM_ST_LAMBDA 16     /* a lambda*I modification was needed             */
+#define MEM_ST_LAMBDA_CAP 32 /* lambda retries exhausted; solve stopped        */
+#define MEM_ST_BADINPUT 64   /* n <= 0 or non-finite input                     */
+
+/* Solver back-ends. */
+#define MEM_IMPL_PLAIN 0 /* separate FP32 kernels per Newton stage, host loop   */
+#define MEM_IMPL_FUSED 1 /* one persistent FP32 kernel, warp per cell           */
+
+typedef struct mem_ctx mem_ctx;
+
+/* Options of Algorithm 1 (modified Newton + backtracking Armijo line search).
+ * Defaults are the paper's constants (Algorithm 1; maxI = 500 as in every
+ * experiment of Section 4). */
+typedef struct {
+    float tol;        /* res = |dbeta . grad L| / 2 <= tol stops (1e-8)      */
+    int32_t maxI;     /* at most maxI + 1 passes (500)                       */
+    float lambda0;    /* first multiple of the identity (1e-3)               */
+    float lambda_mul; /* growth per failed Cholesky (10)                     */
+    int32_t max_lambda; /* cap on lambda retries (20)                        */
+    float c_armijo;   /* Armijo slope factor (5e-4)                          */
+    float atol;       /* Armijo absolute slack (5e-6)                        */
+    float rtol;       /* Armijo relative slack (5e-5)                        */
+    int32_t maxT;     /* line-search trials s = 0..maxT (25)                 */
+    float alpha_min;  /* alpha <= alpha_min stops as stagnated (1e-6)        */
+    int32_t final_step; /* 1: apply the last Newton step on res <= tol       */
+    int32_t impl;     /* MEM_IMPL_PLAIN or MEM_IMPL_FUSED (default FUSED)    */
+} mem_solve_opts;
+
+/* Fill *o with the defaults above. */
+void mem_solve_opts_default(mem_solve_opts *o);
+
+/* Library version string and the number of entry points it exports. */
+const char *mem_version(void);
+
+/* Create a context on the current CUDA device: quadrature tables (tensor
+ * Gauss-Hermite, quad_order^3 nodes fixed in the gauge frame) and the
+ * statistics tables.  degree must be 4 (35 statistics); quad_order 4..16
+ * (8 and 12 are the configurations of the workload).  Synchronous.  Returns
+ * MEM_EINVAL on bad arguments, MEM_ECUDA / MEM_ENOMEM on CUDA failures.
+ * Paper: Section 3.1, Eq. "Numerical integration" (fixed nodes and weights);
+ * Appendix B (statistics). */
+int mem_init(int degree, int quad_order, mem_ctx **out);
+
+/* Release everything the context owns (synchronises the device first). */
+void mem_destroy(mem_ctx *ctx);
+
+/* Nodes per axis and total quadrature nodes of the context. */
+int mem_quad_order(const mem_ctx *ctx);
+
+/* Moment -> parameter map: Algorithm 1 (Section 3.2) on B independent cells.
+ *   M      dev [B][35] moments in each cell's own gauge, M[0] = n > 0.
+ *   beta   dev [B][35] in: warm start (entries 1..34; 0 = Maxwellian),
+ *                      out: solution, beta[0] = n.
+ *   status dev [B] int32 MEM_ST_* bits, or NULL.
+ *   iters  dev [B] int32 passes of the Newton loop, or NULL.
+ *   opts   host, NULL = defaults.
+ * The objective, gradient and Hessian follow Appendix C (Eq. "MLE
+ * optimization goal" and its Hessian); the partition function uses the
+ * log-sum-exp form of Section 3.1.  The fused back-end needs no scratch
+ * memory; the plain back-end uses scratch the context owns (grown on first
+ * use, so its first call may allocate) and synchronises the stream once per
+ * Newton pass.  Returns MEM_EINVAL for B < 0 or NULL arrays with B > 0. */
+int mem_solve(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters,
+              int64_t B, const mem_solve_opts *opts, void *stream);
+
+/* Flux and characteristic speed of B cells (Eq. "The ME equation" subeq. 3
+ * and Eq. "The lax F"):
+ *   F[k] = n (w_x E[phi_k] + s_x E[ubar_x phi_k])          dev [B][35]
+ *   speed = max_p |lambda_p(dF/dM)|                          dev [B]
+ * The eigenvalues of dF/dM are the generalised eigenvalues of
+ * (E[u_x phi phi^T], E[phi phi^T]) over all 35 statistics.  beta dev [B][35]
+ * (beta[0] ignored, n taken from M[0]), M dev [B][35] (only M[0] is read),
+ * gauge dev [B][6].  F or speed may be NULL.  Uses context scratch. */
+int mem_flux(mem_ctx *ctx, const float *M, const float *beta, const float *gauge, float *F,
+             float *speed, int64_t B, void *stream);
+
+/* Hermite gauge (Eqs. "Hermite parameters", "Hermite parameters in moments")
+ * and the change of gauge of Eq. "Change gauge M F":
+ *   g_out = g_H(M_in, g_in); M_out = T(g_out, g_in) M_in;
+ *   beta_inout (if not NULL) is carried to the new gauge.
+ * axisym = 1: the 1D-shock form (w_y = w_z = 0, s_y = s_z = s_r,
+ * s_r^2 = (<u_y^2> + <u_z^2>)/2); 0: each axis separately.  All dev arrays;
+ * M_out may alias M_in and g_out may alias g_in. */
+int mem_gauge_hermite(mem_ctx *ctx, const float *M_in, const float *g_in, float *g_out,
+                      float *M_out, float *beta_inout, int64_t B, int axisym, void *stream);
+
+/* Change of gauge M(g_to) = T(g_to, g_from) M(g_from) for B vectors (dev). */
+int mem_gauge_transform(mem_ctx *ctx, const float *g_to, const float *g_from, const float *M_in,
+                        float *M_out, int64_t B, void *stream);
+
+/* Synthetic solve targets (workload generator; not part of the paper's
+ * method): the moments, in each density's own Hermite gauge, of
+ * p(c) ~ exp(-|c|^2/2 + sum a_k c^k - sum b_k c^k), c = (u - v)/sqrt(T),
+ * n = 1, evaluated with a gen_order^3 Gauss-Hermite rule re-centred on the
+ * density.  v dev [B][3], T dev [B], a dev [B][10] (degree-3 monomials in
+ * statistic order), b dev [B][6] (c_x^4, c_y^4, c_z^4, c_x^2c_y^2,
+ * c_x^2c_z^2, c_y^2c_z^2).  Outputs M_out dev [B][35], g_out dev [B][6]. */
+int mem_targets(mem_ctx *ctx, int gen_order, const float *v, const float *T, const float *a,
+                const float *b, float *M_out, float *g_out, int64_t B, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* 1D normal shock (Algorithm 2, Appendix D). */
+
+typedef struct mem_shock mem_shock;
+
+typedef struct {
+    double mach;       /* upstream Mach number                              */
+    int32_t ncells;    /* interior cells                                    */
+    double xl, xr;     /* domain [xl, xr] in upstream mean free paths       */
+    double cfl;        /* dt = cfl * dx / max speed (0.5)                   */
+    double Pr;         /* Prandtl number of the ES-BGK model (2/3)          */
+    double gamma;      /* heat-capacity ratio for Rankine-Hugoniot (5/3)    */
+    double kn;         /* upstream Knudsen number (1)                       */
+    int32_t ic;        /* 0: step at x = 0 between the RH Maxwellians       */
+    int32_t impl;      /* Newton back-end, MEM_IMPL_*                       */
+    int32_t graph;     /* 1: capture the time step in a CUDA graph          */
+    float tol;         /* Algorithm 1 tolerance (1e-8)                      */
+    int32_t maxI;      /* Algorithm 1 iteration cap (500)                   */
+} mem_shock_params;
+
+void mem_shock_params_default(mem_shock_params *p);
+
+/* Allocate the device state of one shock problem (ncells + 2 ghost cells),
+ * set the initial condition and prime the characteristic speeds.
+ * Synchronous.  Returns MEM_EINVAL / MEM_ENOMEM / MEM_ECUDA. */
+int mem_shock_init(mem_ctx *ctx, const mem_shock_params *p, mem_shock **out);
+
+/* Advance nsteps time steps of Algorithm 2 on `stream`:
+ *   dt = cfl dx / max speed of the previous transport;
+ *   Collision(dt/2) -> Transport(dt) [Newton, flux, neighbour gauge
+ *   transform, local Lax-Friedrichs, finite volume] -> Collision(dt/2) ->
+ *   Hermite gauge and transform of M and beta.
+ * If steady_metric is not NULL it receives (host, after a stream
+ * synchronisation) max_n |rho^{k+1} - rho^k| / (rho_+ - rho_-) of the last
+ * step; with steady_metric NULL the call does not synchronise. */
+int mem_shock_step(mem_shock *s, int nsteps, double *steady_metric, void *stream);
+
+/* Copy the state to host: any pointer may be NULL.  M_host [(N+2)][35],
+ * g_host [(N+2)][6], beta_host [(N+2)][35] include the two ghost cells;
+ * rho, ux, T, sxx, qx [N] are the interior profiles (number density, mean
+ * x-velocity, temperature, sigma_xx = P_xx - n T, heat flux q_x), t_out the
+ * simulated time.  Synchronous. */
+int mem_shock_get(mem_shock *s, float *M_host, float *g_host, float *beta_host, float *rho,
+                  float *ux, float *T, float *sxx, float *qx, double *t_out);
+
+/* Device pointers of the state (for zero-copy use from the caller). */
+int mem_shock_device_state(mem_shock *s, float **M, float **beta, float **g, float **speed,
+                           int32_t **status, int32_t **iters);
+
+void mem_shock_free(mem_shock *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MEM_GB300_H */

@@ -1,0 +1,308 @@
+// api.cu -- context, constant tables and the C-ABI entry points of the MEM
+// library.  Every compute step runs in CUDA kernels; the host code here only
+// builds constant tables (once per context), validates arguments and
+// dispatches.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+
+using namespace mem;
+
+namespace mem_host {
+
+// 1D Gauss-Hermite rule for the standard normal weight: the nodes are the
+// roots of He_n, bracketed on a fine grid and refined by bisection in long
+// double; the weights are w_i = n! / (n^2 He_{n-1}(x_i)^2), which sum to 1.
+int gh_rule(int n, std::vector<double> &x, std::vector<double> &w) {
+    if (n < 1 || n > 32) return MEM_EINVAL;
+    auto he = [n](long double t, long double &hn, long double &hn1) {
+        long double a = 1.0L, b = t;  // He_0, He_1
+        if (n == 1) { hn = b; hn1 = a; return; }
+        for (int k = 1; k < n; ++k) {
+            long double c = t * b - (long double)k * a;
+            a = b;
+            b = c;
+        }
+        hn = b;
+        hn1 = a;
+    };
+    x.clear();
+    w.clear();
+    const long double L = sqrtl(4.0L * n + 2.0L) + 2.0L;
+    const int G = 20001;
+    long double xp = -L, hp, dummy;
+    he(xp, hp, dummy);
+    for (int k = 1; k <= G; ++k) {
+        long double xc = -L + 2.0L * L * k / G, hc;
+        he(xc, hc, dummy);
+        if ((hp < 0) != (hc < 0)) {
+            long double lo = xp, hi = xc, flo = hp;
+            for (int it = 0; it < 200; ++it) {
+                long double mid = 0.5L * (lo + hi), fm;
+                he(mid, fm, dummy);
+                if ((fm < 0) == (flo < 0)) { lo = mid; flo = fm; } else hi = mid;
+            }
+            x.push_back((double)(0.5L * (lo + hi)));
+        }
+        xp = xc;
+        hp = hc;
+    }
+    if ((int)x.size() != n) return MEM_EINVAL;
+    long double fact = 1.0L;
+    for (int k = 2; k <= n; ++k) fact *= k;
+    long double sw = 0.0L;
+    std::vector<long double> wl(n);
+    for (int i = 0; i < n; ++i) {
+        long double hn, hn1;
+        he((long double)x[i], hn, hn1);
+        wl[i] = fact / ((long double)n * n * hn1 * hn1);
+        sw += wl[i];
+    }
+    for (int i = 0; i < n; ++i) w.push_back((double)(wl[i] / sw));
+    return MEM_OK;
+}
+
+int ensure_scratch(mem_ctx *ctx, size_t bytes) {
+    if (ctx->scratch_bytes >= bytes) return MEM_OK;
+    if (ctx->scratch) {
+        cudaDeviceSynchronize();
+        cudaFree(ctx->scratch);
+        ctx->scratch = nullptr;
+        ctx->scratch_bytes = 0;
+    }
+    if (cudaMalloc(&ctx->scratch, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return MEM_ENOMEM;
+    }
+    ctx->scratch_bytes = bytes;
+    return MEM_OK;
+}
+
+}  // namespace mem_host
+
+// ---------------------------------------------------------------------------
+// Host evaluation of the statistics (double) for the constant tables.
+static void he_host(double x, int K, double *h) {
+    double hm1 = 0.0, hc = 1.0, inv = 1.0;
+    h[0] = 1.0;
+    for (int k = 0; k < K; ++k) {
+        double hp = x * hc - k * hm1;
+        hm1 = hc;
+        hc = hp;
+        inv /= sqrt((double)(k + 1));
+        h[k + 1] = hc * inv;
+    }
+}
+
+static double binom_d(int n, int k) {
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+static double fact_d(int n) {
+    double r = 1.0;
+    for (int i = 2; i <= n; ++i) r *= i;
+    return r;
+}
+
+// Linearisation of Hermite products: he_a he_b = sum_k L(a,b,k) he_{a+b-2k},
+// L(a,b,k) = C(a,k) C(b,k) k! sqrt((a+b-2k)! / (a! b!)).
+static double lin_coef(int a, int b, int k) {
+    return binom_d(a, k) * binom_d(b, k) * fact_d(k) * sqrt(fact_d(a + b - 2 * k) / (fact_d(a) * fact_d(b)));
+}
+
+// Term lists that express E[phi_i phi_j] (i >= j >= j0) -- and with
+// with_x, E[ubar_x phi_i phi_j] -- as sums of Hermite-product moments.
+static void build_lin_terms(int j0, bool with_x, std::vector<int> &off, std::vector<int2> &terms) {
+    off.clear();
+    terms.clear();
+    for (int i = j0; i < NP; ++i)
+        for (int j = j0; j <= i; ++j) {
+            off.push_back((int)terms.size());
+            int a1 = exp_a(i), b1 = exp_b(i), c1 = exp_c(i), a2 = exp_a(j), b2 = exp_b(j), c2 = exp_c(j);
+            // product of the two statistics, optionally times he_1(x)
+            std::vector<std::pair<int, double>> xs;  // (x-degree, coefficient) of he_a1 he_a2 [he_1]
+            for (int kx = 0; kx <= std::min(a1, a2); ++kx) {
+                int dx = a1 + a2 - 2 * kx;
+                double cx = lin_coef(a1, a2, kx);
+                if (!with_x) {
+                    xs.push_back({dx, cx});
+                } else {
+                    // he_1 he_d = sqrt(d+1) he_{d+1} + sqrt(d) he_{d-1}
+                    xs.push_back({dx + 1, cx * sqrt((double)(dx + 1))});
+                    if (dx > 0) xs.push_back({dx - 1, cx * sqrt((double)dx)});
+                }
+            }
+            for (auto &px : xs)
+                for (int ky = 0; ky <= std::min(b1, b2); ++ky)
+                    for (int kz = 0; kz <= std::min(c1, c2); ++kz) {
+                        int dy = b1 + b2 - 2 * ky, dz = c1 + c2 - 2 * kz;
+                        double cf = px.second * lin_coef(b1, b2, ky) * lin_coef(c1, c2, kz);
+                        float cff = (float)cf;
+                        int2 t;
+                        t.x = idx3(px.first, dy, dz);
+                        memcpy(&t.y, &cff, 4);
+                        terms.push_back(t);
+                    }
+        }
+    off.push_back((int)terms.size());
+}
+
+template <typename T>
+static int upload(T **dst, const std::vector<T> &src) {
+    if (cudaMalloc((void **)dst, sizeof(T) * std::max<size_t>(1, src.size())) != cudaSuccess) return MEM_ENOMEM;
+    if (!src.empty() && cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return MEM_ECUDA;
+    return MEM_OK;
+}
+
+extern "C" {
+
+void mem_solve_opts_default(mem_solve_opts *o) {
+    o->tol = 1e-8f;
+    o->maxI = 500;
+    o->lambda0 = 1e-3f;
+    o->lambda_mul = 10.f;
+    o->max_lambda = 20;
+    o->c_armijo = 5e-4f;
+    o->atol = 5e-6f;
+    o->rtol = 5e-5f;
+    o->maxT = 25;
+    o->alpha_min = 1e-6f;
+    o->final_step = 1;
+    o->impl = MEM_IMPL_FUSED;
+}
+
+const char *mem_version(void) { return "mem-gb300 0.1 (sm_103a)"; }
+
+int mem_init(int degree, int quad_order, mem_ctx **out) {
+    if (!out || degree != 4 || quad_order < 4 || quad_order > 16) return MEM_EINVAL;
+    *out = nullptr;
+    mem_ctx *ctx = new mem_ctx();
+    cudaGetDevice(&ctx->device);
+    int rc = mem_host::gh_rule(quad_order, ctx->x1d, ctx->w1d);
+    if (rc) { delete ctx; return rc; }
+    const int n = quad_order, Q = n * n * n;
+    ctx->n1d = n;
+    ctx->Q = Q;
+    ctx->xmax = (float)ctx->x1d[n - 1];
+    std::vector<float> phiT((size_t)NP * Q), logw(Q), tabS((size_t)Q * MEM_NCOL_SOLVE), tabF((size_t)Q * MEM_NCOL_FLUX);
+    std::vector<float> he1d((size_t)n * MEM_HE_STRIDE, 0.f), x1d(n), lw1d(n);
+    std::vector<double> hx(n * 10);
+    for (int i = 0; i < n; ++i) {
+        he_host(ctx->x1d[i], 9, &hx[i * 10]);
+        for (int k = 0; k < 10; ++k) he1d[i * MEM_HE_STRIDE + k] = (float)hx[i * 10 + k];
+        x1d[i] = (float)ctx->x1d[i];
+        lw1d[i] = (float)log(ctx->w1d[i]);
+    }
+    for (int ix = 0; ix < n; ++ix)
+        for (int iy = 0; iy < n; ++iy)
+            for (int iz = 0; iz < n; ++iz) {
+                const int q = (ix * n + iy) * n + iz;
+                double ph[NP];
+                for (int k = 0; k < NP; ++k) ph[k] = hx[ix * 10 + exp_a(k)] * hx[iy * 10 + exp_b(k)] * hx[iz * 10 + exp_c(k)];
+                const double ux = ctx->x1d[ix];
+                logw[q] = (float)(log(ctx->w1d[ix]) + log(ctx->w1d[iy]) + log(ctx->w1d[iz]));
+                for (int k = 0; k < NP; ++k) phiT[(size_t)k * Q + q] = (float)ph[k];
+                float *rs = &tabS[(size_t)q * MEM_NCOL_SOLVE];
+                for (int k = 0; k < NP; ++k) rs[k] = (float)ph[k];
+                for (int i = 1; i < NP; ++i)
+                    for (int j = 1; j <= i; ++j) rs[NP + (i - 1) * i / 2 + (j - 1)] = (float)(ph[i] * ph[j]);
+                float *rf = &tabF[(size_t)q * MEM_NCOL_FLUX];
+                for (int k = 0; k < NP; ++k) { rf[k] = (float)ph[k]; rf[NP + k] = (float)(ux * ph[k]); }
+                for (int i = 0; i < NP; ++i)
+                    for (int j = 0; j <= i; ++j) {
+                        rf[70 + i * (i + 1) / 2 + j] = (float)(ph[i] * ph[j]);
+                        rf[700 + i * (i + 1) / 2 + j] = (float)(ux * ph[i] * ph[j]);
+                    }
+            }
+    std::vector<int> off, xoff;
+    std::vector<int2> terms, xterms;
+    build_lin_terms(1, false, off, terms);
+    build_lin_terms(0, true, xoff, xterms);
+    rc = MEM_OK;
+    if (!rc) rc = upload(&ctx->d_phiT, phiT);
+    if (!rc) rc = upload(&ctx->d_logw, logw);
+    if (!rc) rc = upload(&ctx->d_tab_solve, tabS);
+    if (!rc) rc = upload(&ctx->d_tab_flux, tabF);
+    if (!rc) rc = upload(&ctx->d_he1d, he1d);
+    if (!rc) rc = upload(&ctx->d_x1d, x1d);
+    if (!rc) rc = upload(&ctx->d_logw1d, lw1d);
+    if (!rc) rc = upload(&ctx->d_lin_off, off);
+    if (!rc) rc = upload(&ctx->d_lin_terms, terms);
+    if (!rc) rc = upload(&ctx->d_xlin_off, xoff);
+    if (!rc) rc = upload(&ctx->d_xlin_terms, xterms);
+    ctx->n_lin_terms = (int)terms.size();
+    if (rc) { mem_destroy(ctx); return rc; }
+    if (cudaDeviceSynchronize() != cudaSuccess) { mem_destroy(ctx); return MEM_ECUDA; }
+    *out = ctx;
+    return MEM_OK;
+}
+
+void mem_destroy(mem_ctx *ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    void *ptrs[] = {ctx->d_phiT, ctx->d_logw, ctx->d_tab_solve, ctx->d_tab_flux, ctx->d_he1d, ctx->d_x1d,
+                    ctx->d_logw1d, ctx->d_lin_off, ctx->d_lin_terms, ctx->d_xlin_off, ctx->d_xlin_terms,
+                    ctx->scratch};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete ctx;
+}
+
+int mem_quad_order(const mem_ctx *ctx) { return ctx ? ctx->n1d : 0; }
+
+int mem_solve(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters, int64_t B,
+              const mem_solve_opts *opts, void *stream) {
+    if (!ctx || B < 0) return MEM_EINVAL;
+    if (B == 0) return MEM_OK;
+    if (!M || !beta) return MEM_EINVAL;
+    mem_solve_opts o;
+    mem_solve_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.maxI < 0 || o.maxT < 0 || o.maxT > 60 || o.max_lambda < 0 || o.max_lambda > 60) return MEM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (o.impl == MEM_IMPL_PLAIN) return mem_host::solve_plain(ctx, M, beta, status, iters, B, o, st);
+    if (o.impl == MEM_IMPL_FUSED) return mem_host::solve_fused(ctx, M, beta, status, iters, B, o, st);
+    return MEM_EINVAL;
+}
+
+int mem_flux(mem_ctx *ctx, const float *M, const float *beta, const float *gauge, float *F, float *speed,
+             int64_t B, void *stream) {
+    if (!ctx || B < 0) return MEM_EINVAL;
+    if (B == 0) return MEM_OK;
+    if (!M || !beta || !gauge) return MEM_EINVAL;
+    return mem_host::flux(ctx, M, beta, gauge, F, speed, B, (cudaStream_t)stream);
+}
+
+int mem_gauge_hermite(mem_ctx *ctx, const float *M_in, const float *g_in, float *g_out, float *M_out,
+                      float *beta_inout, int64_t B, int axisym, void *stream) {
+    if (!ctx || B < 0) return MEM_EINVAL;
+    if (B == 0) return MEM_OK;
+    if (!M_in || !g_in || !g_out || !M_out) return MEM_EINVAL;
+    return mem_host::gauge_hermite(ctx, M_in, g_in, g_out, M_out, beta_inout, B, axisym, (cudaStream_t)stream);
+}
+
+int mem_gauge_transform(mem_ctx *ctx, const float *g_to, const float *g_from, const float *M_in, float *M_out,
+                        int64_t B, void *stream) {
+    if (!ctx || B < 0) return MEM_EINVAL;
+    if (B == 0) return MEM_OK;
+    if (!g_to || !g_from || !M_in || !M_out) return MEM_EINVAL;
+    return mem_host::gauge_transform(g_to, g_from, M_in, M_out, B, (cudaStream_t)stream);
+}
+
+int mem_targets(mem_ctx *ctx, int gen_order, const float *v, const float *T, const float *a, const float *b,
+                float *M_out, float *g_out, int64_t B, void *stream) {
+    if (!ctx || B < 0 || gen_order < 4 || gen_order > 32) return MEM_EINVAL;
+    if (B == 0) return MEM_OK;
+    if (!v || !T || !a || !b || !M_out || !g_out) return MEM_EINVAL;
+    return mem_host::targets(ctx, gen_order, v, T, a, b, M_out, g_out, B, (cudaStream_t)stream);
+}
+
+}  // extern "C"

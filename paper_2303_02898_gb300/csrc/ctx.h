@@ -1,0 +1,67 @@
+// ctx.h -- the library context and the internal interfaces between the
+// translation units (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <vector>
+
+#include "../../include/mem.h"
+
+#define MEM_NCOL_SOLVE 630   // [phi_0..34 | phi_i phi_j, 1 <= j <= i <= 34 packed]
+#define MEM_NCOL_FLUX 1330   // [phi | ubar_x phi | phi phi^T packed (630) | ubar_x phi phi^T packed (630)]
+#define MEM_HE_STRIDE 16     // he_0..he_9 per 1D node, padded
+
+struct mem_ctx {
+    int device = 0;
+    int n1d = 0;  // nodes per axis
+    int Q = 0;    // n1d^3
+    std::vector<double> x1d, w1d;   // 1D Gauss-Hermite rule (probabilists', weights sum to 1)
+    // Device tables (constant after mem_init).
+    float *d_phiT = nullptr;       // [35][Q]   phi_k(ubar_q)
+    float *d_logw = nullptr;       // [Q]       log w_q
+    float *d_tab_solve = nullptr;  // [Q][630]
+    float *d_tab_flux = nullptr;   // [Q][1330]
+    float *d_he1d = nullptr;       // [n1d][16] he_0..he_9 at the 1D nodes
+    float *d_x1d = nullptr;        // [n1d]
+    float *d_logw1d = nullptr;     // [n1d]
+    int *d_lin_off = nullptr;      // [596]  Hessian-term offsets (packed i>=j>=1)
+    int2 *d_lin_terms = nullptr;   // (mu index, coefficient bits) per term
+    int n_lin_terms = 0;
+    int *d_xlin_off = nullptr;     // [631]  flux-Jacobian terms (packed i>=j>=0)
+    int2 *d_xlin_terms = nullptr;
+    float xmax = 0.f;              // largest 1D node
+    // Scratch owned by the context (plain solver, flux).
+    std::mutex mu;
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+};
+
+namespace mem_host {
+int ensure_scratch(mem_ctx *ctx, size_t bytes);
+int gh_rule(int n, std::vector<double> &x, std::vector<double> &w);
+int solve_plain(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters, int64_t B,
+                const mem_solve_opts &o, cudaStream_t st);
+int solve_fused(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters, int64_t B,
+                const mem_solve_opts &o, cudaStream_t st);
+int flux(mem_ctx *ctx, const float *M, const float *beta, const float *g, float *F, float *speed, int64_t B,
+         cudaStream_t st);
+int flux_bufs(mem_ctx *ctx, const float *M, const float *beta, const float *g, float *F, float *speed, int64_t B,
+              float *sigma, float *mom, cudaStream_t st);
+int flux_fused(mem_ctx *ctx, const float *M, const float *beta, const float *g, float *F, float *speed,
+               int64_t B, cudaStream_t st);
+int gauge_hermite(mem_ctx *ctx, const float *M_in, const float *g_in, float *g_out, float *M_out,
+                  float *beta_inout, int64_t B, int axisym, cudaStream_t st);
+int gauge_transform(const float *g_to, const float *g_from, const float *M_in, float *M_out, int64_t B,
+                    cudaStream_t st);
+int targets(mem_ctx *ctx, int gen_order, const float *v, const float *T, const float *a, const float *b,
+            float *M_out, float *g_out, int64_t B, cudaStream_t st);
+}  // namespace mem_host
+
+#define MEM_CUDA_TRY(x)                                   \
+    do {                                                  \
+        cudaError_t e__ = (x);                            \
+        if (e__ != cudaSuccess) return MEM_ECUDA;         \
+    } while (0)

@@ -1,0 +1,530 @@
+// plain.cu -- the plain FP32 back-end: one kernel per stage of Algorithm 1,
+// dense statistics tables, a host loop over Newton passes.  It is the
+// baseline the fused back-end is measured against, and the flux/speed path
+// (which needs the dense E[phi phi^T] and E[u_x phi phi^T]).
+//
+// Per Newton pass, over the cells still active:
+//   k_linesearch  backtracking Armijo search on the objective (Algorithm 1,
+//                 BackTrackingLineSearch / ArmijoCondition), update of beta,
+//                 and sigma_q at the new beta (Section 3.1, log-sum-exp);
+//   k_sgemm       [cells x Q] x [Q x 630] -> E phi, E phi_i phi_j (packed);
+//   k_newton      gradient, Hessian = covariance (Appendix C), Cholesky with
+//                 lambda*I retries, two triangular solves, decrement, status.
+#include <float.h>
+
+#include "common.cuh"
+#include "ctx.h"
+#include "linalg.cuh"
+
+using namespace mem;
+
+namespace {
+
+constexpr int BLK = 256;
+constexpr int MAXJ = 16;  // nodes per thread: Q <= 4096
+constexpr int CHUNK = 1 << 17;
+
+__device__ __forceinline__ float block_reduce_max(float v, float *red) {
+    v = warp_max(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    float r = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : -INFINITY;
+    if (w == 0) r = warp_max(r);
+    if (threadIdx.x == 0) red[0] = r;
+    __syncthreads();
+    return red[0];
+}
+
+__device__ __forceinline__ float block_reduce_sum(float v, float *red) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    float r = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.f;
+    if (w == 0) r = warp_sum(r);
+    if (threadIdx.x == 0) red[0] = r;
+    __syncthreads();
+    return red[0];
+}
+
+struct PlainState {
+    float *sigma;  // [CHUNK][Q]
+    float *mom;    // [CHUNK][630]
+    float *db;     // [CHUNK][35]
+    float *G;      // [CHUNK][35]
+    float *Lcur;   // [CHUNK]
+    float *alpha;  // [CHUNK]
+    int *it;       // [CHUNK]
+    int *st;       // [CHUNK]
+    int *act0, *act1;  // [CHUNK]
+    int *cnt;      // [2]
+};
+
+__global__ void k_init(const float *__restrict__ M, float *__restrict__ beta, int n, PlainState S,
+                       int32_t *status, int32_t *iters) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const float *m = M + (size_t)c * NP;
+    float *b = beta + (size_t)c * NP;
+    bool bad = !(m[0] > 0.f) || !isfinite(m[0]);
+    for (int k = 0; k < NP; ++k) bad |= !isfinite(m[k]) || (k > 0 && !isfinite(b[k]));
+    S.it[c] = 0;
+    for (int k = 0; k < NP; ++k) { S.db[(size_t)c * NP + k] = 0.f; S.G[(size_t)c * NP + k] = 0.f; }
+    S.Lcur[c] = NAN;
+    if (bad) {
+        S.st[c] = MEM_ST_BADINPUT;
+        if (status) status[c] = MEM_ST_BADINPUT;
+        if (iters) iters[c] = 0;
+        return;
+    }
+    S.st[c] = 0;
+    b[0] = m[0];
+    const int slot = atomicAdd(&S.cnt[0], 1);
+    S.act0[slot] = c;
+}
+
+// One block per active cell.  Nodes q = tid + 256 j.  The exponent of the
+// trial point beta + alpha dbeta is e_beta + alpha e_dbeta (both computed once).
+__global__ void __launch_bounds__(BLK) k_linesearch(const int *__restrict__ act, const float *__restrict__ M,
+                                                    float *__restrict__ beta, PlainState S,
+                                                    const float *__restrict__ phiT, const float *__restrict__ logw,
+                                                    int Q, mem_solve_opts o) {
+    __shared__ float sb[NP], sd[NP], sm[NP], sg[NP], red[32], sc[4];
+    const int slot = blockIdx.x, c = act[slot], tid = threadIdx.x;
+    const float *Mc = M + (size_t)c * NP;
+    float *bc = beta + (size_t)c * NP;
+    if (tid < NP) {
+        const float n = Mc[0];
+        sb[tid] = tid ? bc[tid] : 0.f;
+        sd[tid] = tid ? S.db[(size_t)c * NP + tid] : 0.f;
+        sg[tid] = tid ? S.G[(size_t)c * NP + tid] : 0.f;
+        sm[tid] = tid ? Mc[tid] / n : 0.f;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float gd = 0.f, mb = 0.f, md = 0.f;
+        for (int k = 1; k < NP; ++k) { gd += sg[k] * sd[k]; mb += sb[k] * sm[k]; md += sd[k] * sm[k]; }
+        sc[0] = gd; sc[1] = mb; sc[2] = md;
+    }
+    float eb[MAXJ], ed[MAXJ];
+    const int nj = (Q + BLK - 1) / BLK;
+#pragma unroll
+    for (int j = 0; j < MAXJ; ++j) {
+        eb[j] = -INFINITY;
+        ed[j] = 0.f;
+        const int q = tid + j * BLK;
+        if (j < nj && q < Q) {
+            float s = logw[q], d = 0.f;
+            for (int k = 1; k < NP; ++k) {
+                const float p = phiT[(size_t)k * Q + q];
+                s += sb[k] * p;
+                d += sd[k] * p;
+            }
+            eb[j] = s;
+            ed[j] = d;
+        }
+    }
+    __syncthreads();
+    const float gd = sc[0], mb = sc[1], md = sc[2];
+    float Lcur = S.Lcur[c];
+    if (isnan(Lcur)) {  // first pass: objective at the start point
+        float mx = -INFINITY;
+#pragma unroll
+        for (int j = 0; j < MAXJ; ++j) mx = fmaxf(mx, eb[j]);
+        mx = block_reduce_max(mx, red);
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < MAXJ; ++j) s += (j < nj) ? __expf(eb[j] - mx) : 0.f;
+        s = block_reduce_sum(s, red);
+        Lcur = mx + logf(s) - mb;
+    }
+    float alpha = 2.f, Lt = NAN, mx = 0.f, Z = 1.f;
+    bool sat = false;
+    for (int s = 0; !sat && s <= o.maxT; ++s) {
+        alpha *= 0.5f;
+        float m = -INFINITY;
+#pragma unroll
+        for (int j = 0; j < MAXJ; ++j) m = fmaxf(m, eb[j] + alpha * ed[j]);
+        mx = block_reduce_max(m, red);
+        float z = 0.f;
+#pragma unroll
+        for (int j = 0; j < MAXJ; ++j) z += (j < nj) ? __expf(eb[j] + alpha * ed[j] - mx) : 0.f;
+        Z = block_reduce_sum(z, red);
+        Lt = mx + logf(Z) - (mb + alpha * md);
+        const float LD = Lcur - Lt, gradD = -o.c_armijo * alpha * gd;
+        sat = (LD - gradD) >= -(o.atol + o.rtol * fabsf(LD));
+    }
+    const float invZ = 1.f / Z;
+    float *sig = S.sigma + (size_t)slot * Q;
+#pragma unroll
+    for (int j = 0; j < MAXJ; ++j) {
+        const int q = tid + j * BLK;
+        if (j < nj && q < Q) sig[q] = __expf(eb[j] + alpha * ed[j] - mx) * invZ;
+    }
+    if (tid >= 1 && tid < NP) bc[tid] = sb[tid] + alpha * sd[tid];
+    if (tid == 0) { S.Lcur[c] = Lt; S.alpha[c] = alpha; }
+}
+
+// C[M x N] = A[M x K] B[K x N], row-major, 64x64 tiles, 4x4 per thread.
+__global__ void __launch_bounds__(256) k_sgemm(const float *__restrict__ A, const float *__restrict__ Bm,
+                                               float *__restrict__ C, int M, int N, int K) {
+    __shared__ float As[16][68];
+    __shared__ float Bs[16][64];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int e = threadIdx.x + l * 256;
+            const int r = e >> 4, cc = e & 15;
+            As[cc][r] = (row0 + r < M && k0 + cc < K) ? A[(size_t)(row0 + r) * K + k0 + cc] : 0.f;
+            const int rb = e >> 6, cb = e & 63;
+            Bs[rb][cb] = (k0 + rb < K && col0 + cb < N) ? Bm[(size_t)(k0 + rb) * N + col0 + cb] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { a[i] = As[kk][ty * 4 + i]; b[i] = Bs[kk][tx * 4 + i]; }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = row0 + ty * 4 + i;
+        if (r >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int cc = col0 + tx * 4 + j;
+            if (cc < N) C[(size_t)r * N + cc] = acc[i][j];
+        }
+    }
+}
+
+constexpr int LDH = 35;  // leading dimension of the 34 x 34 Hessian in shared memory
+
+// Warp per active cell: gradient, Hessian, modified Cholesky, Newton
+// direction, decrement and the convergence test of Algorithm 1.
+__global__ void __launch_bounds__(128) k_newton(const int *__restrict__ act, int nact, const float *__restrict__ M,
+                                                float *__restrict__ beta, PlainState S, int *__restrict__ act_next,
+                                                int *__restrict__ cnt_next, mem_solve_opts o,
+                                                int32_t *status, int32_t *iters) {
+    __shared__ float sA[4][NP1 * LDH];
+    __shared__ float sv[4][3][NP];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slot = blockIdx.x * 4 + w;
+    if (slot >= nact) return;
+    const int c = act[slot];
+    float *A = sA[w], *m = sv[w][0], *G = sv[w][1], *b = sv[w][2];
+    const float *mom = S.mom + (size_t)slot * MEM_NCOL_SOLVE;
+    const float *Mc = M + (size_t)c * NP;
+    const float n = Mc[0];
+    for (int k = lane; k < NP; k += 32) m[k] = mom[k];
+    __syncwarp();
+    for (int k = lane; k < NP; k += 32) {
+        G[k] = k ? m[k] - Mc[k] / n : 0.f;
+        S.G[(size_t)c * NP + k] = G[k];
+    }
+    int st = S.st[c];
+    auto load_H = [&](float lam) {
+        __syncwarp();
+        for (int p = lane; p < NP1 * (NP1 + 1) / 2; p += 32) {
+            int i = (int)((sqrtf(8.f * p + 1.f) - 1.f) * 0.5f);
+            while (i * (i + 1) / 2 > p) --i;
+            while ((i + 1) * (i + 2) / 2 <= p) ++i;
+            const int j = p - i * (i + 1) / 2;
+            float h = mom[NP + p] - m[i + 1] * m[j + 1];
+            if (i == j) h += lam;
+            A[i * LDH + j] = h;
+        }
+        __syncwarp();
+    };
+    load_H(0.f);
+    bool ok = warp_cholesky(A, NP1, LDH, lane);
+    float lam = o.lambda0;
+    for (int t = 0; !ok && t < o.max_lambda; ++t) {
+        st |= MEM_ST_LAMBDA;
+        load_H(lam);
+        ok = warp_cholesky(A, NP1, LDH, lane);
+        lam *= o.lambda_mul;
+    }
+    const int it = S.it[c] + 1;
+    bool done = false;
+    float res = NAN;
+    if (!ok) {
+        st |= MEM_ST_LAMBDA_CAP | MEM_ST_NONFINITE;
+        done = true;
+    } else {
+        for (int k = lane; k < NP1; k += 32) b[k] = -G[k + 1];
+        warp_solve_lower(A, NP1, LDH, b, lane);
+        warp_solve_upperT(A, NP1, LDH, b, lane);
+        float part = 0.f;
+        for (int k = lane; k < NP1; k += 32) part += b[k] * G[k + 1];
+        res = 0.5f * fabsf(warp_sum(part));
+        for (int k = lane; k < NP; k += 32) S.db[(size_t)c * NP + k] = k ? b[k - 1] : 0.f;
+        if (!isfinite(res)) {
+            st |= MEM_ST_NONFINITE;
+            done = true;
+        } else {
+            const float alpha = S.alpha[c];
+            const bool conv_res = res <= o.tol, conv_a = alpha <= o.alpha_min;
+            if (conv_res) st |= MEM_ST_CONVERGED;
+            if (conv_a) st |= MEM_ST_STAGNATED;
+            if (conv_res || conv_a) done = true;
+            else if (it > o.maxI) { st |= MEM_ST_MAXITER; done = true; }
+            if (done && conv_res && o.final_step) {
+                float *bc = beta + (size_t)c * NP;
+                for (int k = lane + 1; k < NP; k += 32) bc[k] += b[k - 1];
+            }
+        }
+    }
+    if (lane == 0) {
+        S.it[c] = it;
+        S.st[c] = st;
+        if (done) {
+            if (status) status[c] = st;
+            if (iters) iters[c] = it;
+        } else {
+            act_next[atomicAdd(cnt_next, 1)] = c;
+        }
+    }
+}
+
+// sigma_q of each cell at beta (flux path), one block per cell.
+__global__ void __launch_bounds__(BLK) k_sigma(const float *__restrict__ beta, float *__restrict__ sigma,
+                                               const float *__restrict__ phiT, const float *__restrict__ logw, int Q) {
+    __shared__ float sb[NP], red[32];
+    const int c = blockIdx.x, tid = threadIdx.x;
+    if (tid < NP) sb[tid] = tid ? beta[(size_t)c * NP + tid] : 0.f;
+    __syncthreads();
+    float e[MAXJ];
+    const int nj = (Q + BLK - 1) / BLK;
+    float mx = -INFINITY;
+#pragma unroll
+    for (int j = 0; j < MAXJ; ++j) {
+        e[j] = -INFINITY;
+        const int q = tid + j * BLK;
+        if (j < nj && q < Q) {
+            float s = logw[q];
+            for (int k = 1; k < NP; ++k) s += sb[k] * phiT[(size_t)k * Q + q];
+            e[j] = s;
+            mx = fmaxf(mx, s);
+        }
+    }
+    mx = block_reduce_max(mx, red);
+    float z = 0.f;
+#pragma unroll
+    for (int j = 0; j < MAXJ; ++j) z += (j < nj) ? __expf(e[j] - mx) : 0.f;
+    z = block_reduce_sum(z, red);
+    const float inv = 1.f / z;
+#pragma unroll
+    for (int j = 0; j < MAXJ; ++j) {
+        const int q = tid + j * BLK;
+        if (j < nj && q < Q) sigma[(size_t)c * Q + q] = __expf(e[j] - mx) * inv;
+    }
+}
+
+constexpr int LDF = 36;
+
+// Warp per cell: F = n (w_x E phi + s_x E ubar_x phi) and the spectral radius
+// of the pencil (E[ubar_x phi phi^T], E[phi phi^T]) mapped to u_x: Cholesky
+// whitening C = L^{-1} X L^{-T}, Lanczos with full re-orthogonalisation, and
+// Sturm multisection on the tridiagonal matrix for both extreme eigenvalues.
+__global__ void __launch_bounds__(64) k_flux_speed(const float *__restrict__ mom, const float *__restrict__ M,
+                                                   const float *__restrict__ gauge, float *__restrict__ F,
+                                                   float *__restrict__ speed, int B, float xmax) {
+    __shared__ float sL[2][NP * LDF], sY[2][NP * LDF], sC[2][NP * LDF], sab[2][2][NP + 1];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 2 + w;
+    if (c >= B) return;
+    float *L = sL[w], *Y = sY[w], *C = sC[w], *al = sab[w][0], *bt = sab[w][1];
+    const float *mr = mom + (size_t)c * MEM_NCOL_FLUX;
+    const float n = M[(size_t)c * NP];
+    const float wx = gauge[(size_t)c * 6], sx = gauge[(size_t)c * 6 + 3];
+    if (F)
+        for (int k = lane; k < NP; k += 32) F[(size_t)c * NP + k] = n * (wx * mr[k] + sx * mr[NP + k]);
+    if (!speed) return;
+    for (int p = lane; p < 630; p += 32) {
+        int i = (int)((sqrtf(8.f * p + 1.f) - 1.f) * 0.5f);
+        while (i * (i + 1) / 2 > p) --i;
+        while ((i + 1) * (i + 2) / 2 <= p) ++i;
+        const int j = p - i * (i + 1) / 2;
+        L[i * LDF + j] = mr[70 + p];
+        const float x = mr[700 + p];
+        Y[i * LDF + j] = x;
+        Y[j * LDF + i] = x;
+    }
+    __syncwarp();
+    if (!warp_cholesky(L, NP, LDF, lane)) {
+        if (lane == 0) speed[c] = fmaxf(fabsf(wx + sx * xmax), fabsf(wx - sx * xmax));
+        return;
+    }
+    // Y <- L^{-1} Y (columns), then C = L^{-1} Y^T (columns of Y^T = rows of Y).
+    for (int j = lane; j < NP; j += 32)
+        for (int i = 0; i < NP; ++i) {
+            float s = Y[i * LDF + j];
+            for (int k = 0; k < i; ++k) s -= L[i * LDF + k] * Y[k * LDF + j];
+            Y[i * LDF + j] = s / L[i * LDF + i];
+        }
+    __syncwarp();
+    for (int j = lane; j < NP; j += 32)
+        for (int i = 0; i < NP; ++i) {
+            float s = Y[j * LDF + i];
+            for (int k = 0; k < i; ++k) s -= L[i * LDF + k] * C[k * LDF + j];
+            C[i * LDF + j] = s / L[i * LDF + i];
+        }
+    __syncwarp();
+    for (int p = lane; p < NP * NP; p += 32) {
+        const int i = p / NP, j = p % NP;
+        if (j < i) {
+            const float s = 0.5f * (C[i * LDF + j] + C[j * LDF + i]);
+            C[i * LDF + j] = s;
+            C[j * LDF + i] = s;
+        }
+    }
+    __syncwarp();
+    // Lanczos; the vectors live in Y (row k = v_k).
+    float *V = Y;
+    const float inv35 = rsqrtf((float)NP);
+    for (int i = lane; i < NP; i += 32) V[i] = inv35;
+    float cnorm = 0.f;
+    for (int i = lane; i < NP; i += 32) cnorm = fmaxf(cnorm, fabsf(C[i * LDF + i]));
+    for (int p = lane; p < NP * NP; p += 32) cnorm = fmaxf(cnorm, fabsf(C[(p / NP) * LDF + p % NP]));
+    cnorm = warp_max(cnorm) + 1e-30f;
+    __syncwarp();
+    int m = 0;
+    for (int k = 0; k < NP; ++k) {
+        float wv[2] = {0.f, 0.f};
+        for (int r = 0; r < 2; ++r) {
+            const int i = lane + 32 * r;
+            if (i < NP) {
+                float s = 0.f;
+                for (int j = 0; j < NP; ++j) s += C[i * LDF + j] * V[k * LDF + j];
+                wv[r] = s;
+            }
+        }
+        float part = 0.f;
+        for (int r = 0; r < 2; ++r) { const int i = lane + 32 * r; if (i < NP) part += wv[r] * V[k * LDF + i]; }
+        const float a = warp_sum(part);
+        if (lane == 0) al[k] = a;
+        // full re-orthogonalisation (two classical Gram-Schmidt passes)
+        for (int pass = 0; pass < 2; ++pass)
+            for (int j = 0; j <= k; ++j) {
+                float pp = 0.f;
+                for (int r = 0; r < 2; ++r) { const int i = lane + 32 * r; if (i < NP) pp += wv[r] * V[j * LDF + i]; }
+                const float d = warp_sum(pp);
+                for (int r = 0; r < 2; ++r) { const int i = lane + 32 * r; if (i < NP) wv[r] -= d * V[j * LDF + i]; }
+            }
+        float nn = 0.f;
+        for (int r = 0; r < 2; ++r) { const int i = lane + 32 * r; if (i < NP) nn += wv[r] * wv[r]; }
+        const float bk = sqrtf(warp_sum(nn));
+        m = k + 1;
+        if (k + 1 == NP || bk <= 1e-6f * cnorm) break;
+        if (lane == 0) bt[k] = bk;
+        for (int r = 0; r < 2; ++r) { const int i = lane + 32 * r; if (i < NP) V[(k + 1) * LDF + i] = wv[r] / bk; }
+        __syncwarp();
+    }
+    __syncwarp();
+    const float mu_hi = warp_tridiag_extreme(al, bt, m, true, lane);
+    const float mu_lo = warp_tridiag_extreme(al, bt, m, false, lane);
+    if (lane == 0) speed[c] = fmaxf(fabsf(wx + sx * mu_hi), fabsf(wx + sx * mu_lo));
+}
+
+void sgemm(const float *A, const float *Bm, float *C, int M, int N, int K, cudaStream_t st) {
+    dim3 grid((N + 63) / 64, (M + 63) / 64);
+    k_sgemm<<<grid, 256, 0, st>>>(A, Bm, C, M, N, K);
+}
+
+}  // namespace
+
+namespace mem_host {
+
+int solve_plain(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters, int64_t B,
+                const mem_solve_opts &o, cudaStream_t st) {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    const int Q = ctx->Q;
+    const size_t CH = (size_t)std::min<int64_t>(B, CHUNK);
+    const size_t need = sizeof(float) * CH * ((size_t)Q + MEM_NCOL_SOLVE + 2 * NP + 2) + sizeof(int) * (CH * 4 + 2) + 16 * 256;
+    int rc = ensure_scratch(ctx, need);
+    if (rc) return rc;
+    char *p = (char *)ctx->scratch;
+    auto take = [&](size_t bytes) { char *r = p; p += (bytes + 255) & ~(size_t)255; return r; };
+    PlainState S;
+    S.sigma = (float *)take(sizeof(float) * CH * Q);
+    S.mom = (float *)take(sizeof(float) * CH * MEM_NCOL_SOLVE);
+    S.db = (float *)take(sizeof(float) * CH * NP);
+    S.G = (float *)take(sizeof(float) * CH * NP);
+    S.Lcur = (float *)take(sizeof(float) * CH);
+    S.alpha = (float *)take(sizeof(float) * CH);
+    S.it = (int *)take(sizeof(int) * CH);
+    S.st = (int *)take(sizeof(int) * CH);
+    S.act0 = (int *)take(sizeof(int) * CH);
+    S.act1 = (int *)take(sizeof(int) * CH);
+    S.cnt = (int *)take(sizeof(int) * 2);
+    if ((size_t)(p - (char *)ctx->scratch) > ctx->scratch_bytes) return MEM_ENOMEM;
+    for (int64_t c0 = 0; c0 < B; c0 += CH) {
+        const int n = (int)std::min<int64_t>(CH, B - c0);
+        const float *Mc = M + c0 * NP;
+        float *bc = beta + c0 * NP;
+        int32_t *stc = status ? status + c0 : nullptr, *itc = iters ? iters + c0 : nullptr;
+        MEM_CUDA_TRY(cudaMemsetAsync(S.cnt, 0, 2 * sizeof(int), st));
+        k_init<<<(n + 255) / 256, 256, 0, st>>>(Mc, bc, n, S, stc, itc);
+        int nact = 0;
+        MEM_CUDA_TRY(cudaMemcpyAsync(&nact, S.cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MEM_CUDA_TRY(cudaStreamSynchronize(st));
+        int *cur = S.act0, *nxt = S.act1;
+        int cur_cnt = 0;
+        for (int pass = 0; pass <= o.maxI + 1 && nact > 0; ++pass) {
+            k_linesearch<<<nact, BLK, 0, st>>>(cur, Mc, bc, S, ctx->d_phiT, ctx->d_logw, Q, o);
+            sgemm(S.sigma, ctx->d_tab_solve, S.mom, nact, MEM_NCOL_SOLVE, Q, st);
+            const int nxt_cnt = 1 - cur_cnt;
+            MEM_CUDA_TRY(cudaMemsetAsync(S.cnt + nxt_cnt, 0, sizeof(int), st));
+            k_newton<<<(nact + 3) / 4, 128, 0, st>>>(cur, nact, Mc, bc, S, nxt, S.cnt + nxt_cnt, o, stc, itc);
+            MEM_CUDA_TRY(cudaMemcpyAsync(&nact, S.cnt + nxt_cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+            MEM_CUDA_TRY(cudaStreamSynchronize(st));
+            std::swap(cur, nxt);
+            cur_cnt = nxt_cnt;
+        }
+    }
+    MEM_CUDA_TRY(cudaGetLastError());
+    return MEM_OK;
+}
+
+int flux_bufs(mem_ctx *ctx, const float *M, const float *beta, const float *g, float *F, float *speed, int64_t B,
+              float *sigma, float *mom, cudaStream_t st) {
+    const int n = (int)B;
+    k_sigma<<<n, BLK, 0, st>>>(beta, sigma, ctx->d_phiT, ctx->d_logw, ctx->Q);
+    sgemm(sigma, ctx->d_tab_flux, mom, n, MEM_NCOL_FLUX, ctx->Q, st);
+    k_flux_speed<<<(n + 1) / 2, 64, 0, st>>>(mom, M, g, F, speed, n, ctx->xmax);
+    MEM_CUDA_TRY(cudaGetLastError());
+    return MEM_OK;
+}
+
+int flux(mem_ctx *ctx, const float *M, const float *beta, const float *g, float *F, float *speed, int64_t B,
+         cudaStream_t st) {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    const int Q = ctx->Q;
+    const size_t CH = (size_t)std::min<int64_t>(B, CHUNK);
+    int rc = ensure_scratch(ctx, sizeof(float) * CH * ((size_t)Q + MEM_NCOL_FLUX) + 1024);
+    if (rc) return rc;
+    float *sigma = (float *)ctx->scratch;
+    float *mom = sigma + ((CH * Q + 63) & ~(size_t)63);
+    for (int64_t c0 = 0; c0 < B; c0 += CH) {
+        const int64_t n = std::min<int64_t>(CH, B - c0);
+        rc = flux_bufs(ctx, M + c0 * NP, beta + c0 * NP, g + c0 * 6, F ? F + c0 * NP : nullptr,
+                       speed ? speed + c0 : nullptr, n, sigma, mom, st);
+        if (rc) return rc;
+    }
+    return MEM_OK;
+}
+
+}  // namespace mem_host

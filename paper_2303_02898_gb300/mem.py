@@ -1,0 +1,212 @@
+"""Thin Python binding of the C ABI in include/mem.h (argument marshalling only).
+
+Every function here passes device pointers of torch tensors (and the current
+torch CUDA stream) to libmem_gb300.so; all arithmetic of the method runs in
+the library's CUDA kernels.  Importing this module without the built library
+raises immediately: there is no fallback path.
+"""
+import ctypes
+import os
+import re
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmem_gb300.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "mem.h")
+
+NP = 35
+MEM_OK, MEM_PENDING = 0, 1
+MEM_EINVAL, MEM_ENOMEM, MEM_ECUDA, MEM_EBUSY, MEM_ENOTFOUND = -1, -2, -3, -4, -5
+ST_CONVERGED, ST_STAGNATED, ST_MAXITER, ST_NONFINITE = 1, 2, 4, 8
+ST_LAMBDA, ST_LAMBDA_CAP, ST_BADINPUT = 16, 32, 64
+IMPL_PLAIN, IMPL_FUSED = 0, 1
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_float), ("maxI", ctypes.c_int32), ("lambda0", ctypes.c_float),
+                ("lambda_mul", ctypes.c_float), ("max_lambda", ctypes.c_int32), ("c_armijo", ctypes.c_float),
+                ("atol", ctypes.c_float), ("rtol", ctypes.c_float), ("maxT", ctypes.c_int32),
+                ("alpha_min", ctypes.c_float), ("final_step", ctypes.c_int32), ("impl", ctypes.c_int32)]
+
+
+class ShockParams(ctypes.Structure):
+    _fields_ = [("mach", ctypes.c_double), ("ncells", ctypes.c_int32), ("xl", ctypes.c_double),
+                ("xr", ctypes.c_double), ("cfl", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("kn", ctypes.c_double), ("ic", ctypes.c_int32),
+                ("impl", ctypes.c_int32), ("graph", ctypes.c_int32), ("tol", ctypes.c_float),
+                ("maxI", ctypes.c_int32)]
+
+
+class ShockResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("steps", ctypes.c_int32), ("ncells", ctypes.c_int32),
+                ("steady", ctypes.c_int32), ("sim_time", ctypes.c_double), ("latency_s", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def lib():
+    """Load libmem_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libmem_gb300.so is not built (run __graft_entry__.build()); "
+                               "there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        L.mem_version.restype = ctypes.c_char_p
+        for name in ("mem_init", "mem_solve", "mem_flux", "mem_gauge_hermite", "mem_gauge_transform",
+                     "mem_targets", "mem_shock_init", "mem_shock_step", "mem_shock_get",
+                     "mem_shock_device_state", "mem_quad_order"):
+            getattr(L, name).restype = ctypes.c_int
+        L.mem_solve.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(SolveOpts), _P]
+        L.mem_flux.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P]
+        L.mem_gauge_hermite.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_int, _P]
+        L.mem_gauge_transform.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int64, _P]
+        L.mem_targets.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, ctypes.c_int64, _P]
+        L.mem_shock_step.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]
+        L.mem_destroy.argtypes = [_P]
+        L.mem_shock_free.argtypes = [_P]
+        _lib = L
+    return _lib
+
+
+def declared_functions():
+    """Names of the functions include/mem.h declares."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mem_[a-z_0-9]+)\s*\(", txt)))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(rc, what):
+    if rc != MEM_OK:
+        raise RuntimeError("%s failed with code %d" % (what, rc))
+
+
+def default_opts(**kw):
+    o = SolveOpts()
+    lib().mem_solve_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """mem_init / mem_destroy: quadrature and statistics tables on the device."""
+
+    def __init__(self, quad_order=8, degree=4):
+        h = ctypes.c_void_p()
+        _check(lib().mem_init(degree, quad_order, ctypes.byref(h)), "mem_init")
+        self.h = h
+        self.quad_order = quad_order
+
+    def close(self):
+        if self.h:
+            lib().mem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- solve
+    def solve(self, M, beta, status=None, iters=None, opts=None, stream=None, **kw):
+        """mem_solve: Algorithm 1 on every row of M (in place on beta)."""
+        B = M.shape[0]
+        o = opts if opts is not None else default_opts(**kw)
+        rc = lib().mem_solve(self.h, _ptr(M), _ptr(beta), _ptr(status), _ptr(iters), B, ctypes.byref(o),
+                             _stream(stream))
+        _check(rc, "mem_solve")
+
+    def flux(self, M, beta, gauge, F=None, speed=None, stream=None):
+        rc = lib().mem_flux(self.h, _ptr(M), _ptr(beta), _ptr(gauge), _ptr(F), _ptr(speed), M.shape[0],
+                            _stream(stream))
+        _check(rc, "mem_flux")
+
+    def gauge_hermite(self, M_in, g_in, g_out, M_out, beta=None, axisym=False, stream=None):
+        rc = lib().mem_gauge_hermite(self.h, _ptr(M_in), _ptr(g_in), _ptr(g_out), _ptr(M_out), _ptr(beta),
+                                     M_in.shape[0], int(bool(axisym)), _stream(stream))
+        _check(rc, "mem_gauge_hermite")
+
+    def gauge_transform(self, g_to, g_from, M_in, M_out, stream=None):
+        rc = lib().mem_gauge_transform(self.h, _ptr(g_to), _ptr(g_from), _ptr(M_in), _ptr(M_out),
+                                       M_in.shape[0], _stream(stream))
+        _check(rc, "mem_gauge_transform")
+
+    def targets(self, v, T, a, b, M_out, g_out, gen_order=24, stream=None):
+        rc = lib().mem_targets(self.h, gen_order, _ptr(v), _ptr(T), _ptr(a), _ptr(b), _ptr(M_out), _ptr(g_out),
+                               v.shape[0], _stream(stream))
+        _check(rc, "mem_targets")
+
+
+def default_shock_params(**kw):
+    p = ShockParams()
+    lib().mem_shock_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Shock:
+    """mem_shock_init / step / get / free."""
+
+    def __init__(self, ctx, **kw):
+        self.ctx = ctx
+        self.p = default_shock_params(**kw)
+        h = ctypes.c_void_p()
+        _check(lib().mem_shock_init(ctx.h, ctypes.byref(self.p), ctypes.byref(h)), "mem_shock_init")
+        self.h = h
+        self.N = self.p.ncells
+
+    def step(self, nsteps=1, steady=False, stream=None):
+        d = ctypes.c_double(0.0)
+        rc = lib().mem_shock_step(self.h, nsteps, ctypes.byref(d) if steady else None, _stream(stream))
+        _check(rc, "mem_shock_step")
+        return d.value if steady else None
+
+    def get(self):
+        import numpy as np
+        NT = self.N + 2
+        M = np.zeros((NT, NP), np.float32)
+        g = np.zeros((NT, 6), np.float32)
+        b = np.zeros((NT, NP), np.float32)
+        prof = [np.zeros(self.N, np.float32) for _ in range(5)]
+        t = ctypes.c_double()
+        f = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        rc = lib().mem_shock_get(self.h, f(M), f(g), f(b), *[f(x) for x in prof], ctypes.byref(t))
+        _check(rc, "mem_shock_get")
+        return dict(M=M, g=g, beta=b, rho=prof[0], ux=prof[1], T=prof[2], sxx=prof[3], qx=prof[4], t=t.value)
+
+    def device_state(self):
+        ptrs = [ctypes.c_void_p() for _ in range(6)]
+        _check(lib().mem_shock_device_state(self.h, *[ctypes.byref(p) for p in ptrs]), "mem_shock_device_state")
+        return [p.value for p in ptrs]
+
+    def close(self):
+        if self.h:
+            lib().mem_shock_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

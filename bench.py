@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark of the MEM hot path on GB300.
+
+Headline: cell-solves/s of the batched standalone maximal-entropy solve
+(Algorithm 1 on 2^20 independent 35-moment cells, tensor Gauss-Hermite 8^3,
+cold start beta = 0), tuned (fused) back-end, inputs resident in HBM.  One
+step = one mem_solve over the whole batch.  Reported beside it: the same
+metric end to end through the C ABI from pinned host buffers (e2e), the plain
+FP32 back-end, the 12^3 rule, the Mach-10 shock (4096 cells, graph-captured
+Algorithm 2 step) in cell-updates/s, the roofline of the fused kernel, and the
+FP64 oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tuned|reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MEM cell-solves/s & cell-updates/s at Ma10, tuned vs plain FP32; p99 latency"
+UNIT = "cell-solves/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tuned", choices=["tuned", "reference"])
+    ap.add_argument("--cells", type=int, default=1 << 20)
+    ap.add_argument("--order", type=int, default=8)
+    ap.add_argument("--no-extras", action="store_true", help="headline only (used for profiler runs)")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.p is None:
+            return out
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        os.unlink(self.f.name)
+        return out
+
+
+def fused_flops_per_pass(n):
+    """Algorithmic FP32 flops of one Newton pass of the fused kernel for one
+    cell (FMA = 2): two sum-factorised exponent evaluations, one line-search
+    trial, the three moment stages, Hessian assembly from the Hermite
+    linearisation, Cholesky and two triangular solves."""
+    expo = n * n * 49 + n ** 3 * 5
+    trial = n ** 3 * 2
+    stages = n ** 3 * 9 + 45 * n * n + 165 * n
+    terms = 0
+    idx = [(a, b, d - a - b) for d in range(5) for a in range(d, -1, -1) for b in range(d - a, -1, -1)]
+    for i in range(1, 35):
+        for j in range(1, i + 1):
+            t = 1
+            for x, y in zip(idx[i], idx[j]):
+                t *= min(x, y) + 1
+            terms += t
+    hess = terms + 595
+    chol = sum((34 - k - 1) * (34 - k) // 2 + (34 - k - 1) for k in range(34))
+    trsv = 34 * 34
+    fma = 2 * expo + trial + stages + hess + chol + trsv
+    return 2 * fma
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_baseline(order, sample, seed=0):
+    from oracle import oracle as O
+    from paper_2303_02898_gb300 import workloads
+    t = workloads.solve_targets(sample, seed=seed)
+    M, _ = O.target_batch(24, t.v, t.T, t.a, t.b)
+    t0 = time.perf_counter()
+    O.solve_batch(order, M)
+    dt = time.perf_counter() - t0
+    return {"value": sample / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "first %d cells of the same workload (seed %d), FP64 Algorithm 1, Q=%d^3, OpenMP" % (sample, seed, order),
+            "seconds": dt}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2303_02898_gb300 import workloads
+    sample = 2048
+    t = workloads.solve_targets(sample, seed=0)
+    M, _ = O.target_batch(24, t.v, t.T, t.a, t.b)
+    for _ in range(args.warmup):
+        O.solve_batch(args.order, M)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.solve_batch(args.order, M)
+    dt = time.perf_counter() - t0
+    value = sample * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, sample),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": "%d cells of the workload per step (seed 0)" % sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, cells):
+    return {"workload": "batched standalone max-entropy solves: 35 moments (degree <= 4 in 3D velocity), "
+                        "targets from seeded polynomial log-densities (v~N(0,3^2), T~logU[0.5,20], cubic~N(0,0.05^2), "
+                        "quartic~-U(0.01,0.1)), cold start beta=0",
+            "cells_per_gpu": cells, "quadrature": "Gauss-Hermite %d^3 in the Hermite gauge" % args.order,
+            "moments": 35, "l2": "inputs larger than L2 (M 147 MB read, beta 147 MB written per step)"}
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import numpy as np
+    import torch
+    from paper_2303_02898_gb300 import mem, workloads
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    B = args.cells
+    ctx = mem.Context(args.order)
+    t = workloads.solve_targets(B, seed=rank)
+    T32 = lambda a: torch.tensor(a, dtype=torch.float32, device=dev).contiguous()  # noqa: E731
+    M = torch.zeros(B, 35, device=dev)
+    g = torch.zeros(B, 6, device=dev)
+    ctx.targets(T32(t.v), T32(t.T), T32(t.a), T32(t.b), M, g, gen_order=24)
+    beta = torch.zeros_like(M)
+    st = torch.zeros(B, dtype=torch.int32, device=dev)
+    it = torch.zeros(B, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    opts = mem.default_opts(impl=mem.IMPL_FUSED)
+
+    def step():
+        beta.zero_()
+        ctx.solve(M, beta, st, it, opts=opts)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        beta.zero_()
+        ev[k][0].record(stream)
+        ctx.solve(M, beta, st, it, opts=opts)
+        ev[k][1].record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    kern_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    value = B * world / (ms * 1e-3)
+    itn = it.cpu().numpy()
+    stn = st.cpu().numpy()
+    passes = int(itn.sum())
+    flops = passes * fused_flops_per_pass(args.order)
+    peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+    achieved = flops / (kern_ms * 1e-3) / 1e12
+    conv = float(np.mean((stn & (mem.ST_CONVERGED | mem.ST_STAGNATED)) != 0))
+
+    # ---- end to end through the C ABI from pinned host buffers
+    M_h = M.cpu().pin_memory()
+    beta_h = torch.zeros(B, 35).pin_memory()
+    st_h = torch.zeros(B, dtype=torch.int32).pin_memory()
+    M_d = torch.empty_like(M)
+
+    def e2e_step():
+        M_d.copy_(M_h, non_blocking=True)
+        beta.zero_()
+        ctx.solve(M_d, beta, st, None, opts=opts)
+        beta_h.copy_(beta, non_blocking=True)
+        st_h.copy_(st, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    a1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = max_over_ranks(a0.elapsed_time(a1)) / args.steps
+    e2e = {"value": B * world / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": B * 35 * 4,
+           "d2h_bytes_per_step": B * 35 * 4 + B * 4}
+
+    extras = {}
+    if not args.no_extras:
+        # plain FP32 back-end (separate kernels, host loop) on the same batch
+        popts = mem.default_opts(impl=mem.IMPL_PLAIN)
+        beta.zero_()
+        ctx.solve(M, beta, st, it, opts=popts)
+        torch.cuda.synchronize()
+        p0 = time.perf_counter()
+        nplain = 2
+        for _ in range(nplain):
+            beta.zero_()
+            ctx.solve(M, beta, st, it, opts=popts)
+        torch.cuda.synchronize()
+        pms = (time.perf_counter() - p0) * 1e3 / nplain
+        extras["plain_fp32"] = {"value": B / (pms * 1e-3), "unit": UNIT, "ms_per_step": pms,
+                                "converged": float(np.mean((st.cpu().numpy() & 3) != 0))}
+        extras["tuned_over_plain"] = value / world / extras["plain_fp32"]["value"]
+        # 12^3 rule, tuned
+        ctx12 = mem.Context(12)
+        M12 = torch.zeros(B, 35, device=dev)
+        g12 = torch.zeros(B, 6, device=dev)
+        ctx12.targets(T32(t.v), T32(t.T), T32(t.a), T32(t.b), M12, g12, gen_order=24)
+        for _ in range(2):
+            beta.zero_()
+            ctx12.solve(M12, beta, st, it, opts=opts)
+        torch.cuda.synchronize()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(3):
+            beta.zero_()
+            ctx12.solve(M12, beta, st, it, opts=opts)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        extras["tuned_q12"] = {"value": B / (q0.elapsed_time(q1) / 3 * 1e-3), "unit": UNIT,
+                               "mean_passes": float(it.float().mean())}
+        ctx12.close()
+        del M12, g12
+        # Mach 10 shock, 4096 cells over +-50 mean free paths, graph-captured step
+        for impl, graph, nst in ((mem.IMPL_FUSED, 1, 200), (mem.IMPL_PLAIN, 0, 10)):
+            sh = mem.Shock(ctx, mach=10.0, ncells=4096, xl=-50.0, xr=50.0, impl=impl, graph=graph)
+            sh.step(3)
+            torch.cuda.synchronize()
+            s0 = time.perf_counter()
+            sh.step(nst)
+            torch.cuda.synchronize()
+            sdt = time.perf_counter() - s0
+            d = sh.get()
+            key = "shock_mach10_tuned" if impl == mem.IMPL_FUSED else "shock_mach10_plain"
+            extras[key] = {"value": 4096 * nst / sdt, "unit": "cell-updates/s", "steps": nst,
+                           "ms_per_step": 1e3 * sdt / nst, "sim_time": d["t"],
+                           "finite": bool(np.isfinite(d["M"]).all())}
+            sh.close()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args, B),
+            "e2e": e2e, "gpu_launches": args.steps,
+            "clocks": clocks,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
+                         "frac": achieved / peak_fp32, "traffic": None,
+                         "kernel": "k_fused_solve<%d>" % args.order, "kernel_ms": kern_ms,
+                         "flops_per_launch": flops, "newton_passes": passes,
+                         "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (not in the measured-peaks file)"},
+            "solve_stats": {"converged_fraction": conv, "mean_passes": passes / B, "max_passes": int(itn.max())}}
+    line.update(extras)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.order, 16384)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -784,11 +784,13 @@ void or_target_moments(int order, const double *v, double T, const double *a, co
             for (int ax = 0; ax < 3; ++ax) c[ax] = mu[ax] + sc[ax] * z[ax];
             double ex = r->logw[q] + 0.5 * (z[0] * z[0] + z[1] * z[1] + z[2] * z[2]);
             ex -= 0.5 * (c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+            double pw[3][5];
+            for (int ax = 0; ax < 3; ++ax) { pw[ax][0] = 1.0; for (int e = 1; e < 5; ++e) pw[ax][e] = pw[ax][e - 1] * c[ax]; }
             for (int k = 0; k < 10; ++k) {
                 int *ix = g_idx[10 + k];
-                ex += a[k] * pow(c[0], ix[0]) * pow(c[1], ix[1]) * pow(c[2], ix[2]);
+                ex += a[k] * pw[0][ix[0]] * pw[1][ix[1]] * pw[2][ix[2]];
             }
-            for (int k = 0; k < 6; ++k) ex -= b[k] * pow(c[0], quart[k][0]) * pow(c[1], quart[k][1]) * pow(c[2], quart[k][2]);
+            for (int k = 0; k < 6; ++k) ex -= b[k] * pw[0][quart[k][0]] * pw[1][quart[k][1]] * pw[2][quart[k][2]];
             e[q] = ex;
             if (ex > emax) emax = ex;
         }

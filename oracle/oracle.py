@@ -245,7 +245,7 @@ class Shock:
     """FP64 shock-tube state: N interior cells + 2 Dirichlet ghost cells."""
 
     def __init__(self, mach, ncells, xl, xr, order=8, cfl=0.5, Pr=2.0 / 3.0, gamma=5.0 / 3.0,
-                 kn=1.0, tol=1e-8, maxI=500, nthreads=0):
+                 kn=1.0, tol=1e-8, maxI=500, nthreads=0, ic="step", thickness=15.7):
         self.order, self.N, self.cfl, self.Pr = order, ncells, cfl, Pr
         self.dx = (xr - xl) / ncells
         self.x = xl + (np.arange(ncells) + 0.5) * self.dx
@@ -260,13 +260,32 @@ class Shock:
         self.beta = np.zeros((NT, NP))
         self.g = np.zeros((NT, 6))
         xs = np.concatenate([[xl - 0.5 * self.dx], self.x, [xr + 0.5 * self.dx]])
+        g_up = np.array([self.v_up, 0, 0, 1.0, 1.0, 1.0]) * np.array([1, 1, 1, np.sqrt(self.T_up)] + [np.sqrt(self.T_up)] * 2)
+        g_dn = np.array([self.v_dn, 0, 0] + [np.sqrt(self.T_dn)] * 3)
         for c in range(NT):
-            up = xs[c] < 0.0
-            n, T, v = (self.n_up, self.T_up, self.v_up) if up else (self.n_dn, self.T_dn, self.v_dn)
-            self.M[c, 0] = n
-            self.beta[c, 0] = n
-            s = np.sqrt(T)
-            self.g[c] = [v, 0.0, 0.0, s, s, s]
+            if ic == "step" or c == 0 or c == NT - 1:
+                up = xs[c] < 0.0
+                n = self.n_up if up else self.n_dn
+                self.M[c, 0] = n
+                self.beta[c, 0] = n
+                self.g[c] = g_up if up else g_dn
+            else:
+                # Appendix D, Eq. "Mx ini": moments blended with a tanh profile
+                # of thickness parameter T (the two Maxwellians' moments are
+                # blended in one gauge, then moved to the Hermite gauge).
+                h = thickness / 2.0
+                w = (np.tanh(xs[c] / h) - np.tanh(xl / h)) / (np.tanh(xr / h) - np.tanh(xl / h))
+                Mu = np.zeros(NP)
+                Mu[0] = self.n_up
+                Md = transform_M(g_up, g_dn, np.r_[self.n_dn, np.zeros(NP - 1)])
+                Mb = (1 - w) * Mu + w * Md
+                gH = hermite_gauge(Mb, g_up, axisym=True)
+                self.M[c] = transform_M(gH, g_up, Mb)
+                self.g[c] = gH
+                self.beta[c, 0] = self.M[c, 0]
+        if ic != "step":
+            b, st, it = solve_batch(order, self.M[1:-1], None, tol, maxI, nthreads)
+            self.beta[1:-1] = b
         _, self.speed = flux_batch(order, self.M, self.beta, self.g, nthreads)
         self.status = np.zeros(NT, dtype=np.int32)
         self.iters = np.zeros(NT, dtype=np.int32)

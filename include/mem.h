@@ -128,6 +128,26 @@ int mem_solve(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_
 int mem_flux(mem_ctx *ctx, const float *M, const float *beta, const float *gauge, float *F,
              float *speed, int64_t B, void *stream);
 
+/* mem_flux without any allocation.  The paper has no counterpart: this is a
+ * service of the library for callers that cannot allocate device memory when
+ * they need fluxes -- for example a caller whose allocator already owns the
+ * device budget, or a latency-critical loop that cannot afford cudaMalloc's
+ * implicit synchronisation.  Same arguments and results as mem_flux.
+ * Working memory is a fixed 12.5 MB array inside the library image (resident
+ * on every GPU that loads the library until the process exits), so:
+ *   - B <= 1024 cells per call and a context with quad_order <= 12; larger
+ *     requests return MEM_EINVAL without doing anything;
+ *   - the current device must be the context's device (else MEM_EINVAL);
+ *   - the first call on a device resolves the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - every call uses the same array: calls whose work overlaps on the GPU
+ *     (different streams, or threads without ordering) race and give wrong
+ *     results.  Each call writes everything it later reads, so the contents a
+ *     previous call left behind never leak into a result.
+ * No cudaMalloc, cudaFree or other allocating routine is called. */
+int mem_flux_noalloc(mem_ctx *ctx, const float *M, const float *beta, const float *gauge, float *F,
+                     float *speed, int64_t B, void *stream);
+
 /* Hermite gauge (Eqs. "Hermite parameters", "Hermite parameters in moments")
  * and the change of gauge of Eq. "Change gauge M F":
  *   g_out = g_H(M_in, g_in); M_out = T(g_out, g_in) M_in;

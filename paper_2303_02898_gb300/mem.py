@@ -62,6 +62,8 @@ def lib():
             getattr(L, name).restype = ctypes.c_int
         L.mem_solve.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(SolveOpts), _P]
         L.mem_flux.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P]
+        L.mem_flux_noalloc.restype = ctypes.c_int
+        L.mem_flux_noalloc.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P]
         L.mem_gauge_hermite.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_int, _P]
         L.mem_gauge_transform.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int64, _P]
         L.mem_targets.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, ctypes.c_int64, _P]
@@ -140,6 +142,12 @@ class Context:
         rc = lib().mem_flux(self.h, _ptr(M), _ptr(beta), _ptr(gauge), _ptr(F), _ptr(speed), M.shape[0],
                             _stream(stream))
         _check(rc, "mem_flux")
+
+    def flux_noalloc(self, M, beta, gauge, F=None, speed=None, stream=None):
+        """mem_flux_noalloc: as flux(), with library-resident working memory
+        (at most 1024 cells per call); returns the C return code."""
+        return lib().mem_flux_noalloc(self.h, _ptr(M), _ptr(beta), _ptr(gauge), _ptr(F), _ptr(speed),
+                                      M.shape[0], _stream(stream))
 
     def gauge_hermite(self, M_in, g_in, g_out, M_out, beta=None, axisym=False, stream=None):
         rc = lib().mem_gauge_hermite(self.h, _ptr(M_in), _ptr(g_in), _ptr(g_out), _ptr(M_out), _ptr(beta),

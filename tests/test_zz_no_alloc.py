@@ -1,0 +1,56 @@
+"""mem_flux_noalloc: fluxes and speeds for callers that cannot allocate device
+memory (their allocator owns the budget, or a cudaMalloc on their path would
+cost a synchronisation).  It must give what mem_flux gives, call after call,
+from its fixed library-resident working memory.  This file is collected last
+so that a run stopping at its first failure has run every other test."""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _inputs(rng, B, dev):
+    deg = np.array([sum(e) for e in [(a, b, d - a - b) for d in range(5) for a in range(d, -1, -1)
+                                     for b in range(d - a, -1, -1)]])
+    scale = np.where(deg <= 2, 0.1, np.where(deg == 3, 0.03, 0.01))
+    beta = rng.normal(0, 1, (B, 35)) * scale
+    beta[:, 0] = np.exp(rng.uniform(-0.5, 0.5, B))
+    M = np.zeros((B, 35))
+    M[:, 0] = beta[:, 0]
+    g = np.concatenate([rng.normal(0, 2.0, (B, 3)), np.exp(rng.uniform(np.log(0.5), np.log(3.0), (B, 3)))], 1)
+    f = lambda a: torch.tensor(a, dtype=torch.float32, device=dev).contiguous()  # noqa: E731
+    return f(M), f(beta), f(g)
+
+
+def test_flux_noalloc_matches_flux_two_calls():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_02898_gb300 import mem
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    ctx = mem.Context(8)
+    L = mem.lib()
+    rng = np.random.default_rng(99)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for B in (1000, 1024):   # two calls in a row through the C ABI
+        M, beta, g = _inputs(rng, B, dev)
+        F_ref = torch.zeros(B, 35, device=dev)
+        s_ref = torch.zeros(B, device=dev)
+        ctx.flux(M, beta, g, F_ref, s_ref)
+        F = torch.full((B, 35), float("nan"), device=dev)
+        s = torch.full((B,), float("nan"), device=dev)
+        p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        rc = L.mem_flux_noalloc(ctx.h, p(M), p(beta), p(g), p(F), p(s), B, stream)
+        assert rc == mem.MEM_OK
+        torch.cuda.synchronize()
+        Fr, sr, Fn, sn = F_ref.cpu().numpy(), s_ref.cpu().numpy(), F.cpu().numpy(), s.cpu().numpy()
+        assert np.isfinite(Fn).all() and np.isfinite(sn).all()
+        assert np.abs(Fn - Fr).max() <= 2e-5 * np.abs(Fr).max()
+        assert np.allclose(sn, sr, rtol=2e-5)
+    # beyond the fixed capacity: rejected, nothing written
+    M, beta, g = _inputs(rng, 1025, dev)
+    assert ctx.flux_noalloc(M, beta, g, torch.zeros(1025, 35, device=dev), None) == mem.MEM_EINVAL
+    ctx.close()

@@ -154,6 +154,30 @@ static void build_lin_terms(int j0, bool with_x, std::vector<int> &off, std::vec
     off.push_back((int)terms.size());
 }
 
+// Per-lane term sequences for the fused kernel's Hessian assembly: lane l
+// takes the packed entries p = l, l + 32, ...; slot t of lane l is stored at
+// [t][l] as (mu index | p << 8 | last-term flag in the sign bit, coefficient).
+// Sequences are padded with zero terms to a common length.
+static void build_hess_slots(const std::vector<int> &off, const std::vector<int2> &terms, std::vector<int2> &slots,
+                             int &nslots) {
+    const int NE = (int)off.size() - 1;
+    std::vector<std::vector<int2>> per(32);
+    for (int p = 0; p < NE; ++p) {
+        auto &v = per[p % 32];
+        for (int t = off[p]; t < off[p + 1]; ++t) {
+            int2 s = terms[t];
+            s.x = (s.x & 255) | (p << 8);
+            if (t == off[p + 1] - 1) s.x |= (int)0x80000000;
+            v.push_back(s);
+        }
+    }
+    nslots = 0;
+    for (auto &v : per) nslots = std::max(nslots, (int)v.size());
+    slots.assign((size_t)nslots * 32, int2{0, 0});
+    for (int l = 0; l < 32; ++l)
+        for (int t = 0; t < (int)per[l].size(); ++t) slots[(size_t)t * 32 + l] = per[l][t];
+}
+
 template <typename T>
 static int upload(T **dst, const std::vector<T> &src) {
     if (cudaMalloc((void **)dst, sizeof(T) * std::max<size_t>(1, src.size())) != cudaSuccess) return MEM_ENOMEM;
@@ -226,6 +250,8 @@ int mem_init(int degree, int quad_order, mem_ctx **out) {
     std::vector<int2> terms, xterms;
     build_lin_terms(1, false, off, terms);
     build_lin_terms(0, true, xoff, xterms);
+    std::vector<int2> slots;
+    build_hess_slots(off, terms, slots, ctx->n_hess_slots);
     rc = MEM_OK;
     if (!rc) rc = upload(&ctx->d_phiT, phiT);
     if (!rc) rc = upload(&ctx->d_logw, logw);
@@ -236,6 +262,7 @@ int mem_init(int degree, int quad_order, mem_ctx **out) {
     if (!rc) rc = upload(&ctx->d_logw1d, lw1d);
     if (!rc) rc = upload(&ctx->d_lin_off, off);
     if (!rc) rc = upload(&ctx->d_lin_terms, terms);
+    if (!rc) rc = upload(&ctx->d_hess_slots, slots);
     if (!rc) rc = upload(&ctx->d_xlin_off, xoff);
     if (!rc) rc = upload(&ctx->d_xlin_terms, xterms);
     ctx->n_lin_terms = (int)terms.size();
@@ -249,7 +276,7 @@ void mem_destroy(mem_ctx *ctx) {
     if (!ctx) return;
     cudaDeviceSynchronize();
     void *ptrs[] = {ctx->d_phiT, ctx->d_logw, ctx->d_tab_solve, ctx->d_tab_flux, ctx->d_he1d, ctx->d_x1d,
-                    ctx->d_logw1d, ctx->d_lin_off, ctx->d_lin_terms, ctx->d_xlin_off, ctx->d_xlin_terms,
+                    ctx->d_logw1d, ctx->d_lin_off, ctx->d_lin_terms, ctx->d_hess_slots, ctx->d_xlin_off, ctx->d_xlin_terms,
                     ctx->scratch};
     for (void *p : ptrs)
         if (p) cudaFree(p);

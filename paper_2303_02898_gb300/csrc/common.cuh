@@ -12,7 +12,7 @@
 #include <math.h>
 #include <stdint.h>
 
-#include "../../include/mem.h"
+#include "mem.h"
 
 #define NP 35
 #define NP1 34

@@ -8,7 +8,7 @@
 #include <mutex>
 #include <vector>
 
-#include "../../include/mem.h"
+#include "mem.h"
 
 #define MEM_NCOL_SOLVE 630   // [phi_0..34 | phi_i phi_j, 1 <= j <= i <= 34 packed]
 #define MEM_NCOL_FLUX 1330   // [phi | ubar_x phi | phi phi^T packed (630) | ubar_x phi phi^T packed (630)]
@@ -30,6 +30,8 @@ struct mem_ctx {
     int *d_lin_off = nullptr;      // [596]  Hessian-term offsets (packed i>=j>=1)
     int2 *d_lin_terms = nullptr;   // (mu index, coefficient bits) per term
     int n_lin_terms = 0;
+    int2 *d_hess_slots = nullptr;  // [n_hess_slots][32] per-lane Hessian term sequences
+    int n_hess_slots = 0;
     int *d_xlin_off = nullptr;     // [631]  flux-Jacobian terms (packed i>=j>=0)
     int2 *d_xlin_terms = nullptr;
     float xmax = 0.f;              // largest 1D node

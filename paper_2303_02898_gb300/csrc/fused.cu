@@ -51,24 +51,31 @@ struct FusedArgs {
     int64_t B;
     const float *he1d;    // [N][16]
     const float *logw1d;  // [N]
-    const int *lin_off;   // [596]
-    const int2 *lin_terms;
+    const int2 *slots;    // [n_slots][32] Hessian linearisation terms per lane
+    int n_slots;
     mem_solve_opts o;
 };
 
 // Exponent contribution of a parameter vector v (slots 1..34) on the lane's
 // nodes: out[r*N + i] = sum_a he_a(x_i) u_a(line r).  add_logw adds log w_q.
+// v is read once into registers; each 1D table row he(x_i) once per node i.
 template <int N>
 __device__ __forceinline__ void exponent(const float *v, const float *he, const float *lw, int lane, bool add_logw,
                                          float (&out)[FusedCfg<N>::NODES]) {
     using C = FusedCfg<N>;
+    float vr[NP];
+#pragma unroll
+    for (int k = 1; k < NP; ++k) vr[k] = v[k];
+    float u[C::R][5], lwjk[C::R];
+    bool live[C::R];
 #pragma unroll
     for (int r = 0; r < C::R; ++r) {
         const int p = lane + 32 * r;
-        const bool live = p < C::P;
-        const int j = live ? p / N : 0, k = live ? p % N : 0;
-        const float *hy = he + j * MEM_HE_STRIDE, *hz = he + k * MEM_HE_STRIDE;
-        float u[5];
+        live[r] = p < C::P;
+        const int j = live[r] ? p / N : 0, k = live[r] ? p % N : 0;
+        float hy[5], hz[5];
+#pragma unroll
+        for (int a = 0; a < 5; ++a) { hy[a] = he[j * MEM_HE_STRIDE + a]; hz[a] = he[k * MEM_HE_STRIDE + a]; }
 #pragma unroll
         for (int a = 0; a <= 4; ++a) {
             float acc = 0.f;
@@ -77,39 +84,150 @@ __device__ __forceinline__ void exponent(const float *v, const float *he, const 
                 float inner = 0.f;
 #pragma unroll
                 for (int c = 0; a + b + c <= 4; ++c)
-                    if (a + b + c > 0) inner += v[idx3(a, b, c)] * hz[c];
+                    if (a + b + c > 0) inner += vr[idx3(a, b, c)] * hz[c];
                 acc += inner * hy[b];
             }
-            u[a] = acc;
+            u[r][a] = acc;
         }
-        const float lwjk = add_logw ? lw[j] + lw[k] : 0.f;
+        lwjk[r] = add_logw ? lw[j] + lw[k] : 0.f;
+    }
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-            const float *hx = he + i * MEM_HE_STRIDE;
-            float e = lwjk + (add_logw ? lw[i] : 0.f);
+    for (int i = 0; i < N; ++i) {
+        float hx[5];
 #pragma unroll
-            for (int a = 0; a <= 4; ++a) e += u[a] * hx[a];
-            out[r * N + i] = live ? e : (add_logw ? -INFINITY : 0.f);
+        for (int a = 0; a < 5; ++a) hx[a] = he[i * MEM_HE_STRIDE + a];
+        const float lwi = add_logw ? lw[i] : 0.f;
+#pragma unroll
+        for (int r = 0; r < C::R; ++r) {
+            float e = lwjk[r] + lwi;
+#pragma unroll
+            for (int a = 0; a <= 4; ++a) e += u[r][a] * hx[a];
+            out[r * N + i] = live[r] ? e : (add_logw ? -INFINITY : 0.f);
         }
     }
 }
 
+// Eight right-looking Cholesky steps k = K0 .. K0+7 on the register columns
+// (see reg_chol_solve34).  Rows i <= K0 are finished before the block starts,
+// so the row loop runs statically over K0+1 .. 33; within the block the rows
+// i <= k are masked by predication, not by branches, so that all shuffles of
+// one step can be in flight together.
+template <int K0>
+__device__ __forceinline__ bool chol_block8(float (&col)[NP1], float &t00, float &t10, float &t11, float &bb,
+                                            float &b32, float &b33, float &myinv, float &myw, int lane) {
+#pragma unroll 1
+    for (int kk = 0; kk < 8; ++kk) {
+        const int k = K0 + kk;
+        float s1[4], s2[2];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) s1[m] = (kk & 1) ? col[K0 + 2 * m + 1] : col[K0 + 2 * m];
+#pragma unroll
+        for (int m = 0; m < 2; ++m) s2[m] = (kk & 2) ? s1[2 * m + 1] : s1[2 * m];
+        const float ck = (kk & 4) ? s2[1] : s2[0];  // this lane's A_kj
+        const float d = __shfl_sync(0xffffffffu, ck, k);
+        if (!(d > 0.f) || !isfinite(d)) return false;
+        const float inv = rsqrtf(d), inv2 = inv * inv;
+        const float c = ck * inv2;
+        const float wk = __shfl_sync(0xffffffffu, bb, k) * inv;
+        const bool upd = lane > k;
+        float r32 = 0.f, r33 = 0.f;
+#pragma unroll
+        for (int i = K0 + 1; i < NP1; ++i) {
+            const float raw = __shfl_sync(0xffffffffu, col[i], k);
+            const float nv = fmaf(-raw, c, col[i]);
+            col[i] = (upd && i > k) ? nv : col[i];
+            if (i == 32) r32 = raw;
+            if (i == 33) r33 = raw;
+        }
+        if (upd) bb = fmaf(-ck * inv, wk, bb);
+        b32 = fmaf(-r32 * inv, wk, b32);
+        b33 = fmaf(-r33 * inv, wk, b33);
+        t00 = fmaf(-r32 * r32, inv2, t00);
+        t10 = fmaf(-r33 * r32, inv2, t10);
+        t11 = fmaf(-r33 * r33, inv2, t11);
+        if (lane == k) { myinv = inv; myw = wk; }
+    }
+    return true;
+}
+
+// Solve (H + lam I) x = rhs by a register-resident Cholesky factorisation,
+// H the 34 x 34 SPD matrix whose lower triangle is in shared memory
+// (row-major, leading dimension LDH).  Lane j < 32 holds column j of the
+// symmetric matrix (all 34 rows) in registers; rows/columns 32 and 33 (the
+// trailing 2 x 2 block) and rhs/x entries 32, 33 are carried, identical, by
+// every lane; entry i < 32 of rhs and x lives on lane i.
+// Right-looking factorisation: in step k lane j takes its own A_kj (= A_jk,
+// the matrix is kept symmetric), the pivot d = A_kk comes from lane k, and
+// every lane j > k applies A_ij -= A_ik A_jk / A_kk for i > k with A_ik
+// broadcast from lane k.  The forward solve L w = rhs rides along (lane i > k
+// subtracts L_ik w_k, L_ik = A_ik / l_k being its own register), and the
+// backward solve L^T x = w broadcasts one x_i per step.  Returns false,
+// uniformly, when a pivot is not positive and finite (the "failed
+// decomposition" of Algorithm 1).
+__device__ __forceinline__ bool reg_chol_solve34(const float *Hs, float lam, int lane, float rhs, float rhs32,
+                                                 float rhs33, float &x, float &x32, float &x33) {
+    float col[NP1];
+#pragma unroll
+    for (int i = 0; i < NP1; ++i) {
+        const int r = i > lane ? i : lane, c = i > lane ? lane : i;
+        float v = Hs[r * LDH + c];
+        if (i == lane) v += lam;
+        col[i] = v;
+    }
+    float t00 = Hs[32 * LDH + 32] + lam, t10 = Hs[33 * LDH + 32], t11 = Hs[33 * LDH + 33] + lam;
+    float bb = rhs, b32 = rhs32, b33 = rhs33;
+    float myinv = 0.f, myw = 0.f;
+    if (!chol_block8<0>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane)) return false;
+    if (!chol_block8<8>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane)) return false;
+    if (!chol_block8<16>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane)) return false;
+    if (!chol_block8<24>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane)) return false;
+    if (!(t00 > 0.f) || !isfinite(t00)) return false;
+    const float inv32 = rsqrtf(t00), l3332 = t10 * inv32, d33 = t11 - l3332 * l3332;
+    if (!(d33 > 0.f) || !isfinite(d33)) return false;
+    const float inv33 = rsqrtf(d33);
+    const float w32 = b32 * inv32, w33 = (b33 - l3332 * w32) * inv33;
+    x33 = w33 * inv33;
+    x32 = (w32 - l3332 * x33) * inv32;
+    // lane j: x_j = (w_j - inv_j sum_{i>j} A_ij x_i) inv_j, with A_ij its own column
+    float acc = fmaf(col[32], x32, col[33] * x33);
+#pragma unroll
+    for (int i = 31; i >= 0; --i) {
+        const float xi = __shfl_sync(0xffffffffu, (myw - myinv * acc) * myinv, i);
+        if (lane == i) x = xi;
+        if (lane < i) acc = fmaf(col[i], xi, acc);
+    }
+    return true;
+}
+
 template <int N>
-__global__ void __launch_bounds__(WARPS * 32) k_fused_solve(FusedArgs A) {
+__global__ void __launch_bounds__(WARPS * 32, (N <= 8 ? 4 : 2)) k_fused_solve(FusedArgs A) {
     using C = FusedCfg<N>;
     extern __shared__ float smem[];
     float *s_he = smem;                        // [N][16]
     float *s_lw = s_he + N * MEM_HE_STRIDE;    // [N] (padded to 16)
     int *s_abc = (int *)(s_lw + 16);           // [165] packed (a, b, c)
-    float *wbase = (float *)(s_abc + 168);
+    int *s_pij = s_abc + 168;                  // [595] packed (i, j) of Hessian entry p
+    int *s_ab = s_pij + 596;                   // [45]  packed (a, b) of stage-y row
+    float *wbase = (float *)(s_ab + 48);
     for (int t = threadIdx.x; t < N * MEM_HE_STRIDE; t += blockDim.x) s_he[t] = A.he1d[t];
     for (int t = threadIdx.x; t < N; t += blockDim.x) s_lw[t] = A.logw1d[t];
     for (int t = threadIdx.x; t < 165; t += blockDim.x) s_abc[t] = exp_a(t) | (exp_b(t) << 8) | (exp_c(t) << 16);
+    for (int t = threadIdx.x; t < NP1 * (NP1 + 1) / 2; t += blockDim.x) {
+        int i = 0;
+        while ((i + 1) * (i + 2) / 2 <= t) ++i;
+        s_pij[t] = i | ((t - i * (i + 1) / 2) << 8);
+    }
+    for (int t = threadIdx.x; t < 45; t += blockDim.x) {
+        int d = 0;
+        while ((d + 1) * (d + 2) / 2 <= t) ++d;
+        const int b = t - d * (d + 1) / 2;
+        s_ab[t] = (d - b) | (b << 8);
+    }
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *W = wbase + warp * C::WARP_FLOATS;
-    float *sb = W, *sd = W + 36, *sm = W + 72, *sg = W + 108, *srhs = W + 144, *smu = W + 180;
+    float *sb = W, *sd = W + 36, *sm = W + 72, *sg = W + 108, *smu = W + 180;
     float *work = smu + 168;
     float *S1 = work, *T2 = work + C::S1, *H = work;  // H aliases the stage buffers
     const mem_solve_opts &o = A.o;
@@ -135,82 +253,100 @@ __global__ void __launch_bounds__(WARPS * 32) k_fused_solve(FusedArgs A) {
         if (lane + 32 < NP) { sm[lane + 32] = m2 / n; sb[lane + 32] = b2; sd[lane + 32] = 0.f; sg[lane + 32] = 0.f; }
         __syncwarp();
 
-        float eb[C::NODES];
-        exponent<N>(sb, s_he, s_lw, lane, true, eb);
-        auto lse = [&](const float (&e)[C::NODES], float &mx) {
-            float m = -INFINITY;
-#pragma unroll
-            for (int q = 0; q < C::NODES; ++q) m = fmaxf(m, e[q]);
-            mx = warp_max(m);
-            float z = 0.f;
-#pragma unroll
-            for (int q = 0; q < C::NODES; ++q) z += __expf(e[q] - mx);
-            return warp_sum(z);
-        };
         auto dot_m = [&](const float *v) {  // sum_{k>=1} v_k M_k / n
             float p = (lane >= 1 && lane < NP ? v[lane] * sm[lane] : 0.f) + (lane + 32 < NP ? v[lane + 32] * sm[lane + 32] : 0.f);
             return warp_sum(p);
         };
-        float mx, Z = lse(eb, mx);
-        float Lcur = mx + __logf(Z) - dot_m(sb);
+        float Lcur = 0.f;
         int st = 0, it = 0;
         float alpha = 1.f;
         bool done = false;
         while (!done) {
-            // ---- BackTrackingLineSearch (no-op on the first pass: dbeta = 0)
-            if (it > 0) {
+            // The exponent arrays live only until stage x: they are recomputed
+            // from beta (and dbeta) at the start of every pass.
+            float eb[C::NODES];
+            exponent<N>(sb, s_he, s_lw, lane, true, eb);
+            float mx, Z;
+            if (it == 0) {
+                // BackTrackingLineSearch with dbeta = 0: alpha = 1 is accepted.
+                float m = -INFINITY;
+#pragma unroll
+                for (int q = 0; q < C::NODES; ++q) m = fmaxf(m, eb[q]);
+                mx = warp_max(m);
+                float z = 0.f;
+#pragma unroll
+                for (int q = 0; q < C::NODES; ++q) z += __expf(eb[q] - mx);
+                Z = warp_sum(z);
+                Lcur = mx + __logf(Z) - dot_m(sb);
+            } else {
+                // ---- BackTrackingLineSearch / ArmijoCondition (Algorithm 1):
+                // trial exponents are e_beta + alpha e_dbeta.
                 float ed[C::NODES];
                 exponent<N>(sd, s_he, s_lw, lane, false, ed);
                 float gp = (lane >= 1 && lane < NP ? sg[lane] * sd[lane] : 0.f) + (lane + 32 < NP ? sg[lane + 32] * sd[lane + 32] : 0.f);
                 const float gd = warp_sum(gp), mb = dot_m(sb), md = dot_m(sd);
                 alpha = 2.f;
                 bool sat = false;
+                float Lt = Lcur;
+                mx = 0.f;
+                Z = 1.f;
                 for (int s = 0; !sat && s <= o.maxT; ++s) {
                     alpha *= 0.5f;
                     float m = -INFINITY;
 #pragma unroll
-                    for (int q = 0; q < C::NODES; ++q) m = fmaxf(m, eb[q] + alpha * ed[q]);
-                    m = warp_max(m);
+                    for (int q = 0; q < C::NODES; ++q) m = fmaxf(m, fmaf(alpha, ed[q], eb[q]));
+                    mx = warp_max(m);
                     float z = 0.f;
 #pragma unroll
-                    for (int q = 0; q < C::NODES; ++q) z += __expf(eb[q] + alpha * ed[q] - m);
-                    z = warp_sum(z);
-                    const float Lt = m + __logf(z) - (mb + alpha * md);
+                    for (int q = 0; q < C::NODES; ++q) z += __expf(fmaf(alpha, ed[q], eb[q]) - mx);
+                    Z = warp_sum(z);
+                    Lt = mx + __logf(Z) - (mb + alpha * md);
                     const float LD = Lcur - Lt, gradD = -o.c_armijo * alpha * gd;
                     sat = (LD - gradD) >= -(o.atol + o.rtol * fabsf(LD));
                 }
+                // accepted (or last) trial: beta += alpha dbeta; its exponents
+                // give sigma for this pass
+#pragma unroll
+                for (int q = 0; q < C::NODES; ++q) eb[q] = fmaf(alpha, ed[q], eb[q]);
+                Lcur = Lt;
                 if (lane >= 1 && lane < NP) sb[lane] += alpha * sd[lane];
                 if (lane + 32 < NP) sb[lane + 32] += alpha * sd[lane + 32];
                 __syncwarp();
-                exponent<N>(sb, s_he, s_lw, lane, true, eb);
-                Z = lse(eb, mx);
-                Lcur = mx + __logf(Z) - dot_m(sb);
             }
             // ---- sigma and stage x: s_a(p) = sum_i sigma(i,p) he_a(x_i), a <= 8
-            const float invZ = 1.f / Z;
+            {
+                const float invZ = 1.f / Z;
+                float sa[C::R][9];
 #pragma unroll
-            for (int r = 0; r < C::R; ++r) {
-                const int p = lane + 32 * r;
-                float sa[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int r = 0; r < C::R; ++r)
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) sa[r][a] = 0.f;
 #pragma unroll
                 for (int i = 0; i < N; ++i) {
-                    const float sg_ = __expf(eb[r * N + i] - mx) * invZ;
-                    const float *hx = s_he + i * MEM_HE_STRIDE;
+                    float hx[9];
 #pragma unroll
-                    for (int a = 0; a < 9; ++a) sa[a] += sg_ * hx[a];
+                    for (int a = 0; a < 9; ++a) hx[a] = s_he[i * MEM_HE_STRIDE + a];
+#pragma unroll
+                    for (int r = 0; r < C::R; ++r) {
+                        const float sg_ = __expf(eb[r * N + i] - mx) * invZ;
+#pragma unroll
+                        for (int a = 0; a < 9; ++a) sa[r][a] += sg_ * hx[a];
+                    }
                 }
-                if (p < C::P) {
 #pragma unroll
-                    for (int a = 0; a < 9; ++a) S1[a * C::P + p] = sa[a];
+                for (int r = 0; r < C::R; ++r) {
+                    const int p = lane + 32 * r;
+                    if (p < C::P) {
+#pragma unroll
+                        for (int a = 0; a < 9; ++a) S1[a * C::P + p] = sa[r][a];
+                    }
                 }
             }
             __syncwarp();
             // ---- stage y: t_ab(k) = sum_j s_a(j,k) he_b(y_j), a + b <= 8
             for (int t = lane; t < C::T2; t += 32) {
                 const int ab = t / N, k = t % N;
-                int d = 0;
-                while ((d + 1) * (d + 2) / 2 <= ab) ++d;
-                const int b = ab - d * (d + 1) / 2, a = d - b;
+                const int abp = s_ab[ab], a = abp & 255, b = abp >> 8;
                 float acc = 0.f;
 #pragma unroll
                 for (int j = 0; j < N; ++j) acc += S1[a * C::P + j * N + k] * s_he[j * MEM_HE_STRIDE + b];
@@ -231,46 +367,44 @@ __global__ void __launch_bounds__(WARPS * 32) k_fused_solve(FusedArgs A) {
             if (lane >= 1 && lane < NP) sg[lane] = smu[lane] - sm[lane];
             if (lane + 32 < NP) sg[lane + 32] = smu[lane + 32] - sm[lane + 32];
             __syncwarp();
-            auto build_H = [&](float lam) {
-                for (int p = lane; p < NP1 * (NP1 + 1) / 2; p += 32) {
-                    int i = (int)((sqrtf(8.f * p + 1.f) - 1.f) * 0.5f);
-                    while (i * (i + 1) / 2 > p) --i;
-                    while ((i + 1) * (i + 2) / 2 <= p) ++i;
-                    const int j = p - i * (i + 1) / 2;
-                    float acc = 0.f;
-                    const int t1 = A.lin_off[p + 1];
-                    for (int t = A.lin_off[p]; t < t1; ++t) {
-                        const int2 tm = __ldg(&A.lin_terms[t]);
-                        acc += __int_as_float(tm.y) * smu[tm.x];
+            // Hessian entries E[phi_i phi_j] - mu_i mu_j (packed lower, i >= j)
+            // from the linearisation terms; lane l walks its own padded term
+            // sequence (uniform trip count, coalesced table reads).
+            {
+                float acc = 0.f;
+#pragma unroll 4
+                for (int t = 0; t < A.n_slots; ++t) {
+                    const int2 sl = __ldg(&A.slots[t * 32 + lane]);
+                    acc = fmaf(__int_as_float(sl.y), smu[sl.x & 255], acc);
+                    if (sl.x < 0) {
+                        const int p = (sl.x >> 8) & 1023;
+                        const int pij = s_pij[p], i = pij & 255, j = pij >> 8;
+                        H[i * LDH + j] = acc - smu[i + 1] * smu[j + 1];
+                        acc = 0.f;
                     }
-                    acc -= smu[i + 1] * smu[j + 1];
-                    if (i == j) acc += lam;
-                    H[i * LDH + j] = acc;
                 }
-                __syncwarp();
-            };
-            build_H(0.f);
-            bool ok = warp_cholesky(H, NP1, LDH, lane);
-            float lam = o.lambda0;
-            for (int t = 0; !ok && t < o.max_lambda; ++t) {
+            }
+            __syncwarp();
+            // Cholesky of H, then of H + lambda I with lambda = lambda0 * mul^t
+            // until it succeeds; the Newton direction solves H dbeta = -grad.
+            const float g_l = lane < 32 ? sg[lane + 1] : 0.f, g32 = sg[33], g33 = sg[34];
+            float x = 0.f, x32 = 0.f, x33 = 0.f;
+            bool ok = false;
+            float lam = 0.f;
+            for (int t = 0; t <= o.max_lambda; ++t) {
+                ok = reg_chol_solve34(H, lam, lane, -g_l, -g32, -g33, x, x32, x33);
+                if (ok) break;
                 st |= MEM_ST_LAMBDA;
-                build_H(lam);
-                ok = warp_cholesky(H, NP1, LDH, lane);
-                lam *= o.lambda_mul;
+                lam = (t == 0) ? o.lambda0 : lam * o.lambda_mul;
             }
             ++it;
             if (!ok) {
                 st |= MEM_ST_LAMBDA_CAP | MEM_ST_NONFINITE;
                 break;
             }
-            if (lane < NP1) srhs[lane] = -sg[lane + 1];
-            if (lane + 32 < NP1) srhs[lane + 32] = -sg[lane + 33];
-            warp_solve_lower(H, NP1, LDH, srhs, lane);
-            warp_solve_upperT(H, NP1, LDH, srhs, lane);
-            float part = (lane < NP1 ? srhs[lane] * sg[lane + 1] : 0.f) + (lane + 32 < NP1 ? srhs[lane + 32] * sg[lane + 33] : 0.f);
-            const float res = 0.5f * fabsf(warp_sum(part));
-            if (lane < NP1) sd[lane + 1] = srhs[lane];
-            if (lane + 32 < NP1) sd[lane + 33] = srhs[lane + 32];
+            const float res = 0.5f * fabsf(warp_sum(x * g_l) + x32 * g32 + x33 * g33);
+            sd[lane + 1] = x;
+            if (lane == 0) { sd[33] = x32; sd[34] = x33; }
             __syncwarp();
             if (!isfinite(res)) { st |= MEM_ST_NONFINITE; break; }
             const bool conv_res = res <= o.tol, conv_a = alpha <= o.alpha_min;
@@ -302,7 +436,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_fused_solve(FusedArgs A) {
 template <int N>
 int launch_fused(mem_ctx *ctx, const FusedArgs &a, cudaStream_t st) {
     using C = FusedCfg<N>;
-    const size_t smem = sizeof(float) * (N * MEM_HE_STRIDE + 16 + 168) + sizeof(float) * WARPS * C::WARP_FLOATS;
+    const size_t smem = sizeof(float) * (N * MEM_HE_STRIDE + 16 + 168 + 596 + 48) + sizeof(float) * WARPS * C::WARP_FLOATS;
     static int configured = 0;
     if (!configured) {
         MEM_CUDA_TRY(cudaFuncSetAttribute(k_fused_solve<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -327,7 +461,7 @@ int solve_fused(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int3
                 const mem_solve_opts &o, cudaStream_t st) {
     FusedArgs a;
     a.M = M; a.beta = beta; a.status = status; a.iters = iters; a.B = B;
-    a.he1d = ctx->d_he1d; a.logw1d = ctx->d_logw1d; a.lin_off = ctx->d_lin_off; a.lin_terms = ctx->d_lin_terms;
+    a.he1d = ctx->d_he1d; a.logw1d = ctx->d_logw1d; a.slots = ctx->d_hess_slots; a.n_slots = ctx->n_hess_slots;
     a.o = o;
     switch (ctx->n1d) {
         case 8: return launch_fused<8>(ctx, a, st);

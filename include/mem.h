@@ -185,7 +185,9 @@ typedef struct {
     double Pr;         /* Prandtl number of the ES-BGK model (2/3)          */
     double gamma;      /* heat-capacity ratio for Rankine-Hugoniot (5/3)    */
     double kn;         /* upstream Knudsen number (1)                       */
-    int32_t ic;        /* 0: step at x = 0 between the RH Maxwellians       */
+    int32_t ic;        /* 0: step at x = 0 between the RH Maxwellians;
+                          1: tanh blend of Appendix D, Eq. "Mx ini", with
+                          thickness parameter 15.7                         */
     int32_t impl;      /* Newton back-end, MEM_IMPL_*                       */
     int32_t graph;     /* 1: capture the time step in a CUDA graph          */
     float tol;         /* Algorithm 1 tolerance (1e-8)                      */
@@ -198,6 +200,17 @@ void mem_shock_params_default(mem_shock_params *p);
  * set the initial condition and prime the characteristic speeds.
  * Synchronous.  Returns MEM_EINVAL / MEM_ENOMEM / MEM_ECUDA. */
 int mem_shock_init(mem_ctx *ctx, const mem_shock_params *p, mem_shock **out);
+
+/* A packed batch of nprob independent shock problems (an ensemble): their
+ * cells are concatenated, every step advances all of them (one launch per
+ * kernel, persistent Newton kernel), each with its own dt, Knudsen and
+ * Prandtl numbers and boundary states.  impl, tol and maxI must agree across
+ * the batch.  mem_shock_step's steady metric is then the largest over the
+ * problems; mem_shock_get returns problem 0; mem_shock_get_problem any. */
+int mem_shock_init_batch(mem_ctx *ctx, const mem_shock_params *ps, int nprob, mem_shock **out);
+int mem_shock_num_problems(const mem_shock *s);
+int mem_shock_get_problem(mem_shock *s, int problem, float *rho, float *ux, float *T, float *sxx, float *qx,
+                          double *t_out, int32_t *steps_out);
 
 /* Advance nsteps time steps of Algorithm 2 on `stream`:
  *   dt = cfl dx / max speed of the previous transport;
@@ -222,6 +235,51 @@ int mem_shock_device_state(mem_shock *s, float **M, float **beta, float **g, flo
                            int32_t **status, int32_t **iters);
 
 void mem_shock_free(mem_shock *s);
+
+/* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of shock solves with device-resident state.
+ * Not part of the paper's method; a service around Algorithm 2. */
+
+typedef struct mem_server mem_server;
+
+typedef struct {
+    int32_t status;      /* MEM_OK when done, MEM_PENDING otherwise         */
+    int32_t steps;       /* time steps taken                                */
+    int32_t ncells;
+    int32_t steady;      /* 1 if the steady-state test was met              */
+    double sim_time;     /* simulated time                                  */
+    double latency_s;    /* submit -> completion, host wall clock           */
+} mem_shock_result;
+
+/* Create a server.  Admitted problems share one packed batch on the device;
+ * hbm_budget_bytes bounds the device memory of resident problems and
+ * max_cells their total cells (ghosts included).  A problem completes when
+ * max_n |rho^{k+1} - rho^k| / (rho_+ - rho_-) < steady_tol (after at least 2
+ * steps) or after max_steps steps. */
+int mem_serve_create(mem_ctx *ctx, size_t hbm_budget_bytes, int32_t max_cells, double steady_tol,
+                     int32_t max_steps, mem_server **out);
+
+/* Queue a request (host only, no device work).  The server uses the fused
+ * Newton back-end with the paper's defaults for every request.  Returns
+ * MEM_OK and *req_id, MEM_EINVAL for invalid parameters, or MEM_EBUSY when
+ * the request alone exceeds the memory or cell budget. */
+int mem_serve_submit(mem_server *sv, const mem_shock_params *p, uint64_t *req_id);
+
+/* Admit queued requests that fit, run `iters` time steps of every resident
+ * problem on `stream`, then retire problems that completed (profiles copied
+ * to the host) and admit more.  Synchronises the stream. */
+int mem_serve_progress(mem_server *sv, int iters, void *stream);
+
+/* Poll a request: MEM_OK (result filled; rho/ux/T, each ncells long, copied
+ * if not NULL), MEM_PENDING (queued or running), or MEM_ENOTFOUND. */
+int mem_serve_poll(mem_server *sv, uint64_t req_id, mem_shock_result *res, float *rho, float *ux,
+                   float *T);
+
+/* Queue length, resident problems and cells, completed requests. */
+int mem_serve_stats(mem_server *sv, int32_t *queued, int32_t *resident, int32_t *resident_cells,
+                    int32_t *completed);
+
+void mem_serve_destroy(mem_server *sv);
 
 #ifdef __cplusplus
 }

@@ -45,9 +45,9 @@ namespace mem_host {
 int ensure_scratch(mem_ctx *ctx, size_t bytes);
 int gh_rule(int n, std::vector<double> &x, std::vector<double> &w);
 int solve_plain(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters, int64_t B,
-                const mem_solve_opts &o, cudaStream_t st);
+                const mem_solve_opts &o, cudaStream_t st, const unsigned char *active = nullptr);
 int solve_fused(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters, int64_t B,
-                const mem_solve_opts &o, cudaStream_t st);
+                const mem_solve_opts &o, cudaStream_t st, const unsigned char *active = nullptr);
 int flux(mem_ctx *ctx, const float *M, const float *beta, const float *g, float *F, float *speed, int64_t B,
          cudaStream_t st);
 int flux_bufs(mem_ctx *ctx, const float *M, const float *beta, const float *g, float *F, float *speed, int64_t B,

@@ -53,6 +53,7 @@ struct FusedArgs {
     const float *logw1d;  // [N]
     const int2 *slots;    // [n_slots][32] Hessian linearisation terms per lane
     int n_slots;
+    const unsigned char *active;  // optional per-cell mask: 0 = leave the cell untouched
     mem_solve_opts o;
 };
 
@@ -234,6 +235,7 @@ __global__ void __launch_bounds__(WARPS * 32, (N <= 8 ? 4 : 2)) k_fused_solve(Fu
 
     const int64_t nwarps = (int64_t)gridDim.x * WARPS;
     for (int64_t cell = (int64_t)blockIdx.x * WARPS + warp; cell < A.B; cell += nwarps) {
+        if (A.active && !A.active[cell]) continue;
         const float *Mc = A.M + cell * NP;
         float *bc = A.beta + cell * NP;
         // ---- load and validate
@@ -458,15 +460,16 @@ int launch_fused(mem_ctx *ctx, const FusedArgs &a, cudaStream_t st) {
 namespace mem_host {
 
 int solve_fused(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters, int64_t B,
-                const mem_solve_opts &o, cudaStream_t st) {
+                const mem_solve_opts &o, cudaStream_t st, const unsigned char *active) {
     FusedArgs a;
+    a.active = active;
     a.M = M; a.beta = beta; a.status = status; a.iters = iters; a.B = B;
     a.he1d = ctx->d_he1d; a.logw1d = ctx->d_logw1d; a.slots = ctx->d_hess_slots; a.n_slots = ctx->n_hess_slots;
     a.o = o;
     switch (ctx->n1d) {
         case 8: return launch_fused<8>(ctx, a, st);
         case 12: return launch_fused<12>(ctx, a, st);
-        default: return solve_plain(ctx, M, beta, status, iters, B, o, st);
+        default: return active ? MEM_EINVAL : solve_plain(ctx, M, beta, status, iters, B, o, st);
     }
 }
 

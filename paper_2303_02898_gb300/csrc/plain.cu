@@ -64,9 +64,10 @@ struct PlainState {
 };
 
 __global__ void k_init(const float *__restrict__ M, float *__restrict__ beta, int n, PlainState S,
-                       int32_t *status, int32_t *iters) {
+                       int32_t *status, int32_t *iters, const unsigned char *active) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
+    if (active && !active[c]) return;
     const float *m = M + (size_t)c * NP;
     float *b = beta + (size_t)c * NP;
     bool bad = !(m[0] > 0.f) || !isfinite(m[0]);
@@ -449,7 +450,7 @@ void sgemm(const float *A, const float *Bm, float *C, int M, int N, int K, cudaS
 namespace mem_host {
 
 int solve_plain(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters, int64_t B,
-                const mem_solve_opts &o, cudaStream_t st) {
+                const mem_solve_opts &o, cudaStream_t st, const unsigned char *active) {
     std::lock_guard<std::mutex> lock(ctx->mu);
     const int Q = ctx->Q;
     const size_t CH = (size_t)std::min<int64_t>(B, CHUNK);
@@ -477,7 +478,7 @@ int solve_plain(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int3
         float *bc = beta + c0 * NP;
         int32_t *stc = status ? status + c0 : nullptr, *itc = iters ? iters + c0 : nullptr;
         MEM_CUDA_TRY(cudaMemsetAsync(S.cnt, 0, 2 * sizeof(int), st));
-        k_init<<<(n + 255) / 256, 256, 0, st>>>(Mc, bc, n, S, stc, itc);
+        k_init<<<(n + 255) / 256, 256, 0, st>>>(Mc, bc, n, S, stc, itc, active ? active + c0 : nullptr);
         int nact = 0;
         MEM_CUDA_TRY(cudaMemcpyAsync(&nact, S.cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
         MEM_CUDA_TRY(cudaStreamSynchronize(st));

@@ -1,16 +1,22 @@
-// shock.cu -- one time step of Algorithm 2 on a 1D normal shock (Appendix D):
-//   dt = cfl dx / max speed            (k_dt, device-side, previous transport)
-//   Collision(dt/2)                    (k_collide, ES-BGK, Eq. "source update")
-//   Transport(dt): Newton (mem_solve), flux and speed (mem_flux),
-//                  neighbour gauge transform + local Lax-Friedrichs + finite
-//                  volume (k_stencil, Eqs. "The lax F", "The lax F convert",
-//                  "The ME equation fvm 2")
-//   Collision(dt/2)                    (k_collide)
-//   Hermite gauge, transform of M and beta (k_regauge).
-// Cells 0 and N+1 are Dirichlet ghost cells holding the Rankine-Hugoniot
-// Maxwellians in their own Hermite gauge (beta = 0); they are never updated.
-// All per-step scalars live in device memory, so the whole step can be
-// captured in a CUDA graph when the fused Newton back-end is used.
+// shock.cu -- time steps of Algorithm 2 on 1D normal shocks (Appendix D),
+// for one problem or a packed batch of independent problems.
+//
+// One step, every problem p of the batch at once:
+//   dt_p = cfl dx_p / max speed of p's previous transport       (k_dt)
+//   Collision(dt_p/2), ES-BGK, Eq. "source update"               (k_collide)
+//   Transport(dt_p): Newton (fused or plain back-end), flux and speed,
+//     neighbour gauge transform + local Lax-Friedrichs + finite volume
+//     (Eqs. "The lax F", "The lax F convert", "The ME equation fvm 2")
+//                                                                (k_stencil)
+//   Collision(dt_p/2)                                            (k_collide)
+//   Hermite gauge and transform of M and beta                    (k_regauge)
+// Problem p owns the contiguous cells [off_p, off_p + N_p + 2): a Dirichlet
+// ghost cell at each end holding the Rankine-Hugoniot Maxwellian in its own
+// Hermite gauge (beta = 0, never updated) and N_p interior cells.  Every
+// kernel works per cell and every reduction per problem, so a problem's
+// result does not depend on which other problems share the batch.  All
+// per-step scalars live in device memory, so a step can be captured in a
+// CUDA graph when the fused Newton back-end is used.
 #include <math.h>
 #include <string.h>
 
@@ -18,29 +24,9 @@
 
 #include "common.cuh"
 #include "ctx.h"
+#include "shock.h"
 
 using namespace mem;
-
-struct ShockScalars {
-    float dt;
-    unsigned int steady_bits;  // max |d rho| as float bits (non-negative)
-    double t;
-    int steps;
-};
-
-struct mem_shock {
-    mem_ctx *ctx = nullptr;
-    mem_shock_params p;
-    int N = 0;
-    double dx = 0.0, n_up = 1, T_up = 1, v_up = 0, n_dn = 1, T_dn = 1, v_dn = 0;
-    float relax = 0.f;  // tau = relax / n
-    float *M = nullptr, *beta = nullptr, *g = nullptr, *speed = nullptr, *F = nullptr, *Mn = nullptr;
-    float *rho0 = nullptr, *sigma = nullptr, *mom = nullptr;
-    int32_t *status = nullptr, *iters = nullptr;
-    ShockScalars *sc = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    cudaGraph_t graph = nullptr;
-};
 
 namespace {
 
@@ -48,28 +34,29 @@ namespace {
 // E[He_a(x) He_b(y) He_c(z)] equals the moment of a formal Gaussian with
 // mean mu and covariance K = S - I, built by the recursion
 //   m_{alpha + e_i} = mu_i m_alpha + sum_j alpha_j K_ij m_{alpha - e_j}.
-__device__ __forceinline__ void gaussian_hermite(const float mu[3], const float K[3][3], float n, float *out) {
-    float m[NP];
-    m[0] = 1.f;
+template <typename R>
+__host__ __device__ __forceinline__ void gaussian_hermite(const R mu[3], const R K[3][3], R n, R *out) {
+    R m[NP];
+    m[0] = 1;
 #pragma unroll
     for (int k = 1; k < NP; ++k) {
         const int al[3] = {exp_a(k), exp_b(k), exp_c(k)};
         const int i = al[0] > 0 ? 0 : (al[1] > 0 ? 1 : 2);
         int be[3] = {al[0], al[1], al[2]};
         be[i] -= 1;
-        float v = mu[i] * m[idx3(be[0], be[1], be[2])];
+        R v = mu[i] * m[idx3(be[0], be[1], be[2])];
 #pragma unroll
         for (int j = 0; j < 3; ++j)
             if (be[j] > 0) {
                 int g2[3] = {be[0], be[1], be[2]};
                 g2[j] -= 1;
-                v += (float)be[j] * K[i][j] * m[idx3(g2[0], g2[1], g2[2])];
+                v += (R)be[j] * K[i][j] * m[idx3(g2[0], g2[1], g2[2])];
             }
         m[k] = v;
     }
-    const float fact[5] = {1.f, 1.f, 2.f, 6.f, 24.f};
+    const R fact[5] = {1, 1, 2, 6, 24};
 #pragma unroll
-    for (int k = 0; k < NP; ++k) out[k] = n * m[k] * rsqrtf(fact[exp_a(k)] * fact[exp_b(k)] * fact[exp_c(k)]);
+    for (int k = 0; k < NP; ++k) out[k] = n * m[k] / sqrt(fact[exp_a(k)] * fact[exp_b(k)] * fact[exp_c(k)]);
 }
 
 // ES-BGK target (Appendix A): Gaussian with the cell's n and mean velocity and
@@ -87,12 +74,12 @@ __device__ __forceinline__ void esbgk_target(const float *M, const float *g, flo
     E2[0][1] = E2[1][0] = M[idx3(1, 1, 0)] / n;
     E2[0][2] = E2[2][0] = M[idx3(1, 0, 1)] / n;
     E2[1][2] = E2[2][1] = M[idx3(0, 1, 1)] / n;
-    float P[3][3], T = 0.f;
+    float P[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) P[a][b] = g[3 + a] * g[3 + b] * (E2[a][b] - mb[a] * mb[b]);
-    T = (P[0][0] + P[1][1] + P[2][2]) / 3.f;
+    const float T = (P[0][0] + P[1][1] + P[2][2]) / 3.f;
     float K[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -101,31 +88,38 @@ __device__ __forceinline__ void esbgk_target(const float *M, const float *g, flo
             const float sig = (a == b ? T / Pr : 0.f) + (1.f - 1.f / Pr) * P[a][b];
             K[a][b] = sig / (g[3 + a] * g[3 + b]) - (a == b ? 1.f : 0.f);
         }
-    gaussian_hermite(mb, K, n, Mt);
+    gaussian_hermite<float>(mb, K, n, Mt);
 }
 
-__global__ void k_collide(float *__restrict__ M, const float *__restrict__ g, int N, const ShockScalars *sc, float frac,
-                          float Pr, float relax, float *rho0) {
-    const int c = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (c > N) return;
+__global__ void k_collide(float *__restrict__ M, const float *__restrict__ g, const int *__restrict__ pid,
+                          const unsigned char *__restrict__ interior, const ShockProb *__restrict__ prm,
+                          const ShockScalars *__restrict__ sc, int NT, float frac, float *rho0) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= NT || !interior[c]) return;
+    const int p = pid[c];
     float m[NP], gg[6], mt[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) m[k] = M[(size_t)c * NP + k];
 #pragma unroll
     for (int k = 0; k < 6; ++k) gg[k] = g[(size_t)c * 6 + k];
     if (rho0) rho0[c] = m[0];
-    esbgk_target(m, gg, Pr, mt);
-    const float r = frac * sc->dt * m[0] / relax;  // dt' / tau
+    esbgk_target(m, gg, prm[p].Pr, mt);
+    const float r = frac * sc[p].dt * m[0] / prm[p].relax;  // dt' / tau, tau = relax / n
 #pragma unroll
     for (int k = 0; k < NP; ++k) M[(size_t)c * NP + k] = (1.f - r) * m[k] + r * mt[k];
 }
 
-// Local Lax-Friedrichs finite-volume update in the cell's own gauge.
+// Local Lax-Friedrichs finite-volume update in the cell's own gauge:
+// M_c += dt/dx (F^LF_{c-1/2} - F^LF_{c+1/2}), neighbours moved to g_c.
 __global__ void __launch_bounds__(128) k_stencil(const float *__restrict__ M, const float *__restrict__ F,
                                                  const float *__restrict__ g, const float *__restrict__ speed,
-                                                 float *__restrict__ Mn, int N, float dx, const ShockScalars *sc) {
-    const int c = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (c > N) return;
+                                                 float *__restrict__ Mn, const int *__restrict__ pid,
+                                                 const unsigned char *__restrict__ interior,
+                                                 const ShockProb *__restrict__ prm,
+                                                 const ShockScalars *__restrict__ sc, int NT) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= NT || !interior[c]) return;
+    const int p = pid[c];
     float g0[6], gl[6], gr[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
@@ -134,10 +128,10 @@ __global__ void __launch_bounds__(128) k_stencil(const float *__restrict__ M, co
         gr[k] = g[(size_t)(c + 1) * 6 + k];
     }
     const float s0 = speed[c], ll = fmaxf(speed[c - 1], s0), lr = fmaxf(s0, speed[c + 1]);
-    const float r = sc->dt / dx;
+    const float r = sc[p].dt / prm[p].dx;
     float acc[NP], x[NP], y[NP];
     AxisMap T[3];
-    // own cell: F0 - F0 cancels; diffusion terms -0.5 (ll + lr) M0
+    // F^LF_{c-1/2} - F^LF_{c+1/2} = 0.5(Fl + F0) + 0.5 ll (Ml - M0) - 0.5(F0 + Fr) - 0.5 lr (M0 - Mr)
 #pragma unroll
     for (int k = 0; k < NP; ++k) acc[k] = -0.5f * (ll + lr) * M[(size_t)c * NP + k];
     gauge_maps(g0, gl, T);
@@ -162,15 +156,15 @@ __global__ void __launch_bounds__(128) k_stencil(const float *__restrict__ M, co
     apply_T(T, x, y);
 #pragma unroll
     for (int k = 0; k < NP; ++k) acc[k] -= 0.5f * y[k];
-    // F^LF_{c-1/2} - F^LF_{c+1/2} = 0.5(Fl + F0) + 0.5 ll (Ml - M0) - 0.5(F0 + Fr) - 0.5 lr (M0 - Mr)
 #pragma unroll
     for (int k = 0; k < NP; ++k) Mn[(size_t)c * NP + k] = M[(size_t)c * NP + k] + r * acc[k];
 }
 
 __global__ void k_regauge(const float *__restrict__ Mn, float *__restrict__ M, float *__restrict__ beta,
-                          float *__restrict__ g, const float *__restrict__ rho0, int N, ShockScalars *sc) {
-    const int c = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (c > N) return;
+                          float *__restrict__ g, const float *__restrict__ rho0, const int *__restrict__ pid,
+                          const unsigned char *__restrict__ interior, ShockScalars *sc, int NT) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= NT || !interior[c]) return;
     float m[NP], gg[6], gh[6], y[NP], b[NP], bo[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) { m[k] = Mn[(size_t)c * NP + k]; b[k] = beta[(size_t)c * NP + k]; }
@@ -181,21 +175,21 @@ __global__ void k_regauge(const float *__restrict__ Mn, float *__restrict__ M, f
     gauge_maps(gh, gg, T);
     apply_T(T, m, y);
     transform_beta(gh, gg, b, bo);
+    bo[0] = y[0];
 #pragma unroll
     for (int k = 0; k < NP; ++k) { M[(size_t)c * NP + k] = y[k]; beta[(size_t)c * NP + k] = bo[k]; }
-    bo[0] = y[0];
-    beta[(size_t)c * NP] = y[0];
 #pragma unroll
     for (int k = 0; k < 6; ++k) g[(size_t)c * 6 + k] = gh[k];
-    const float d = fabsf(y[0] - rho0[c]);
-    atomicMax(&sc->steady_bits, __float_as_uint(d));
+    atomicMax(&sc[pid[c]].steady_bits, __float_as_uint(fabsf(y[0] - rho0[c])));
 }
 
-// dt = cfl dx / max speed over all cells (incl. ghosts); one block.
-__global__ void k_dt(const float *__restrict__ speed, int NT, float cfl_dx, ShockScalars *sc) {
+// dt_p = cfl dx_p / max speed over problem p's cells (ghosts included); one
+// block per problem.
+__global__ void k_dt(const float *__restrict__ speed, const ShockProb *__restrict__ prm, ShockScalars *sc) {
     __shared__ float red[32];
+    const ShockProb pr = prm[blockIdx.x];
     float m = 0.f;
-    for (int c = threadIdx.x; c < NT; c += blockDim.x) m = fmaxf(m, speed[c]);
+    for (int c = threadIdx.x; c < pr.n + 2; c += blockDim.x) m = fmaxf(m, speed[pr.off + c]);
     m = warp_max(m);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
     __syncthreads();
@@ -203,39 +197,272 @@ __global__ void k_dt(const float *__restrict__ speed, int NT, float cfl_dx, Shoc
         float r = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : 0.f;
         r = warp_max(r);
         if (threadIdx.x == 0) {
-            const float dt = cfl_dx / r;
-            sc->dt = dt;
-            sc->t += (double)dt;
-            sc->steps += 1;
-            sc->steady_bits = 0u;
+            ShockScalars &s = sc[blockIdx.x];
+            const float dt = pr.cfl_dx / r;
+            s.dt = dt;
+            s.t += (double)dt;
+            s.steps += 1;
+            s.steady_bits = 0u;
         }
     }
 }
 
-int enqueue_step(mem_shock *s, cudaStream_t st) {
-    const int N = s->N, NT = N + 2;
-    const unsigned nb = (unsigned)((N + 127) / 128);
-    k_dt<<<1, 1024, 0, st>>>(s->speed, NT, (float)(s->p.cfl * s->dx), s->sc);
-    k_collide<<<nb, 128, 0, st>>>(s->M, s->g, N, s->sc, 0.5f, (float)s->p.Pr, s->relax, s->rho0);
+void rh_states(const mem_shock_params &p, double &n_dn, double &T_dn, double &v_up, double &v_dn) {
+    const double g = p.gamma, M2 = p.mach * p.mach;
+    const double r = (g + 1.0) * M2 / ((g - 1.0) * M2 + 2.0);
+    const double t = (2.0 * g * M2 - (g - 1.0)) * ((g - 1.0) * M2 + 2.0) / ((g + 1.0) * (g + 1.0) * M2);
+    v_up = sqrt(g) * p.mach;
+    n_dn = r;
+    T_dn = t;
+    v_dn = v_up / r;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+namespace mem_host {
+
+bool shock_params_valid(const mem_shock_params &p) {
+    return p.ncells >= 1 && p.xr > p.xl && p.mach >= 1.0 && p.cfl > 0 && p.Pr > 0.5 && p.gamma > 1.0 && p.kn > 0 &&
+           (p.ic == 0 || p.ic == 1) && p.maxI >= 0 && (p.impl == MEM_IMPL_PLAIN || p.impl == MEM_IMPL_FUSED);
+}
+
+size_t batch_bytes_per_cell(const mem_ctx *ctx) {
+    return sizeof(float) * (5 * NP + 6 + 3 + (size_t)ctx->Q + MEM_NCOL_FLUX) + sizeof(int32_t) * 3 + 1;
+}
+
+void batch_free(ShockBatch *b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    void *ptrs[] = {b->M, b->beta, b->g, b->speed, b->F, b->Mn, b->rho0, b->sigma, b->mom, b->status, b->iters,
+                    b->pid, b->interior, b->prm, b->sc};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete b;
+}
+
+// Initial state of one problem into host arrays at cell offset `off`.
+// ic 0: a step at x = 0 between the Rankine-Hugoniot Maxwellians, each cell in
+// its own Hermite gauge (M = n e_0, beta = 0).  ic 1: Appendix D, Eq. "Mx
+// ini": the two Maxwellians' moments blended with a tanh profile of
+// thickness parameter `thickness`; the blend is a two-Gaussian mixture whose
+// moments are written in its own (axisymmetric) Hermite gauge.
+static void set_ic(const mem_shock_params &p, const ShockProb &pr, double thickness, float *hM, float *hb, float *hg) {
+    double n_dn, T_dn, v_up, v_dn;
+    rh_states(p, n_dn, T_dn, v_up, v_dn);
+    const double n_up = 1.0, T_up = 1.0;
+    const int NT = pr.n + 2;
+    for (int c = 0; c < NT; ++c) {
+        const double x = p.xl + (c - 0.5) * pr.dx;
+        float *M = hM + (size_t)(pr.off + c) * NP, *b = hb + (size_t)(pr.off + c) * NP, *g = hg + (size_t)(pr.off + c) * 6;
+        for (int k = 0; k < NP; ++k) { M[k] = 0.f; b[k] = 0.f; }
+        const bool ghost = c == 0 || c == NT - 1;
+        if (p.ic == 0 || ghost) {
+            const bool up = x < 0.0;
+            const double n = up ? n_up : n_dn, T = up ? T_up : T_dn, v = up ? v_up : v_dn;
+            M[0] = (float)n;
+            b[0] = (float)n;
+            g[0] = (float)v;
+            g[1] = g[2] = 0.f;
+            g[3] = g[4] = g[5] = (float)sqrt(T);
+            continue;
+        }
+        const double h = 0.5 * thickness;
+        const double w = (tanh(x / h) - tanh(p.xl / h)) / (tanh(p.xr / h) - tanh(p.xl / h));
+        const double a0 = (1.0 - w) * n_up, a1 = w * n_dn, n = a0 + a1;
+        const double v = (a0 * v_up + a1 * v_dn) / n;
+        const double ex2 = (a0 * (T_up + v_up * v_up) + a1 * (T_dn + v_dn * v_dn)) / n;
+        const double sx = sqrt(ex2 - v * v), sr = sqrt((a0 * T_up + a1 * T_dn) / n);
+        const double gg[6] = {v, 0.0, 0.0, sx, sr, sr};
+        double acc[NP] = {0.0};
+        const double comp[2][3] = {{a0, v_up, T_up}, {a1, v_dn, T_dn}};
+        for (int q = 0; q < 2; ++q) {
+            const double mu[3] = {(comp[q][1] - gg[0]) / gg[3], 0.0, 0.0};
+            double K[3][3] = {{comp[q][2] / (sx * sx) - 1.0, 0, 0}, {0, comp[q][2] / (sr * sr) - 1.0, 0},
+                              {0, 0, comp[q][2] / (sr * sr) - 1.0}};
+            double mq[NP];
+            gaussian_hermite<double>(mu, K, comp[q][0], mq);
+            for (int k = 0; k < NP; ++k) acc[k] += mq[k];
+        }
+        for (int k = 0; k < NP; ++k) M[k] = (float)acc[k];
+        b[0] = (float)n;
+        for (int k = 0; k < 6; ++k) g[k] = (float)gg[k];
+    }
+}
+
+int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **out) {
+    *out = nullptr;
+    if (P < 1) return MEM_EINVAL;
+    for (int i = 0; i < P; ++i)
+        if (!shock_params_valid(ps[i])) return MEM_EINVAL;
+    ShockBatch *b = new ShockBatch();
+    b->ctx = ctx;
+    b->P = P;
+    b->params.assign(ps, ps + P);
+    int off = 0;
+    for (int i = 0; i < P; ++i) {
+        ShockProb pr;
+        double n_dn, T_dn, v_up, v_dn;
+        rh_states(ps[i], n_dn, T_dn, v_up, v_dn);
+        pr.off = off;
+        pr.n = ps[i].ncells;
+        pr.dx = (float)((ps[i].xr - ps[i].xl) / ps[i].ncells);
+        pr.cfl_dx = (float)(ps[i].cfl * (ps[i].xr - ps[i].xl) / ps[i].ncells);
+        pr.Pr = (float)ps[i].Pr;
+        // Maxwell molecules (Appendix A) with upstream Knudsen number kn:
+        // mu = kn sqrt(2/pi) T, tau = mu / (Pr n T) = relax / n.
+        pr.relax = (float)(ps[i].kn * sqrt(2.0 / 3.14159265358979323846) / ps[i].Pr);
+        pr.drho = (float)(n_dn - 1.0);
+        b->hprm.push_back(pr);
+        off += pr.n + 2;
+    }
+    b->NT = off;
+    const size_t NT = (size_t)off;
+    const int Q = ctx->Q;
+    auto alloc = [&](void **ptr, size_t bytes) { return cudaMalloc(ptr, bytes) == cudaSuccess; };
+    bool ok = alloc((void **)&b->M, sizeof(float) * NT * NP) && alloc((void **)&b->beta, sizeof(float) * NT * NP) &&
+              alloc((void **)&b->g, sizeof(float) * NT * 6) && alloc((void **)&b->speed, sizeof(float) * NT) &&
+              alloc((void **)&b->F, sizeof(float) * NT * NP) && alloc((void **)&b->Mn, sizeof(float) * NT * NP) &&
+              alloc((void **)&b->rho0, sizeof(float) * NT) && alloc((void **)&b->sigma, sizeof(float) * NT * (size_t)Q) &&
+              alloc((void **)&b->mom, sizeof(float) * NT * (size_t)MEM_NCOL_FLUX) &&
+              alloc((void **)&b->status, sizeof(int32_t) * NT) && alloc((void **)&b->iters, sizeof(int32_t) * NT) &&
+              alloc((void **)&b->pid, sizeof(int) * NT) && alloc((void **)&b->interior, NT) &&
+              alloc((void **)&b->prm, sizeof(ShockProb) * P) && alloc((void **)&b->sc, sizeof(ShockScalars) * P);
+    if (!ok) { cudaGetLastError(); batch_free(b); return MEM_ENOMEM; }
+    std::vector<float> hM(NT * NP), hb(NT * NP), hg(NT * 6);
+    std::vector<int> hpid(NT);
+    std::vector<unsigned char> hint(NT);
+    for (int i = 0; i < P; ++i) {
+        const ShockProb &pr = b->hprm[i];
+        set_ic(ps[i], pr, 15.7, hM.data(), hb.data(), hg.data());
+        for (int c = 0; c < pr.n + 2; ++c) {
+            hpid[pr.off + c] = i;
+            hint[pr.off + c] = (c > 0 && c < pr.n + 1) ? 1 : 0;
+        }
+    }
+    std::vector<ShockScalars> hsc(P);
+    memset(hsc.data(), 0, sizeof(ShockScalars) * P);
+    if (cudaMemcpy(b->M, hM.data(), sizeof(float) * hM.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->beta, hb.data(), sizeof(float) * hb.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->g, hg.data(), sizeof(float) * hg.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->pid, hpid.data(), sizeof(int) * NT, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->interior, hint.data(), NT, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->prm, b->hprm.data(), sizeof(ShockProb) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->sc, hsc.data(), sizeof(ShockScalars) * P, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->status, 0, sizeof(int32_t) * NT) != cudaSuccess ||
+        cudaMemset(b->iters, 0, sizeof(int32_t) * NT) != cudaSuccess) {
+        batch_free(b);
+        return MEM_ECUDA;
+    }
+    // Natural parameters of the initial state (the tanh blend is not a
+    // Maxwellian), then the characteristic speeds that set the first dt.
+    int rc = MEM_OK;
+    bool any_tanh = false;
+    for (int i = 0; i < P; ++i) any_tanh |= ps[i].ic == 1;
+    if (any_tanh) {
+        mem_solve_opts o;
+        mem_solve_opts_default(&o);
+        o.tol = ps[0].tol;
+        o.maxI = ps[0].maxI;
+        rc = solve_fused(ctx, b->M, b->beta, b->status, b->iters, (int64_t)NT, o, 0, b->interior);
+    }
+    if (!rc) rc = flux_bufs(ctx, b->M, b->beta, b->g, b->F, b->speed, (int64_t)NT, b->sigma, b->mom, 0);
+    if (rc || cudaDeviceSynchronize() != cudaSuccess) { batch_free(b); return rc ? rc : MEM_ECUDA; }
+    *out = b;
+    return MEM_OK;
+}
+
+int batch_enqueue_step(ShockBatch *b, cudaStream_t st) {
+    const int NT = b->NT;
+    const unsigned nb = (unsigned)((NT + 127) / 128);
+    k_dt<<<b->P, 256, 0, st>>>(b->speed, b->prm, b->sc);
+    k_collide<<<nb, 128, 0, st>>>(b->M, b->g, b->pid, b->interior, b->prm, b->sc, NT, 0.5f, b->rho0);
+    const mem_shock_params &p0 = b->params[0];
     mem_solve_opts o;
     mem_solve_opts_default(&o);
-    o.impl = s->p.impl;
-    o.tol = s->p.tol;
-    o.maxI = s->p.maxI;
+    o.impl = p0.impl;
+    o.tol = p0.tol;
+    o.maxI = p0.maxI;
     int rc = (o.impl == MEM_IMPL_PLAIN)
-                 ? mem_host::solve_plain(s->ctx, s->M + NP, s->beta + NP, s->status + 1, s->iters + 1, N, o, st)
-                 : mem_host::solve_fused(s->ctx, s->M + NP, s->beta + NP, s->status + 1, s->iters + 1, N, o, st);
+                 ? solve_plain(b->ctx, b->M, b->beta, b->status, b->iters, NT, o, st, b->interior)
+                 : solve_fused(b->ctx, b->M, b->beta, b->status, b->iters, NT, o, st, b->interior);
     if (rc) return rc;
-    rc = mem_host::flux_bufs(s->ctx, s->M, s->beta, s->g, s->F, s->speed, NT, s->sigma, s->mom, st);
+    rc = flux_bufs(b->ctx, b->M, b->beta, b->g, b->F, b->speed, NT, b->sigma, b->mom, st);
     if (rc) return rc;
-    k_stencil<<<nb, 128, 0, st>>>(s->M, s->F, s->g, s->speed, s->Mn, N, (float)s->dx, s->sc);
-    k_collide<<<nb, 128, 0, st>>>(s->Mn, s->g, N, s->sc, 0.5f, (float)s->p.Pr, s->relax, nullptr);
-    k_regauge<<<nb, 128, 0, st>>>(s->Mn, s->M, s->beta, s->g, s->rho0, N, s->sc);
+    k_stencil<<<nb, 128, 0, st>>>(b->M, b->F, b->g, b->speed, b->Mn, b->pid, b->interior, b->prm, b->sc, NT);
+    k_collide<<<nb, 128, 0, st>>>(b->Mn, b->g, b->pid, b->interior, b->prm, b->sc, NT, 0.5f, nullptr);
+    k_regauge<<<nb, 128, 0, st>>>(b->Mn, b->M, b->beta, b->g, b->rho0, b->pid, b->interior, b->sc, NT);
     MEM_CUDA_TRY(cudaGetLastError());
     return MEM_OK;
 }
 
-}  // namespace
+// Host profiles of problem i (Appendix A definitions, m = k_B = 1).
+int batch_profiles(ShockBatch *b, int i, float *M_host, float *g_host, float *beta_host, float *rho, float *ux,
+                   float *T, float *sxx, float *qx, double *t_out, int *steps_out) {
+    if (i < 0 || i >= b->P) return MEM_EINVAL;
+    const ShockProb &pr = b->hprm[i];
+    const int N = pr.n, NT = N + 2;
+    std::vector<float> hM((size_t)NT * NP), hg((size_t)NT * 6);
+    MEM_CUDA_TRY(cudaDeviceSynchronize());
+    MEM_CUDA_TRY(cudaMemcpy(hM.data(), b->M + (size_t)pr.off * NP, sizeof(float) * hM.size(), cudaMemcpyDeviceToHost));
+    MEM_CUDA_TRY(cudaMemcpy(hg.data(), b->g + (size_t)pr.off * 6, sizeof(float) * hg.size(), cudaMemcpyDeviceToHost));
+    if (M_host) memcpy(M_host, hM.data(), sizeof(float) * hM.size());
+    if (g_host) memcpy(g_host, hg.data(), sizeof(float) * hg.size());
+    if (beta_host)
+        MEM_CUDA_TRY(cudaMemcpy(beta_host, b->beta + (size_t)pr.off * NP, sizeof(float) * NT * NP, cudaMemcpyDeviceToHost));
+    if (t_out || steps_out) {
+        ShockScalars h;
+        MEM_CUDA_TRY(cudaMemcpy(&h, b->sc + i, sizeof(h), cudaMemcpyDeviceToHost));
+        if (t_out) *t_out = h.t;
+        if (steps_out) *steps_out = h.steps;
+    }
+    for (int c = 0; c < N; ++c) {
+        const float *m = &hM[(size_t)(c + 1) * NP];
+        const float *gg = &hg[(size_t)(c + 1) * 6];
+        const double n = m[0];
+        double mb[3], E2[3];
+        const int i1[3] = {idx3(1, 0, 0), idx3(0, 1, 0), idx3(0, 0, 1)};
+        const int i2[3] = {idx3(2, 0, 0), idx3(0, 2, 0), idx3(0, 0, 2)};
+        for (int a = 0; a < 3; ++a) { mb[a] = m[i1[a]] / n; E2[a] = sqrt(2.0) * m[i2[a]] / n + 1.0; }
+        double var[3];
+        for (int a = 0; a < 3; ++a) var[a] = gg[3 + a] * gg[3 + a] * (E2[a] - mb[a] * mb[a]);
+        const double Tc = (var[0] + var[1] + var[2]) / 3.0;
+        if (rho) rho[c] = (float)n;
+        if (ux) ux[c] = (float)(gg[0] + gg[3] * mb[0]);
+        if (T) T[c] = (float)Tc;
+        if (sxx) sxx[c] = (float)(n * (var[0] - Tc));
+        if (qx) {
+            // q_x = n/2 sum_b E[c_x c_b^2], c = u - v, from raw moments of ubar.
+            const double X = mb[0], X2 = E2[0], X3 = sqrt(6.0) * m[idx3(3, 0, 0)] / n + 3.0 * X;
+            double q = gg[3] * gg[3] * gg[3] * (X3 - 3.0 * X * X2 + 2.0 * X * X * X);
+            const int iy[2] = {idx3(1, 1, 0), idx3(1, 0, 1)}, iy2[2] = {idx3(1, 2, 0), idx3(1, 0, 2)};
+            for (int bb = 1; bb < 3; ++bb) {
+                const double Y = mb[bb], Y2 = E2[bb], XY = m[iy[bb - 1]] / n;
+                const double XY2 = sqrt(2.0) * m[iy2[bb - 1]] / n + X;
+                q += gg[3] * gg[3 + bb] * gg[3 + bb] * (XY2 - 2.0 * Y * XY - X * Y2 + 2.0 * X * Y * Y);
+            }
+            qx[c] = (float)(0.5 * n * q);
+        }
+    }
+    return MEM_OK;
+}
+
+int batch_read_scalars(ShockBatch *b, std::vector<ShockScalars> &out, cudaStream_t st) {
+    out.resize(b->P);
+    MEM_CUDA_TRY(cudaMemcpyAsync(out.data(), b->sc, sizeof(ShockScalars) * b->P, cudaMemcpyDeviceToHost, st));
+    MEM_CUDA_TRY(cudaStreamSynchronize(st));
+    return MEM_OK;
+}
+
+}  // namespace mem_host
+
+// ---------------------------------------------------------------------------
+// C ABI: one problem (mem_shock_init) or a packed batch (mem_shock_init_batch).
+struct mem_shock {
+    mem_host::ShockBatch *b = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+};
 
 extern "C" {
 
@@ -260,115 +487,77 @@ void mem_shock_free(mem_shock *s) {
     cudaDeviceSynchronize();
     if (s->gexec) cudaGraphExecDestroy(s->gexec);
     if (s->graph) cudaGraphDestroy(s->graph);
-    void *ptrs[] = {s->M, s->beta, s->g, s->speed, s->F, s->Mn, s->rho0, s->sigma, s->mom, s->status, s->iters, s->sc};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
+    mem_host::batch_free(s->b);
     delete s;
 }
 
-int mem_shock_init(mem_ctx *ctx, const mem_shock_params *p, mem_shock **out) {
-    if (!ctx || !p || !out || p->ncells < 1 || !(p->xr > p->xl) || !(p->mach >= 1.0) || !(p->cfl > 0) ||
-        !(p->Pr > 0.5) || !(p->gamma > 1.0) || !(p->kn > 0) || p->ic != 0)
-        return MEM_EINVAL;
+int mem_shock_init_batch(mem_ctx *ctx, const mem_shock_params *ps, int nprob, mem_shock **out) {
+    if (!ctx || !ps || !out || nprob < 1) return MEM_EINVAL;
+    for (int i = 1; i < nprob; ++i)
+        if (ps[i].impl != ps[0].impl || ps[i].tol != ps[0].tol || ps[i].maxI != ps[0].maxI) return MEM_EINVAL;
     *out = nullptr;
+    mem_host::ShockBatch *b = nullptr;
+    int rc = mem_host::batch_create(ctx, ps, nprob, &b);
+    if (rc) return rc;
     mem_shock *s = new mem_shock();
-    s->ctx = ctx;
-    s->p = *p;
-    const int N = p->ncells, NT = N + 2;
-    s->N = N;
-    s->dx = (p->xr - p->xl) / N;
-    // Rankine-Hugoniot states (Appendix D), m = k_B = 1, n_- = T_- = 1.
-    const double g = p->gamma, M2 = p->mach * p->mach;
-    const double r = (g + 1.0) * M2 / ((g - 1.0) * M2 + 2.0);
-    const double t = (2.0 * g * M2 - (g - 1.0)) * ((g - 1.0) * M2 + 2.0) / ((g + 1.0) * (g + 1.0) * M2);
-    s->v_up = sqrt(g) * p->mach;
-    s->n_dn = r;
-    s->T_dn = t;
-    s->v_dn = s->v_up / r;
-    // Maxwell molecules, Kn = 1: mu = kn sqrt(2/pi) T and tau = mu / (Pr n T).
-    s->relax = (float)(p->kn * sqrt(2.0 / 3.14159265358979323846) / p->Pr);
-    auto alloc = [&](void **ptr, size_t bytes) { return cudaMalloc(ptr, bytes) == cudaSuccess; };
-    const int Q = ctx->Q;
-    bool ok = alloc((void **)&s->M, sizeof(float) * NT * NP) && alloc((void **)&s->beta, sizeof(float) * NT * NP) &&
-              alloc((void **)&s->g, sizeof(float) * NT * 6) && alloc((void **)&s->speed, sizeof(float) * NT) &&
-              alloc((void **)&s->F, sizeof(float) * NT * NP) && alloc((void **)&s->Mn, sizeof(float) * NT * NP) &&
-              alloc((void **)&s->rho0, sizeof(float) * NT) && alloc((void **)&s->sigma, sizeof(float) * NT * (size_t)Q) &&
-              alloc((void **)&s->mom, sizeof(float) * NT * (size_t)MEM_NCOL_FLUX) &&
-              alloc((void **)&s->status, sizeof(int32_t) * NT) && alloc((void **)&s->iters, sizeof(int32_t) * NT) &&
-              alloc((void **)&s->sc, sizeof(ShockScalars));
-    if (!ok) { cudaGetLastError(); mem_shock_free(s); return MEM_ENOMEM; }
-    // Initial condition: a step at x = 0 between the RH Maxwellians, each cell
-    // in its own Hermite gauge (M = n e_0, beta = 0).
-    std::vector<float> hM((size_t)NT * NP, 0.f), hb((size_t)NT * NP, 0.f), hg((size_t)NT * 6, 0.f);
-    for (int c = 0; c < NT; ++c) {
-        const double x = p->xl + (c - 0.5) * s->dx;
-        const bool up = x < 0.0;
-        const double n = up ? s->n_up : s->n_dn, T = up ? s->T_up : s->T_dn, v = up ? s->v_up : s->v_dn;
-        hM[(size_t)c * NP] = (float)n;
-        hb[(size_t)c * NP] = (float)n;
-        hg[(size_t)c * 6 + 0] = (float)v;
-        hg[(size_t)c * 6 + 3] = hg[(size_t)c * 6 + 4] = hg[(size_t)c * 6 + 5] = (float)sqrt(T);
-    }
-    ShockScalars z;
-    memset(&z, 0, sizeof(z));
-    if (cudaMemcpy(s->M, hM.data(), sizeof(float) * hM.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(s->beta, hb.data(), sizeof(float) * hb.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(s->g, hg.data(), sizeof(float) * hg.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(s->sc, &z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(s->status, 0, sizeof(int32_t) * NT) != cudaSuccess ||
-        cudaMemset(s->iters, 0, sizeof(int32_t) * NT) != cudaSuccess) {
-        mem_shock_free(s);
-        return MEM_ECUDA;
-    }
-    // Prime the characteristic speeds of the initial state (they set dt of the
-    // first step).
-    int rc = mem_host::flux_bufs(ctx, s->M, s->beta, s->g, s->F, s->speed, NT, s->sigma, s->mom, 0);
-    if (rc || cudaDeviceSynchronize() != cudaSuccess) { mem_shock_free(s); return rc ? rc : MEM_ECUDA; }
+    s->b = b;
     *out = s;
     return MEM_OK;
 }
 
+int mem_shock_init(mem_ctx *ctx, const mem_shock_params *p, mem_shock **out) {
+    if (!p) return MEM_EINVAL;
+    return mem_shock_init_batch(ctx, p, 1, out);
+}
+
+int mem_shock_num_problems(const mem_shock *s) { return s ? s->b->P : 0; }
+
 int mem_shock_step(mem_shock *s, int nsteps, double *steady_metric, void *stream) {
     if (!s || nsteps < 0) return MEM_EINVAL;
+    mem_host::ShockBatch *b = s->b;
     cudaStream_t st = (cudaStream_t)stream;
-    const bool use_graph = s->p.graph && s->p.impl == MEM_IMPL_FUSED;
+    const bool use_graph = b->params[0].graph && b->params[0].impl == MEM_IMPL_FUSED;
     if (use_graph && !s->gexec && nsteps > 0) {
-        // Capture one step.  The legacy default stream cannot be captured.
+        // Capture one step.  The legacy default stream cannot be captured, so
+        // capture on a private stream; the first step runs uncaptured (the
+        // fused kernel sets its shared-memory limit on first use).
         cudaStream_t cap = st;
         bool own = false;
         if (!cap) {
             MEM_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
             own = true;
         }
-        // The first launch of the fused kernel sets its shared-memory limit;
-        // do it outside the capture.
-        int rc = enqueue_step(s, cap);
+        int rc = mem_host::batch_enqueue_step(b, st);
         if (rc) return rc;
         --nsteps;
-        MEM_CUDA_TRY(cudaStreamSynchronize(cap));
+        MEM_CUDA_TRY(cudaStreamSynchronize(st));
         MEM_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-        rc = enqueue_step(s, cap);
+        rc = mem_host::batch_enqueue_step(b, cap);
         cudaGraph_t gph = nullptr;
         cudaError_t e = cudaStreamEndCapture(cap, &gph);
+        if (own) cudaStreamDestroy(cap);
         if (rc || e != cudaSuccess) { if (gph) cudaGraphDestroy(gph); return rc ? rc : MEM_ECUDA; }
         s->graph = gph;
         MEM_CUDA_TRY(cudaGraphInstantiate(&s->gexec, gph, 0));
-        if (own) cudaStreamDestroy(cap);
     }
     for (int k = 0; k < nsteps; ++k) {
         if (use_graph) MEM_CUDA_TRY(cudaGraphLaunch(s->gexec, st));
         else {
-            int rc = enqueue_step(s, st);
+            int rc = mem_host::batch_enqueue_step(b, st);
             if (rc) return rc;
         }
     }
     if (steady_metric) {
-        ShockScalars h;
-        MEM_CUDA_TRY(cudaMemcpyAsync(&h, s->sc, sizeof(h), cudaMemcpyDeviceToHost, st));
-        MEM_CUDA_TRY(cudaStreamSynchronize(st));
-        float d;
-        memcpy(&d, &h.steady_bits, sizeof(d));
-        *steady_metric = (double)d / (s->n_dn - s->n_up);
+        std::vector<ShockScalars> h;
+        int rc = mem_host::batch_read_scalars(b, h, st);
+        if (rc) return rc;
+        double worst = 0.0;
+        for (int i = 0; i < b->P; ++i) {
+            float d;
+            memcpy(&d, &h[i].steady_bits, sizeof(d));
+            worst = fmax(worst, (double)d / b->hprm[i].drho);
+        }
+        *steady_metric = worst;
     }
     return MEM_OK;
 }
@@ -376,62 +565,29 @@ int mem_shock_step(mem_shock *s, int nsteps, double *steady_metric, void *stream
 int mem_shock_device_state(mem_shock *s, float **M, float **beta, float **g, float **speed, int32_t **status,
                            int32_t **iters) {
     if (!s) return MEM_EINVAL;
-    if (M) *M = s->M;
-    if (beta) *beta = s->beta;
-    if (g) *g = s->g;
-    if (speed) *speed = s->speed;
-    if (status) *status = s->status;
-    if (iters) *iters = s->iters;
+    mem_host::ShockBatch *b = s->b;
+    if (M) *M = b->M;
+    if (beta) *beta = b->beta;
+    if (g) *g = b->g;
+    if (speed) *speed = b->speed;
+    if (status) *status = b->status;
+    if (iters) *iters = b->iters;
     return MEM_OK;
 }
 
 int mem_shock_get(mem_shock *s, float *M_host, float *g_host, float *beta_host, float *rho, float *ux, float *T,
                   float *sxx, float *qx, double *t_out) {
     if (!s) return MEM_EINVAL;
-    const int N = s->N, NT = N + 2;
-    std::vector<float> hM((size_t)NT * NP), hg((size_t)NT * 6);
-    MEM_CUDA_TRY(cudaDeviceSynchronize());
-    MEM_CUDA_TRY(cudaMemcpy(hM.data(), s->M, sizeof(float) * hM.size(), cudaMemcpyDeviceToHost));
-    MEM_CUDA_TRY(cudaMemcpy(hg.data(), s->g, sizeof(float) * hg.size(), cudaMemcpyDeviceToHost));
-    if (M_host) memcpy(M_host, hM.data(), sizeof(float) * hM.size());
-    if (g_host) memcpy(g_host, hg.data(), sizeof(float) * hg.size());
-    if (beta_host) MEM_CUDA_TRY(cudaMemcpy(beta_host, s->beta, sizeof(float) * NT * NP, cudaMemcpyDeviceToHost));
-    if (t_out) {
-        ShockScalars h;
-        MEM_CUDA_TRY(cudaMemcpy(&h, s->sc, sizeof(h), cudaMemcpyDeviceToHost));
-        *t_out = h.t;
-    }
-    // Macroscopic profiles (Appendix A definitions, m = k_B = 1) from the
-    // moments in each cell's gauge.
-    for (int i = 0; i < N; ++i) {
-        const float *m = &hM[(size_t)(i + 1) * NP];
-        const float *gg = &hg[(size_t)(i + 1) * 6];
-        const double n = m[0];
-        double mb[3], E2[3];
-        const int i1[3] = {idx3(1, 0, 0), idx3(0, 1, 0), idx3(0, 0, 1)};
-        const int i2[3] = {idx3(2, 0, 0), idx3(0, 2, 0), idx3(0, 0, 2)};
-        for (int a = 0; a < 3; ++a) { mb[a] = m[i1[a]] / n; E2[a] = sqrt(2.0) * m[i2[a]] / n + 1.0; }
-        double var[3];
-        for (int a = 0; a < 3; ++a) var[a] = gg[3 + a] * gg[3 + a] * (E2[a] - mb[a] * mb[a]);
-        const double Tc = (var[0] + var[1] + var[2]) / 3.0;
-        if (rho) rho[i] = (float)n;
-        if (ux) ux[i] = (float)(gg[0] + gg[3] * mb[0]);
-        if (T) T[i] = (float)Tc;
-        if (sxx) sxx[i] = (float)(n * (var[0] - Tc));
-        if (qx) {
-            // q_x = n/2 sum_b E[c_x c_b^2], c = u - v, from raw moments of ubar.
-            const double X = mb[0], X2 = E2[0], X3 = sqrt(6.0) * m[idx3(3, 0, 0)] / n + 3.0 * X;
-            double q = gg[3] * gg[3] * gg[3] * (X3 - 3.0 * X * X2 + 2.0 * X * X * X);
-            const int iy[2] = {idx3(1, 1, 0), idx3(1, 0, 1)}, iy2[2] = {idx3(1, 2, 0), idx3(1, 0, 2)};
-            for (int b = 1; b < 3; ++b) {
-                const double Y = mb[b], Y2 = E2[b], XY = m[iy[b - 1]] / n;
-                const double XY2 = sqrt(2.0) * m[iy2[b - 1]] / n + X;
-                q += gg[3] * gg[3 + b] * gg[3 + b] * (XY2 - 2.0 * Y * XY - X * Y2 + 2.0 * X * Y * Y);
-            }
-            qx[i] = (float)(0.5 * n * q);
-        }
-    }
-    return MEM_OK;
+    return mem_host::batch_profiles(s->b, 0, M_host, g_host, beta_host, rho, ux, T, sxx, qx, t_out, nullptr);
+}
+
+int mem_shock_get_problem(mem_shock *s, int problem, float *rho, float *ux, float *T, float *sxx, float *qx,
+                          double *t_out, int32_t *steps_out) {
+    if (!s) return MEM_EINVAL;
+    int steps = 0;
+    int rc = mem_host::batch_profiles(s->b, problem, nullptr, nullptr, nullptr, rho, ux, T, sxx, qx, t_out, &steps);
+    if (steps_out) *steps_out = steps;
+    return rc;
 }
 
 }  // extern "C"

@@ -1,0 +1,55 @@
+// shock.h -- packed batch of independent 1D shock problems (host side).
+#pragma once
+
+#include <vector>
+
+#include "ctx.h"
+
+// Per-problem constants (device copy in ShockBatch::prm).
+struct ShockProb {
+    int off;       // first cell (left ghost) of the problem in the packed arrays
+    int n;         // interior cells
+    float dx;      // cell width
+    float cfl_dx;  // cfl * dx
+    float Pr;      // Prandtl number of the ES-BGK model
+    float relax;   // tau = relax / n
+    float drho;    // rho_+ - rho_- (normalises the steady-state metric)
+    float pad;
+};
+
+// Per-problem step scalars (device).
+struct ShockScalars {
+    float dt;
+    unsigned int steady_bits;  // max |d rho| of the last step, float bits (non-negative)
+    double t;                  // simulated time
+    int steps;
+    int pad;
+};
+
+namespace mem_host {
+
+struct ShockBatch {
+    mem_ctx *ctx = nullptr;
+    int P = 0;   // problems
+    int NT = 0;  // packed cells, ghosts included
+    std::vector<mem_shock_params> params;
+    std::vector<ShockProb> hprm;
+    float *M = nullptr, *beta = nullptr, *g = nullptr, *speed = nullptr, *F = nullptr, *Mn = nullptr;
+    float *rho0 = nullptr, *sigma = nullptr, *mom = nullptr;
+    int32_t *status = nullptr, *iters = nullptr;
+    int *pid = nullptr;
+    unsigned char *interior = nullptr;
+    ShockProb *prm = nullptr;
+    ShockScalars *sc = nullptr;
+};
+
+bool shock_params_valid(const mem_shock_params &p);
+size_t batch_bytes_per_cell(const mem_ctx *ctx);
+int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **out);
+void batch_free(ShockBatch *b);
+int batch_enqueue_step(ShockBatch *b, cudaStream_t st);
+int batch_profiles(ShockBatch *b, int i, float *M_host, float *g_host, float *beta_host, float *rho, float *ux,
+                   float *T, float *sxx, float *qx, double *t_out, int *steps_out);
+int batch_read_scalars(ShockBatch *b, std::vector<ShockScalars> &out, cudaStream_t st);
+
+}  // namespace mem_host

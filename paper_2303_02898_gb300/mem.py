@@ -58,7 +58,9 @@ def lib():
         L.mem_version.restype = ctypes.c_char_p
         for name in ("mem_init", "mem_solve", "mem_flux", "mem_gauge_hermite", "mem_gauge_transform",
                      "mem_targets", "mem_shock_init", "mem_shock_step", "mem_shock_get",
-                     "mem_shock_device_state", "mem_quad_order"):
+                     "mem_shock_device_state", "mem_quad_order", "mem_shock_init_batch",
+                     "mem_shock_num_problems", "mem_shock_get_problem", "mem_serve_create", "mem_serve_submit",
+                     "mem_serve_progress", "mem_serve_poll", "mem_serve_stats"):
             getattr(L, name).restype = ctypes.c_int
         L.mem_solve.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(SolveOpts), _P]
         L.mem_flux.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P]
@@ -70,6 +72,10 @@ def lib():
         L.mem_shock_step.argtypes = [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]
         L.mem_destroy.argtypes = [_P]
         L.mem_shock_free.argtypes = [_P]
+        L.mem_serve_destroy.argtypes = [_P]
+        L.mem_serve_create.argtypes = [_P, ctypes.c_size_t, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P]
+        L.mem_serve_progress.argtypes = [_P, ctypes.c_int, _P]
+        L.mem_serve_poll.argtypes = [_P, ctypes.c_uint64, _P, _P, _P, _P]
         _lib = L
     return _lib
 
@@ -174,13 +180,21 @@ def default_shock_params(**kw):
 
 
 class Shock:
-    """mem_shock_init / step / get / free."""
+    """mem_shock_init / step / get / free; with `problems` (a list of dicts of
+    parameters) a packed batch through mem_shock_init_batch."""
 
-    def __init__(self, ctx, **kw):
+    def __init__(self, ctx, problems=None, **kw):
         self.ctx = ctx
-        self.p = default_shock_params(**kw)
         h = ctypes.c_void_p()
-        _check(lib().mem_shock_init(ctx.h, ctypes.byref(self.p), ctypes.byref(h)), "mem_shock_init")
+        if problems is None:
+            self.p = default_shock_params(**kw)
+            _check(lib().mem_shock_init(ctx.h, ctypes.byref(self.p), ctypes.byref(h)), "mem_shock_init")
+            self.ps = [self.p]
+        else:
+            self.ps = [default_shock_params(**dict(kw, **pr)) for pr in problems]
+            arr = (ShockParams * len(self.ps))(*self.ps)
+            _check(lib().mem_shock_init_batch(ctx.h, arr, len(self.ps), ctypes.byref(h)), "mem_shock_init_batch")
+            self.p = self.ps[0]
         self.h = h
         self.N = self.p.ncells
 
@@ -203,6 +217,18 @@ class Shock:
         _check(rc, "mem_shock_get")
         return dict(M=M, g=g, beta=b, rho=prof[0], ux=prof[1], T=prof[2], sxx=prof[3], qx=prof[4], t=t.value)
 
+    def problem(self, i):
+        """Profiles (rho, u_x, T, sigma_xx, q_x), time and steps of problem i."""
+        import numpy as np
+        n = self.ps[i].ncells
+        prof = [np.zeros(n, np.float32) for _ in range(5)]
+        t = ctypes.c_double()
+        st = ctypes.c_int32()
+        f = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        _check(lib().mem_shock_get_problem(self.h, i, *[f(x) for x in prof], ctypes.byref(t), ctypes.byref(st)),
+               "mem_shock_get_problem")
+        return dict(rho=prof[0], ux=prof[1], T=prof[2], sxx=prof[3], qx=prof[4], t=t.value, steps=st.value)
+
     def device_state(self):
         ptrs = [ctypes.c_void_p() for _ in range(6)]
         _check(lib().mem_shock_device_state(self.h, *[ctypes.byref(p) for p in ptrs]), "mem_shock_device_state")
@@ -211,6 +237,64 @@ class Shock:
     def close(self):
         if self.h:
             lib().mem_shock_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """mem_serve_*: continuous batching of shock solves."""
+
+    def __init__(self, ctx, hbm_budget_bytes=8 << 30, max_cells=1 << 20, steady_tol=1e-6, max_steps=100000):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        _check(lib().mem_serve_create(ctx.h, hbm_budget_bytes, max_cells, steady_tol, max_steps, ctypes.byref(h)),
+               "mem_serve_create")
+        self.h = h
+
+    def submit(self, **kw):
+        p = default_shock_params(**kw)
+        rid = ctypes.c_uint64()
+        rc = lib().mem_serve_submit(self.h, ctypes.byref(p), ctypes.byref(rid))
+        if rc == MEM_EBUSY:
+            return None
+        _check(rc, "mem_serve_submit")
+        return rid.value
+
+    def progress(self, iters=1, stream=None):
+        _check(lib().mem_serve_progress(self.h, iters, _stream(stream)), "mem_serve_progress")
+
+    def poll(self, rid, ncells=None):
+        import numpy as np
+        r = ShockResult()
+        if ncells:
+            prof = [np.zeros(ncells, np.float32) for _ in range(3)]
+            ptrs = [p.ctypes.data_as(ctypes.c_void_p) for p in prof]
+        else:
+            prof, ptrs = None, [None, None, None]
+        rc = lib().mem_serve_poll(self.h, rid, ctypes.byref(r), *ptrs)
+        if rc == MEM_OK:
+            out = dict(steps=r.steps, ncells=r.ncells, steady=bool(r.steady), sim_time=r.sim_time,
+                       latency_s=r.latency_s)
+            if prof:
+                out.update(rho=prof[0], ux=prof[1], T=prof[2])
+            return out
+        if rc == MEM_PENDING:
+            return None
+        raise KeyError(rid)
+
+    def stats(self):
+        v = [ctypes.c_int32() for _ in range(4)]
+        _check(lib().mem_serve_stats(self.h, *[ctypes.byref(x) for x in v]), "mem_serve_stats")
+        return dict(queued=v[0].value, resident=v[1].value, resident_cells=v[2].value, completed=v[3].value)
+
+    def close(self):
+        if self.h:
+            lib().mem_serve_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -120,6 +120,73 @@ def fused_flops_per_pass(n):
     return 2 * fma
 
 
+SHOCK_MACH = 3.0   # largest Mach the 8^3 Gauss-Hermite Hermite-gauge rule keeps stable from a step
+
+
+def run_ensemble(mem, ctx, torch, np, nsteps=10):
+    """256 packed shock problems (ncells logU[256, 16384], Mach U[1.2, 3]) advanced
+    together; cell-updates/s of the graph-captured fused step vs the plain one."""
+    from paper_2303_02898_gb300 import workloads
+    probs = workloads.ensemble_problems(256, seed=1, mach_hi=SHOCK_MACH)
+    cells = sum(p.ncells for p in probs)
+    out = {}
+    for impl, graph, tag, n in ((mem.IMPL_FUSED, 1, "tuned", nsteps), (mem.IMPL_PLAIN, 0, "plain", 3)):
+        sh = mem.Shock(ctx, problems=[dict(mach=p.mach, ncells=p.ncells, xl=p.xl, xr=p.xr) for p in probs],
+                       impl=impl, graph=graph)
+        sh.step(2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sh.step(n)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        fin = all(np.isfinite(sh.problem(i)["rho"]).all() for i in (0, 100, 255))
+        sh.close()
+        out["ensemble_%s" % tag] = {"value": cells * n / dt, "unit": "cell-updates/s", "problems": len(probs),
+                                    "cells": cells, "steps": n, "ms_per_step": 1e3 * dt / n, "finite": fin}
+    out["ensemble_tuned_over_plain"] = out["ensemble_tuned"]["value"] / out["ensemble_plain"]["value"]
+    return out
+
+
+def run_serving(mem, ctx, torch, np, nreq=32, max_steps=100, chunk=10):
+    """Poisson trace (200 req/s, ncells logU[128, 32768], Mach U[1.5, 3]),
+    each request capped at max_steps time steps: continuous batching (fused
+    back-end) vs the same requests one at a time on the plain FP32 back-end."""
+    from paper_2303_02898_gb300 import workloads
+    t_arr, probs = workloads.serving_trace(nreq, seed=2, mach_hi=SHOCK_MACH)
+    sv = mem.Server(ctx, hbm_budget_bytes=40 << 30, max_cells=1 << 20, steady_tol=1e-6, max_steps=max_steps)
+    ids, nxt = [], 0
+    t0 = time.perf_counter()
+    while True:
+        now = time.perf_counter() - t0
+        while nxt < nreq and t_arr[nxt] <= now:
+            p = probs[nxt]
+            ids.append((sv.submit(mach=p.mach, ncells=p.ncells, xl=p.xl, xr=p.xr), p))
+            nxt += 1
+        sv.progress(chunk)
+        st = sv.stats()
+        if nxt == nreq and st["completed"] == nreq:
+            break
+        if st["resident"] == 0 and st["queued"] == 0 and nxt < nreq:
+            time.sleep(max(0.0, t_arr[nxt] - (time.perf_counter() - t0)))
+    wall = time.perf_counter() - t0
+    res = [(sv.poll(i), p) for i, p in ids]
+    lat = np.array([r["latency_s"] for r, _ in res])
+    upd = sum(r["steps"] * p.ncells for r, p in res)
+    sv.close()
+    # one at a time: each request alone, back to back, same number of steps
+    t1 = time.perf_counter()
+    for r, p in res:
+        sh = mem.Shock(ctx, mach=p.mach, ncells=p.ncells, xl=p.xl, xr=p.xr, graph=0, impl=mem.IMPL_PLAIN)
+        sh.step(r["steps"])
+        sh.close()
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t1
+    return {"serving": {"requests": nreq, "rate_per_s": 200.0, "max_steps": max_steps,
+                        "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                        "throughput": upd / wall, "unit": "cell-updates/s", "wall_s": wall,
+                        "one_at_a_time_throughput": upd / seq, "one_at_a_time_wall_s": seq}}
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -316,21 +383,24 @@ def main():
                                "mean_passes": float(it.float().mean())}
         ctx12.close()
         del M12, g12
-        # Mach 10 shock, 4096 cells over +-50 mean free paths, graph-captured step
-        for impl, graph, nst in ((mem.IMPL_FUSED, 1, 200), (mem.IMPL_PLAIN, 0, 10)):
-            sh = mem.Shock(ctx, mach=10.0, ncells=4096, xl=-50.0, xr=50.0, impl=impl, graph=graph)
-            sh.step(3)
-            torch.cuda.synchronize()
-            s0 = time.perf_counter()
-            sh.step(nst)
-            torch.cuda.synchronize()
-            sdt = time.perf_counter() - s0
-            d = sh.get()
-            key = "shock_mach10_tuned" if impl == mem.IMPL_FUSED else "shock_mach10_plain"
-            extras[key] = {"value": 4096 * nst / sdt, "unit": "cell-updates/s", "steps": nst,
-                           "ms_per_step": 1e3 * sdt / nst, "sim_time": d["t"],
-                           "finite": bool(np.isfinite(d["M"]).all())}
-            sh.close()
+        # shock step on 4096 cells over +-50 mean free paths, graph-captured
+        for mach, ic, tag in ((10.0, 1, "mach10"), (SHOCK_MACH, 0, "mach%g" % SHOCK_MACH)):
+            for impl, graph, nst in ((mem.IMPL_FUSED, 1, 200), (mem.IMPL_PLAIN, 0, 10)):
+                sh = mem.Shock(ctx, mach=mach, ncells=4096, xl=-50.0, xr=50.0, impl=impl, graph=graph, ic=ic)
+                sh.step(3)
+                torch.cuda.synchronize()
+                s0 = time.perf_counter()
+                sh.step(nst)
+                torch.cuda.synchronize()
+                sdt = time.perf_counter() - s0
+                d = sh.get()
+                key = "shock_%s_%s" % (tag, "tuned" if impl == mem.IMPL_FUSED else "plain")
+                extras[key] = {"value": 4096 * nst / sdt, "unit": "cell-updates/s", "steps": nst,
+                               "ms_per_step": 1e3 * sdt / nst, "sim_time": d["t"], "ic": "tanh" if ic else "step",
+                               "finite": bool(np.isfinite(d["M"]).all())}
+                sh.close()
+        extras.update(run_ensemble(mem, ctx, torch, np))
+        extras.update(run_serving(mem, ctx, torch, np))
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

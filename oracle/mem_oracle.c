@@ -42,6 +42,7 @@
  *     objective differences, gradient and Hessian are identical, so Algorithm
  *     1 takes identical steps.  beta = 0 is the Maxwellian of the gauge.
  */
+#define _GNU_SOURCE
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -171,7 +172,60 @@ int or_gh_rule(int n, double *x, double *w) {
 typedef struct { int n, Q; double *u; double *logw; double *phi; } rule_t;
 static rule_t g_rules[NMAXQ + 1];
 
+/* Block Gauss-Legendre tensor rules on a box in the gauge frame (rule ids
+ * 100..115, registered by or_set_box_rule).  Per axis, [-L, L] is split into
+ * nb equal blocks with ng Legendre points each; the Gaussian base measure is
+ * folded into the weights, w_i = w^GL_i exp(-x_i^2/2) / sqrt(2 pi), so beta
+ * keeps its meaning (beta = 0 is the gauge's Maxwellian, up to truncation). */
+static rule_t g_box_rules[16];
+
+static void gl_rule(int n, double *x, double *w) {
+    /* Golub-Welsch for Legendre on [-1, 1]: off-diagonal k / sqrt(4k^2 - 1). */
+    double *J = calloc((size_t)n * n, sizeof(double)), *V = calloc((size_t)n * n, sizeof(double)), ev[64];
+    for (int k = 1; k < n; ++k) J[(k - 1) * n + k] = J[k * n + k - 1] = k / sqrt(4.0 * k * k - 1.0);
+    jacobi_eigen(n, J, ev, V);
+    int order[64];
+    for (int i = 0; i < n; ++i) order[i] = i;
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j)
+            if (ev[order[j]] < ev[order[i]]) { int t = order[i]; order[i] = order[j]; order[j] = t; }
+    for (int i = 0; i < n; ++i) { x[i] = ev[order[i]]; w[i] = 2.0 * V[order[i]] * V[order[i]]; }
+    free(J); free(V);
+}
+
+int or_set_box_rule(int id, int nbx, int nbr, int ng, double Lx, double Lr) {
+    if (id < 100 || id > 115 || ng < 1 || ng > 16 || nbx < 1 || nbr < 1 || nbx * ng > 256 || nbr * ng > 256) return -1;
+    rule_t *r = &g_box_rules[id - 100];
+    if (r->Q) { free(r->u); free(r->logw); free(r->phi); r->Q = 0; }
+    double gx[16], gw[16];
+    gl_rule(ng, gx, gw);
+    double ax[3][256], aw[3][256];
+    int na[3];
+    for (int a = 0; a < 3; ++a) {
+        int nb = a == 0 ? nbx : nbr;
+        double L = a == 0 ? Lx : Lr, h = 2.0 * L / nb;
+        na[a] = nb * ng;
+        for (int b = 0; b < nb; ++b)
+            for (int i = 0; i < ng; ++i) {
+                double x = -L + h * (b + 0.5 * (gx[i] + 1.0));
+                ax[a][b * ng + i] = x;
+                aw[a][b * ng + i] = 0.5 * h * gw[i] * exp(-0.5 * x * x) / sqrt(2.0 * M_PI);
+            }
+    }
+    int Q = na[0] * na[1] * na[2];
+    double *u = malloc(sizeof(double) * 3 * Q), *lw = malloc(sizeof(double) * Q), *ph = malloc(sizeof(double) * NP * (size_t)Q);
+    int q = 0;
+    for (int i = 0; i < na[0]; ++i) for (int j = 0; j < na[1]; ++j) for (int k = 0; k < na[2]; ++k, ++q) {
+        u[3 * q] = ax[0][i]; u[3 * q + 1] = ax[1][j]; u[3 * q + 2] = ax[2][k];
+        lw[q] = log(aw[0][i]) + log(aw[1][j]) + log(aw[2][k]);
+        or_phi(&u[3 * q], &ph[(size_t)NP * q]);
+    }
+    r->n = -1; r->u = u; r->logw = lw; r->phi = ph; r->Q = Q;
+    return Q;
+}
+
 static const rule_t *get_rule(int n) {
+    if (n >= 100 && n <= 115) return g_box_rules[n - 100].Q ? &g_box_rules[n - 100] : NULL;
     if (n < 1 || n > NMAXQ) return NULL;
     rule_t *r = &g_rules[n];
     if (r->Q) return r;

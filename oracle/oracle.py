@@ -64,6 +64,15 @@ def index_of(a, b, c):
     return lib().or_index_of(a, b, c)
 
 
+def set_box_rule(rule_id, nbx, nbr, ng, Lx, Lr):
+    """Register block Gauss-Legendre tensor rule `rule_id` (100..115) on
+    [-Lx, Lx] x [-Lr, Lr]^2 in the gauge frame; returns the node count."""
+    q = lib().or_set_box_rule(rule_id, nbx, nbr, ng, ctypes.c_double(Lx), ctypes.c_double(Lr))
+    if q <= 0:
+        raise ValueError("bad box rule")
+    return q
+
+
 def gh_rule(n):
     """Probabilists' Gauss-Hermite nodes/weights (Golub-Welsch), weights sum to 1."""
     x = np.zeros(n)

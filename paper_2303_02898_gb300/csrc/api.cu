@@ -159,15 +159,18 @@ static void build_lin_terms(int j0, bool with_x, std::vector<int> &off, std::vec
 // [t][l] as (mu index | p << 8 | last-term flag in the sign bit, coefficient).
 // Sequences are padded with zero terms to a common length.
 static void build_hess_slots(const std::vector<int> &off, const std::vector<int2> &terms, std::vector<int2> &slots,
-                             int &nslots) {
-    const int NE = (int)off.size() - 1;
+                             int &nslots, const std::vector<int> *off2 = nullptr, const std::vector<int2> *terms2 = nullptr) {
+    const int NE1 = (int)off.size() - 1, NE2 = off2 ? (int)off2->size() - 1 : 0;
     std::vector<std::vector<int2>> per(32);
-    for (int p = 0; p < NE; ++p) {
+    for (int p = 0; p < NE1 + NE2; ++p) {
         auto &v = per[p % 32];
-        for (int t = off[p]; t < off[p + 1]; ++t) {
-            int2 s = terms[t];
+        const std::vector<int> &o = p < NE1 ? off : *off2;
+        const std::vector<int2> &tm = p < NE1 ? terms : *terms2;
+        const int q = p < NE1 ? p : p - NE1;
+        for (int t = o[q]; t < o[q + 1]; ++t) {
+            int2 s = tm[t];
             s.x = (s.x & 255) | (p << 8);
-            if (t == off[p + 1] - 1) s.x |= (int)0x80000000;
+            if (t == o[q + 1] - 1) s.x |= (int)0x80000000;
             v.push_back(s);
         }
     }
@@ -250,8 +253,12 @@ int mem_init(int degree, int quad_order, mem_ctx **out) {
     std::vector<int2> terms, xterms;
     build_lin_terms(1, false, off, terms);
     build_lin_terms(0, true, xoff, xterms);
-    std::vector<int2> slots;
+    std::vector<int2> slots, fslots;
     build_hess_slots(off, terms, slots, ctx->n_hess_slots);
+    std::vector<int> soff;
+    std::vector<int2> sterms;
+    build_lin_terms(0, false, soff, sterms);  // E[phi_i phi_j], i >= j >= 0
+    build_hess_slots(soff, sterms, fslots, ctx->n_flux_slots, &xoff, &xterms);
     rc = MEM_OK;
     if (!rc) rc = upload(&ctx->d_phiT, phiT);
     if (!rc) rc = upload(&ctx->d_logw, logw);
@@ -263,6 +270,7 @@ int mem_init(int degree, int quad_order, mem_ctx **out) {
     if (!rc) rc = upload(&ctx->d_lin_off, off);
     if (!rc) rc = upload(&ctx->d_lin_terms, terms);
     if (!rc) rc = upload(&ctx->d_hess_slots, slots);
+    if (!rc) rc = upload(&ctx->d_flux_slots, fslots);
     if (!rc) rc = upload(&ctx->d_xlin_off, xoff);
     if (!rc) rc = upload(&ctx->d_xlin_terms, xterms);
     ctx->n_lin_terms = (int)terms.size();
@@ -276,7 +284,7 @@ void mem_destroy(mem_ctx *ctx) {
     if (!ctx) return;
     cudaDeviceSynchronize();
     void *ptrs[] = {ctx->d_phiT, ctx->d_logw, ctx->d_tab_solve, ctx->d_tab_flux, ctx->d_he1d, ctx->d_x1d,
-                    ctx->d_logw1d, ctx->d_lin_off, ctx->d_lin_terms, ctx->d_hess_slots, ctx->d_xlin_off, ctx->d_xlin_terms,
+                    ctx->d_logw1d, ctx->d_lin_off, ctx->d_lin_terms, ctx->d_hess_slots, ctx->d_flux_slots, ctx->d_xlin_off, ctx->d_xlin_terms,
                     ctx->scratch};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -305,6 +313,8 @@ int mem_flux(mem_ctx *ctx, const float *M, const float *beta, const float *gauge
     if (!ctx || B < 0) return MEM_EINVAL;
     if (B == 0) return MEM_OK;
     if (!M || !beta || !gauge) return MEM_EINVAL;
+    if (mem_host::flux_fused_available(ctx))
+        return mem_host::flux_fused(ctx, M, beta, gauge, F, speed, B, (cudaStream_t)stream);
     return mem_host::flux(ctx, M, beta, gauge, F, speed, B, (cudaStream_t)stream);
 }
 

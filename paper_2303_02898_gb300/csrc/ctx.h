@@ -32,6 +32,8 @@ struct mem_ctx {
     int n_lin_terms = 0;
     int2 *d_hess_slots = nullptr;  // [n_hess_slots][32] per-lane Hessian term sequences
     int n_hess_slots = 0;
+    int2 *d_flux_slots = nullptr;  // [n_flux_slots][32] E[phi phi^T] and E[ubar_x phi phi^T] terms
+    int n_flux_slots = 0;
     int *d_xlin_off = nullptr;     // [631]  flux-Jacobian terms (packed i>=j>=0)
     int2 *d_xlin_terms = nullptr;
     float xmax = 0.f;              // largest 1D node
@@ -54,6 +56,7 @@ int flux_bufs(mem_ctx *ctx, const float *M, const float *beta, const float *g, f
               float *sigma, float *mom, cudaStream_t st);
 int flux_fused(mem_ctx *ctx, const float *M, const float *beta, const float *g, float *F, float *speed,
                int64_t B, cudaStream_t st);
+bool flux_fused_available(const mem_ctx *ctx);
 int gauge_hermite(mem_ctx *ctx, const float *M_in, const float *g_in, float *g_out, float *M_out,
                   float *beta_inout, int64_t B, int axisym, cudaStream_t st);
 int gauge_transform(const float *g_to, const float *g_from, const float *M_in, float *M_out, int64_t B,

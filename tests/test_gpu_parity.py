@@ -197,11 +197,17 @@ def test_plain_and_fused_agree(O, mem, ctx8, dev):
 
 
 # ------------------------------------------------------------------ flux
-def test_flux_and_speed_match_oracle(O, mem, ctx8, dev):
-    rng = np.random.default_rng(30)
+@pytest.mark.parametrize("order", [8, 12])
+def test_flux_and_speed_match_oracle(O, mem, dev, order, ctx8, ctx12):
+    ctx = ctx8 if order == 8 else ctx12
+    rng = np.random.default_rng(30 + order)
     B = 70
     deg = O.basis_index().sum(1)
-    scale = np.where(deg <= 2, 0.1, np.where(deg == 3, 0.03, 0.01))
+    # FP32 speeds lose ~1e-7 cond(E[phi phi^T]) relative accuracy; the
+    # degree-3/4 parameters are scaled so that cond stays below ~1e5 (on the
+    # outer nodes of the 12-point rule he_4 reaches ~60, so 12^3 takes 0.3x).
+    f = 1.0 if order == 8 else 0.3
+    scale = np.where(deg <= 2, 0.1, np.where(deg == 3, 0.03 * f, 0.01 * f))
     beta = rng.normal(0, 1, (B, 35)) * scale
     beta[:, 0] = np.exp(rng.uniform(-0.5, 0.5, B))
     M = np.zeros((B, 35))
@@ -210,11 +216,11 @@ def test_flux_and_speed_match_oracle(O, mem, ctx8, dev):
     Mt, bt, gt = T32(M, dev), T32(beta, dev), T32(g, dev)
     F = torch.zeros(B, 35, device=dev)
     sp = torch.zeros(B, device=dev)
-    ctx8.flux(Mt, bt, gt, F, sp)
+    ctx.flux(Mt, bt, gt, F, sp)
     Fg, spg = np64(F), np64(sp)
     bf, gf, Mf = np64(bt), np64(gt), np64(Mt)
     for c in range(B):
-        Fo, so, lo, hi = O.flux(8, bf[c], gf[c], Mf[c, 0])
+        Fo, so, lo, hi = O.flux(order, bf[c], gf[c], Mf[c, 0])
         assert np.abs(Fg[c] - Fo).max() <= 2e-5 * np.abs(Fo).max(), c
         assert spg[c] == pytest.approx(so, rel=2e-5), (c, spg[c], so)
     # Maxwellian: |w_x| + sqrt(5 + sqrt 10) s_x
@@ -222,7 +228,7 @@ def test_flux_and_speed_match_oracle(O, mem, ctx8, dev):
     Mx[:, 0] = 1.0
     gx = T32([[0.0, 0, 0, 1, 1, 1], [2.0, 0, 0, 0.5, 1, 1], [-3.0, 0, 0, 2.0, 1, 1], [12.9, 0, 0, 1.0, 1, 1]], dev)
     spx = torch.zeros(4, device=dev)
-    ctx8.flux(Mx, Mx.clone(), gx, None, spx)
+    ctx.flux(Mx, Mx.clone(), gx, None, spx)
     r = math.sqrt(5 + math.sqrt(10))
     exp = [r, 2 + 0.5 * r, 3 + 2 * r, 12.9 + r]
     assert np.allclose(np64(spx), exp, rtol=1e-5)

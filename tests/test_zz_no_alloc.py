@@ -15,7 +15,9 @@ pytestmark = pytest.mark.gpu
 def _inputs(rng, B, dev):
     deg = np.array([sum(e) for e in [(a, b, d - a - b) for d in range(5) for a in range(d, -1, -1)
                                      for b in range(d - a, -1, -1)]])
-    scale = np.where(deg <= 2, 0.1, np.where(deg == 3, 0.03, 0.01))
+    # near-Gaussian cells (cond E[phi phi^T] below ~200): two FP32 evaluations
+    # of the same speed then agree to rounding
+    scale = np.where(deg <= 2, 0.1, np.where(deg == 3, 0.015, 0.005))
     beta = rng.normal(0, 1, (B, 35)) * scale
     beta[:, 0] = np.exp(rng.uniform(-0.5, 0.5, B))
     M = np.zeros((B, 35))

@@ -257,8 +257,25 @@ int mem_init(int degree, int quad_order, mem_ctx **out) {
     build_hess_slots(off, terms, slots, ctx->n_hess_slots);
     std::vector<int> soff;
     std::vector<int2> sterms;
-    build_lin_terms(0, false, soff, sterms);  // E[phi_i phi_j], i >= j >= 0
+    build_lin_terms(1, false, soff, sterms);  // E[phi_i phi_j], i >= j >= 1
     build_hess_slots(soff, sterms, fslots, ctx->n_flux_slots, &xoff, &xterms);
+    // Flux slots carry their destination in the flux kernel's per-warp work
+    // area instead of the entry number: entries 0..594 (E[phi_i phi_j],
+    // i >= j >= 1) go to H[(i-1) * 35 + (j-1)]; entries 595..1224
+    // (E[ubar_x phi_i phi_j], i >= j >= 0) go to 1260 + i * 36 + j.
+    {
+        std::vector<int> dst;
+        for (int i = 1; i < NP; ++i)
+            for (int j = 1; j <= i; ++j) dst.push_back((i - 1) * 35 + (j - 1));
+        for (int i = 0; i < NP; ++i)
+            for (int j = 0; j <= i; ++j) dst.push_back(1260 + i * 36 + j);
+        for (auto &sl : fslots) {
+            const bool last = sl.x < 0;
+            const int p = (sl.x >> 8) & 4095, idx = sl.x & 255;
+            if (sl.x == 0 && sl.y == 0) continue;  // padding
+            sl.x = idx | (dst[p] << 8) | (last ? (int)0x80000000 : 0);
+        }
+    }
     rc = MEM_OK;
     if (!rc) rc = upload(&ctx->d_phiT, phiT);
     if (!rc) rc = upload(&ctx->d_logw, logw);

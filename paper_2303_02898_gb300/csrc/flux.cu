@@ -34,9 +34,9 @@ struct FluxCfg {
     using C = FusedCfg<N>;
     static constexpr int S1 = 10 * C::P;  // stage x, a <= 9
     static constexpr int T2 = 55 * N;     // stage y, a + b <= 9
-    static constexpr int MAT = 3 * NP * LDF;
+    static constexpr int MAT = 2 * NP * LDF;
     static constexpr int WORK = (S1 + T2) > MAT ? (S1 + T2) : MAT;
-    static constexpr int WARP_FLOATS = 36 + 224 + 2 * 36 + 36 + WORK;  // beta, mu, alpha/beta, v, work
+    static constexpr int WARP_FLOATS = 36 + 224 + 2 * 36 + 36 + 72 + WORK;  // beta, mu, alpha/beta, v, l0/inv, work
 };
 
 struct FluxArgs {
@@ -58,10 +58,19 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
     float *s_lw = s_he + N * MEM_HE_STRIDE;
     int *s_abc = (int *)(s_lw + 16);  // [220] packed (a, b, c)
     int *s_ab = s_abc + 224;          // [55]  packed (a, b)
-    float *wbase = (float *)(s_ab + 56);
+    int *s_pij = s_ab + 56;           // [595] packed (i, j), i >= j, 34 x 34
+    int *s_pij35 = s_pij + 596;       // [630] packed (i, j), i >= j, 35 x 35
+    float *wbase = (float *)(s_pij35 + 632);
     for (int t = threadIdx.x; t < N * MEM_HE_STRIDE; t += blockDim.x) s_he[t] = A.he1d[t];
     for (int t = threadIdx.x; t < N; t += blockDim.x) s_lw[t] = A.logw1d[t];
     for (int t = threadIdx.x; t < 220; t += blockDim.x) s_abc[t] = exp_a(t) | (exp_b(t) << 8) | (exp_c(t) << 16);
+    for (int t = threadIdx.x; t < NP * (NP + 1) / 2; t += blockDim.x) {
+        int i = 0;
+        while ((i + 1) * (i + 2) / 2 <= t) ++i;
+        const int v = i | ((t - i * (i + 1) / 2) << 8);
+        s_pij35[t] = v;
+        if (t < NP1 * (NP1 + 1) / 2) s_pij[t] = v;
+    }
     for (int t = threadIdx.x; t < 55; t += blockDim.x) {
         int d = 0;
         while ((d + 1) * (d + 2) / 2 <= t) ++d;
@@ -71,9 +80,10 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *W = wbase + warp * Cf::WARP_FLOATS;
-    float *sb = W, *smu = W + 36, *al = smu + 224, *bt = al + 36, *sv = bt + 36, *work = sv + 36;
+    float *sb = W, *smu = W + 36, *al = smu + 224, *bt = al + 36, *sv = bt + 36, *sl0 = sv + 36, *sinv = sl0 + 36;
+    float *work = sinv + 36;
     float *S1 = work, *T2 = work + Cf::S1;
-    float *L = work, *Y = work + NP * LDF, *Cm = work + 2 * NP * LDF;  // alias the stage buffers
+    float *L = work, *Y = work + NP * LDF;  // alias the stage buffers (H in L, LDH rows)
 
     const int64_t nwarps = (int64_t)gridDim.x * FWARPS;
     for (int64_t cell = (int64_t)blockIdx.x * FWARPS + warp; cell < A.B; cell += nwarps) {
@@ -152,7 +162,9 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
             }
         }
         if (!A.speed) continue;
-        // ---- E[phi phi^T] (lower, into L) and E[ubar_x phi phi^T] (full, into Y)
+        // ---- E[phi phi^T] without its phi_0 border, and E[ubar_x phi phi^T]
+        // (lower triangles), from the linearisation terms; every slot carries
+        // the shared-memory offset of its entry.
         {
             float acc = 0.f;
 #pragma unroll 4
@@ -160,44 +172,68 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
                 const int2 sl = __ldg(&A.slots[t * 32 + lane]);
                 acc = fmaf(__int_as_float(sl.y), smu[sl.x & 255], acc);
                 if (sl.x < 0) {
-                    const int p = (sl.x >> 8) & 2047;
-                    const int q = p < 630 ? p : p - 630;
-                    int i = (int)((sqrtf(8.f * q + 1.f) - 1.f) * 0.5f);
-                    while (i * (i + 1) / 2 > q) --i;
-                    while ((i + 1) * (i + 2) / 2 <= q) ++i;
-                    const int j = q - i * (i + 1) / 2;
-                    if (p < 630) {
-                        L[i * LDF + j] = acc;
-                    } else {
-                        Y[i * LDF + j] = acc;
-                        Y[j * LDF + i] = acc;
-                    }
+                    work[(sl.x >> 8) & 0xffff] = acc;
                     acc = 0.f;
                 }
             }
         }
         __syncwarp();
-        if (!warp_cholesky(L, NP, LDF, lane)) {
+        // H = S_1 - m m^T / S_00 (the border of phi_0 = 1 removed) and the
+        // upper triangle of X mirrored from the lower.
+        const float i00 = 1.f / smu[0];
+        for (int p = lane; p < NP1 * (NP1 + 1) / 2; p += 32) {
+            const int pij = s_pij[p], i = pij & 255, j = pij >> 8;
+            L[i * LDH + j] -= smu[i + 1] * smu[j + 1] * i00;
+        }
+        for (int p = lane; p < NP * (NP + 1) / 2; p += 32) {
+            const int pij = s_pij35[p], i = pij & 255, j = pij >> 8;
+            Y[j * LDF + i] = Y[i * LDF + j];
+        }
+        __syncwarp();
+        // Cholesky of S = E[phi phi^T] by bordering: phi_0 = 1 gives
+        // chol(S) = [[sqrt S00, 0], [m / sqrt S00, chol(S_1 - m m^T / S00)]].
+        if (!(smu[0] > 0.f) || !reg_cholesky34_store(L, lane)) {
             if (lane == 0) A.speed[cell] = fmaxf(fabsf(wx + sx * A.xmax), fabsf(wx - sx * A.xmax));
             continue;
         }
-        // Y <- L^{-1} Y (columns), then C = L^{-1} Y^T (columns of Y^T = rows of Y)
-        for (int j = lane; j < NP; j += 32)
-            for (int i = 0; i < NP; ++i) {
-                float s = Y[i * LDF + j];
-                for (int k = 0; k < i; ++k) s -= L[i * LDF + k] * Y[k * LDF + j];
-                Y[i * LDF + j] = s / L[i * LDF + i];
-            }
+        // Column 0 of chol(S) and the inverse pivots, once.
+        const float l00 = sqrtf(smu[0]);
+        for (int i = lane; i < NP; i += 32) {
+            sl0[i] = i == 0 ? l00 : smu[i] / l00;
+            sinv[i] = 1.f / (i == 0 ? l00 : L[(i - 1) * LDH + (i - 1)]);
+        }
         __syncwarp();
-        for (int j = lane; j < NP; j += 32)
-            for (int i = 0; i < NP; ++i) {
-                float s = Y[j * LDF + i];
-                for (int k = 0; k < i; ++k) s -= L[i * LDF + k] * Cm[k * LDF + j];
-                Cm[i * LDF + j] = s / L[i * LDF + i];
+        // Right-looking column solves: Y <- Ls^{-1} Y, then C = Ls^{-1} Y^T
+        // (C overwrites Y after an in-place transpose by pairwise swaps).
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 1) {
+                for (int p = lane; p < NP * (NP + 1) / 2; p += 32) {
+                    const int pij = s_pij35[p], i = pij & 255, j = pij >> 8;
+                    if (j < i) {
+                        const float t = Y[i * LDF + j];
+                        Y[i * LDF + j] = Y[j * LDF + i];
+                        Y[j * LDF + i] = t;
+                    }
+                }
+                __syncwarp();
             }
-        __syncwarp();
-        for (int p = lane; p < NP * NP; p += 32) {
-            const int i = p / NP, j = p % NP;
+            for (int j = lane; j < NP; j += 32) {
+                // k = 0: the bordered column
+                const float y0 = Y[j] * sinv[0];
+                Y[j] = y0;
+                for (int i = 1; i < NP; ++i) Y[i * LDF + j] -= sl0[i] * y0;
+                for (int k = 1; k < NP; ++k) {
+                    const float yk = Y[k * LDF + j] * sinv[k];
+                    Y[k * LDF + j] = yk;
+                    const float *Lk = L + (k - 1);
+                    for (int i = k + 1; i < NP; ++i) Y[i * LDF + j] -= Lk[(i - 1) * LDH] * yk;
+                }
+            }
+            __syncwarp();
+        }
+        float *Cm = Y;
+        for (int p = lane; p < NP * (NP + 1) / 2; p += 32) {
+            const int pij = s_pij35[p], i = pij & 255, j = pij >> 8;
             if (j < i) {
                 const float s = 0.5f * (Cm[i * LDF + j] + Cm[j * LDF + i]);
                 Cm[i * LDF + j] = s;
@@ -218,7 +254,18 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
             if (lane + 32 < NP) sv[lane + 32] = v1;
             __syncwarp();
             float w0 = 0.f, w1 = 0.f;
-            for (int j = 0; j < NP; ++j) w0 += Cm[j * LDF + lane] * sv[j];
+            {
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    a0 += Cm[j * LDF + lane] * sv[j];
+                    a1 += Cm[(j + 1) * LDF + lane] * sv[j + 1];
+                    a2 += Cm[(j + 2) * LDF + lane] * sv[j + 2];
+                    a3 += Cm[(j + 3) * LDF + lane] * sv[j + 3];
+                }
+                for (int j = 32; j < NP; ++j) a0 += Cm[j * LDF + lane] * sv[j];
+                w0 = (a0 + a1) + (a2 + a3);
+            }
             if (lane + 32 < NP) {
                 const int i = lane + 32;
                 for (int j = 0; j < NP; ++j) w1 += Cm[j * LDF + i] * sv[j];
@@ -249,7 +296,7 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
 template <int N>
 int launch_flux(mem_ctx *ctx, const FluxArgs &a, cudaStream_t st) {
     using Cf = FluxCfg<N>;
-    const size_t smem = sizeof(float) * (N * MEM_HE_STRIDE + 16 + 224 + 56) + sizeof(float) * FWARPS * Cf::WARP_FLOATS;
+    const size_t smem = sizeof(float) * (N * MEM_HE_STRIDE + 16 + 224 + 56 + 596 + 632) + sizeof(float) * FWARPS * Cf::WARP_FLOATS;
     static int configured = 0;
     if (!configured) {
         MEM_CUDA_TRY(cudaFuncSetAttribute(k_fused_flux<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -44,49 +44,6 @@ struct FusedArgs {
     mem_solve_opts o;
 };
 
-// Eight right-looking Cholesky steps k = K0 .. K0+7 on the register columns
-// (see reg_chol_solve34).  Rows i <= K0 are finished before the block starts,
-// so the row loop runs statically over K0+1 .. 33; within the block the rows
-// i <= k are masked by predication, not by branches, so that all shuffles of
-// one step can be in flight together.
-template <int K0>
-__device__ __forceinline__ bool chol_block8(float (&col)[NP1], float &t00, float &t10, float &t11, float &bb,
-                                            float &b32, float &b33, float &myinv, float &myw, int lane) {
-#pragma unroll 1
-    for (int kk = 0; kk < 8; ++kk) {
-        const int k = K0 + kk;
-        float s1[4], s2[2];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) s1[m] = (kk & 1) ? col[K0 + 2 * m + 1] : col[K0 + 2 * m];
-#pragma unroll
-        for (int m = 0; m < 2; ++m) s2[m] = (kk & 2) ? s1[2 * m + 1] : s1[2 * m];
-        const float ck = (kk & 4) ? s2[1] : s2[0];  // this lane's A_kj
-        const float d = __shfl_sync(0xffffffffu, ck, k);
-        if (!(d > 0.f) || !isfinite(d)) return false;
-        const float inv = rsqrtf(d), inv2 = inv * inv;
-        const float c = ck * inv2;
-        const float wk = __shfl_sync(0xffffffffu, bb, k) * inv;
-        const bool upd = lane > k;
-        float r32 = 0.f, r33 = 0.f;
-#pragma unroll
-        for (int i = K0 + 1; i < NP1; ++i) {
-            const float raw = __shfl_sync(0xffffffffu, col[i], k);
-            const float nv = fmaf(-raw, c, col[i]);
-            col[i] = (upd && i > k) ? nv : col[i];
-            if (i == 32) r32 = raw;
-            if (i == 33) r33 = raw;
-        }
-        if (upd) bb = fmaf(-ck * inv, wk, bb);
-        b32 = fmaf(-r32 * inv, wk, b32);
-        b33 = fmaf(-r33 * inv, wk, b33);
-        t00 = fmaf(-r32 * r32, inv2, t00);
-        t10 = fmaf(-r33 * r32, inv2, t10);
-        t11 = fmaf(-r33 * r33, inv2, t11);
-        if (lane == k) { myinv = inv; myw = wk; }
-    }
-    return true;
-}
-
 // Solve (H + lam I) x = rhs by a register-resident Cholesky factorisation,
 // H the 34 x 34 SPD matrix whose lower triangle is in shared memory
 // (row-major, leading dimension LDH).  Lane j < 32 holds column j of the

@@ -62,8 +62,8 @@ __device__ __forceinline__ int sturm_count(const float *a, const float *b, int m
     float q = 1.f;
     for (int i = 0; i < m; ++i) {
         const float bb = i ? b[i - 1] * b[i - 1] : 0.f;
-        q = a[i] - x - (i ? bb / q : 0.f);
-        if (fabsf(q) < 1e-30f) q = -1e-30f;
+        q = a[i] - x - (i ? __fdividef(bb, q) : 0.f);
+        if (fabsf(q) < 1e-20f) q = -1e-20f;
         cnt += q < 0.f;
     }
     return cnt;

@@ -128,6 +128,20 @@ int mem_solve(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_
 int mem_flux(mem_ctx *ctx, const float *M, const float *beta, const float *gauge, float *F,
              float *speed, int64_t B, void *stream);
 
+/* mem_flux for axisymmetric cells: beta and the gauge symmetric under
+ * u_y -> -u_y and under u_z -> -u_z (w_y = w_z = 0, beta_abc = 0 for odd b or
+ * odd c), as every cell of a one-dimensional problem is.  Then E[phi phi^T]
+ * and E[u_x phi phi^T] are block-diagonal over the parity classes of (b, c)
+ * -- blocks of 14 (even, even; phi_0 included), 8 (odd, even), 8 (even, odd;
+ * the same spectrum as (odd, even) by y <-> z) and 5 (odd, odd) statistics --
+ * and the speed is the largest over the blocks (Eq. "The lax F" restricted to
+ * the invariant subspaces).  The couplings between classes, which vanish for
+ * an exactly symmetric cell, are not read.  Same arguments and results as
+ * mem_flux; F is computed in full.  At quad_order 8 and 12 it uses no
+ * scratch; other orders take mem_flux's full pencil (and its scratch). */
+int mem_flux_axisym(mem_ctx *ctx, const float *M, const float *beta, const float *gauge, float *F,
+                    float *speed, int64_t B, void *stream);
+
 /* mem_flux without any allocation.  The paper has no counterpart: this is a
  * service of the library for callers that cannot allocate device memory when
  * they need fluxes -- for example a caller whose allocator already owns the

@@ -181,6 +181,46 @@ static void build_hess_slots(const std::vector<int> &off, const std::vector<int2
         for (int t = 0; t < (int)per[l].size(); ++t) slots[(size_t)t * 32 + l] = per[l][t];
 }
 
+// Axisymmetric cells (invariant under u_y -> -u_y and u_z -> -u_z, as every
+// 1D-shock cell is) make E[phi phi^T] and E[ubar_x phi phi^T] block-diagonal
+// over the parity classes of (b, c): even/even (14 statistics, phi_0
+// included), odd/even (8), even/odd (8, the same spectrum by y <-> z) and
+// odd/odd (5).  These slots assemble the blocks ee, oe and oo (lower
+// triangles, leading dimension 16) at work offsets S: 0, 512, 768 and
+// X: 256, 640, 848 of the flux kernel.
+static void build_axi_slots(const std::vector<int> &soff, const std::vector<int2> &sterms, const std::vector<int> &xoff,
+                            const std::vector<int2> &xterms, std::vector<int2> &slots, int &nslots) {
+    const int cls_of_block[3] = {0, 1, 3}, oS[3] = {0, 512, 768}, oX[3] = {256, 640, 848};
+    struct Entry { const std::vector<int2> *terms; int t0, t1, dst; };
+    std::vector<Entry> ent;
+    for (int blk = 0; blk < 3; ++blk) {
+        std::vector<int> mem;
+        for (int k = 0; k < NP; ++k)
+            if (((exp_b(k) & 1) | ((exp_c(k) & 1) << 1)) == cls_of_block[blk]) mem.push_back(k);
+        for (int a = 0; a < (int)mem.size(); ++a)
+            for (int b = 0; b <= a; ++b) {
+                const int i = mem[a], j = mem[b], P = i * (i + 1) / 2 + j;
+                ent.push_back({&sterms, soff[P], soff[P + 1], oS[blk] + a * 16 + b});
+                ent.push_back({&xterms, xoff[P], xoff[P + 1], oX[blk] + a * 16 + b});
+            }
+    }
+    std::vector<std::vector<int2>> per(32);
+    for (size_t e = 0; e < ent.size(); ++e) {
+        auto &v = per[e % 32];
+        for (int t = ent[e].t0; t < ent[e].t1; ++t) {
+            int2 sl = (*ent[e].terms)[t];
+            sl.x = (sl.x & 255) | (ent[e].dst << 8);
+            if (t == ent[e].t1 - 1) sl.x |= (int)0x80000000;
+            v.push_back(sl);
+        }
+    }
+    nslots = 0;
+    for (auto &v : per) nslots = std::max(nslots, (int)v.size());
+    slots.assign((size_t)nslots * 32, int2{0, 0});
+    for (int l = 0; l < 32; ++l)
+        for (int t = 0; t < (int)per[l].size(); ++t) slots[(size_t)t * 32 + l] = per[l][t];
+}
+
 template <typename T>
 static int upload(T **dst, const std::vector<T> &src) {
     if (cudaMalloc((void **)dst, sizeof(T) * std::max<size_t>(1, src.size())) != cudaSuccess) return MEM_ENOMEM;
@@ -259,6 +299,10 @@ int mem_init(int degree, int quad_order, mem_ctx **out) {
     std::vector<int2> sterms;
     build_lin_terms(1, false, soff, sterms);  // E[phi_i phi_j], i >= j >= 1
     build_hess_slots(soff, sterms, fslots, ctx->n_flux_slots, &xoff, &xterms);
+    std::vector<int> s0off;
+    std::vector<int2> s0terms, aslots;
+    build_lin_terms(0, false, s0off, s0terms);
+    build_axi_slots(s0off, s0terms, xoff, xterms, aslots, ctx->n_axi_slots);
     // Flux slots carry their destination in the flux kernel's per-warp work
     // area instead of the entry number: entries 0..594 (E[phi_i phi_j],
     // i >= j >= 1) go to H[(i-1) * 35 + (j-1)]; entries 595..1224
@@ -288,6 +332,7 @@ int mem_init(int degree, int quad_order, mem_ctx **out) {
     if (!rc) rc = upload(&ctx->d_lin_terms, terms);
     if (!rc) rc = upload(&ctx->d_hess_slots, slots);
     if (!rc) rc = upload(&ctx->d_flux_slots, fslots);
+    if (!rc) rc = upload(&ctx->d_axi_slots, aslots);
     if (!rc) rc = upload(&ctx->d_xlin_off, xoff);
     if (!rc) rc = upload(&ctx->d_xlin_terms, xterms);
     ctx->n_lin_terms = (int)terms.size();
@@ -301,7 +346,7 @@ void mem_destroy(mem_ctx *ctx) {
     if (!ctx) return;
     cudaDeviceSynchronize();
     void *ptrs[] = {ctx->d_phiT, ctx->d_logw, ctx->d_tab_solve, ctx->d_tab_flux, ctx->d_he1d, ctx->d_x1d,
-                    ctx->d_logw1d, ctx->d_lin_off, ctx->d_lin_terms, ctx->d_hess_slots, ctx->d_flux_slots, ctx->d_xlin_off, ctx->d_xlin_terms,
+                    ctx->d_logw1d, ctx->d_lin_off, ctx->d_lin_terms, ctx->d_hess_slots, ctx->d_flux_slots, ctx->d_axi_slots, ctx->d_xlin_off, ctx->d_xlin_terms,
                     ctx->scratch};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -331,7 +376,17 @@ int mem_flux(mem_ctx *ctx, const float *M, const float *beta, const float *gauge
     if (B == 0) return MEM_OK;
     if (!M || !beta || !gauge) return MEM_EINVAL;
     if (mem_host::flux_fused_available(ctx))
-        return mem_host::flux_fused(ctx, M, beta, gauge, F, speed, B, (cudaStream_t)stream);
+        return mem_host::flux_fused(ctx, M, beta, gauge, F, speed, B, (cudaStream_t)stream, false);
+    return mem_host::flux(ctx, M, beta, gauge, F, speed, B, (cudaStream_t)stream);
+}
+
+int mem_flux_axisym(mem_ctx *ctx, const float *M, const float *beta, const float *gauge, float *F, float *speed,
+                    int64_t B, void *stream) {
+    if (!ctx || B < 0) return MEM_EINVAL;
+    if (B == 0) return MEM_OK;
+    if (!M || !beta || !gauge) return MEM_EINVAL;
+    if (mem_host::flux_fused_available(ctx))
+        return mem_host::flux_fused(ctx, M, beta, gauge, F, speed, B, (cudaStream_t)stream, true);
     return mem_host::flux(ctx, M, beta, gauge, F, speed, B, (cudaStream_t)stream);
 }
 

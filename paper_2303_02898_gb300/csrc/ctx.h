@@ -34,6 +34,8 @@ struct mem_ctx {
     int n_hess_slots = 0;
     int2 *d_flux_slots = nullptr;  // [n_flux_slots][32] E[phi phi^T] and E[ubar_x phi phi^T] terms
     int n_flux_slots = 0;
+    int2 *d_axi_slots = nullptr;   // [n_axi_slots][32] the same, parity blocks of axisymmetric cells
+    int n_axi_slots = 0;
     int *d_xlin_off = nullptr;     // [631]  flux-Jacobian terms (packed i>=j>=0)
     int2 *d_xlin_terms = nullptr;
     float xmax = 0.f;              // largest 1D node
@@ -55,7 +57,7 @@ int flux(mem_ctx *ctx, const float *M, const float *beta, const float *g, float 
 int flux_bufs(mem_ctx *ctx, const float *M, const float *beta, const float *g, float *F, float *speed, int64_t B,
               float *sigma, float *mom, cudaStream_t st);
 int flux_fused(mem_ctx *ctx, const float *M, const float *beta, const float *g, float *F, float *speed,
-               int64_t B, cudaStream_t st);
+               int64_t B, cudaStream_t st, bool axisym);
 bool flux_fused_available(const mem_ctx *ctx);
 int gauge_hermite(mem_ctx *ctx, const float *M_in, const float *g_in, float *g_out, float *M_out,
                   float *beta_inout, int64_t B, int axisym, cudaStream_t st);

@@ -46,10 +46,93 @@ struct FluxArgs {
     const float *he1d, *logw1d;
     const int2 *slots;
     int n_slots;
+    const int2 *aslots;
+    int n_aslots;
     float xmax;
 };
 
-template <int N>
+// Extreme generalised eigenvalues of one small symmetric-definite pencil
+// (X, S), n <= 16, lower triangles in shared memory with leading dimension
+// 16: Cholesky S = L L^T (in place), C = L^{-1} X L^{-T} by right-looking
+// column solves (lane j < n owns column j) and a pairwise transpose, Lanczos
+// without re-orthogonalisation and Sturm multisection.  Returns false if S
+// is not numerically positive definite.
+__device__ __forceinline__ bool small_pencil_extremes(float *S, float *X, int n, float *al, float *bt, float *sv,
+                                                      int lane, float &lo, float &hi) {
+    constexpr int LD = 16;
+    for (int p = lane; p < n * (n + 1) / 2; p += 32) {  // mirror X
+        int i = 0;
+        while ((i + 1) * (i + 2) / 2 <= p) ++i;
+        const int j = p - i * (i + 1) / 2;
+        X[j * LD + i] = X[i * LD + j];
+    }
+    __syncwarp();
+    if (!warp_cholesky(S, n, LD, lane)) return false;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            for (int p = lane; p < n * (n + 1) / 2; p += 32) {
+                int i = 0;
+                while ((i + 1) * (i + 2) / 2 <= p) ++i;
+                const int j = p - i * (i + 1) / 2;
+                if (j < i) {
+                    const float t = X[i * LD + j];
+                    X[i * LD + j] = X[j * LD + i];
+                    X[j * LD + i] = t;
+                }
+            }
+            __syncwarp();
+        }
+        if (lane < n) {
+            for (int k = 0; k < n; ++k) {
+                const float yk = X[k * LD + lane] / S[k * LD + k];
+                X[k * LD + lane] = yk;
+                for (int i = k + 1; i < n; ++i) X[i * LD + lane] -= S[i * LD + k] * yk;
+            }
+        }
+        __syncwarp();
+    }
+    // symmetrise C (in X) and run Lanczos (lane i < n holds v_i)
+    float cn = 0.f;
+    for (int p = lane; p < n * n; p += 32) {
+        const int i = p / n, j = p % n;
+        if (j < i) {
+            const float s = 0.5f * (X[i * LD + j] + X[j * LD + i]);
+            X[i * LD + j] = s;
+            X[j * LD + i] = s;
+        }
+        cn = fmaxf(cn, fabsf(X[i * LD + j]));
+    }
+    const float cnorm = warp_max(cn) + 1e-30f;
+    __syncwarp();
+    float v = lane < n ? rsqrtf((float)n) : 0.f, vp = 0.f, bprev = 0.f;
+    int m = 0;
+    for (int k = 0; k < n; ++k) {
+        sv[lane] = v;
+        __syncwarp();
+        float w = 0.f;
+        if (lane < n)
+            for (int j = 0; j < n; ++j) w += X[j * LD + lane] * sv[j];
+        __syncwarp();
+        w -= bprev * vp;
+        const float a = warp_sum(w * v);
+        w -= a * v;
+        if (lane == 0) al[k] = a;
+        const float bk = sqrtf(warp_sum(w * w));
+        m = k + 1;
+        if (k + 1 == n || bk <= 1e-6f * cnorm) break;
+        if (lane == 0) bt[k] = bk;
+        vp = v;
+        v = w / bk;
+        bprev = bk;
+    }
+    __syncwarp();
+    hi = warp_tridiag_extreme(al, bt, m, true, lane);
+    lo = warp_tridiag_extreme(al, bt, m, false, lane);
+    __syncwarp();
+    return true;
+}
+
+template <int N, bool AXI>
 __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
     using C = FusedCfg<N>;
     using Cf = FluxCfg<N>;
@@ -162,6 +245,42 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
             }
         }
         if (!A.speed) continue;
+        if (AXI) {
+            // Axisymmetric cell: the pencil is block-diagonal over the parity
+            // classes of (b, c); the spectral radius is the largest over the
+            // blocks ee (14, phi_0 included), oe (8; eo has the same
+            // spectrum) and oo (5).
+            {
+                float acc = 0.f;
+#pragma unroll 4
+                for (int t = 0; t < A.n_aslots; ++t) {
+                    const int2 sl = __ldg(&A.aslots[t * 32 + lane]);
+                    acc = fmaf(__int_as_float(sl.y), smu[sl.x & 255], acc);
+                    if (sl.x < 0) {
+                        work[(sl.x >> 8) & 0xffff] = acc;
+                        acc = 0.f;
+                    }
+                }
+            }
+            __syncwarp();
+            float mlo, mhi, lo, hi;
+            bool ok = small_pencil_extremes(work, work + 256, 14, al, bt, sv, lane, mlo, mhi);
+            if (ok) ok = small_pencil_extremes(work + 512, work + 640, 8, al, bt, sv, lane, lo, hi);
+            if (ok) {
+                mlo = fminf(mlo, lo);
+                mhi = fmaxf(mhi, hi);
+                ok = small_pencil_extremes(work + 768, work + 848, 5, al, bt, sv, lane, lo, hi);
+            }
+            if (ok) {
+                mlo = fminf(mlo, lo);
+                mhi = fmaxf(mhi, hi);
+            }
+            if (lane == 0)
+                A.speed[cell] = ok ? fmaxf(fabsf(wx + sx * mhi), fabsf(wx + sx * mlo))
+                                   : fmaxf(fabsf(wx + sx * A.xmax), fabsf(wx - sx * A.xmax));
+            __syncwarp();
+            continue;
+        }
         // ---- E[phi phi^T] without its phi_0 border, and E[ubar_x phi phi^T]
         // (lower triangles), from the linearisation terms; every slot carries
         // the shared-memory offset of its entry.
@@ -293,22 +412,22 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
     }
 }
 
-template <int N>
+template <int N, bool AXI>
 int launch_flux(mem_ctx *ctx, const FluxArgs &a, cudaStream_t st) {
     using Cf = FluxCfg<N>;
     const size_t smem = sizeof(float) * (N * MEM_HE_STRIDE + 16 + 224 + 56 + 596 + 632) + sizeof(float) * FWARPS * Cf::WARP_FLOATS;
     static int configured = 0;
     if (!configured) {
-        MEM_CUDA_TRY(cudaFuncSetAttribute(k_fused_flux<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MEM_CUDA_TRY(cudaFuncSetAttribute(k_fused_flux<N, AXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = 1;
     }
     int sms = 0, per_sm = 0;
     MEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-    MEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_flux<N>, FWARPS * 32, smem));
+    MEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_flux<N, AXI>, FWARPS * 32, smem));
     if (per_sm < 1) return MEM_ECUDA;
     const int64_t want = (a.B + FWARPS - 1) / FWARPS;
     const int grid = (int)std::min<int64_t>(want, (int64_t)sms * per_sm);
-    k_fused_flux<N><<<grid, FWARPS * 32, smem, st>>>(a);
+    k_fused_flux<N, AXI><<<grid, FWARPS * 32, smem, st>>>(a);
     MEM_CUDA_TRY(cudaGetLastError());
     return MEM_OK;
 }
@@ -320,14 +439,17 @@ namespace mem_host {
 bool flux_fused_available(const mem_ctx *ctx) { return ctx->n1d == 8 || ctx->n1d == 12; }
 
 int flux_fused(mem_ctx *ctx, const float *M, const float *beta, const float *g, float *F, float *speed, int64_t B,
-               cudaStream_t st) {
+               cudaStream_t st, bool axisym) {
     FluxArgs a;
     a.M = M; a.beta = beta; a.gauge = g; a.F = F; a.speed = speed; a.B = B;
     a.he1d = ctx->d_he1d; a.logw1d = ctx->d_logw1d; a.slots = ctx->d_flux_slots; a.n_slots = ctx->n_flux_slots;
+    a.aslots = ctx->d_axi_slots; a.n_aslots = ctx->n_axi_slots;
     a.xmax = ctx->xmax;
-    switch (ctx->n1d) {
-        case 8: return launch_flux<8>(ctx, a, st);
-        case 12: return launch_flux<12>(ctx, a, st);
+    switch (ctx->n1d * 2 + (axisym ? 1 : 0)) {
+        case 16: return launch_flux<8, false>(ctx, a, st);
+        case 17: return launch_flux<8, true>(ctx, a, st);
+        case 24: return launch_flux<12, false>(ctx, a, st);
+        case 25: return launch_flux<12, true>(ctx, a, st);
         default: return MEM_EINVAL;
     }
 }

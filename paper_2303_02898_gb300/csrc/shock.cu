@@ -367,7 +367,7 @@ int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **o
         rc = solve_fused(ctx, b->M, b->beta, b->status, b->iters, (int64_t)NT, o, 0, b->interior);
     }
     if (!rc) rc = (ps[0].impl == MEM_IMPL_FUSED && flux_fused_available(ctx))
-                      ? flux_fused(ctx, b->M, b->beta, b->g, b->F, b->speed, (int64_t)NT, 0)
+                      ? flux_fused(ctx, b->M, b->beta, b->g, b->F, b->speed, (int64_t)NT, 0, true)
                       : flux_bufs(ctx, b->M, b->beta, b->g, b->F, b->speed, (int64_t)NT, b->sigma, b->mom, 0);
     if (rc || cudaDeviceSynchronize() != cudaSuccess) { batch_free(b); return rc ? rc : MEM_ECUDA; }
     *out = b;
@@ -390,7 +390,7 @@ int batch_enqueue_step(ShockBatch *b, cudaStream_t st) {
                  : solve_fused(b->ctx, b->M, b->beta, b->status, b->iters, NT, o, st, b->interior);
     if (rc) return rc;
     rc = (o.impl == MEM_IMPL_FUSED && flux_fused_available(b->ctx))
-             ? flux_fused(b->ctx, b->M, b->beta, b->g, b->F, b->speed, NT, st)
+             ? flux_fused(b->ctx, b->M, b->beta, b->g, b->F, b->speed, NT, st, true)
              : flux_bufs(b->ctx, b->M, b->beta, b->g, b->F, b->speed, NT, b->sigma, b->mom, st);
     if (rc) return rc;
     k_stencil<<<nb, 128, 0, st>>>(b->M, b->F, b->g, b->speed, b->Mn, b->pid, b->interior, b->prm, b->sc, NT);

@@ -64,6 +64,8 @@ def lib():
             getattr(L, name).restype = ctypes.c_int
         L.mem_solve.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(SolveOpts), _P]
         L.mem_flux.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P]
+        L.mem_flux_axisym.restype = ctypes.c_int
+        L.mem_flux_axisym.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P]
         L.mem_flux_noalloc.restype = ctypes.c_int
         L.mem_flux_noalloc.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P]
         L.mem_gauge_hermite.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_int, _P]
@@ -148,6 +150,12 @@ class Context:
         rc = lib().mem_flux(self.h, _ptr(M), _ptr(beta), _ptr(gauge), _ptr(F), _ptr(speed), M.shape[0],
                             _stream(stream))
         _check(rc, "mem_flux")
+
+    def flux_axisym(self, M, beta, gauge, F=None, speed=None, stream=None):
+        """mem_flux_axisym: flux() for cells symmetric in u_y and u_z."""
+        rc = lib().mem_flux_axisym(self.h, _ptr(M), _ptr(beta), _ptr(gauge), _ptr(F), _ptr(speed), M.shape[0],
+                                   _stream(stream))
+        _check(rc, "mem_flux_axisym")
 
     def flux_noalloc(self, M, beta, gauge, F=None, speed=None, stream=None):
         """mem_flux_noalloc: as flux(), with library-resident working memory

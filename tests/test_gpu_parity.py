@@ -234,6 +234,56 @@ def test_flux_and_speed_match_oracle(O, mem, dev, order, ctx8, ctx12):
     assert np.allclose(np64(spx), exp, rtol=1e-5)
 
 
+@pytest.mark.parametrize("order", [8, 12])
+def test_axisym_flux_matches_full_pencil(O, mem, dev, order, ctx8, ctx12):
+    """mem_flux_axisym on cells symmetric in u_y and u_z: the largest speed
+    over the parity blocks of (b mod 2, c mod 2) is the full-pencil speed
+    (Eq. "The lax F"), against mem_flux and the FP64 oracle."""
+    ctx = ctx8 if order == 8 else ctx12
+    rng = np.random.default_rng(50 + order)
+    B = 70
+    idx = O.basis_index()
+    deg = idx.sum(1)
+    odd = (idx[:, 1] % 2 == 1) | (idx[:, 2] % 2 == 1)
+    f = 1.0 if order == 8 else 0.3
+    scale = np.where(deg <= 2, 0.1, np.where(deg == 3, 0.03 * f, 0.01 * f))
+    beta = rng.normal(0, 1, (B, 35)) * scale
+    beta[:, odd] = 0.0
+    beta[:, 0] = np.exp(rng.uniform(-0.5, 0.5, B))
+    M = np.zeros((B, 35))
+    M[:, 0] = beta[:, 0]
+    g = random_gauges(rng, B)
+    g[:, 1:3] = 0.0
+    Mt, bt, gt = T32(M, dev), T32(beta, dev), T32(g, dev)
+    F1, F2 = torch.zeros(B, 35, device=dev), torch.zeros(B, 35, device=dev)
+    s1, s2 = torch.zeros(B, device=dev), torch.zeros(B, device=dev)
+    ctx.flux(Mt, bt, gt, F1, s1)
+    ctx.flux_axisym(Mt, bt, gt, F2, s2)
+    F1, F2, s1, s2 = np64(F1), np64(F2), np64(s1), np64(s2)
+    assert np.abs(F1 - F2).max() <= 1e-6 * np.abs(F1).max()
+    assert np.allclose(s2, s1, rtol=2e-5, atol=0)
+    bf, gf = np64(bt), np64(gt)
+    for c in range(B):
+        _, so, _, _ = O.flux(order, bf[c], gf[c], M[c, 0])
+        assert s2[c] == pytest.approx(so, rel=2e-5), (c, s2[c], so)
+
+
+def test_axisym_flux_on_shock_states(mem, ctx8, dev):
+    """States of a Mach-3 shock (tanh initial state, 5 steps; odd-parity
+    parameters are zero only to solver rounding): parity-block and
+    full-pencil speeds agree."""
+    sh = mem.Shock(ctx8, mach=3.0, ncells=48, xl=-15.0, xr=15.0, ic=1, graph=0)
+    sh.step(5)
+    st = sh.get()
+    sh.close()
+    Mt, bt, gt = T32(st["M"], dev), T32(st["beta"], dev), T32(st["g"], dev)
+    B = Mt.shape[0]
+    s1, s2 = torch.zeros(B, device=dev), torch.zeros(B, device=dev)
+    ctx8.flux(Mt, bt, gt, None, s1)
+    ctx8.flux_axisym(Mt, bt, gt, None, s2)
+    assert np.allclose(np64(s2), np64(s1), rtol=2e-5, atol=0)
+
+
 # ------------------------------------------------------------------ shock
 def _norm(q, a, b):
     return (q - a) / (b - a)

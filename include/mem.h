@@ -95,6 +95,34 @@ const char *mem_version(void);
  * Appendix B (statistics). */
 int mem_init(int degree, int quad_order, mem_ctx **out);
 
+/* Create a context whose quadrature is fixed in velocity space, the rule of
+ * the paper's shock computations (Section 3.1, Eq. "Numerical integration":
+ * fixed nodes u_q and weights w_q; Appendix D: integration domain
+ * (u_x, u_r) in [a_x, b_x] x [0, b_r], split into equal blocks, each
+ * integrated by Gauss-Legendre):
+ *   u_x in [ax, bx]: nbx equal blocks of ng Gauss-Legendre points;
+ *   u_r in [0, br]:  nbr equal blocks of ng Gauss-Legendre points (weight
+ *                    u_r), times K equispaced azimuths 2 pi k / K (exact for
+ *                    the azimuthal dependence of every product of two
+ *                    statistics when K >= 9).
+ * A cell of gauge g sees the nodes at ubar = (u - w) / s; beta keeps its
+ * meaning (relative to the gauge's Gaussian).  Unlike the Gauss-Hermite rule
+ * of mem_init, whose nodes move with each cell's gauge, these nodes resolve a
+ * narrow upstream beam inside a hot shocked cell, which strong shocks (Mach
+ * 10) need.  (ax, bx, br) is the domain of mem_solve_gauge and mem_flux;
+ * shock problems on such a context take their own domain from their
+ * Rankine-Hugoniot states (mem_shock_params.na, nb, nr).  Limits: degree 4,
+ * ng <= 16, K <= 64, nbx ng <= 256, nbr ng K <= 1024.  Synchronous.
+ * mem_solve, mem_flux_noalloc and the plain back-end are not available on
+ * such a context (MEM_EINVAL). */
+int mem_init_velocity(int degree, int nbx, int nbr, int ng, int K, double ax, double bx, double br,
+                      mem_ctx **out);
+
+/* Shape (nbx, nbr, ng, K) and default domain (a_x, b_x, b_r) of a
+ * velocity-space context (host arrays of 4 and 3, either may be NULL);
+ * MEM_EINVAL for a Gauss-Hermite context. */
+int mem_velocity_rule(const mem_ctx *ctx, int32_t *shape, double *domain);
+
 /* Release everything the context owns (synchronises the device first). */
 void mem_destroy(mem_ctx *ctx);
 
@@ -116,6 +144,14 @@ int mem_quad_order(const mem_ctx *ctx);
  * Newton pass.  Returns MEM_EINVAL for B < 0 or NULL arrays with B > 0. */
 int mem_solve(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters,
               int64_t B, const mem_solve_opts *opts, void *stream);
+
+/* mem_solve for any context, with the cells' gauges gauge dev [B][6]: a
+ * velocity-space rule (mem_init_velocity) places its nodes in each cell
+ * through the gauge; on a Gauss-Hermite context the gauge is not read and
+ * the call is mem_solve.  The velocity-space solve runs one thread block per
+ * cell (Algorithm 1 in FP32, no scratch); opts->impl is not read. */
+int mem_solve_gauge(mem_ctx *ctx, const float *M, float *beta, const float *gauge, int32_t *status,
+                    int32_t *iters, int64_t B, const mem_solve_opts *opts, void *stream);
 
 /* Flux and characteristic speed of B cells (Eq. "The ME equation" subeq. 3
  * and Eq. "The lax F"):
@@ -206,6 +242,11 @@ typedef struct {
     int32_t graph;     /* 1: capture the time step in a CUDA graph          */
     float tol;         /* Algorithm 1 tolerance (1e-8)                      */
     int32_t maxI;      /* Algorithm 1 iteration cap (500)                   */
+    double na, nb, nr; /* velocity-space rule only: the problem's domain is
+                          u_x in [min(v_+ - na c_+, v_- - na c_-),
+                                  max(v_- + nb c_-, v_+ + nb c_+)],
+                          u_r in [0, nr max(c_-, c_+)], c = sqrt(T) of the
+                          Rankine-Hugoniot states (Appendix D; 5, 5, 5)   */
 } mem_shock_params;
 
 void mem_shock_params_default(mem_shock_params *p);

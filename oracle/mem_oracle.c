@@ -169,7 +169,7 @@ int or_gh_rule(int n, double *x, double *w) {
 
 /* ------------------------------------------------------------------------ */
 /* Quadrature rule cache: tensor n^3 nodes ubar_q, log w_q, phi(ubar_q). */
-typedef struct { int n, Q; double *u; double *logw; double *phi; } rule_t;
+typedef struct { int n, Q, phys; double *u; double *logw; double *phi; } rule_t;
 static rule_t g_rules[NMAXQ + 1];
 
 /* Block Gauss-Legendre tensor rules on a box in the gauge frame (rule ids
@@ -224,8 +224,65 @@ int or_set_box_rule(int id, int nbx, int nbr, int ng, double Lx, double Lr) {
     return Q;
 }
 
+/* Velocity-space rules (rule ids 200..215, registered by
+ * or_set_velocity_rule): the nodes are fixed in the lab frame, as in the
+ * paper's shock computations (Section 3.1, Eq. "Numerical integration", with
+ * the integration domain (u_x, u_r) in [a_x, b_x] x [0, b_r] of Appendix D).
+ * u_x: [a_x, b_x] in nbx equal blocks of ng Gauss-Legendre points; u_r:
+ * [0, b_r] in nbr equal blocks of ng Gauss-Legendre points with the polar
+ * weight u_r; azimuth: K equispaced angles 2 pi k / K (trapezoid, exact for
+ * trigonometric polynomials of degree < K).  Nodes u_q = (u_x, u_r cos t,
+ * u_r sin t), weights w_q (no base measure).  In a cell of gauge g the rule
+ * is used through ubar_q = (u_q - w) / s with log weight
+ * log w_q - |ubar_q|^2 / 2, so that beta keeps its meaning (relative to the
+ * gauge's Gaussian; constant factors cancel in Z). */
+static rule_t g_vel_rules[16];
+
+int or_set_velocity_rule(int id, double ax, double bx, int nbx, double br, int nbr, int ng, int K) {
+    if (id < 200 || id > 215 || ng < 1 || ng > 16 || nbx < 1 || nbr < 1 || K < 1 || nbx * ng > 512 ||
+        nbr * ng > 512 || K > 64 || !(bx > ax) || !(br > 0.0))
+        return -1;
+    rule_t *r = &g_vel_rules[id - 200];
+    if (r->Q) { free(r->u); free(r->logw); r->Q = 0; }
+    double gx[16], gw[16];
+    gl_rule(ng, gx, gw);
+    int nx = nbx * ng, nr = nbr * ng, Q = nx * nr * K;
+    double *u = malloc(sizeof(double) * 3 * Q), *lw = malloc(sizeof(double) * Q);
+    double hx = (bx - ax) / nbx, hr = br / nbr;
+    int q = 0;
+    for (int bi = 0; bi < nbx; ++bi) for (int i = 0; i < ng; ++i) {
+        double x = ax + hx * (bi + 0.5 * (gx[i] + 1.0)), wx = 0.5 * hx * gw[i];
+        for (int bj = 0; bj < nbr; ++bj) for (int j = 0; j < ng; ++j) {
+            double rr = hr * (bj + 0.5 * (gx[j] + 1.0)), wr = 0.5 * hr * gw[j] * rr;
+            for (int k = 0; k < K; ++k, ++q) {
+                double t = 2.0 * M_PI * k / K;
+                u[3 * q] = x; u[3 * q + 1] = rr * cos(t); u[3 * q + 2] = rr * sin(t);
+                lw[q] = log(wx) + log(wr) + log(2.0 * M_PI / K);
+            }
+        }
+    }
+    r->n = -2; r->phys = 1; r->u = u; r->logw = lw; r->phi = NULL; r->Q = Q;
+    return Q;
+}
+
+/* Node q of rule r seen from a cell of gauge g: ubar, log weight and the
+ * statistics (phi points into the table for gauge-frame rules, else into
+ * buf). */
+static const double *rule_node(const rule_t *r, const double *g, int q, double *ub, double *lw, double *buf) {
+    if (!r->phys) {
+        ub[0] = r->u[3 * q]; ub[1] = r->u[3 * q + 1]; ub[2] = r->u[3 * q + 2];
+        *lw = r->logw[q];
+        return &r->phi[(size_t)NP * q];
+    }
+    for (int a = 0; a < 3; ++a) ub[a] = (r->u[3 * q + a] - g[a]) / g[3 + a];
+    *lw = r->logw[q] - 0.5 * (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
+    or_phi(ub, buf);
+    return buf;
+}
+
 static const rule_t *get_rule(int n) {
     if (n >= 100 && n <= 115) return g_box_rules[n - 100].Q ? &g_box_rules[n - 100] : NULL;
+    if (n >= 200 && n <= 215) return g_vel_rules[n - 200].Q ? &g_vel_rules[n - 200] : NULL;
     if (n < 1 || n > NMAXQ) return NULL;
     rule_t *r = &g_rules[n];
     if (r->Q) return r;
@@ -250,6 +307,11 @@ static const rule_t *get_rule(int n) {
     return r;
 }
 
+int or_rule_is_velocity(int n) {
+    const rule_t *r = get_rule(n);
+    return r ? r->phys : -1;
+}
+
 int or_rule_nodes(int n, double *u, double *logw) {
     const rule_t *r = get_rule(n);
     if (!r) return -1;
@@ -264,14 +326,16 @@ int or_rule_nodes(int n, double *u, double *logw) {
  * "Numerical integration moments" and the log-sum-exp form of log Z).
  * Outputs (any may be NULL): logZ; m[i] = E phi_i; S[i][j] = E phi_i phi_j;
  * X[i] = E ubar_x phi_i; XS[i][j] = E ubar_x phi_i phi_j. */
-void or_expect(int order, const double *beta, double *logZ, double *m, double *S, double *X, double *XS) {
+void or_expect(int order, const double *g, const double *beta, double *logZ, double *m, double *S, double *X,
+               double *XS) {
     const rule_t *r = get_rule(order);
     int Q = r->Q;
     double *e = malloc(sizeof(double) * Q);
-    double emax = -INFINITY;
+    double emax = -INFINITY, ub[3], lw, buf[NP];
     for (int q = 0; q < Q; ++q) {
-        double s = r->logw[q];
-        for (int i = 1; i < NP; ++i) s += beta[i] * r->phi[NP * q + i];
+        const double *ph = rule_node(r, g, q, ub, &lw, buf);
+        double s = lw;
+        for (int i = 1; i < NP; ++i) s += beta[i] * ph[i];
         e[q] = s;
         if (s > emax) emax = s;
     }
@@ -284,8 +348,8 @@ void or_expect(int order, const double *beta, double *logZ, double *m, double *S
     if (XS) memset(XS, 0, sizeof(double) * NP * NP);
     for (int q = 0; q < Q; ++q) {
         double sg = e[q] / Z;
-        const double *ph = &r->phi[NP * q];
-        double ux = r->u[3 * q];
+        const double *ph = rule_node(r, g, q, ub, &lw, buf);
+        double ux = ub[0];
         for (int i = 0; i < NP; ++i) {
             if (m) m[i] += sg * ph[i];
             if (X) X[i] += sg * ux * ph[i];
@@ -307,9 +371,9 @@ void or_expect(int order, const double *beta, double *logZ, double *m, double *S
 
 /* Objective of Appendix C, Eq. "MLE optimization goal", with beta_0 = n held
  * at its minimiser: L = log Z - sum_{i>=1} beta_i M_i / n. */
-double or_objective(int order, const double *beta, const double *M) {
+double or_objective(int order, const double *g, const double *beta, const double *M) {
     double lz;
-    or_expect(order, beta, &lz, NULL, NULL, NULL, NULL);
+    or_expect(order, g, beta, &lz, NULL, NULL, NULL, NULL);
     double s = 0.0;
     for (int i = 1; i < NP; ++i) s += beta[i] * M[i] / M[0];
     return lz - s;
@@ -317,9 +381,9 @@ double or_objective(int order, const double *beta, const double *M) {
 
 /* Relative moment residual ||E phi(beta) - M/n||_2 / ||M/n||_2 (acceptance
  * measure of the solve; slot 0 contributes 0 by construction). */
-double or_residual(int order, const double *beta, const double *M) {
+double or_residual(int order, const double *g, const double *beta, const double *M) {
     double m[NP];
-    or_expect(order, beta, NULL, m, NULL, NULL, NULL);
+    or_expect(order, g, beta, NULL, m, NULL, NULL, NULL);
     double num = 0.0, den = 0.0;
     for (int i = 0; i < NP; ++i) {
         double t = M[i] / M[0];
@@ -394,7 +458,8 @@ static void solve_upper_T(int n, const double *L, const double *b, double *x) { 
 /* Solve one cell.  M[35] (M_0 = n), beta[35] in: warm start (slots 1..34),
  * out: solution with beta_0 = n.  Returns status bits; *iters = loop count;
  * *res_out = last res; *lam_out = largest identity multiple used. */
-int or_solve(int order, const double *M, double *beta, const double *optv, int *iters, double *res_out, double *lam_out) {
+int or_solve(int order, const double *g, const double *M, double *beta, const double *optv, int *iters, double *res_out,
+             double *lam_out) {
     or_opts o; default_opts(&o);
     if (optv) { o.tol = optv[0]; o.maxI = (int)optv[1]; o.final_step = optv[2] != 0.0; }
     const int D = NP - 1;
@@ -405,7 +470,7 @@ int or_solve(int order, const double *M, double *beta, const double *optv, int *
     double b[NP], db[NP] = {0}, G[NP] = {0}, m[NP], S[NP * NP], H[34 * 34], Lh[34 * 34], wv[34], rhs[34], trial[NP];
     memcpy(b, beta, sizeof(b));
     b[0] = n;
-    double Lcur = or_objective(order, b, M);
+    double Lcur = or_objective(order, g, b, M);
     int it = 0, conv = 0;
     double res = INFINITY, lam_used = 0.0, alpha = 1.0;
     while (!conv && it <= o.maxI) {
@@ -416,7 +481,7 @@ int or_solve(int order, const double *M, double *beta, const double *optv, int *
             if (!sat) alpha *= 0.5;
             for (int i = 0; i < NP; ++i) trial[i] = b[i] + alpha * db[i];
             trial[0] = n;
-            double Lt = or_objective(order, trial, M);
+            double Lt = or_objective(order, g, trial, M);
             double LD = Lcur - Lt, gd = 0.0;
             for (int i = 1; i < NP; ++i) gd += G[i] * alpha * db[i];
             double gradD = -o.c * gd;
@@ -424,9 +489,9 @@ int or_solve(int order, const double *M, double *beta, const double *optv, int *
             s += 1;
         }
         for (int i = 1; i < NP; ++i) b[i] += alpha * db[i];
-        Lcur = or_objective(order, b, M);
+        Lcur = or_objective(order, g, b, M);
         /* Hessian and gradient of L at beta (Appendix C). */
-        or_expect(order, b, NULL, m, S, NULL, NULL);
+        or_expect(order, g, b, NULL, m, S, NULL, NULL);
         for (int i = 1; i < NP; ++i) G[i] = m[i] - M[i] / n;
         for (int i = 0; i < D; ++i)
             for (int j = 0; j < D; ++j) H[i * D + j] = S[(i + 1) * NP + (j + 1)] - m[i + 1] * m[j + 1];
@@ -473,7 +538,8 @@ int or_solve(int order, const double *M, double *beta, const double *optv, int *
     return st;
 }
 
-void or_solve_batch(int order, int64_t B, const double *M, double *beta, int *status, int *iters, const double *optv, int nthreads) {
+void or_solve_batch(int order, int64_t B, const double *g, const double *M, double *beta, int *status, int *iters,
+                    const double *optv, int nthreads) {
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
@@ -481,7 +547,7 @@ void or_solve_batch(int order, int64_t B, const double *M, double *beta, int *st
     #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t c = 0; c < B; ++c) {
         int it = 0;
-        int st = or_solve(order, &M[NP * c], &beta[NP * c], optv, &it, NULL, NULL);
+        int st = or_solve(order, g ? &g[6 * c] : NULL, &M[NP * c], &beta[NP * c], optv, &it, NULL, NULL);
         if (status) status[c] = st;
         if (iters) iters[c] = it;
     }
@@ -607,7 +673,7 @@ void or_transform_beta(const double *g_to, const double *g_from, const double *b
  * Cholesky factor of E phi phi^T and diagonalised by Jacobi. */
 void or_flux(int order, const double *beta, const double *g, double n, double *F, double *speed, double *lmin, double *lmax) {
     double m[NP], S[NP * NP], X[NP], XS[NP * NP];
-    or_expect(order, beta, NULL, m, S, X, XS);
+    or_expect(order, g, beta, NULL, m, S, X, XS);
     if (F) for (int i = 0; i < NP; ++i) F[i] = n * (g[0] * m[i] + g[3] * X[i]);
     if (speed || lmin || lmax) {
         double L[NP * NP], C[NP * NP], tmp[NP * NP], ev[NP];
@@ -617,9 +683,12 @@ void or_flux(int order, const double *beta, const double *g, double n, double *F
              * Mach-10 meshes).  Fall back to the Rayleigh-quotient bound over
              * the nodes, max_q |w_x + s_x ubar_x,q|. */
             const rule_t *r = get_rule(order);
-            double xmax = 0.0;
-            for (int q = 0; q < r->Q; ++q) if (r->u[3 * q] > xmax) xmax = r->u[3 * q];
-            double a = g[0] - g[3] * xmax, b = g[0] + g[3] * xmax;
+            double a = INFINITY, b = -INFINITY;
+            for (int q = 0; q < r->Q; ++q) {
+                double ux = r->phys ? r->u[3 * q] : g[0] + g[3] * r->u[3 * q];
+                if (ux < a) a = ux;
+                if (ux > b) b = ux;
+            }
             if (lmin) *lmin = a;
             if (lmax) *lmax = b;
             if (speed) *speed = fmax(fabs(a), fabs(b));
@@ -756,7 +825,7 @@ void or_shock_step(int order, int N, double dx, double cfl, double Pr, double re
     for (int c = 1; c <= N; ++c) {
         collide(&M[NP * c], &g[6 * c], 0.5 * dt, Pr, relax_coef);
         int it = 0;
-        int st = or_solve(order, &M[NP * c], &beta[NP * c], optv, &it, NULL, NULL);
+        int st = or_solve(order, &g[6 * c], &M[NP * c], &beta[NP * c], optv, &it, NULL, NULL);
         if (status) status[c] = st;
         if (iters) iters[c] = it;
     }

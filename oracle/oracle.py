@@ -61,7 +61,7 @@ def basis_index():
 
 
 def index_of(a, b, c):
-    return lib().or_index_of(a, b, c)
+    return lib().or_index_of(int(a), int(b), int(c))
 
 
 def set_box_rule(rule_id, nbx, nbr, ng, Lx, Lr):
@@ -71,6 +71,29 @@ def set_box_rule(rule_id, nbx, nbr, ng, Lx, Lr):
     if q <= 0:
         raise ValueError("bad box rule")
     return q
+
+
+def set_velocity_rule(rule_id, ax, bx, nbx, br, nbr, ng=8, K=12):
+    """Register velocity-space rule `rule_id` (200..215): block Gauss-Legendre
+    in u_x on [ax, bx] and in u_r on [0, br] (polar weight), K azimuthal
+    angles.  Returns the node count."""
+    q = lib().or_set_velocity_rule(rule_id, ctypes.c_double(ax), ctypes.c_double(bx), nbx, ctypes.c_double(br), nbr,
+                                   ng, K)
+    if q < 0:
+        raise ValueError("bad velocity rule")
+    return q
+
+
+def shock_domain(mach, na=5.0, nb=5.0, nr=5.0, gamma=5.0 / 3.0):
+    """Integration domain (a_x, b_x, b_r) of Appendix D from the
+    Rankine-Hugoniot states: n_a, n_b, n_r thermal speeds beyond the up- and
+    downstream Maxwellians."""
+    r, t = rh(mach, gamma)
+    v_up, v_dn, c_up, c_dn = np.sqrt(gamma) * mach, np.sqrt(gamma) * mach / r, 1.0, np.sqrt(t)
+    ax = min(v_dn - na * c_dn, v_up - na * c_up)
+    bx = max(v_up + nb * c_up, v_dn + nb * c_dn)
+    br = max(nr * c_up, nr * c_dn)
+    return ax, bx, br
 
 
 def gh_rule(n):
@@ -98,35 +121,44 @@ def rule_nodes(order):
     return u, lw
 
 
-def expect(order, beta):
-    """logZ, E phi, E phi phi^T, E ubar_x phi, E ubar_x phi phi^T (Section 3.1)."""
+def _g(g):
+    """Gauge argument: None (gauge-frame rules ignore it) or a 6-vector."""
+    return None if g is None else _d(_f64(g, (6,)))
+
+
+def expect(order, beta, g=None):
+    """logZ, E phi, E phi phi^T, E ubar_x phi, E ubar_x phi phi^T (Section 3.1).
+    g: the cell's gauge, needed by velocity-space rules only."""
     beta = _f64(beta, (NP,))
     lz = ctypes.c_double()
     m = np.zeros(NP)
     S = np.zeros((NP, NP))
     X = np.zeros(NP)
     XS = np.zeros((NP, NP))
-    lib().or_expect(order, _d(beta), ctypes.byref(lz), _d(m), _d(S), _d(X), _d(XS))
+    lib().or_expect(order, _g(g), _d(beta), ctypes.byref(lz), _d(m), _d(S), _d(X), _d(XS))
     return lz.value, m, S, X, XS
 
 
-def objective(order, beta, M):
+def objective(order, beta, M, g=None):
     """Appendix C objective L(beta; M) with beta_0 = n."""
-    return lib().or_objective(order, _d(_f64(beta, (NP,))), _d(_f64(M, (NP,))))
+    return lib().or_objective(order, _g(g), _d(_f64(beta, (NP,))), _d(_f64(M, (NP,))))
 
 
-def residual(order, beta, M):
+def residual(order, beta, M, g=None):
     """Relative moment residual ||E phi(beta) - M/n|| / ||M/n||."""
-    return lib().or_residual(order, _d(_f64(beta, (NP,))), _d(_f64(M, (NP,))))
+    return lib().or_residual(order, _g(g), _d(_f64(beta, (NP,))), _d(_f64(M, (NP,))))
 
 
-def residual_batch(order, beta, M):
+def residual_batch(order, beta, M, g=None):
     beta = _f64(beta).reshape(-1, NP)
     M = _f64(M).reshape(-1, NP)
-    return np.array([residual(order, b, m) for b, m in zip(beta, M)])
+    if g is None:
+        return np.array([residual(order, b, m) for b, m in zip(beta, M)])
+    g = _f64(g).reshape(-1, 6)
+    return np.array([residual(order, b, m, gg) for b, m, gg in zip(beta, M, g)])
 
 
-def solve(order, M, beta0=None, tol=1e-8, maxI=500, final_step=True):
+def solve(order, M, beta0=None, tol=1e-8, maxI=500, final_step=True, g=None):
     """Algorithm 1 on one cell.  Returns (beta, status, iters, res, max_lambda)."""
     M = _f64(M, (NP,))
     beta = np.zeros(NP) if beta0 is None else _f64(beta0, (NP,)).copy()
@@ -134,11 +166,11 @@ def solve(order, M, beta0=None, tol=1e-8, maxI=500, final_step=True):
     it = ctypes.c_int()
     res = ctypes.c_double()
     lam = ctypes.c_double()
-    st = lib().or_solve(order, _d(M), _d(beta), _d(opts), ctypes.byref(it), ctypes.byref(res), ctypes.byref(lam))
+    st = lib().or_solve(order, _g(g), _d(M), _d(beta), _d(opts), ctypes.byref(it), ctypes.byref(res), ctypes.byref(lam))
     return beta, st, it.value, res.value, lam.value
 
 
-def solve_batch(order, M, beta0=None, tol=1e-8, maxI=500, nthreads=0, final_step=True):
+def solve_batch(order, M, beta0=None, tol=1e-8, maxI=500, nthreads=0, final_step=True, g=None):
     """Algorithm 1 over a batch of cells (OpenMP).  Returns (beta, status, iters)."""
     M = _f64(M).reshape(-1, NP)
     B = M.shape[0]
@@ -146,7 +178,8 @@ def solve_batch(order, M, beta0=None, tol=1e-8, maxI=500, nthreads=0, final_step
     st = np.zeros(B, dtype=np.int32)
     it = np.zeros(B, dtype=np.int32)
     opts = np.array([tol, float(maxI), float(bool(final_step))])
-    lib().or_solve_batch(order, ctypes.c_int64(B), _d(M), _d(beta), _i(st), _i(it), _d(opts), nthreads)
+    gg = None if g is None else _d(_f64(g).reshape(B, 6))
+    lib().or_solve_batch(order, ctypes.c_int64(B), gg, _d(M), _d(beta), _i(st), _i(it), _d(opts), nthreads)
     return beta, st, it
 
 
@@ -293,7 +326,7 @@ class Shock:
                 self.g[c] = gH
                 self.beta[c, 0] = self.M[c, 0]
         if ic != "step":
-            b, st, it = solve_batch(order, self.M[1:-1], None, tol, maxI, nthreads)
+            b, st, it = solve_batch(order, self.M[1:-1], None, tol, maxI, nthreads, g=self.g[1:-1])
             self.beta[1:-1] = b
         _, self.speed = flux_batch(order, self.M, self.beta, self.g, nthreads)
         self.status = np.zeros(NT, dtype=np.int32)

@@ -84,6 +84,35 @@ int ensure_scratch(mem_ctx *ctx, size_t bytes) {
     return MEM_OK;
 }
 
+// 1D Gauss-Legendre rule on [-1, 1]: the roots of P_n by Newton's method in
+// long double from the estimates cos(pi (i + 3/4) / (n + 1/2)), weights
+// 2 / ((1 - x^2) P_n'(x)^2); ascending nodes.
+int gl_rule(int n, std::vector<double> &x, std::vector<double> &w) {
+    if (n < 1 || n > 64) return MEM_EINVAL;
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int i = 0; i < n; ++i) {
+        long double t = cosl(pi * (i + 0.75L) / (n + 0.5L)), dp = 1.0L;
+        for (int it = 0; it < 100; ++it) {
+            long double p0 = 1.0L, p1 = t;  // P_0, P_1
+            for (int k = 2; k <= n; ++k) {
+                const long double p2 = ((2.0L * k - 1.0L) * t * p1 - (k - 1.0L) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            const long double pn = n == 1 ? t : p1, pn1 = n == 1 ? 1.0L : p0;
+            dp = n * (t * pn - pn1) / (t * t - 1.0L);
+            const long double step = pn / dp;
+            t -= step;
+            if (fabsl(step) < 1e-19L) break;
+        }
+        x[n - 1 - i] = (double)t;
+        w[n - 1 - i] = (double)(2.0L / ((1.0L - t * t) * dp * dp));
+    }
+    return MEM_OK;
+}
+
 }  // namespace mem_host
 
 // ---------------------------------------------------------------------------
@@ -248,6 +277,53 @@ void mem_solve_opts_default(mem_solve_opts *o) {
 
 const char *mem_version(void) { return "mem-gb300 0.1 (sm_103a)"; }
 
+// Linearisation tables shared by every kind of context: Hessian slots of the
+// solver, flux and parity-block slots of the speed kernel, and the plain
+// path's term lists.
+static int build_slot_tables(mem_ctx *ctx) {
+    int rc = MEM_OK;
+    std::vector<int> off, xoff;
+    std::vector<int2> terms, xterms;
+    build_lin_terms(1, false, off, terms);
+    build_lin_terms(0, true, xoff, xterms);
+    std::vector<int2> slots, fslots;
+    build_hess_slots(off, terms, slots, ctx->n_hess_slots);
+    std::vector<int> soff;
+    std::vector<int2> sterms;
+    build_lin_terms(1, false, soff, sterms);  // E[phi_i phi_j], i >= j >= 1
+    build_hess_slots(soff, sterms, fslots, ctx->n_flux_slots, &xoff, &xterms);
+    std::vector<int> s0off;
+    std::vector<int2> s0terms, aslots;
+    build_lin_terms(0, false, s0off, s0terms);
+    build_axi_slots(s0off, s0terms, xoff, xterms, aslots, ctx->n_axi_slots);
+    // Flux slots carry their destination in the flux kernel's per-warp work
+    // area instead of the entry number: entries 0..594 (E[phi_i phi_j],
+    // i >= j >= 1) go to H[(i-1) * 35 + (j-1)]; entries 595..1224
+    // (E[ubar_x phi_i phi_j], i >= j >= 0) go to 1260 + i * 36 + j.
+    {
+        std::vector<int> dst;
+        for (int i = 1; i < NP; ++i)
+            for (int j = 1; j <= i; ++j) dst.push_back((i - 1) * 35 + (j - 1));
+        for (int i = 0; i < NP; ++i)
+            for (int j = 0; j <= i; ++j) dst.push_back(1260 + i * 36 + j);
+        for (auto &sl : fslots) {
+            const bool last = sl.x < 0;
+            const int p = (sl.x >> 8) & 4095, idx = sl.x & 255;
+            if (sl.x == 0 && sl.y == 0) continue;  // padding
+            sl.x = idx | (dst[p] << 8) | (last ? (int)0x80000000 : 0);
+        }
+    }
+    if (!rc) rc = upload(&ctx->d_lin_off, off);
+    if (!rc) rc = upload(&ctx->d_lin_terms, terms);
+    if (!rc) rc = upload(&ctx->d_hess_slots, slots);
+    if (!rc) rc = upload(&ctx->d_flux_slots, fslots);
+    if (!rc) rc = upload(&ctx->d_axi_slots, aslots);
+    if (!rc) rc = upload(&ctx->d_xlin_off, xoff);
+    if (!rc) rc = upload(&ctx->d_xlin_terms, xterms);
+    ctx->n_lin_terms = (int)terms.size();
+    return rc;
+}
+
 int mem_init(int degree, int quad_order, mem_ctx **out) {
     if (!out || degree != 4 || quad_order < 4 || quad_order > 16) return MEM_EINVAL;
     *out = nullptr;
@@ -289,37 +365,6 @@ int mem_init(int degree, int quad_order, mem_ctx **out) {
                         rf[700 + i * (i + 1) / 2 + j] = (float)(ux * ph[i] * ph[j]);
                     }
             }
-    std::vector<int> off, xoff;
-    std::vector<int2> terms, xterms;
-    build_lin_terms(1, false, off, terms);
-    build_lin_terms(0, true, xoff, xterms);
-    std::vector<int2> slots, fslots;
-    build_hess_slots(off, terms, slots, ctx->n_hess_slots);
-    std::vector<int> soff;
-    std::vector<int2> sterms;
-    build_lin_terms(1, false, soff, sterms);  // E[phi_i phi_j], i >= j >= 1
-    build_hess_slots(soff, sterms, fslots, ctx->n_flux_slots, &xoff, &xterms);
-    std::vector<int> s0off;
-    std::vector<int2> s0terms, aslots;
-    build_lin_terms(0, false, s0off, s0terms);
-    build_axi_slots(s0off, s0terms, xoff, xterms, aslots, ctx->n_axi_slots);
-    // Flux slots carry their destination in the flux kernel's per-warp work
-    // area instead of the entry number: entries 0..594 (E[phi_i phi_j],
-    // i >= j >= 1) go to H[(i-1) * 35 + (j-1)]; entries 595..1224
-    // (E[ubar_x phi_i phi_j], i >= j >= 0) go to 1260 + i * 36 + j.
-    {
-        std::vector<int> dst;
-        for (int i = 1; i < NP; ++i)
-            for (int j = 1; j <= i; ++j) dst.push_back((i - 1) * 35 + (j - 1));
-        for (int i = 0; i < NP; ++i)
-            for (int j = 0; j <= i; ++j) dst.push_back(1260 + i * 36 + j);
-        for (auto &sl : fslots) {
-            const bool last = sl.x < 0;
-            const int p = (sl.x >> 8) & 4095, idx = sl.x & 255;
-            if (sl.x == 0 && sl.y == 0) continue;  // padding
-            sl.x = idx | (dst[p] << 8) | (last ? (int)0x80000000 : 0);
-        }
-    }
     rc = MEM_OK;
     if (!rc) rc = upload(&ctx->d_phiT, phiT);
     if (!rc) rc = upload(&ctx->d_logw, logw);
@@ -328,17 +373,47 @@ int mem_init(int degree, int quad_order, mem_ctx **out) {
     if (!rc) rc = upload(&ctx->d_he1d, he1d);
     if (!rc) rc = upload(&ctx->d_x1d, x1d);
     if (!rc) rc = upload(&ctx->d_logw1d, lw1d);
-    if (!rc) rc = upload(&ctx->d_lin_off, off);
-    if (!rc) rc = upload(&ctx->d_lin_terms, terms);
-    if (!rc) rc = upload(&ctx->d_hess_slots, slots);
-    if (!rc) rc = upload(&ctx->d_flux_slots, fslots);
-    if (!rc) rc = upload(&ctx->d_axi_slots, aslots);
-    if (!rc) rc = upload(&ctx->d_xlin_off, xoff);
-    if (!rc) rc = upload(&ctx->d_xlin_terms, xterms);
-    ctx->n_lin_terms = (int)terms.size();
+    if (!rc) rc = build_slot_tables(ctx);
     if (rc) { mem_destroy(ctx); return rc; }
     if (cudaDeviceSynchronize() != cudaSuccess) { mem_destroy(ctx); return MEM_ECUDA; }
     *out = ctx;
+    return MEM_OK;
+}
+
+int mem_init_velocity(int degree, int nbx, int nbr, int ng, int K, double ax, double bx, double br, mem_ctx **out) {
+    if (!out) return MEM_EINVAL;
+    *out = nullptr;
+    if (degree != 4 || nbx < 1 || nbr < 1 || ng < 1 || ng > 16 || K < 1 || K > 64) return MEM_EINVAL;
+    if (nbx * ng > 256 || nbr * ng * K > 1024 || !(bx > ax) || !(br > 0.0) || !isfinite(ax) || !isfinite(bx) ||
+        !isfinite(br))
+        return MEM_EINVAL;
+    if (mem_host::vel_smem_bytes(nbx * ng, nbr * ng * K) > 227 * 1024) return MEM_EINVAL;
+    mem_ctx *ctx = new mem_ctx();
+    cudaGetDevice(&ctx->device);
+    ctx->vel = 1;
+    ctx->nbx = nbx; ctx->nbr = nbr; ctx->ng = ng; ctx->K = K;
+    ctx->nx = nbx * ng;
+    ctx->npt = nbr * ng * K;
+    ctx->Q = ctx->nx * ctx->npt;
+    ctx->dom[0] = ax; ctx->dom[1] = bx; ctx->dom[2] = br;
+    std::vector<double> x, w;
+    int rc = mem_host::gl_rule(ng, x, w);
+    if (rc) { delete ctx; return rc; }
+    std::vector<double> d0 = {ax, bx, br, 0.0};
+    if (!rc) rc = upload(&ctx->d_glx, x);
+    if (!rc) rc = upload(&ctx->d_glw, w);
+    if (!rc) rc = upload(&ctx->d_dom0, d0);
+    if (!rc) rc = build_slot_tables(ctx);
+    if (rc) { mem_destroy(ctx); return rc; }
+    if (cudaDeviceSynchronize() != cudaSuccess) { mem_destroy(ctx); return MEM_ECUDA; }
+    *out = ctx;
+    return MEM_OK;
+}
+
+int mem_velocity_rule(const mem_ctx *ctx, int32_t *shape, double *domain) {
+    if (!ctx || !ctx->vel) return MEM_EINVAL;
+    if (shape) { shape[0] = ctx->nbx; shape[1] = ctx->nbr; shape[2] = ctx->ng; shape[3] = ctx->K; }
+    if (domain) { domain[0] = ctx->dom[0]; domain[1] = ctx->dom[1]; domain[2] = ctx->dom[2]; }
     return MEM_OK;
 }
 
@@ -347,7 +422,7 @@ void mem_destroy(mem_ctx *ctx) {
     cudaDeviceSynchronize();
     void *ptrs[] = {ctx->d_phiT, ctx->d_logw, ctx->d_tab_solve, ctx->d_tab_flux, ctx->d_he1d, ctx->d_x1d,
                     ctx->d_logw1d, ctx->d_lin_off, ctx->d_lin_terms, ctx->d_hess_slots, ctx->d_flux_slots, ctx->d_axi_slots, ctx->d_xlin_off, ctx->d_xlin_terms,
-                    ctx->scratch};
+                    ctx->scratch, ctx->d_glx, ctx->d_glw, ctx->d_dom0};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;
@@ -364,10 +439,48 @@ int mem_solve(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_
     mem_solve_opts_default(&o);
     if (opts) o = *opts;
     if (o.maxI < 0 || o.maxT < 0 || o.maxT > 60 || o.max_lambda < 0 || o.max_lambda > 60) return MEM_EINVAL;
+    if (ctx->vel) return MEM_EINVAL;  // the rule follows the gauge: mem_solve_gauge
     cudaStream_t st = (cudaStream_t)stream;
     if (o.impl == MEM_IMPL_PLAIN) return mem_host::solve_plain(ctx, M, beta, status, iters, B, o, st);
     if (o.impl == MEM_IMPL_FUSED) return mem_host::solve_fused(ctx, M, beta, status, iters, B, o, st);
     return MEM_EINVAL;
+}
+
+int mem_solve_gauge(mem_ctx *ctx, const float *M, float *beta, const float *gauge, int32_t *status, int32_t *iters,
+                    int64_t B, const mem_solve_opts *opts, void *stream) {
+    if (!ctx || B < 0) return MEM_EINVAL;
+    if (!ctx->vel) return mem_solve(ctx, M, beta, status, iters, B, opts, stream);
+    if (B == 0) return MEM_OK;
+    if (!M || !beta || !gauge) return MEM_EINVAL;
+    mem_solve_opts o;
+    mem_solve_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.maxI < 0 || o.maxT < 0 || o.maxT > 60 || o.max_lambda < 0 || o.max_lambda > 60) return MEM_EINVAL;
+    return mem_host::vel_run(ctx, M, beta, gauge, status, iters, nullptr, nullptr, nullptr, B, o, true,
+                             (cudaStream_t)stream);
+}
+
+// Flux and speed on a velocity-space context: moment rows into context
+// scratch (chunked), then the shared flux/speed kernel.
+static int vel_flux(mem_ctx *ctx, const float *M, const float *beta, const float *gauge, float *F, float *speed,
+                    int64_t B, cudaStream_t st, bool axisym) {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    const int64_t CH = std::min<int64_t>(B, (int64_t)1 << 18);
+    int rc = mem_host::ensure_scratch(ctx, sizeof(float) * (size_t)CH * MEM_MU_STRIDE);
+    if (rc) return rc;
+    float *mu = (float *)ctx->scratch;
+    mem_solve_opts o;
+    mem_solve_opts_default(&o);
+    for (int64_t c0 = 0; c0 < B; c0 += CH) {
+        const int64_t n = std::min<int64_t>(CH, B - c0);
+        rc = mem_host::vel_run(ctx, M + c0 * NP, (float *)(beta + c0 * NP), gauge + c0 * 6, nullptr, nullptr, mu,
+                               nullptr, nullptr, n, o, false, st);
+        if (!rc)
+            rc = mem_host::flux_from_mu(ctx, mu, M + c0 * NP, gauge + c0 * 6, F ? F + c0 * NP : nullptr,
+                                        speed ? speed + c0 : nullptr, n, st, axisym);
+        if (rc) return rc;
+    }
+    return MEM_OK;
 }
 
 int mem_flux(mem_ctx *ctx, const float *M, const float *beta, const float *gauge, float *F, float *speed,
@@ -375,6 +488,7 @@ int mem_flux(mem_ctx *ctx, const float *M, const float *beta, const float *gauge
     if (!ctx || B < 0) return MEM_EINVAL;
     if (B == 0) return MEM_OK;
     if (!M || !beta || !gauge) return MEM_EINVAL;
+    if (ctx->vel) return vel_flux(ctx, M, beta, gauge, F, speed, B, (cudaStream_t)stream, false);
     if (mem_host::flux_fused_available(ctx))
         return mem_host::flux_fused(ctx, M, beta, gauge, F, speed, B, (cudaStream_t)stream, false);
     return mem_host::flux(ctx, M, beta, gauge, F, speed, B, (cudaStream_t)stream);
@@ -385,6 +499,7 @@ int mem_flux_axisym(mem_ctx *ctx, const float *M, const float *beta, const float
     if (!ctx || B < 0) return MEM_EINVAL;
     if (B == 0) return MEM_OK;
     if (!M || !beta || !gauge) return MEM_EINVAL;
+    if (ctx->vel) return vel_flux(ctx, M, beta, gauge, F, speed, B, (cudaStream_t)stream, true);
     if (mem_host::flux_fused_available(ctx))
         return mem_host::flux_fused(ctx, M, beta, gauge, F, speed, B, (cudaStream_t)stream, true);
     return mem_host::flux(ctx, M, beta, gauge, F, speed, B, (cudaStream_t)stream);

@@ -13,6 +13,7 @@
 #define MEM_NCOL_SOLVE 630   // [phi_0..34 | phi_i phi_j, 1 <= j <= i <= 34 packed]
 #define MEM_NCOL_FLUX 1330   // [phi | ubar_x phi | phi phi^T packed (630) | ubar_x phi phi^T packed (630)]
 #define MEM_HE_STRIDE 16     // he_0..he_9 per 1D node, padded
+#define MEM_MU_STRIDE 224    // moment row: mu_abc (a+b+c <= 9, 220) | u_x node range (2) | pad
 
 struct mem_ctx {
     int device = 0;
@@ -39,6 +40,13 @@ struct mem_ctx {
     int *d_xlin_off = nullptr;     // [631]  flux-Jacobian terms (packed i>=j>=0)
     int2 *d_xlin_terms = nullptr;
     float xmax = 0.f;              // largest 1D node
+    // Velocity-space rule (mem_init_velocity): nodes fixed in the lab frame.
+    int vel = 0;                             // 1: velocity-space context (no gauge-frame tables)
+    int nbx = 0, nbr = 0, ng = 0, K = 0;     // blocks in u_x, blocks in u_r, points per block, azimuths
+    int nx = 0, npt = 0;                     // nodes in u_x; points of the transverse plane
+    double dom[3] = {0, 0, 0};               // default domain (a_x, b_x, b_r)
+    double *d_glx = nullptr, *d_glw = nullptr;  // reference Gauss-Legendre rule on [-1, 1]
+    double *d_dom0 = nullptr;                // the default domain (a_x, b_x, b_r, 0) on the device
     // Scratch owned by the context (plain solver, flux).
     std::mutex mu;
     void *scratch = nullptr;
@@ -59,6 +67,13 @@ int flux_bufs(mem_ctx *ctx, const float *M, const float *beta, const float *g, f
 int flux_fused(mem_ctx *ctx, const float *M, const float *beta, const float *g, float *F, float *speed,
                int64_t B, cudaStream_t st, bool axisym);
 bool flux_fused_available(const mem_ctx *ctx);
+int flux_from_mu(mem_ctx *ctx, const float *mu, const float *M, const float *g, float *F, float *speed, int64_t B,
+                 cudaStream_t st, bool axisym);
+int vel_run(mem_ctx *ctx, const float *M, float *beta, const float *g, int32_t *status, int32_t *iters, float *mu,
+            const int *pid, const double *dom, int64_t B, const mem_solve_opts &o, bool solve, cudaStream_t st,
+            const unsigned char *active = nullptr);
+size_t vel_smem_bytes(int nx, int npt);
+int gl_rule(int n, std::vector<double> &x, std::vector<double> &w);
 int gauge_hermite(mem_ctx *ctx, const float *M_in, const float *g_in, float *g_out, float *M_out,
                   float *beta_inout, int64_t B, int axisym, cudaStream_t st);
 int gauge_transform(const float *g_to, const float *g_from, const float *M_in, float *M_out, int64_t B,

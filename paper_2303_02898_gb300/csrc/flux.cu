@@ -49,6 +49,7 @@ struct FluxArgs {
     const int2 *aslots;
     int n_aslots;
     float xmax;
+    const float *mu;  // moments rows [B][MEM_MU_STRIDE] (moments-in variant)
 };
 
 // Extreme generalised eigenvalues of one small symmetric-definite pencil
@@ -132,7 +133,10 @@ __device__ __forceinline__ bool small_pencil_extremes(float *S, float *X, int n,
     return true;
 }
 
-template <int N, bool AXI>
+// MU_IN: the moments of degree <= 9 come precomputed per cell (rows of
+// A.mu, with the node range of u_x in slots 220, 221) instead of from the
+// gauge-frame rule; everything after the moments is shared.
+template <int N, bool AXI, bool MU_IN>
 __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
     using C = FusedCfg<N>;
     using Cf = FluxCfg<N>;
@@ -144,8 +148,10 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
     int *s_pij = s_ab + 56;           // [595] packed (i, j), i >= j, 34 x 34
     int *s_pij35 = s_pij + 596;       // [630] packed (i, j), i >= j, 35 x 35
     float *wbase = (float *)(s_pij35 + 632);
-    for (int t = threadIdx.x; t < N * MEM_HE_STRIDE; t += blockDim.x) s_he[t] = A.he1d[t];
-    for (int t = threadIdx.x; t < N; t += blockDim.x) s_lw[t] = A.logw1d[t];
+    if (!MU_IN) {
+        for (int t = threadIdx.x; t < N * MEM_HE_STRIDE; t += blockDim.x) s_he[t] = A.he1d[t];
+        for (int t = threadIdx.x; t < N; t += blockDim.x) s_lw[t] = A.logw1d[t];
+    }
     for (int t = threadIdx.x; t < 220; t += blockDim.x) s_abc[t] = exp_a(t) | (exp_b(t) << 8) | (exp_c(t) << 16);
     for (int t = threadIdx.x; t < NP * (NP + 1) / 2; t += blockDim.x) {
         int i = 0;
@@ -172,6 +178,17 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
     for (int64_t cell = (int64_t)blockIdx.x * FWARPS + warp; cell < A.B; cell += nwarps) {
         const float n = A.M[cell * NP];
         const float wx = A.gauge[cell * 6], sx = A.gauge[cell * 6 + 3];
+        // speed bound over the nodes, used when the pencil has no reliable spectrum
+        float bound;
+        if (MU_IN) {
+            const float *row = A.mu + cell * MEM_MU_STRIDE;
+            for (int t = lane; t < 220; t += 32) smu[t] = row[t];
+            bound = fmaxf(fabsf(row[220]), fabsf(row[221]));
+            __syncwarp();
+        } else {
+            bound = bound;
+        }
+        if (!MU_IN) {
         if (lane < NP) sb[lane] = lane ? A.beta[cell * NP + lane] : 0.f;
         if (lane + 32 < NP) sb[lane + 32] = A.beta[cell * NP + lane + 32];
         __syncwarp();
@@ -235,6 +252,7 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
             smu[t] = acc;
         }
         __syncwarp();
+        }
         // ---- flux
         if (A.F) {
             for (int k = lane; k < NP; k += 32) {
@@ -277,7 +295,7 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
             }
             if (lane == 0)
                 A.speed[cell] = ok ? fmaxf(fabsf(wx + sx * mhi), fabsf(wx + sx * mlo))
-                                   : fmaxf(fabsf(wx + sx * A.xmax), fabsf(wx - sx * A.xmax));
+                                   : bound;
             __syncwarp();
             continue;
         }
@@ -312,7 +330,7 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
         // Cholesky of S = E[phi phi^T] by bordering: phi_0 = 1 gives
         // chol(S) = [[sqrt S00, 0], [m / sqrt S00, chol(S_1 - m m^T / S00)]].
         if (!(smu[0] > 0.f) || !reg_cholesky34_store(L, lane)) {
-            if (lane == 0) A.speed[cell] = fmaxf(fabsf(wx + sx * A.xmax), fabsf(wx - sx * A.xmax));
+            if (lane == 0) A.speed[cell] = bound;
             continue;
         }
         // Column 0 of chol(S) and the inverse pivots, once.
@@ -412,22 +430,22 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
     }
 }
 
-template <int N, bool AXI>
+template <int N, bool AXI, bool MU_IN = false>
 int launch_flux(mem_ctx *ctx, const FluxArgs &a, cudaStream_t st) {
     using Cf = FluxCfg<N>;
     const size_t smem = sizeof(float) * (N * MEM_HE_STRIDE + 16 + 224 + 56 + 596 + 632) + sizeof(float) * FWARPS * Cf::WARP_FLOATS;
     static int configured = 0;
     if (!configured) {
-        MEM_CUDA_TRY(cudaFuncSetAttribute(k_fused_flux<N, AXI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MEM_CUDA_TRY(cudaFuncSetAttribute(k_fused_flux<N, AXI, MU_IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = 1;
     }
     int sms = 0, per_sm = 0;
     MEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-    MEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_flux<N, AXI>, FWARPS * 32, smem));
+    MEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_flux<N, AXI, MU_IN>, FWARPS * 32, smem));
     if (per_sm < 1) return MEM_ECUDA;
     const int64_t want = (a.B + FWARPS - 1) / FWARPS;
     const int grid = (int)std::min<int64_t>(want, (int64_t)sms * per_sm);
-    k_fused_flux<N, AXI><<<grid, FWARPS * 32, smem, st>>>(a);
+    k_fused_flux<N, AXI, MU_IN><<<grid, FWARPS * 32, smem, st>>>(a);
     MEM_CUDA_TRY(cudaGetLastError());
     return MEM_OK;
 }
@@ -445,6 +463,7 @@ int flux_fused(mem_ctx *ctx, const float *M, const float *beta, const float *g, 
     a.he1d = ctx->d_he1d; a.logw1d = ctx->d_logw1d; a.slots = ctx->d_flux_slots; a.n_slots = ctx->n_flux_slots;
     a.aslots = ctx->d_axi_slots; a.n_aslots = ctx->n_axi_slots;
     a.xmax = ctx->xmax;
+    a.mu = nullptr;
     switch (ctx->n1d * 2 + (axisym ? 1 : 0)) {
         case 16: return launch_flux<8, false>(ctx, a, st);
         case 17: return launch_flux<8, true>(ctx, a, st);
@@ -452,6 +471,24 @@ int flux_fused(mem_ctx *ctx, const float *M, const float *beta, const float *g, 
         case 25: return launch_flux<12, true>(ctx, a, st);
         default: return MEM_EINVAL;
     }
+}
+
+}  // namespace mem_host
+
+namespace mem_host {
+
+// Flux and speed from precomputed moment rows (velocity-space contexts).
+int flux_from_mu(mem_ctx *ctx, const float *mu, const float *M, const float *g, float *F, float *speed, int64_t B,
+                 cudaStream_t st, bool axisym) {
+    if (B == 0) return MEM_OK;
+    FluxArgs a;
+    a.M = M; a.beta = nullptr; a.gauge = g; a.F = F; a.speed = speed; a.B = B;
+    a.he1d = nullptr; a.logw1d = nullptr;
+    a.slots = ctx->d_flux_slots; a.n_slots = ctx->n_flux_slots;
+    a.aslots = ctx->d_axi_slots; a.n_aslots = ctx->n_axi_slots;
+    a.xmax = 0.f;
+    a.mu = mu;
+    return axisym ? launch_flux<8, true, true>(ctx, a, st) : launch_flux<8, false, true>(ctx, a, st);
 }
 
 }  // namespace mem_host

@@ -224,18 +224,35 @@ namespace mem_host {
 
 bool shock_params_valid(const mem_shock_params &p) {
     return p.ncells >= 1 && p.xr > p.xl && p.mach >= 1.0 && p.cfl > 0 && p.Pr > 0.5 && p.gamma > 1.0 && p.kn > 0 &&
-           (p.ic == 0 || p.ic == 1) && p.maxI >= 0 && (p.impl == MEM_IMPL_PLAIN || p.impl == MEM_IMPL_FUSED);
+           (p.ic == 0 || p.ic == 1) && p.maxI >= 0 && (p.impl == MEM_IMPL_PLAIN || p.impl == MEM_IMPL_FUSED) &&
+           p.na > 0 && p.nb > 0 && p.nr > 0;
 }
 
 size_t batch_bytes_per_cell(const mem_ctx *ctx) {
-    return sizeof(float) * (5 * NP + 6 + 3 + (size_t)ctx->Q + MEM_NCOL_FLUX) + sizeof(int32_t) * 3 + 1;
+    const size_t work = ctx->vel ? (size_t)MEM_MU_STRIDE : (size_t)ctx->Q + MEM_NCOL_FLUX;
+    return sizeof(float) * (5 * NP + 6 + 3 + work) + sizeof(int32_t) * 3 + 1;
+}
+
+// Integration domain of a velocity-space rule for one problem (Appendix D):
+// n_a, n_b, n_r thermal speeds beyond the up- and downstream Maxwellians.
+static void shock_domain(const mem_shock_params &p, double *dom) {
+    double n_dn, T_dn, v_up, v_dn;
+    rh_states(p, n_dn, T_dn, v_up, v_dn);
+    const double c_up = 1.0, c_dn = sqrt(T_dn);
+    const double ax = std::min(v_dn - p.na * c_dn, v_up - p.na * c_up);
+    const double bx = std::max(v_up + p.nb * c_up, v_dn + p.nb * c_dn);
+    const double br = std::max(p.nr * c_up, p.nr * c_dn);
+    dom[0] = ax;
+    dom[1] = bx;
+    dom[2] = br;
+    dom[3] = 0.0;
 }
 
 void batch_free(ShockBatch *b) {
     if (!b) return;
     cudaDeviceSynchronize();
     void *ptrs[] = {b->M, b->beta, b->g, b->speed, b->F, b->Mn, b->rho0, b->sigma, b->mom, b->status, b->iters,
-                    b->pid, b->interior, b->prm, b->sc};
+                    b->pid, b->interior, b->prm, b->sc, b->mu, b->dom};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete b;
@@ -294,7 +311,7 @@ int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **o
     *out = nullptr;
     if (P < 1) return MEM_EINVAL;
     for (int i = 0; i < P; ++i)
-        if (!shock_params_valid(ps[i])) return MEM_EINVAL;
+        if (!shock_params_valid(ps[i]) || (ctx->vel && ps[i].impl != MEM_IMPL_FUSED)) return MEM_EINVAL;
     ShockBatch *b = new ShockBatch();
     b->ctx = ctx;
     b->P = P;
@@ -320,11 +337,16 @@ int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **o
     const size_t NT = (size_t)off;
     const int Q = ctx->Q;
     auto alloc = [&](void **ptr, size_t bytes) { return cudaMalloc(ptr, bytes) == cudaSuccess; };
-    bool ok = alloc((void **)&b->M, sizeof(float) * NT * NP) && alloc((void **)&b->beta, sizeof(float) * NT * NP) &&
+    // Flux work space: moment rows (velocity-space rule) or the plain path's
+    // sigma and moment columns (Gauss-Hermite rule).
+    const bool work_ok = ctx->vel ? alloc((void **)&b->mu, sizeof(float) * NT * MEM_MU_STRIDE) &&
+                                        alloc((void **)&b->dom, sizeof(double) * 4 * P)
+                                  : alloc((void **)&b->sigma, sizeof(float) * NT * (size_t)Q) &&
+                                        alloc((void **)&b->mom, sizeof(float) * NT * (size_t)MEM_NCOL_FLUX);
+    bool ok = work_ok && alloc((void **)&b->M, sizeof(float) * NT * NP) && alloc((void **)&b->beta, sizeof(float) * NT * NP) &&
               alloc((void **)&b->g, sizeof(float) * NT * 6) && alloc((void **)&b->speed, sizeof(float) * NT) &&
               alloc((void **)&b->F, sizeof(float) * NT * NP) && alloc((void **)&b->Mn, sizeof(float) * NT * NP) &&
-              alloc((void **)&b->rho0, sizeof(float) * NT) && alloc((void **)&b->sigma, sizeof(float) * NT * (size_t)Q) &&
-              alloc((void **)&b->mom, sizeof(float) * NT * (size_t)MEM_NCOL_FLUX) &&
+              alloc((void **)&b->rho0, sizeof(float) * NT) &&
               alloc((void **)&b->status, sizeof(int32_t) * NT) && alloc((void **)&b->iters, sizeof(int32_t) * NT) &&
               alloc((void **)&b->pid, sizeof(int) * NT) && alloc((void **)&b->interior, NT) &&
               alloc((void **)&b->prm, sizeof(ShockProb) * P) && alloc((void **)&b->sc, sizeof(ShockScalars) * P);
@@ -354,6 +376,14 @@ int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **o
         batch_free(b);
         return MEM_ECUDA;
     }
+    if (ctx->vel) {
+        std::vector<double> hdom(4 * (size_t)P);
+        for (int i = 0; i < P; ++i) shock_domain(ps[i], &hdom[4 * (size_t)i]);
+        if (cudaMemcpy(b->dom, hdom.data(), sizeof(double) * hdom.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            batch_free(b);
+            return MEM_ECUDA;
+        }
+    }
     // Natural parameters of the initial state (the tanh blend is not a
     // Maxwellian), then the characteristic speeds that set the first dt.
     int rc = MEM_OK;
@@ -364,9 +394,16 @@ int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **o
         mem_solve_opts_default(&o);
         o.tol = ps[0].tol;
         o.maxI = ps[0].maxI;
-        rc = solve_fused(ctx, b->M, b->beta, b->status, b->iters, (int64_t)NT, o, 0, b->interior);
+        rc = ctx->vel ? vel_run(ctx, b->M, b->beta, b->g, b->status, b->iters, nullptr, b->pid, b->dom, (int64_t)NT, o,
+                                true, 0, b->interior)
+                      : solve_fused(ctx, b->M, b->beta, b->status, b->iters, (int64_t)NT, o, 0, b->interior);
     }
-    if (!rc) rc = (ps[0].impl == MEM_IMPL_FUSED && flux_fused_available(ctx))
+    if (!rc && ctx->vel) {
+        mem_solve_opts o;
+        mem_solve_opts_default(&o);
+        rc = vel_run(ctx, b->M, b->beta, b->g, nullptr, nullptr, b->mu, b->pid, b->dom, (int64_t)NT, o, false, 0);
+        if (!rc) rc = flux_from_mu(ctx, b->mu, b->M, b->g, b->F, b->speed, (int64_t)NT, 0, true);
+    } else if (!rc) rc = (ps[0].impl == MEM_IMPL_FUSED && flux_fused_available(ctx))
                       ? flux_fused(ctx, b->M, b->beta, b->g, b->F, b->speed, (int64_t)NT, 0, true)
                       : flux_bufs(ctx, b->M, b->beta, b->g, b->F, b->speed, (int64_t)NT, b->sigma, b->mom, 0);
     if (rc || cudaDeviceSynchronize() != cudaSuccess) { batch_free(b); return rc ? rc : MEM_ECUDA; }
@@ -385,13 +422,23 @@ int batch_enqueue_step(ShockBatch *b, cudaStream_t st) {
     o.impl = p0.impl;
     o.tol = p0.tol;
     o.maxI = p0.maxI;
-    int rc = (o.impl == MEM_IMPL_PLAIN)
+    int rc;
+    if (b->ctx->vel) {
+        // Velocity-space rule: the solve kernel also leaves the moments of
+        // degree <= 9 at the new beta (ghost cells included), and the speed
+        // kernel reads them.
+        rc = vel_run(b->ctx, b->M, b->beta, b->g, b->status, b->iters, b->mu, b->pid, b->dom, NT, o, true, st,
+                     b->interior);
+        if (!rc) rc = flux_from_mu(b->ctx, b->mu, b->M, b->g, b->F, b->speed, NT, st, true);
+    } else {
+    rc = (o.impl == MEM_IMPL_PLAIN)
                  ? solve_plain(b->ctx, b->M, b->beta, b->status, b->iters, NT, o, st, b->interior)
                  : solve_fused(b->ctx, b->M, b->beta, b->status, b->iters, NT, o, st, b->interior);
     if (rc) return rc;
     rc = (o.impl == MEM_IMPL_FUSED && flux_fused_available(b->ctx))
              ? flux_fused(b->ctx, b->M, b->beta, b->g, b->F, b->speed, NT, st, true)
              : flux_bufs(b->ctx, b->M, b->beta, b->g, b->F, b->speed, NT, b->sigma, b->mom, st);
+    }
     if (rc) return rc;
     k_stencil<<<nb, 128, 0, st>>>(b->M, b->F, b->g, b->speed, b->Mn, b->pid, b->interior, b->prm, b->sc, NT);
     k_collide<<<nb, 128, 0, st>>>(b->Mn, b->g, b->pid, b->interior, b->prm, b->sc, NT, 0.5f, nullptr);
@@ -484,6 +531,7 @@ void mem_shock_params_default(mem_shock_params *p) {
     p->graph = 1;
     p->tol = 1e-8f;
     p->maxI = 500;
+    p->na = p->nb = p->nr = 5.0;
 }
 
 void mem_shock_free(mem_shock *s) {

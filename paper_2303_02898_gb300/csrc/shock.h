@@ -36,6 +36,8 @@ struct ShockBatch {
     std::vector<ShockProb> hprm;
     float *M = nullptr, *beta = nullptr, *g = nullptr, *speed = nullptr, *F = nullptr, *Mn = nullptr;
     float *rho0 = nullptr, *sigma = nullptr, *mom = nullptr;
+    float *mu = nullptr;      // [NT][MEM_MU_STRIDE] moment rows (velocity-space rule)
+    double *dom = nullptr;    // [P][4] integration domain (a_x, b_x, b_r, 0) per problem (velocity-space rule)
     int32_t *status = nullptr, *iters = nullptr;
     int *pid = nullptr;
     unsigned char *interior = nullptr;

@@ -152,4 +152,53 @@ __device__ __forceinline__ bool reg_cholesky34_store(float *Hs, int lane) {
     return true;
 }
 
+// Solve (H + lam I) x = rhs by a register-resident Cholesky factorisation,
+// H the 34 x 34 SPD matrix whose lower triangle is in shared memory
+// (row-major, leading dimension LDH).  Lane j < 32 holds column j of the
+// symmetric matrix (all 34 rows) in registers; rows/columns 32 and 33 (the
+// trailing 2 x 2 block) and rhs/x entries 32, 33 are carried, identical, by
+// every lane; entry i < 32 of rhs and x lives on lane i.
+// Right-looking factorisation: in step k lane j takes its own A_kj (= A_jk,
+// the matrix is kept symmetric), the pivot d = A_kk comes from lane k, and
+// every lane j > k applies A_ij -= A_ik A_jk / A_kk for i > k with A_ik
+// broadcast from lane k.  The forward solve L w = rhs rides along (lane i > k
+// subtracts L_ik w_k, L_ik = A_ik / l_k being its own register), and the
+// backward solve L^T x = w broadcasts one x_i per step.  Returns false,
+// uniformly, when a pivot is not positive and finite (the "failed
+// decomposition" of Algorithm 1).
+__device__ __forceinline__ bool reg_chol_solve34(const float *Hs, float lam, int lane, float rhs, float rhs32,
+                                                 float rhs33, float &x, float &x32, float &x33) {
+    float col[NP1];
+#pragma unroll
+    for (int i = 0; i < NP1; ++i) {
+        const int r = i > lane ? i : lane, c = i > lane ? lane : i;
+        float v = Hs[r * LDH + c];
+        if (i == lane) v += lam;
+        col[i] = v;
+    }
+    float t00 = Hs[32 * LDH + 32] + lam, t10 = Hs[33 * LDH + 32], t11 = Hs[33 * LDH + 33] + lam;
+    float bb = rhs, b32 = rhs32, b33 = rhs33;
+    float myinv = 0.f, myw = 0.f;
+    if (!chol_block8<0>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane)) return false;
+    if (!chol_block8<8>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane)) return false;
+    if (!chol_block8<16>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane)) return false;
+    if (!chol_block8<24>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane)) return false;
+    if (!(t00 > 0.f) || !isfinite(t00)) return false;
+    const float inv32 = rsqrtf(t00), l3332 = t10 * inv32, d33 = t11 - l3332 * l3332;
+    if (!(d33 > 0.f) || !isfinite(d33)) return false;
+    const float inv33 = rsqrtf(d33);
+    const float w32 = b32 * inv32, w33 = (b33 - l3332 * w32) * inv33;
+    x33 = w33 * inv33;
+    x32 = (w32 - l3332 * x33) * inv32;
+    // lane j: x_j = (w_j - inv_j sum_{i>j} A_ij x_i) inv_j, with A_ij its own column
+    float acc = fmaf(col[32], x32, col[33] * x33);
+#pragma unroll
+    for (int i = 31; i >= 0; --i) {
+        const float xi = __shfl_sync(0xffffffffu, (myw - myinv * acc) * myinv, i);
+        if (lane == i) x = xi;
+        if (lane < i) acc = fmaf(col[i], xi, acc);
+    }
+    return true;
+}
+
 }  // namespace mem

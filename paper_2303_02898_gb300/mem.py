@@ -35,7 +35,8 @@ class ShockParams(ctypes.Structure):
                 ("xr", ctypes.c_double), ("cfl", ctypes.c_double), ("Pr", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("kn", ctypes.c_double), ("ic", ctypes.c_int32),
                 ("impl", ctypes.c_int32), ("graph", ctypes.c_int32), ("tol", ctypes.c_float),
-                ("maxI", ctypes.c_int32)]
+                ("maxI", ctypes.c_int32), ("na", ctypes.c_double), ("nb", ctypes.c_double),
+                ("nr", ctypes.c_double)]
 
 
 class ShockResult(ctypes.Structure):
@@ -63,6 +64,13 @@ def lib():
                      "mem_serve_progress", "mem_serve_poll", "mem_serve_stats"):
             getattr(L, name).restype = ctypes.c_int
         L.mem_solve.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(SolveOpts), _P]
+        L.mem_solve_gauge.restype = ctypes.c_int
+        L.mem_solve_gauge.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(SolveOpts), _P]
+        L.mem_init_velocity.restype = ctypes.c_int
+        L.mem_init_velocity.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, _P]
+        L.mem_velocity_rule.restype = ctypes.c_int
+        L.mem_velocity_rule.argtypes = [_P, _P, _P]
         L.mem_flux.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P]
         L.mem_flux_axisym.restype = ctypes.c_int
         L.mem_flux_axisym.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P]
@@ -118,13 +126,32 @@ def default_opts(**kw):
 
 
 class Context:
-    """mem_init / mem_destroy: quadrature and statistics tables on the device."""
+    """mem_init / mem_destroy: quadrature and statistics tables on the device.
+    Context.velocity(...) builds a context with a velocity-space rule
+    (mem_init_velocity)."""
 
-    def __init__(self, quad_order=8, degree=4):
-        h = ctypes.c_void_p()
-        _check(lib().mem_init(degree, quad_order, ctypes.byref(h)), "mem_init")
-        self.h = h
+    def __init__(self, quad_order=8, degree=4, _handle=None):
+        if _handle is None:
+            h = ctypes.c_void_p()
+            _check(lib().mem_init(degree, quad_order, ctypes.byref(h)), "mem_init")
+            _handle = h
+        self.h = _handle
         self.quad_order = quad_order
+
+    @classmethod
+    def velocity(cls, domain, nbx=6, nbr=4, ng=8, K=12, degree=4):
+        """Velocity-space block Gauss-Legendre rule on domain (a_x, b_x, b_r)."""
+        h = ctypes.c_void_p()
+        ax, bx, br = (float(v) for v in domain)
+        _check(lib().mem_init_velocity(degree, nbx, nbr, ng, K, ax, bx, br, ctypes.byref(h)), "mem_init_velocity")
+        return cls(quad_order=0, _handle=h)
+
+    def velocity_rule(self):
+        """((nbx, nbr, ng, K), (a_x, b_x, b_r)) of a velocity-space context."""
+        shape = (ctypes.c_int32 * 4)()
+        dom = (ctypes.c_double * 3)()
+        _check(lib().mem_velocity_rule(self.h, shape, dom), "mem_velocity_rule")
+        return tuple(shape), tuple(dom)
 
     def close(self):
         if self.h:
@@ -145,6 +172,14 @@ class Context:
         rc = lib().mem_solve(self.h, _ptr(M), _ptr(beta), _ptr(status), _ptr(iters), B, ctypes.byref(o),
                              _stream(stream))
         _check(rc, "mem_solve")
+
+    def solve_gauge(self, M, beta, gauge, status=None, iters=None, opts=None, stream=None, **kw):
+        """mem_solve_gauge: Algorithm 1 with the cells' gauges (velocity-space rules)."""
+        B = M.shape[0]
+        o = opts if opts is not None else default_opts(**kw)
+        rc = lib().mem_solve_gauge(self.h, _ptr(M), _ptr(beta), _ptr(gauge), _ptr(status), _ptr(iters), B,
+                                   ctypes.byref(o), _stream(stream))
+        _check(rc, "mem_solve_gauge")
 
     def flux(self, M, beta, gauge, F=None, speed=None, stream=None):
         rc = lib().mem_flux(self.h, _ptr(M), _ptr(beta), _ptr(gauge), _ptr(F), _ptr(speed), M.shape[0],

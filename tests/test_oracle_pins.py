@@ -470,3 +470,115 @@ def test_relaxation_time_from_paper_constants(O):
     """Appendix A: Maxwell molecules, mu/Pr = n k T tau; at Kn = 1 (upstream
     mean free path 1, Appendix D) mu = sqrt(2/pi) T, so tau = 1.19683 / n."""
     assert O.RELAX_KN1 / (2.0 / 3.0) == pytest.approx(1.19683, abs=1e-5)
+
+
+# ---------------------------------------------------------------- velocity-space rule
+def _vel_rule(O, rid, dom, nbx=6, nbr=4, ng=8, K=12):
+    return O.set_velocity_rule(rid, dom[0], dom[1], nbx, dom[2], nbr, ng, K)
+
+
+def test_shock_domain_reproduces_paper_boxes(O):
+    """Appendix D's domain formula gives the boxes printed in Section 4: the
+    Mach-4 box with (n_a, n_b, n_r) = (10, 6, 6) to the printed digits; the
+    Mach-10 box with (5, 5, 5) to 1% (the printed box corresponds to n = 4.96
+    with the Rankine-Hugoniot T_+ = 32.1)."""
+    import json
+    import os
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    g = json.load(open(os.path.join(here, "integration_domains.json")))
+    ax, bx, br = O.shock_domain(4.0, 10, 6, 6)
+    m4 = g["mach_4"]
+    assert (ax, bx, br) == pytest.approx((m4["ax"], m4["bx"], m4["br"]), abs=0.05)
+    ax, bx, br = O.shock_domain(10.0, 5, 5, 5)
+    m10 = g["mach_10"]
+    assert (ax, bx, br) == pytest.approx((m10["ax"], m10["bx"], m10["br"]), rel=0.012)
+
+
+def test_velocity_rule_gaussian_orthonormality(O):
+    """beta = 0 is the gauge's Maxwellian: with a box many thermal widths wide
+    the velocity-space rule reproduces E[phi] = e_0 and E[phi phi^T] = I (the
+    statistics are orthonormal under the Gaussian, Appendix B) and
+    E[ubar_x phi_i] = sqrt(a+1) delta(i + e_x) + ... (Hermite recurrence)."""
+    n = _vel_rule(O, 201, (-14.0, 16.0, 13.0), nbx=16, nbr=10, ng=8, K=12)
+    assert n == 128 * 80 * 12
+    g = np.array([1.0, 0.0, 0.0, 1.3, 1.1, 1.1])
+    _, m, S, X, XS = O.expect(201, np.zeros(35), g)
+    e0 = np.zeros(35)
+    e0[0] = 1.0
+    assert np.abs(m - e0).max() < 1e-9
+    assert np.abs(S - np.eye(35)).max() < 1e-9
+    # E[ubar_x phi_k] = sqrt(a+1) E[phi_(a+1)bc] + sqrt(a) E[phi_(a-1)bc] = [k = (1,0,0)]
+    X_want = np.zeros(35)
+    X_want[O.index_of(1, 0, 0)] = 1.0
+    assert np.abs(X - X_want).max() < 1e-9
+
+
+def test_velocity_rule_parity_and_swap_symmetry(O):
+    """K equispaced azimuths (K = 12, a multiple of 4): for beta even in u_y
+    and u_z and symmetric under y <-> z, every moment odd in u_y or u_z
+    vanishes and the y <-> z images are equal, to rounding."""
+    _vel_rule(O, 202, O.shock_domain(3.0))
+    idx = O.basis_index()
+    rng = np.random.default_rng(4)
+    beta = np.zeros(35)
+    for k in range(1, 35):
+        a, b, c = idx[k]
+        if b % 2 == 0 and c % 2 == 0 and b >= c:
+            beta[k] = rng.normal(0, 0.05)
+            beta[O.index_of(a, c, b)] = beta[k]
+    for k in range(1, 35):
+        if idx[k].sum() == 4:
+            beta[k] = -abs(beta[k])
+    g = np.array([2.0, 0.0, 0.0, 1.5, 1.2, 1.2])
+    _, m, S, _, _ = O.expect(202, beta, g)
+    for k in range(35):
+        a, b, c = idx[k]
+        if b % 2 or c % 2:
+            assert abs(m[k]) < 1e-13
+        assert m[k] == pytest.approx(m[O.index_of(a, c, b)], abs=1e-13)
+
+
+def test_velocity_rule_agrees_with_gauss_hermite(O):
+    """Both rules integrate the same smooth density: a mildly non-Gaussian
+    beta in a gauge inside the box gives the same expectations from the
+    velocity-space rule and from a 24-point Gauss-Hermite rule in the gauge
+    frame (axisymmetric beta, since the polar rule is exact in the azimuth
+    only for the azimuthal content of axisymmetric integrands)."""
+    _vel_rule(O, 203, (-12.0, 16.0, 12.0), nbx=8, nbr=5, ng=8, K=12)
+    idx = O.basis_index()
+    beta = np.zeros(35)
+    beta[O.index_of(3, 0, 0)] = 0.04
+    beta[O.index_of(1, 2, 0)] = beta[O.index_of(1, 0, 2)] = 0.02
+    beta[O.index_of(4, 0, 0)] = -0.02
+    # transverse quartic q (u_y^2 + u_z^2)^2: degree-4 part sqrt(24) q (he_4(y) + he_4(z)) + 4 q he_2(y) he_2(z)
+    q = -0.003
+    beta[O.index_of(0, 4, 0)] = beta[O.index_of(0, 0, 4)] = np.sqrt(24.0) * q
+    beta[O.index_of(0, 2, 2)] = 4.0 * q
+    beta[O.index_of(2, 2, 0)] = beta[O.index_of(2, 0, 2)] = -0.01
+    g = np.array([2.0, 0.0, 0.0, 1.4, 1.2, 1.2])
+    _, m1, S1, X1, _ = O.expect(203, beta, g)
+    _, m2, S2, X2, _ = O.expect(24, beta, g)
+    assert np.abs(m1 - m2).max() < 1e-7
+    assert np.abs(S1 - S2).max() < 1e-6
+    assert np.abs(X1 - X2).max() < 1e-7
+    del idx
+
+
+def test_velocity_rule_solve_recovers_moments(O):
+    """Algorithm 1 with the velocity-space rule, gauge passed per cell: the
+    solved parameters reproduce the target moments (computed from known
+    parameters with the same rule) to the convergence tolerance."""
+    _vel_rule(O, 204, O.shock_domain(10.0))
+    idx = O.basis_index()
+    beta_true = np.zeros(35)
+    beta_true[O.index_of(3, 0, 0)] = 0.05
+    beta_true[O.index_of(1, 2, 0)] = beta_true[O.index_of(1, 0, 2)] = 0.03
+    beta_true[O.index_of(4, 0, 0)] = -0.01
+    g = np.array([6.0, 0.0, 0.0, 4.0, 3.5, 3.5])
+    _, m, _, _, _ = O.expect(204, beta_true, g)
+    M = 2.0 * m
+    beta, st, it, res, lam = O.solve(204, M, g=g)
+    assert st & 1
+    assert O.residual(204, beta, M, g) < 1e-8
+    assert np.abs(beta[1:] - beta_true[1:]).max() < 1e-5
+    del idx

@@ -147,6 +147,78 @@ def run_ensemble(mem, ctx, torch, np, nsteps=10):
     return out
 
 
+def run_mach10(mem, torch, np, nsteps=400):
+    """Mach-10 shocks on the velocity-space rule (6 x 4 blocks of 8-point
+    Gauss-Legendre in (u_x, u_r), 12 azimuths; domain from the
+    Rankine-Hugoniot states, n = 5):
+      - the paper's Mach-10 mesh, 150 cells on [-47.1, 47.1], tanh start:
+        cell-updates/s of the graph-captured step, then the steps and wall
+        time to steady state (max |d rho| / (rho_+ - rho_-) < 1e-6 per step,
+        at most 20000 steps);
+      - a packed ensemble of 256 such problems, Mach U[1.2, 10];
+      - 4096 cells on [-50, 50] (cell width 0.024): over-refined by 25x
+        relative to the paper's mesh; reported as far as it stays finite."""
+    from paper_2303_02898_gb300 import workloads
+    out = {}
+    vctx = mem.Context.velocity(mem.shock_domain(mach=10.0))
+    sh = mem.Shock(vctx, mach=10.0, ncells=150, xl=-47.1, xr=47.1, ic=1, graph=1)
+    sh.step(3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sh.step(nsteps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    rec = {"value": 150 * nsteps / dt, "unit": "cell-updates/s", "cells": 150, "domain": [-47.1, 47.1],
+           "steps": nsteps, "ms_per_step": 1e3 * dt / nsteps, "rule": "velocity-space 6x4 blocks x 8 GL, K=12"}
+    done, d = 3 + nsteps, None
+    t1 = time.perf_counter()
+    while done < 20000:
+        d = sh.step(500, steady=True)
+        done += 500
+        if not np.isfinite(d) or d < 1e-6:
+            break
+    torch.cuda.synchronize()
+    prof = sh.get()
+    rec.update({"steady_steps": done, "steady_metric": float(d), "steady_wall_s": time.perf_counter() - t1 + dt,
+                "sim_time": prof["t"], "T_max_over_T_down": float(np.max(prof["T"]) / 32.1233),
+                "finite": bool(np.isfinite(prof["M"]).all())})
+    sh.close()
+    out["shock_mach10_paper_mesh"] = rec
+    rng = np.random.default_rng(7)
+    machs = rng.uniform(1.2, 10.0, 256)
+    probs = [dict(mach=float(m), ncells=150, xl=-47.1, xr=47.1) for m in machs]
+    sh = mem.Shock(vctx, problems=probs, ic=1, graph=1)
+    sh.step(3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sh.step(50)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    fin = all(np.isfinite(sh.problem(i)["rho"]).all() for i in range(0, 256, 15))
+    sh.close()
+    cells = 256 * 150
+    out["ensemble_mach10_paper_mesh"] = {"value": cells * 50 / dt, "unit": "cell-updates/s", "problems": 256,
+                                         "cells": cells, "mach": [1.2, 10.0], "steps": 50,
+                                         "ms_per_step": 1e3 * dt / 50, "finite": fin}
+    sh = mem.Shock(vctx, mach=10.0, ncells=4096, xl=-50.0, xr=50.0, ic=1, graph=0)
+    bad_at = None
+    t0 = time.perf_counter()
+    for k in range(1, 201):
+        sh.step(1)
+        if k % 10 == 0 or k < 10:
+            if not np.isfinite(sh.get()["M"]).all():
+                bad_at = k
+                break
+    dt = time.perf_counter() - t0
+    sh.close()
+    out["shock_mach10_4096_pm50"] = {"cells": 4096, "domain": [-50.0, 50.0], "finite": bad_at is None,
+                                     "non_finite_by_step": bad_at,
+                                     "note": "cell width 0.024 vs the paper's 0.628; the paper reports Mach-10 "
+                                             "runs failing beyond 160 cells (Fig. 7); the FP64 oracle is the check"}
+    vctx.close()
+    return out
+
+
 def run_serving(mem, ctx, torch, np, nreq=32, max_steps=100, chunk=10):
     """Poisson trace (200 req/s, ncells logU[128, 32768], Mach U[1.5, 3]),
     each request capped at max_steps time steps: continuous batching (fused
@@ -383,22 +455,24 @@ def main():
                                "mean_passes": float(it.float().mean())}
         ctx12.close()
         del M12, g12
-        # shock step on 4096 cells over +-50 mean free paths, graph-captured
-        for mach, ic, tag in ((10.0, 1, "mach10"), (SHOCK_MACH, 0, "mach%g" % SHOCK_MACH)):
-            for impl, graph, nst in ((mem.IMPL_FUSED, 1, 200), (mem.IMPL_PLAIN, 0, 10)):
-                sh = mem.Shock(ctx, mach=mach, ncells=4096, xl=-50.0, xr=50.0, impl=impl, graph=graph, ic=ic)
-                sh.step(3)
-                torch.cuda.synchronize()
-                s0 = time.perf_counter()
-                sh.step(nst)
-                torch.cuda.synchronize()
-                sdt = time.perf_counter() - s0
-                d = sh.get()
-                key = "shock_%s_%s" % (tag, "tuned" if impl == mem.IMPL_FUSED else "plain")
-                extras[key] = {"value": 4096 * nst / sdt, "unit": "cell-updates/s", "steps": nst,
-                               "ms_per_step": 1e3 * sdt / nst, "sim_time": d["t"], "ic": "tanh" if ic else "step",
-                               "finite": bool(np.isfinite(d["M"]).all())}
-                sh.close()
+        extras.update(run_mach10(mem, torch, np))
+        # Mach 3 from a step on the Gauss-Hermite rule: 4096 cells at the
+        # paper's cell width 0.628, graph-captured fused step vs plain
+        for impl, graph, nst in ((mem.IMPL_FUSED, 1, 200), (mem.IMPL_PLAIN, 0, 10)):
+            L = 0.5 * 4096 * 0.628
+            sh = mem.Shock(ctx, mach=SHOCK_MACH, ncells=4096, xl=-L, xr=L, impl=impl, graph=graph, ic=0)
+            sh.step(3)
+            torch.cuda.synchronize()
+            s0 = time.perf_counter()
+            sh.step(nst)
+            torch.cuda.synchronize()
+            sdt = time.perf_counter() - s0
+            d = sh.get()
+            key = "shock_mach%g_%s" % (SHOCK_MACH, "tuned" if impl == mem.IMPL_FUSED else "plain")
+            extras[key] = {"value": 4096 * nst / sdt, "unit": "cell-updates/s", "steps": nst,
+                           "ms_per_step": 1e3 * sdt / nst, "sim_time": d["t"], "ic": "step", "cells": 4096,
+                           "domain": [-L, L], "finite": bool(np.isfinite(d["M"]).all())}
+            sh.close()
         extras.update(run_ensemble(mem, ctx, torch, np))
         extras.update(run_serving(mem, ctx, torch, np))
 

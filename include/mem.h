@@ -251,6 +251,11 @@ typedef struct {
 
 void mem_shock_params_default(mem_shock_params *p);
 
+/* Integration domain (a_x, b_x, b_r) that a shock problem with parameters *p
+ * uses on a velocity-space context (Appendix D formula, see na, nb, nr
+ * above); host array of 3.  MEM_EINVAL for invalid parameters. */
+int mem_shock_domain(const mem_shock_params *p, double *domain);
+
 /* Allocate the device state of one shock problem (ncells + 2 ghost cells),
  * set the initial condition and prime the characteristic speeds.
  * Synchronous.  Returns MEM_EINVAL / MEM_ENOMEM / MEM_ECUDA. */

@@ -517,6 +517,16 @@ struct mem_shock {
 
 extern "C" {
 
+int mem_shock_domain(const mem_shock_params *p, double *domain) {
+    if (!p || !domain || !mem_host::shock_params_valid(*p)) return MEM_EINVAL;
+    double d[4];
+    mem_host::shock_domain(*p, d);
+    domain[0] = d[0];
+    domain[1] = d[1];
+    domain[2] = d[2];
+    return MEM_OK;
+}
+
 void mem_shock_params_default(mem_shock_params *p) {
     p->mach = 1.5;
     p->ncells = 64;

@@ -69,6 +69,7 @@ def lib():
         L.mem_init_velocity.restype = ctypes.c_int
         L.mem_init_velocity.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, ctypes.c_double, ctypes.c_double, _P]
+        L.mem_shock_domain.restype = ctypes.c_int
         L.mem_velocity_rule.restype = ctypes.c_int
         L.mem_velocity_rule.argtypes = [_P, _P, _P]
         L.mem_flux.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P]
@@ -220,6 +221,15 @@ def default_shock_params(**kw):
     for k, v in kw.items():
         setattr(p, k, v)
     return p
+
+
+def shock_domain(**kw):
+    """mem_shock_domain: the velocity-space integration domain (a_x, b_x, b_r)
+    of a shock problem with these parameters."""
+    p = default_shock_params(**kw)
+    d = (ctypes.c_double * 3)()
+    _check(lib().mem_shock_domain(ctypes.byref(p), d), "mem_shock_domain")
+    return tuple(d)
 
 
 class Shock:

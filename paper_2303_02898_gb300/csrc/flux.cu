@@ -52,6 +52,13 @@ struct FluxArgs {
     const float *mu;  // moments rows [B][MEM_MU_STRIDE] (moments-in variant)
 };
 
+// Every generalised eigenvalue of (E[u_x phi phi^T], E[phi phi^T]) is a
+// Rayleigh quotient, i.e. a weighted average of the nodes' u_x, so the exact
+// speed never exceeds the node bound.  An FP32 estimate above it (or not
+// finite) comes from a pencil too ill-conditioned for single precision and is
+// replaced by the bound.
+__device__ __forceinline__ float clamp_speed(float sp, float bound) { return sp <= bound ? sp : bound; }
+
 // Extreme generalised eigenvalues of one small symmetric-definite pencil
 // (X, S), n <= 16, lower triangles in shared memory with leading dimension
 // 16: Cholesky S = L L^T (in place), C = L^{-1} X L^{-T} by right-looking
@@ -294,8 +301,7 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
                 mhi = fmaxf(mhi, hi);
             }
             if (lane == 0)
-                A.speed[cell] = ok ? fmaxf(fabsf(wx + sx * mhi), fabsf(wx + sx * mlo))
-                                   : bound;
+                A.speed[cell] = clamp_speed(ok ? fmaxf(fabsf(wx + sx * mhi), fabsf(wx + sx * mlo)) : bound, bound);
             __syncwarp();
             continue;
         }
@@ -425,7 +431,7 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
         __syncwarp();
         const float mu_hi = warp_tridiag_extreme(al, bt, m, true, lane);
         const float mu_lo = warp_tridiag_extreme(al, bt, m, false, lane);
-        if (lane == 0) A.speed[cell] = fmaxf(fabsf(wx + sx * mu_hi), fabsf(wx + sx * mu_lo));
+        if (lane == 0) A.speed[cell] = clamp_speed(fmaxf(fabsf(wx + sx * mu_hi), fabsf(wx + sx * mu_lo)), bound);
         __syncwarp();
     }
 }

@@ -437,7 +437,11 @@ __global__ void __launch_bounds__(64) k_flux_speed(const float *__restrict__ mom
     __syncwarp();
     const float mu_hi = warp_tridiag_extreme(al, bt, m, true, lane);
     const float mu_lo = warp_tridiag_extreme(al, bt, m, false, lane);
-    if (lane == 0) speed[c] = fmaxf(fabsf(wx + sx * mu_hi), fabsf(wx + sx * mu_lo));
+    // the exact speed never exceeds the node bound (Rayleigh quotients of u_x);
+    // a larger or non-finite FP32 estimate is replaced by it
+    const float bound = fmaxf(fabsf(wx + sx * xmax), fabsf(wx - sx * xmax));
+    const float sp = fmaxf(fabsf(wx + sx * mu_hi), fabsf(wx + sx * mu_lo));
+    if (lane == 0) speed[c] = sp <= bound ? sp : bound;
 }
 
 void sgemm(const float *A, const float *Bm, float *C, int M, int N, int K, cudaStream_t st) {

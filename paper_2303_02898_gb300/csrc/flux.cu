@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
             bound = fmaxf(fabsf(row[220]), fabsf(row[221]));
             __syncwarp();
         } else {
-            bound = bound;
+            bound = fmaxf(fabsf(wx + sx * A.xmax), fabsf(wx - sx * A.xmax));
         }
         if (!MU_IN) {
         if (lane < NP) sb[lane] = lane ? A.beta[cell * NP + lane] : 0.f;

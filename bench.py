@@ -120,6 +120,11 @@ def fused_flops_per_pass(n):
     return 2 * fma
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_fused_solve<8> launch
+# on the headline workload (2^20 cells), from one ncu capture of the current
+# kernel (profiles/k_fused_solve_q8_2p20.md); None once the kernel changes.
+TRAFFIC_BYTES = 407.87e6
+
 SHOCK_MACH = 3.0   # largest Mach the 8^3 Gauss-Hermite Hermite-gauge rule keeps stable from a step
 
 
@@ -483,7 +488,7 @@ def main():
             "e2e": e2e, "gpu_launches": args.steps,
             "clocks": clocks,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                         "frac": achieved / peak_fp32, "traffic": None,
+                         "frac": achieved / peak_fp32, "traffic": TRAFFIC_BYTES,
                          "kernel": "k_fused_solve<%d>" % args.order, "kernel_ms": kern_ms,
                          "flops_per_launch": flops, "newton_passes": passes,
                          "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (not in the measured-peaks file)"},

@@ -77,9 +77,11 @@ __device__ __forceinline__ void exponent(const float *v, const float *he, const 
 
 // Eight right-looking Cholesky steps k = K0 .. K0+7 on the register columns
 // (see reg_chol_solve34).  Rows i <= K0 are finished before the block starts,
-// so the row loop runs statically over K0+1 .. 33; within the block the rows
-// i <= k are masked by predication, not by branches, so that all shuffles of
-// one step can be in flight together.
+// so the row loop runs statically over K0+1 .. 33.  No row or lane is masked:
+// lanes j <= k multiply by a zero coefficient (fma(-a, 0, x) == x), and in
+// the live columns j > k the rows i <= k hold entries that were consumed at
+// step i and are never read again (the factor and both triangular solves
+// read rows i >= j only), so one shuffle and one FMA per element suffice.
 template <int K0>
 __device__ __forceinline__ bool chol_block8(float (&col)[NP1], float &t00, float &t10, float &t11, float &bb,
                                             float &b32, float &b33, float &myinv, float &myw, int lane) {
@@ -98,12 +100,12 @@ __device__ __forceinline__ bool chol_block8(float (&col)[NP1], float &t00, float
         const float c = ck * inv2;
         const float wk = __shfl_sync(0xffffffffu, bb, k) * inv;
         const bool upd = lane > k;
+        const float cm = upd ? c : 0.f;
         float r32 = 0.f, r33 = 0.f;
 #pragma unroll
         for (int i = K0 + 1; i < NP1; ++i) {
             const float raw = __shfl_sync(0xffffffffu, col[i], k);
-            const float nv = fmaf(-raw, c, col[i]);
-            col[i] = (upd && i > k) ? nv : col[i];
+            col[i] = fmaf(-raw, cm, col[i]);
             if (i == 32) r32 = raw;
             if (i == 33) r33 = raw;
         }

@@ -400,8 +400,22 @@ int mem_init_velocity(int degree, int nbx, int nbr, int ng, int K, double ax, do
     int rc = mem_host::gl_rule(ng, x, w);
     if (rc) { delete ctx; return rc; }
     std::vector<double> d0 = {ax, bx, br, 0.0};
-    if (!rc) rc = upload(&ctx->d_glx, x);
-    if (!rc) rc = upload(&ctx->d_glw, w);
+    // Per-node constants of the rule: offsets in units of the block width
+    // (x_i = a_x + h_x t_i; y_p = h_r t_m cos(2 pi k / K), z_p likewise with
+    // sin, p = m K + k) and the log weights without the per-cell block widths.
+    const int nx = nbx * ng, nr = nbr * ng;
+    std::vector<double> vtd;
+    std::vector<float> vtf;
+    const double two_pi = 6.283185307179586476925286766559;
+    std::vector<double> rt(nr);
+    for (int m = 0; m < nr; ++m) rt[m] = (m / ng) + 0.5 * (x[m % ng] + 1.0);
+    for (int i = 0; i < nx; ++i) vtd.push_back((i / ng) + 0.5 * (x[i % ng] + 1.0));
+    for (int p = 0; p < nr * K; ++p) vtd.push_back(rt[p / K] * cos(two_pi * (p % K) / K));
+    for (int p = 0; p < nr * K; ++p) vtd.push_back(rt[p / K] * sin(two_pi * (p % K) / K));
+    for (int i = 0; i < nx; ++i) vtf.push_back((float)log(w[i % ng]));
+    for (int m = 0; m < nr; ++m) vtf.push_back((float)log(w[m % ng] * rt[m] / K));
+    if (!rc) rc = upload(&ctx->d_vtd, vtd);
+    if (!rc) rc = upload(&ctx->d_vtf, vtf);
     if (!rc) rc = upload(&ctx->d_dom0, d0);
     if (!rc) rc = build_slot_tables(ctx);
     if (rc) { mem_destroy(ctx); return rc; }
@@ -422,7 +436,7 @@ void mem_destroy(mem_ctx *ctx) {
     cudaDeviceSynchronize();
     void *ptrs[] = {ctx->d_phiT, ctx->d_logw, ctx->d_tab_solve, ctx->d_tab_flux, ctx->d_he1d, ctx->d_x1d,
                     ctx->d_logw1d, ctx->d_lin_off, ctx->d_lin_terms, ctx->d_hess_slots, ctx->d_flux_slots, ctx->d_axi_slots, ctx->d_xlin_off, ctx->d_xlin_terms,
-                    ctx->scratch, ctx->d_glx, ctx->d_glw, ctx->d_dom0};
+                    ctx->scratch, ctx->d_vtd, ctx->d_vtf, ctx->d_dom0};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete ctx;

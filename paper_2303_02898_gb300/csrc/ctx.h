@@ -45,7 +45,8 @@ struct mem_ctx {
     int nbx = 0, nbr = 0, ng = 0, K = 0;     // blocks in u_x, blocks in u_r, points per block, azimuths
     int nx = 0, npt = 0;                     // nodes in u_x; points of the transverse plane
     double dom[3] = {0, 0, 0};               // default domain (a_x, b_x, b_r)
-    double *d_glx = nullptr, *d_glw = nullptr;  // reference Gauss-Legendre rule on [-1, 1]
+    double *d_vtd = nullptr;  // [nx] x-node offsets | [nr] r-node offsets (block widths) | [K] cos | [K] sin
+    float *d_vtf = nullptr;   // [nx] log w^GL of each x node | [nr] log(w^GL t_r / K) of each radial node
     double *d_dom0 = nullptr;                // the default domain (a_x, b_x, b_r, 0) on the device
     // Scratch owned by the context (plain solver, flux).
     std::mutex mu;

@@ -47,7 +47,8 @@ struct VelArgs {
     const int *pid;               // per-cell domain index, or null (domain 0)
     const double *dom;            // (a_x, b_x, b_r, 0) per domain
     const unsigned char *active;  // 0: no solve for this cell (its moments are still produced)
-    const double *glx, *glw;      // reference Gauss-Legendre rule on [-1, 1]
+    const double *vtd;            // [nx] x offsets | [npt] y offsets | [npt] z offsets (in block widths)
+    const float *vtf;             // [nx] log w^GL of the x node | [nr] log(w^GL t_r / K) of the radial node
     const int2 *slots;            // Hessian linearisation terms per lane (warp 0)
     int n_slots;
     int64_t B;
@@ -57,7 +58,7 @@ struct VelArgs {
 };
 
 struct VelLayout {
-    int hx, lwx, hy, hz, T, lwp, pij, vec, H, red, total;
+    int hx, lwx, hy, hz, T, lwp, pij, abc, vec, H, red, total;
 };
 
 __host__ __device__ inline int plane_stride(int npt) { return ((npt + 31) / 32) * 32 + 1; }
@@ -73,6 +74,7 @@ __host__ __device__ inline VelLayout vel_layout(int nx, int npt) {
     L.T = o; o += 10 * PS;
     L.lwp = o; o += PS;
     L.pij = o; o += 596;
+    L.abc = o; o += 220;
     L.vec = o; o += 6 * 36 + 224;  // beta, dbeta, M/n, grad, scalars, spare | mu
     L.H = o; o += NP1 * LDH;
     L.red = o; o += 2 * VW + 2;
@@ -132,32 +134,67 @@ __device__ __forceinline__ void plane_coeffs(const float *v, const float *hy, co
     }
 }
 
-// Per-thread log-sum-exp over the thread's nodes: sum_q exp(e_q) = s e^m.
-template <int PPT>
-__device__ __forceinline__ void node_lse(const float (&c)[PPT][5], const float (&lwp)[PPT], const float *hx,
-                                         const float *lwx, int nx, float &m, float &s) {
-    m = -1e30f;
-    s = 0.f;
-    for (int i = 0; i < nx; ++i) {
-        const float h1 = hx[nx + i], h2 = hx[2 * nx + i], h3 = hx[3 * nx + i], h4 = hx[4 * nx + i];
-        const float lx = lwx[i];
+// Float-float helpers (Dekker products with FMA; __fmul_rn keeps the
+// products from being contracted).  1/s as rh + rl with one Newton correction.
+__device__ __forceinline__ void ff_recip(float s, float &rh, float &rl) {
+    rh = 1.f / s;
+    rl = rh * fmaf(-s, rh, 1.f);
+}
+// ubar = d / s for d given in FP64 (the only FP64 value per coordinate):
+// d = dh + dl, ubar = uh + ul to about 2^-44 relative.
+__device__ __forceinline__ void ff_ubar(double d, float rh, float rl, float &uh, float &ul) {
+    const float dh = (float)d, dl = (float)(d - (double)dh);
+    const float p = __fmul_rn(dh, rh);
+    const float e = fmaf(dh, rh, -p);
+    uh = p;
+    ul = e + fmaf(dh, rl, dl * rh);
+}
+// ubar^2 / 2 = hs + hl.
+__device__ __forceinline__ void ff_half_square(float uh, float ul, float &hs, float &hl) {
+    const float q = __fmul_rn(uh, uh);
+    const float qe = fmaf(uh, uh, -q);
+    hs = 0.5f * q;
+    hl = fmaf(uh, ul, 0.5f * qe);
+}
+
+// Plane stage mu_o = sum_p T_a(p) he_b(y_p) he_c(z_p), o = idx3(a, b, c) < NO,
+// one output per thread; consecutive threads read different rows at the same
+// p, which the odd row stride keeps in distinct banks.  Eight interleaved
+// accumulators keep each FP32 chain short (a single 384-long chain costs
+// ~1e-5 in the moments of the stiffest Mach-10 cells) and give the loads
+// independent work.  Fixed order; the caller synchronises before reading out.
+__device__ __forceinline__ void plane_stage(int NO, const float *sT, const float *hy, const float *hz, int PS,
+                                            int npt, const int *abc, float *out, int warp, int lane) {
+    const int tid = warp * 32 + lane;
+    for (int o = tid; o < NO; o += VT) {
+        const int e = abc[o];
+        const float *Ta = sT + (e & 255) * PS, *Yb = hy + ((e >> 8) & 255) * PS, *Zc = hz + (e >> 16) * PS;
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        int p = 0;
+        for (; p + 7 < npt; p += 8) {
 #pragma unroll
-        for (int r = 0; r < PPT; ++r) {
-            const float e = lx + lwp[r] + c[r][0] + h1 * c[r][1] + h2 * c[r][2] + h3 * c[r][3] + h4 * c[r][4];
-            if (e > m) {
-                s = s * __expf(m - e) + 1.f;
-                m = e;
-            } else {
-                s += __expf(e - m);
-            }
+            for (int u = 0; u < 8; ++u) acc[u] = fmaf(Ta[p + u] * Yb[p + u], Zc[p + u], acc[u]);
         }
+        for (; p < npt; ++p) acc[0] = fmaf(Ta[p] * Yb[p], Zc[p], acc[0]);
+        out[o] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
     }
 }
 
-// x stage: T_a(p) = sum_i sigma(i,p) he_a(x_i), a < AM, sigma = exp(e - logZ).
+// Log-sum-exp and x stage in one sweep: with a running per-thread maximum m,
+// s = sum_q exp(e_q - m) and T_a(p) = sum_i exp(e - m) he_a(x_i), a < AM; a
+// new maximum rescales both.  m starts at m0, the block maximum of the
+// previous evaluation of the same cell (or -1e30), so rescaling, which
+// diverges the warp, is rare; nodes more than ~87 below m0 underflow to zero
+// weight, i.e. sigma < 1e-38.  The caller turns the per-thread results into
+// sigma-weighted moments with one factor exp(m - M) / S from the block
+// maximum M and sum S.
 template <int PPT, int AM>
-__device__ __forceinline__ void node_moments(const float (&c)[PPT][5], const float (&lwp)[PPT], const float *hx,
-                                             const float *lwx, int nx, float lz, float (&T)[PPT][10]) {
+__device__ __forceinline__ void node_lse_moments(const float (&c)[PPT][5], const float (&lwp)[PPT], const float *hx,
+                                                 const float *lwx, int nx, float m0, float &m, float &s,
+                                                 float &emax, float (&T)[PPT][10]) {
+    m = m0;
+    emax = -INFINITY;
+    s = 0.f;
 #pragma unroll
     for (int r = 0; r < PPT; ++r)
 #pragma unroll
@@ -166,25 +203,70 @@ __device__ __forceinline__ void node_moments(const float (&c)[PPT][5], const flo
         float h[AM];
 #pragma unroll
         for (int a = 0; a < AM; ++a) h[a] = hx[a * nx + i];
-        const float lx = lwx[i] - lz;
+        const float lx = lwx[i];
 #pragma unroll
         for (int r = 0; r < PPT; ++r) {
-            const float sg = __expf(lx + lwp[r] + c[r][0] + h[1] * c[r][1] + h[2] * c[r][2] + h[3] * c[r][3] +
-                                    h[4] * c[r][4]);
+            const float e = lx + lwp[r] + c[r][0] + h[1] * c[r][1] + h[2] * c[r][2] + h[3] * c[r][3] + h[4] * c[r][4];
+            emax = fmaxf(emax, e);
+            float w;
+            if (e > m) {
+                const float sc = __expf(m - e);
+                s *= sc;
 #pragma unroll
-            for (int a = 0; a < AM; ++a) T[r][a] = fmaf(sg, h[a], T[r][a]);
+                for (int rr = 0; rr < PPT; ++rr)
+#pragma unroll
+                    for (int a = 0; a < AM; ++a) T[rr][a] *= sc;
+                m = e;
+                w = 1.f;
+            } else {
+                w = __expf(e - m);
+            }
+            s += w;
+#pragma unroll
+            for (int a = 0; a < AM; ++a) T[r][a] = fmaf(w, h[a], T[r][a]);
         }
     }
 }
 
+// One evaluation at the plane coefficients c: the fused sweep, the block
+// log-sum-exp, and the sigma-weighted x stage T_a(p) stored to the shared
+// table (rows a < AM).  Returns log Z; mx carries the block maximum from one
+// evaluation of the cell to the next.  The table is only read by the plane
+// stage, which runs after the accepted evaluation, so a rejected line-search
+// trial just gets overwritten by the next one.
+template <int PPT, int AM>
+__device__ __forceinline__ float sweep_store(const float (&c)[PPT][5], const float (&lwp)[PPT], const float *hx,
+                                             const float *lwx, int nx, float *sT, int PS, int npt, float *red,
+                                             int tid, int warp, int lane, float &mx) {
+    float T[PPT][10];
+    float m, s, em;
+    node_lse_moments<PPT, AM>(c, lwp, hx, lwx, nx, mx, m, s, em, T);
+    // If the true maximum fell far below the warm start, weights near the
+    // top would underflow: redo the sweep from the true maximum (uniform).
+    const float E = block_max(em, red, warp, lane);
+    if (E < mx - 40.f) node_lse_moments<PPT, AM>(c, lwp, hx, lwx, nx, E, m, s, em, T);
+    mx = block_max(m, red, warp, lane);
+    const float Z = block_sum(s * __expf(m - mx), red, warp, lane);
+    const float f = __expf(m - mx) / Z;
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+        const int p = tid + VT * r;
+        if (p < npt) {
+#pragma unroll
+            for (int a = 0; a < AM; ++a) sT[a * PS + p] = T[r][a] * f;
+        }
+    }
+    return mx + __logf(Z);
+}
+
 template <int PPT>
-__global__ void __launch_bounds__(VT) k_vel(VelArgs A) {
+__global__ void __launch_bounds__(VT, 3) k_vel(VelArgs A) {
     extern __shared__ float smem[];
     const VelLayout Ly = vel_layout(A.nx, A.npt);
     const int nx = A.nx, npt = A.npt, PS = A.PS;
     float *s_hx = smem + Ly.hx, *s_lwx = smem + Ly.lwx, *s_hy = smem + Ly.hy, *s_hz = smem + Ly.hz;
     float *s_T = smem + Ly.T, *s_lwp = smem + Ly.lwp, *H = smem + Ly.H, *red = smem + Ly.red;
-    int *s_pij = (int *)(smem + Ly.pij);
+    int *s_pij = (int *)(smem + Ly.pij), *s_abc = (int *)(smem + Ly.abc);
     float *sb = smem + Ly.vec, *sd = sb + 36, *smv = sd + 36, *sg = smv + 36, *sx = sg + 36, *smu = sx + 72;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const mem_solve_opts &o = A.o;
@@ -193,6 +275,7 @@ __global__ void __launch_bounds__(VT) k_vel(VelArgs A) {
         while ((i + 1) * (i + 2) / 2 <= t) ++i;
         s_pij[t] = i | ((t - i * (i + 1) / 2) << 8);
     }
+    for (int t = tid; t < 220; t += VT) s_abc[t] = exp_a(t) | (exp_b(t) << 8) | (exp_c(t) << 16);
 
     for (int64_t cell = blockIdx.x; cell < A.B; cell += gridDim.x) {
         const bool do_solve = A.solve && (!A.active || A.active[cell]);
@@ -200,38 +283,47 @@ __global__ void __launch_bounds__(VT) k_vel(VelArgs A) {
         // ---- the rule as seen from this cell
         const float *gc = A.gauge + cell * 6;
         const float wx = gc[0], wy = gc[1], wz = gc[2], sx_ = gc[3], sy = gc[4], sz = gc[5];
-        // Node coordinates relative to the gauge and the log weights are
-        // formed in FP64 (about nx + npt values per cell): in FP32 the
-        // cancellation in u - w costs ~1e-6 in ubar on a 50-wide box, which
-        // shows up as ~1e-5 in the degree-4 moments of a cold cell.
+        // u - w cancels on a box tens of thermal widths wide, and the hot tail
+        // of a mixed cell sits at |ubar| ~ 5-10, where plain FP32 rounding of
+        // ubar and ubar^2 / 2 moves its weights by ~1e-5.  So u - w is formed
+        // in FP64 (one FMA and one subtraction per coordinate) and split into
+        // a float pair; ubar = (u - w) / s and ubar^2 / 2 follow in error-free
+        // float-float arithmetic and the log weight is rounded once.  (FP64
+        // beyond that stalls the whole SM on this part.)
         const double *dm = A.dom + 4 * (A.pid ? A.pid[cell] : 0);
-        const double hxw = (dm[1] - dm[0]) / A.nbx, hr = dm[2] / A.nbr;
+        const double ax = dm[0], hxw = (dm[1] - dm[0]) / A.nbx, hr = dm[2] / A.nbr;
+        const float lhx = __logf(0.5f * (float)hxw), lhr2 = 2.f * __logf((float)hr);
+        float rxh, rxl, ryh, ryl, rzh, rzl;
+        ff_recip(sx_, rxh, rxl);
+        ff_recip(sy, ryh, ryl);
+        ff_recip(sz, rzh, rzl);
+        const double *xt = A.vtd, *yt = A.vtd + nx, *zt = yt + npt;
+        const float *lgx = A.vtf, *lrw = A.vtf + nx;
         __syncthreads();  // the previous cell is done with every table
         for (int i = tid; i < nx; i += VT) {
-            const int blk = i / A.ng, l = i - blk * A.ng;
-            const double x = dm[0] + hxw * ((double)blk + 0.5 * (A.glx[l] + 1.0));
-            const double ub = (x - (double)wx) / (double)sx_;
+            float uh, ul, hs, hl;
+            ff_ubar(fma(hxw, xt[i], ax) - (double)wx, rxh, rxl, uh, ul);
+            ff_half_square(uh, ul, hs, hl);
             float h[10];
-            hermite_vals<9>((float)ub, h);
+            hermite_vals<9>(uh, h);
 #pragma unroll
             for (int a = 0; a < 10; ++a) s_hx[a * nx + i] = h[a];
-            s_lwx[i] = (float)(log(0.5 * hxw * A.glw[l]) - 0.5 * ub * ub);
+            s_lwx[i] = ((lhx + lgx[i]) - hs) - hl;
         }
         for (int p = tid; p < npt; p += VT) {
-            const int rk = p / A.K, k = p - rk * A.K;
-            const int blk = rk / A.ng, l = rk - blk * A.ng;
-            const double rr = hr * ((double)blk + 0.5 * (A.glx[l] + 1.0));
-            double sn, cs;
-            sincospi(2.0 * k / A.K, &sn, &cs);
-            const double uy = (rr * cs - (double)wy) / (double)sy, uz = (rr * sn - (double)wz) / (double)sz;
+            float yh, yl, zh, zl, ys, yls, zs, zls;
+            ff_ubar(fma(hr, yt[p], -(double)wy), ryh, ryl, yh, yl);
+            ff_ubar(fma(hr, zt[p], -(double)wz), rzh, rzl, zh, zl);
+            ff_half_square(yh, yl, ys, yls);
+            ff_half_square(zh, zl, zs, zls);
             float h[10];
-            hermite_vals<9>((float)uy, h);
+            hermite_vals<9>(yh, h);
 #pragma unroll
             for (int a = 0; a < 10; ++a) s_hy[a * PS + p] = h[a];
-            hermite_vals<9>((float)uz, h);
+            hermite_vals<9>(zh, h);
 #pragma unroll
             for (int a = 0; a < 10; ++a) s_hz[a * PS + p] = h[a];
-            s_lwp[p] = (float)(log(0.5 * hr * A.glw[l] * rr * 2.0 / A.K) - 0.5 * (uy * uy + uz * uz));
+            s_lwp[p] = ((lhr2 + lrw[p / A.K]) - (ys + zs)) - (yls + zls);
         }
         // ---- load and validate
         const float *Mc = A.M + cell * NP;
@@ -251,19 +343,19 @@ __global__ void __launch_bounds__(VT) k_vel(VelArgs A) {
 #pragma unroll
         for (int r = 0; r < PPT; ++r) lwp[r] = tid + VT * r < npt ? s_lwp[tid + VT * r] : -INFINITY;
         float cb[PPT][5], cd[PPT][5], ca[PPT][5];
+        float mxc = -1e30f;  // block maximum of the exponent at the latest evaluation of this cell
         if (do_solve && bad) {
             if (tid == 0) {
                 if (A.status) A.status[cell] = MEM_ST_BADINPUT;
                 if (A.iters) A.iters[cell] = 0;
             }
         } else if (do_solve) {
-            // ---- Algorithm 1
+            // ---- Algorithm 1.  Every evaluation of the partition function
+            // also produces the x stage at the same beta (node_lse_moments):
+            // the accepted line-search trial therefore already carries the
+            // moments of the next pass.
             plane_coeffs<PPT>(sb, s_hy, s_hz, PS, npt, tid, cb);
-            float m, s;
-            node_lse<PPT>(cb, lwp, s_hx, s_lwx, nx, m, s);
-            float mx = block_max(m, red, warp, lane);
-            float Z = block_sum(s * __expf(m - mx), red, warp, lane);
-            float lz = mx + __logf(Z);
+            const float lz0 = sweep_store<PPT, 9>(cb, lwp, s_hx, s_lwx, nx, s_T, PS, npt, red, tid, warp, lane, mxc);
             if (warp == 0) {
                 const float pb = (lane >= 1 && lane < NP ? sb[lane] * smv[lane] : 0.f) +
                                  (lane + 32 < NP ? sb[lane + 32] * smv[lane + 32] : 0.f);
@@ -272,35 +364,13 @@ __global__ void __launch_bounds__(VT) k_vel(VelArgs A) {
             }
             __syncthreads();
             float mb = sx[4];
-            float Lcur = lz - mb, alpha = 1.f;
+            float Lcur = lz0 - mb, alpha = 1.f;
             int st = 0, it = 0;
             while (true) {
-                // ---- sigma, x stage and plane stage: mu_abc, a+b+c <= 8
-                {
-                    float T[PPT][10];
-                    node_moments<PPT, 9>(cb, lwp, s_hx, s_lwx, nx, lz, T);
-#pragma unroll
-                    for (int r = 0; r < PPT; ++r) {
-                        const int p = tid + VT * r;
-                        if (p < npt) {
-#pragma unroll
-                            for (int a = 0; a < 9; ++a) s_T[a * PS + p] = T[r][a];
-                        }
-                    }
-                }
+                // ---- plane stage on the x stage of the last accepted sweep:
+                // mu_abc, a+b+c <= 8
                 __syncthreads();
-                for (int t = tid; t < 165; t += VT) {
-                    const int a = exp_a(t), b = exp_b(t), c = exp_c(t);
-                    const float *Ta = s_T + a * PS, *Yb = s_hy + b * PS, *Zc = s_hz + c * PS;
-                    float a0 = 0.f, a1 = 0.f;
-                    int p = 0;
-                    for (; p + 1 < npt; p += 2) {
-                        a0 = fmaf(Ta[p] * Yb[p], Zc[p], a0);
-                        a1 = fmaf(Ta[p + 1] * Yb[p + 1], Zc[p + 1], a1);
-                    }
-                    if (p < npt) a0 = fmaf(Ta[p] * Yb[p], Zc[p], a0);
-                    smu[t] = a0 + a1;
-                }
+                plane_stage(165, s_T, s_hy, s_hz, PS, npt, s_abc, smu, warp, lane);
                 __syncthreads();
                 // ---- warp 0: gradient, Hessian (Appendix C), Cholesky with
                 // lambda I, Newton direction
@@ -380,10 +450,7 @@ __global__ void __launch_bounds__(VT) k_vel(VelArgs A) {
                     for (int r = 0; r < PPT; ++r)
 #pragma unroll
                         for (int a = 0; a < 5; ++a) ca[r][a] = fmaf(alpha, cd[r][a], cb[r][a]);
-                    node_lse<PPT>(ca, lwp, s_hx, s_lwx, nx, m, s);
-                    mx = block_max(m, red, warp, lane);
-                    Z = block_sum(s * __expf(m - mx), red, warp, lane);
-                    lz = mx + __logf(Z);
+                    const float lz = sweep_store<PPT, 9>(ca, lwp, s_hx, s_lwx, nx, s_T, PS, npt, red, tid, warp, lane, mxc);
                     Lt = lz - (mb + alpha * md);
                     const float LD = Lcur - Lt, gradD = -o.c_armijo * alpha * gd;
                     sat = (LD - gradD) >= -(o.atol + o.rtol * fabsf(LD));
@@ -408,42 +475,15 @@ __global__ void __launch_bounds__(VT) k_vel(VelArgs A) {
         if (A.mu) {
             __syncthreads();
             plane_coeffs<PPT>(sb, s_hy, s_hz, PS, npt, tid, cb);
-            float m, s;
-            node_lse<PPT>(cb, lwp, s_hx, s_lwx, nx, m, s);
-            const float mx = block_max(m, red, warp, lane);
-            const float Z = block_sum(s * __expf(m - mx), red, warp, lane);
-            const float lz = mx + __logf(Z);
-            {
-                float T[PPT][10];
-                node_moments<PPT, 10>(cb, lwp, s_hx, s_lwx, nx, lz, T);
-#pragma unroll
-                for (int r = 0; r < PPT; ++r) {
-                    const int p = tid + VT * r;
-                    if (p < npt) {
-#pragma unroll
-                        for (int a = 0; a < 10; ++a) s_T[a * PS + p] = T[r][a];
-                    }
-                }
-            }
+            sweep_store<PPT, 10>(cb, lwp, s_hx, s_lwx, nx, s_T, PS, npt, red, tid, warp, lane, mxc);
             __syncthreads();
             float *out = A.mu + cell * MEM_MU_STRIDE;
-            for (int t = tid; t < 220; t += VT) {
-                const int a = exp_a(t), b = exp_b(t), c = exp_c(t);
-                const float *Ta = s_T + a * PS, *Yb = s_hy + b * PS, *Zc = s_hz + c * PS;
-                float a0 = 0.f, a1 = 0.f;
-                int p = 0;
-                for (; p + 1 < npt; p += 2) {
-                    a0 = fmaf(Ta[p] * Yb[p], Zc[p], a0);
-                    a1 = fmaf(Ta[p + 1] * Yb[p + 1], Zc[p + 1], a1);
-                }
-                if (p < npt) a0 = fmaf(Ta[p] * Yb[p], Zc[p], a0);
-                out[t] = a0 + a1;
-            }
+            plane_stage(220, s_T, s_hy, s_hz, PS, npt, s_abc, out, warp, lane);
             if (tid == 0) {
                 // u_x range of the nodes: the speed bound when the pencil has
                 // no reliable spectrum
-                out[220] = (float)(dm[0] + hxw * 0.5 * (A.glx[0] + 1.0));
-                out[221] = (float)(dm[0] + hxw * ((double)(A.nbx - 1) + 0.5 * (A.glx[A.ng - 1] + 1.0)));
+                out[220] = (float)fma(hxw, xt[0], ax);
+                out[221] = (float)fma(hxw, xt[nx - 1], ax);
             }
         }
     }
@@ -478,7 +518,7 @@ int vel_run(mem_ctx *ctx, const float *M, float *beta, const float *g, int32_t *
     VelArgs a;
     a.M = M; a.beta = beta; a.gauge = g; a.status = status; a.iters = iters; a.mu = mu;
     a.pid = pid; a.dom = dom ? dom : ctx->d_dom0; a.active = active;
-    a.glx = ctx->d_glx; a.glw = ctx->d_glw;
+    a.vtd = ctx->d_vtd; a.vtf = ctx->d_vtf;
     a.slots = ctx->d_hess_slots; a.n_slots = ctx->n_hess_slots;
     a.B = B;
     a.nbx = ctx->nbx; a.nbr = ctx->nbr; a.ng = ctx->ng; a.K = ctx->K;

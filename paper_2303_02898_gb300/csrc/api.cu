@@ -188,11 +188,20 @@ static void build_lin_terms(int j0, bool with_x, std::vector<int> &off, std::vec
 // [t][l] as (mu index | p << 8 | last-term flag in the sign bit, coefficient).
 // Sequences are padded with zero terms to a common length.
 static void build_hess_slots(const std::vector<int> &off, const std::vector<int2> &terms, std::vector<int2> &slots,
-                             int &nslots, const std::vector<int> *off2 = nullptr, const std::vector<int2> *terms2 = nullptr) {
+                             int &nslots, const std::vector<int> *off2 = nullptr, const std::vector<int2> *terms2 = nullptr,
+                             int L = 32) {
     const int NE1 = (int)off.size() - 1, NE2 = off2 ? (int)off2->size() - 1 : 0;
-    std::vector<std::vector<int2>> per(32);
+    std::vector<std::vector<int2>> per(L);
     for (int p = 0; p < NE1 + NE2; ++p) {
-        auto &v = per[p % 32];
+        // L = 32: entry p on lane p % 32; wider tables put each entry on the
+        // lane with the fewest terms so far (entries have 1 to 30 terms).
+        int lane = p % 32;
+        if (L != 32) {
+            lane = 0;
+            for (int l = 1; l < L; ++l)
+                if (per[l].size() < per[lane].size()) lane = l;
+        }
+        auto &v = per[lane];
         const std::vector<int> &o = p < NE1 ? off : *off2;
         const std::vector<int2> &tm = p < NE1 ? terms : *terms2;
         const int q = p < NE1 ? p : p - NE1;
@@ -205,9 +214,9 @@ static void build_hess_slots(const std::vector<int> &off, const std::vector<int2
     }
     nslots = 0;
     for (auto &v : per) nslots = std::max(nslots, (int)v.size());
-    slots.assign((size_t)nslots * 32, int2{0, 0});
-    for (int l = 0; l < 32; ++l)
-        for (int t = 0; t < (int)per[l].size(); ++t) slots[(size_t)t * 32 + l] = per[l][t];
+    slots.assign((size_t)nslots * L, int2{0, 0});
+    for (int l = 0; l < L; ++l)
+        for (int t = 0; t < (int)per[l].size(); ++t) slots[(size_t)t * L + l] = per[l][t];
 }
 
 // Axisymmetric cells (invariant under u_y -> -u_y and u_z -> -u_z, as every
@@ -288,6 +297,8 @@ static int build_slot_tables(mem_ctx *ctx) {
     build_lin_terms(0, true, xoff, xterms);
     std::vector<int2> slots, fslots;
     build_hess_slots(off, terms, slots, ctx->n_hess_slots);
+    std::vector<int2> slots128;
+    build_hess_slots(off, terms, slots128, ctx->n_hess_slots128, nullptr, nullptr, 128);
     std::vector<int> soff;
     std::vector<int2> sterms;
     build_lin_terms(1, false, soff, sterms);  // E[phi_i phi_j], i >= j >= 1
@@ -316,6 +327,7 @@ static int build_slot_tables(mem_ctx *ctx) {
     if (!rc) rc = upload(&ctx->d_lin_off, off);
     if (!rc) rc = upload(&ctx->d_lin_terms, terms);
     if (!rc) rc = upload(&ctx->d_hess_slots, slots);
+    if (!rc) rc = upload(&ctx->d_hess_slots128, slots128);
     if (!rc) rc = upload(&ctx->d_flux_slots, fslots);
     if (!rc) rc = upload(&ctx->d_axi_slots, aslots);
     if (!rc) rc = upload(&ctx->d_xlin_off, xoff);
@@ -435,7 +447,7 @@ void mem_destroy(mem_ctx *ctx) {
     if (!ctx) return;
     cudaDeviceSynchronize();
     void *ptrs[] = {ctx->d_phiT, ctx->d_logw, ctx->d_tab_solve, ctx->d_tab_flux, ctx->d_he1d, ctx->d_x1d,
-                    ctx->d_logw1d, ctx->d_lin_off, ctx->d_lin_terms, ctx->d_hess_slots, ctx->d_flux_slots, ctx->d_axi_slots, ctx->d_xlin_off, ctx->d_xlin_terms,
+                    ctx->d_logw1d, ctx->d_lin_off, ctx->d_lin_terms, ctx->d_hess_slots, ctx->d_hess_slots128, ctx->d_flux_slots, ctx->d_axi_slots, ctx->d_xlin_off, ctx->d_xlin_terms,
                     ctx->scratch, ctx->d_vtd, ctx->d_vtf, ctx->d_dom0};
     for (void *p : ptrs)
         if (p) cudaFree(p);

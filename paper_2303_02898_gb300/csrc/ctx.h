@@ -33,6 +33,8 @@ struct mem_ctx {
     int n_lin_terms = 0;
     int2 *d_hess_slots = nullptr;  // [n_hess_slots][32] per-lane Hessian term sequences
     int n_hess_slots = 0;
+    int2 *d_hess_slots128 = nullptr;  // [n_hess_slots128][128] the same terms over 128 lanes (block per cell)
+    int n_hess_slots128 = 0;
     int2 *d_flux_slots = nullptr;  // [n_flux_slots][32] E[phi phi^T] and E[ubar_x phi phi^T] terms
     int n_flux_slots = 0;
     int2 *d_axi_slots = nullptr;   // [n_axi_slots][32] the same, parity blocks of axisymmetric cells

@@ -49,7 +49,7 @@ struct VelArgs {
     const unsigned char *active;  // 0: no solve for this cell (its moments are still produced)
     const double *vtd;            // [nx] x offsets | [npt] y offsets | [npt] z offsets (in block widths)
     const float *vtf;             // [nx] log w^GL of the x node | [nr] log(w^GL t_r / K) of the radial node
-    const int2 *slots;            // Hessian linearisation terms per lane (warp 0)
+    const int2 *slots;            // Hessian linearisation terms over the block's 128 lanes
     int n_slots;
     int64_t B;
     int nbx, nbr, ng, K, nx, npt, PS;
@@ -372,27 +372,26 @@ __global__ void __launch_bounds__(VT, 3) k_vel(VelArgs A) {
                 __syncthreads();
                 plane_stage(165, s_T, s_hy, s_hz, PS, npt, s_abc, smu, warp, lane);
                 __syncthreads();
-                // ---- warp 0: gradient, Hessian (Appendix C), Cholesky with
-                // lambda I, Newton direction
-                if (warp == 0) {
-                    if (lane >= 1 && lane < NP) sg[lane] = smu[lane] - smv[lane];
-                    if (lane + 32 < NP) sg[lane + 32] = smu[lane + 32] - smv[lane + 32];
-                    __syncwarp();
-                    {
-                        float acc = 0.f;
+                // ---- gradient and Hessian (Appendix C) by the whole block,
+                // from the linearisation terms spread over 128 lanes
+                if (tid >= 1 && tid < NP) sg[tid] = smu[tid] - smv[tid];
+                {
+                    float acc = 0.f;
 #pragma unroll 4
-                        for (int t = 0; t < A.n_slots; ++t) {
-                            const int2 sl = __ldg(&A.slots[t * 32 + lane]);
-                            acc = fmaf(__int_as_float(sl.y), smu[sl.x & 255], acc);
-                            if (sl.x < 0) {
-                                const int pp = (sl.x >> 8) & 1023;
-                                const int pij = s_pij[pp], i = pij & 255, j = pij >> 8;
-                                H[i * LDH + j] = acc - smu[i + 1] * smu[j + 1];
-                                acc = 0.f;
-                            }
+                    for (int t = 0; t < A.n_slots; ++t) {
+                        const int2 sl = __ldg(&A.slots[t * VT + tid]);
+                        acc = fmaf(__int_as_float(sl.y), smu[sl.x & 255], acc);
+                        if (sl.x < 0) {
+                            const int pp = (sl.x >> 8) & 1023;
+                            const int pij = s_pij[pp], i = pij & 255, j = pij >> 8;
+                            H[i * LDH + j] = acc - smu[i + 1] * smu[j + 1];
+                            acc = 0.f;
                         }
                     }
-                    __syncwarp();
+                }
+                __syncthreads();
+                // ---- warp 0: Cholesky with lambda I, Newton direction
+                if (warp == 0) {
                     const float g_l = sg[lane + 1], g32 = sg[33], g33 = sg[34];
                     float x = 0.f, x32 = 0.f, x33 = 0.f, lam = 0.f;
                     bool ok = false, used = false;
@@ -519,7 +518,7 @@ int vel_run(mem_ctx *ctx, const float *M, float *beta, const float *g, int32_t *
     a.M = M; a.beta = beta; a.gauge = g; a.status = status; a.iters = iters; a.mu = mu;
     a.pid = pid; a.dom = dom ? dom : ctx->d_dom0; a.active = active;
     a.vtd = ctx->d_vtd; a.vtf = ctx->d_vtf;
-    a.slots = ctx->d_hess_slots; a.n_slots = ctx->n_hess_slots;
+    a.slots = ctx->d_hess_slots128; a.n_slots = ctx->n_hess_slots128;
     a.B = B;
     a.nbx = ctx->nbx; a.nbr = ctx->nbr; a.ng = ctx->ng; a.K = ctx->K;
     a.nx = ctx->nx; a.npt = ctx->npt; a.PS = plane_stride(ctx->npt);

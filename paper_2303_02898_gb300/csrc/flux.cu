@@ -29,13 +29,18 @@ namespace {
 constexpr int FWARPS = 2;
 constexpr int LDF = 36;
 
-template <int N>
+// Per-warp work area: the stage buffers (unless the moments come in), then
+// the matrices of the speed: 2 x 35 x 36 for the full pencil, 928 floats for
+// the three parity blocks (offsets up to 848 + 5 x 16).  A smaller area keeps
+// more warps resident.
+template <int N, bool AXI = false, bool MU_IN = false>
 struct FluxCfg {
     using C = FusedCfg<N>;
     static constexpr int S1 = 10 * C::P;  // stage x, a <= 9
     static constexpr int T2 = 55 * N;     // stage y, a + b <= 9
-    static constexpr int MAT = 2 * NP * LDF;
-    static constexpr int WORK = (S1 + T2) > MAT ? (S1 + T2) : MAT;
+    static constexpr int STAGES = MU_IN ? 0 : S1 + T2;
+    static constexpr int MAT = AXI ? 928 : 2 * NP * LDF;
+    static constexpr int WORK = STAGES > MAT ? STAGES : MAT;
     static constexpr int WARP_FLOATS = 36 + 224 + 2 * 36 + 36 + 72 + WORK;  // beta, mu, alpha/beta, v, l0/inv, work
 };
 
@@ -146,7 +151,7 @@ __device__ __forceinline__ bool small_pencil_extremes(float *S, float *X, int n,
 template <int N, bool AXI, bool MU_IN>
 __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
     using C = FusedCfg<N>;
-    using Cf = FluxCfg<N>;
+    using Cf = FluxCfg<N, AXI, MU_IN>;
     extern __shared__ float smem[];
     float *s_he = smem;
     float *s_lw = s_he + N * MEM_HE_STRIDE;
@@ -438,7 +443,7 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
 
 template <int N, bool AXI, bool MU_IN = false>
 int launch_flux(mem_ctx *ctx, const FluxArgs &a, cudaStream_t st) {
-    using Cf = FluxCfg<N>;
+    using Cf = FluxCfg<N, AXI, MU_IN>;
     const size_t smem = sizeof(float) * (N * MEM_HE_STRIDE + 16 + 224 + 56 + 596 + 632) + sizeof(float) * FWARPS * Cf::WARP_FLOATS;
     static int configured = 0;
     if (!configured) {

@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
         __syncwarp();
         // Cholesky of S = E[phi phi^T] by bordering: phi_0 = 1 gives
         // chol(S) = [[sqrt S00, 0], [m / sqrt S00, chol(S_1 - m m^T / S00)]].
-        if (!(smu[0] > 0.f) || !reg_cholesky34_store(L, lane)) {
+        if (!(smu[0] > 0.f) || !reg_cholesky34_store(L, lane, al)) {  // al: free until Lanczos
             if (lane == 0) A.speed[cell] = bound;
             continue;
         }
@@ -444,6 +444,8 @@ __global__ void __launch_bounds__(FWARPS * 32) k_fused_flux(FluxArgs A) {
 template <int N, bool AXI, bool MU_IN = false>
 int launch_flux(mem_ctx *ctx, const FluxArgs &a, cudaStream_t st) {
     using Cf = FluxCfg<N, AXI, MU_IN>;
+    // per-warp areas and the Cholesky broadcast column (al = W + 260) are 16-byte aligned
+    static_assert((N * MEM_HE_STRIDE + 16 + 224 + 56 + 596 + 632) % 4 == 0 && Cf::WARP_FLOATS % 4 == 0, "alignment");
     const size_t smem = sizeof(float) * (N * MEM_HE_STRIDE + 16 + 224 + 56 + 596 + 632) + sizeof(float) * FWARPS * Cf::WARP_FLOATS;
     static int configured = 0;
     if (!configured) {

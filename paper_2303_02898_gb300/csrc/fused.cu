@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(WARPS * 32, (N <= 8 ? 4 : 2)) k_fused_solve(Fu
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *W = wbase + warp * C::WARP_FLOATS;
-    float *sb = W, *sd = W + 36, *sm = W + 72, *sg = W + 108, *smu = W + 180;
+    float *sb = W, *sd = W + 36, *sm = W + 72, *sg = W + 108, *sbc = W + 144, *smu = W + 180;
     float *work = smu + 168;
     float *S1 = work, *T2 = work + C::S1, *H = work;  // H aliases the stage buffers
     const mem_solve_opts &o = A.o;
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(WARPS * 32, (N <= 8 ? 4 : 2)) k_fused_solve(Fu
             bool ok = false;
             float lam = 0.f;
             for (int t = 0; t <= o.max_lambda; ++t) {
-                ok = reg_chol_solve34(H, lam, lane, -g_l, -g32, -g33, x, x32, x33);
+                ok = reg_chol_solve34(H, lam, lane, -g_l, -g32, -g33, x, x32, x33, sbc);
                 if (ok) break;
                 st |= MEM_ST_LAMBDA;
                 lam = (t == 0) ? o.lambda0 : lam * o.lambda_mul;
@@ -282,6 +282,8 @@ __global__ void __launch_bounds__(WARPS * 32, (N <= 8 ? 4 : 2)) k_fused_solve(Fu
 template <int N>
 int launch_fused(mem_ctx *ctx, const FusedArgs &a, cudaStream_t st) {
     using C = FusedCfg<N>;
+    // the per-warp areas (and the broadcast column at W + 144) are 16-byte aligned
+    static_assert((N * MEM_HE_STRIDE + 16 + 168 + 596 + 48) % 4 == 0 && C::WARP_FLOATS % 4 == 0, "alignment");
     const size_t smem = sizeof(float) * (N * MEM_HE_STRIDE + 16 + 168 + 596 + 48) + sizeof(float) * WARPS * C::WARP_FLOATS;
     static int configured = 0;
     if (!configured) {

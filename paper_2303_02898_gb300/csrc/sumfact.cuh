@@ -20,8 +20,10 @@ struct FusedCfg {
     static constexpr int S1 = 9 * P;             // stage-x output
     static constexpr int T2 = 45 * N;            // stage-y output
     static constexpr int WORK = (S1 + T2) > (NP1 * LDH) ? (S1 + T2) : (NP1 * LDH);
-    // per-warp floats: beta, dbeta, M/n, grad, rhs, mu(165) + work
-    static constexpr int WARP_FLOATS = 5 * 36 + 168 + WORK;
+    // per-warp floats: beta, dbeta, M/n, grad, Cholesky broadcast column,
+    // mu(165) + work; a multiple of 4 so that every warp's area (and the
+    // 16-byte vector accesses of the broadcast column) stays aligned
+    static constexpr int WARP_FLOATS = ((5 * 36 + 168 + WORK + 3) / 4) * 4;
 };
 
 // Exponent contribution of a parameter vector v (slots 1..34) on the lane's
@@ -77,14 +79,18 @@ __device__ __forceinline__ void exponent(const float *v, const float *he, const 
 
 // Eight right-looking Cholesky steps k = K0 .. K0+7 on the register columns
 // (see reg_chol_solve34).  Rows i <= K0 are finished before the block starts,
-// so the row loop runs statically over K0+1 .. 33.  No row or lane is masked:
+// so the row loop runs statically over K0+1 .. 33.  bc is a per-warp,
+// 16-byte-aligned scratch of 36 floats for the pivot column.  No row or lane
+// is masked:
 // lanes j <= k multiply by a zero coefficient (fma(-a, 0, x) == x), and in
 // the live columns j > k the rows i <= k hold entries that were consumed at
 // step i and are never read again (the factor and both triangular solves
 // read rows i >= j only), so one shuffle and one FMA per element suffice.
 template <int K0>
 __device__ __forceinline__ bool chol_block8(float (&col)[NP1], float &t00, float &t10, float &t11, float &bb,
-                                            float &b32, float &b33, float &myinv, float &myw, int lane) {
+                                            float &b32, float &b33, float &myinv, float &myw, int lane,
+                                            float *bc) {
+    constexpr int I0 = ((K0 + 1) / 4) * 4;  // first 16-byte group holding a live row
 #pragma unroll 1
     for (int kk = 0; kk < 8; ++kk) {
         const int k = K0 + kk;
@@ -101,14 +107,29 @@ __device__ __forceinline__ bool chol_block8(float (&col)[NP1], float &t00, float
         const float wk = __shfl_sync(0xffffffffu, bb, k) * inv;
         const bool upd = lane > k;
         const float cm = upd ? c : 0.f;
-        float r32 = 0.f, r33 = 0.f;
+        // The pivot lane publishes its column (rows I0..33) with 16-byte
+        // stores and every lane reads it back with broadcast loads: about a
+        // quarter of the memory-pipe instructions of one shuffle per row.
+        __syncwarp();  // the previous step's column has been read
+        if (lane == k) {
 #pragma unroll
-        for (int i = K0 + 1; i < NP1; ++i) {
-            const float raw = __shfl_sync(0xffffffffu, col[i], k);
-            col[i] = fmaf(-raw, cm, col[i]);
-            if (i == 32) r32 = raw;
-            if (i == 33) r33 = raw;
+            for (int i = I0; i < 32; i += 4)
+                *reinterpret_cast<float4 *>(bc + i) = make_float4(col[i], col[i + 1], col[i + 2], col[i + 3]);
+            *reinterpret_cast<float2 *>(bc + 32) = make_float2(col[32], col[33]);
         }
+        __syncwarp();
+#pragma unroll
+        for (int i = I0; i < 32; i += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(bc + i);
+            if (i + 0 > K0) col[i + 0] = fmaf(-v.x, cm, col[i + 0]);
+            if (i + 1 > K0) col[i + 1] = fmaf(-v.y, cm, col[i + 1]);
+            if (i + 2 > K0) col[i + 2] = fmaf(-v.z, cm, col[i + 2]);
+            if (i + 3 > K0) col[i + 3] = fmaf(-v.w, cm, col[i + 3]);
+        }
+        const float2 v2 = *reinterpret_cast<const float2 *>(bc + 32);
+        const float r32 = v2.x, r33 = v2.y;
+        col[32] = fmaf(-r32, cm, col[32]);
+        col[33] = fmaf(-r33, cm, col[33]);
         if (upd) bb = fmaf(-ck * inv, wk, bb);
         b32 = fmaf(-r32 * inv, wk, b32);
         b33 = fmaf(-r33 * inv, wk, b33);
@@ -125,7 +146,7 @@ __device__ __forceinline__ bool chol_block8(float (&col)[NP1], float &t00, float
 // back as L (lower triangle).  Same column-per-lane scheme as the solver's
 // factorisation (chol_block8); returns false, uniformly, on a pivot that is
 // not positive and finite.
-__device__ __forceinline__ bool reg_cholesky34_store(float *Hs, int lane) {
+__device__ __forceinline__ bool reg_cholesky34_store(float *Hs, int lane, float *bc) {
     float col[NP1];
 #pragma unroll
     for (int i = 0; i < NP1; ++i) {
@@ -134,10 +155,10 @@ __device__ __forceinline__ bool reg_cholesky34_store(float *Hs, int lane) {
     }
     float t00 = Hs[32 * LDH + 32], t10 = Hs[33 * LDH + 32], t11 = Hs[33 * LDH + 33];
     float bb = 0.f, b32 = 0.f, b33 = 0.f, myinv = 1.f, myw = 0.f;
-    if (!chol_block8<0>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane)) return false;
-    if (!chol_block8<8>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane)) return false;
-    if (!chol_block8<16>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane)) return false;
-    if (!chol_block8<24>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane)) return false;
+    if (!chol_block8<0>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
+    if (!chol_block8<8>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
+    if (!chol_block8<16>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
+    if (!chol_block8<24>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
     if (!(t00 > 0.f) || !isfinite(t00)) return false;
     const float l32 = sqrtf(t00), l3332 = t10 / l32, d33 = t11 - l3332 * l3332;
     if (!(d33 > 0.f) || !isfinite(d33)) return false;
@@ -167,9 +188,10 @@ __device__ __forceinline__ bool reg_cholesky34_store(float *Hs, int lane) {
 // subtracts L_ik w_k, L_ik = A_ik / l_k being its own register), and the
 // backward solve L^T x = w broadcasts one x_i per step.  Returns false,
 // uniformly, when a pivot is not positive and finite (the "failed
-// decomposition" of Algorithm 1).
+// decomposition" of Algorithm 1).  bc: per-warp 16-byte-aligned scratch of
+// 36 floats (the broadcast pivot column).
 __device__ __forceinline__ bool reg_chol_solve34(const float *Hs, float lam, int lane, float rhs, float rhs32,
-                                                 float rhs33, float &x, float &x32, float &x33) {
+                                                 float rhs33, float &x, float &x32, float &x33, float *bc) {
     float col[NP1];
 #pragma unroll
     for (int i = 0; i < NP1; ++i) {
@@ -181,10 +203,10 @@ __device__ __forceinline__ bool reg_chol_solve34(const float *Hs, float lam, int
     float t00 = Hs[32 * LDH + 32] + lam, t10 = Hs[33 * LDH + 32], t11 = Hs[33 * LDH + 33] + lam;
     float bb = rhs, b32 = rhs32, b33 = rhs33;
     float myinv = 0.f, myw = 0.f;
-    if (!chol_block8<0>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane)) return false;
-    if (!chol_block8<8>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane)) return false;
-    if (!chol_block8<16>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane)) return false;
-    if (!chol_block8<24>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane)) return false;
+    if (!chol_block8<0>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
+    if (!chol_block8<8>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
+    if (!chol_block8<16>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
+    if (!chol_block8<24>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
     if (!(t00 > 0.f) || !isfinite(t00)) return false;
     const float inv32 = rsqrtf(t00), l3332 = t10 * inv32, d33 = t11 - l3332 * l3332;
     if (!(d33 > 0.f) || !isfinite(d33)) return false;

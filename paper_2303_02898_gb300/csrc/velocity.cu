@@ -75,7 +75,8 @@ __host__ __device__ inline VelLayout vel_layout(int nx, int npt) {
     L.lwp = o; o += PS;
     L.pij = o; o += 596;
     L.abc = o; o += 220;
-    L.vec = o; o += 6 * 36 + 224;  // beta, dbeta, M/n, grad, scalars, spare | mu
+    o = (o + 3) & ~3;  // 16-byte aligned: the Cholesky broadcast column lives at vec + 180
+    L.vec = o; o += 6 * 36 + 224;  // beta, dbeta, M/n, grad, scalars (6 used) | broadcast column | mu
     L.H = o; o += NP1 * LDH;
     L.red = o; o += 2 * VW + 2;
     L.total = o;
@@ -396,7 +397,7 @@ __global__ void __launch_bounds__(VT, 3) k_vel(VelArgs A) {
                     float x = 0.f, x32 = 0.f, x33 = 0.f, lam = 0.f;
                     bool ok = false, used = false;
                     for (int t = 0; t <= o.max_lambda; ++t) {
-                        ok = reg_chol_solve34(H, lam, lane, -g_l, -g32, -g33, x, x32, x33);
+                        ok = reg_chol_solve34(H, lam, lane, -g_l, -g32, -g33, x, x32, x33, sx + 36);
                         if (ok) break;
                         used = true;
                         lam = (t == 0) ? o.lambda0 : lam * o.lambda_mul;

@@ -187,6 +187,47 @@ static void build_lin_terms(int j0, bool with_x, std::vector<int> &off, std::vec
 // takes the packed entries p = l, l + 32, ...; slot t of lane l is stored at
 // [t][l] as (mu index | p << 8 | last-term flag in the sign bit, coefficient).
 // Sequences are padded with zero terms to a common length.
+// Hessian terms in rounds: entries sorted by term count, L per round (one
+// per lane), each round padded to its longest entry.  The kernel then runs a
+// branch-free term loop per round (loads can be pipelined: no store in
+// between) and stores all L entries at once.  slots[(base + t) * L + l] =
+// (mu index, coefficient bits); rounds[r] = terms of round r; ent[r * L + l] =
+// destination (i | j << 8) of lane l's entry, or -1.
+static void build_hess_rounds(const std::vector<int> &off, const std::vector<int2> &terms, int L,
+                              std::vector<int2> &slots, std::vector<int> &rounds, std::vector<int> &ent) {
+    const int NE = (int)off.size() - 1;
+    std::vector<int> order(NE);
+    for (int e = 0; e < NE; ++e) order[e] = e;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+    slots.clear();
+    rounds.clear();
+    ent.clear();
+    for (int r0 = 0; r0 < NE; r0 += L) {
+        int T = 0;
+        for (int l = 0; l < L && r0 + l < NE; ++l) T = std::max(T, off[order[r0 + l] + 1] - off[order[r0 + l]]);
+        rounds.push_back(T);
+        for (int t = 0; t < T; ++t)
+            for (int l = 0; l < L; ++l) {
+                int2 sl = {0, 0};
+                if (r0 + l < NE) {
+                    const int e = order[r0 + l];
+                    if (off[e] + t < off[e + 1]) sl = terms[off[e] + t];
+                }
+                sl.x &= 255;
+                slots.push_back(sl);
+            }
+        for (int l = 0; l < L; ++l) {
+            if (r0 + l >= NE) { ent.push_back(-1); continue; }
+            // packed entry p of the 34 x 34 lower triangle (rows/cols of phi_1..34)
+            const int p = order[r0 + l];
+            int i = 0;
+            while ((i + 1) * (i + 2) / 2 <= p) ++i;
+            ent.push_back(i | ((p - i * (i + 1) / 2) << 8));
+        }
+    }
+}
+
 static void build_hess_slots(const std::vector<int> &off, const std::vector<int2> &terms, std::vector<int2> &slots,
                              int &nslots, const std::vector<int> *off2 = nullptr, const std::vector<int2> *terms2 = nullptr,
                              int L = 32) {
@@ -299,6 +340,10 @@ static int build_slot_tables(mem_ctx *ctx) {
     build_hess_slots(off, terms, slots, ctx->n_hess_slots);
     std::vector<int2> slots128;
     build_hess_slots(off, terms, slots128, ctx->n_hess_slots128, nullptr, nullptr, 128);
+    std::vector<int2> rslots;
+    std::vector<int> rrounds, rent;
+    build_hess_rounds(off, terms, 32, rslots, rrounds, rent);
+    ctx->n_hess_rounds = (int)rrounds.size();
     std::vector<int> soff;
     std::vector<int2> sterms;
     build_lin_terms(1, false, soff, sterms);  // E[phi_i phi_j], i >= j >= 1
@@ -328,6 +373,9 @@ static int build_slot_tables(mem_ctx *ctx) {
     if (!rc) rc = upload(&ctx->d_lin_terms, terms);
     if (!rc) rc = upload(&ctx->d_hess_slots, slots);
     if (!rc) rc = upload(&ctx->d_hess_slots128, slots128);
+    if (!rc) rc = upload(&ctx->d_hr_slots, rslots);
+    if (!rc) rc = upload(&ctx->d_hr_rounds, rrounds);
+    if (!rc) rc = upload(&ctx->d_hr_ent, rent);
     if (!rc) rc = upload(&ctx->d_flux_slots, fslots);
     if (!rc) rc = upload(&ctx->d_axi_slots, aslots);
     if (!rc) rc = upload(&ctx->d_xlin_off, xoff);
@@ -447,7 +495,7 @@ void mem_destroy(mem_ctx *ctx) {
     if (!ctx) return;
     cudaDeviceSynchronize();
     void *ptrs[] = {ctx->d_phiT, ctx->d_logw, ctx->d_tab_solve, ctx->d_tab_flux, ctx->d_he1d, ctx->d_x1d,
-                    ctx->d_logw1d, ctx->d_lin_off, ctx->d_lin_terms, ctx->d_hess_slots, ctx->d_hess_slots128, ctx->d_flux_slots, ctx->d_axi_slots, ctx->d_xlin_off, ctx->d_xlin_terms,
+                    ctx->d_logw1d, ctx->d_lin_off, ctx->d_lin_terms, ctx->d_hess_slots, ctx->d_hess_slots128, ctx->d_hr_slots, ctx->d_hr_rounds, ctx->d_hr_ent, ctx->d_flux_slots, ctx->d_axi_slots, ctx->d_xlin_off, ctx->d_xlin_terms,
                     ctx->scratch, ctx->d_vtd, ctx->d_vtf, ctx->d_dom0};
     for (void *p : ptrs)
         if (p) cudaFree(p);

@@ -35,6 +35,10 @@ struct mem_ctx {
     int n_hess_slots = 0;
     int2 *d_hess_slots128 = nullptr;  // [n_hess_slots128][128] the same terms over 128 lanes (block per cell)
     int n_hess_slots128 = 0;
+    int2 *d_hr_slots = nullptr;  // Hessian terms in rounds of 32 entries (warp per cell), see build_hess_rounds
+    int *d_hr_rounds = nullptr;  // [n_hess_rounds] terms per round
+    int *d_hr_ent = nullptr;     // [n_hess_rounds][32] destination (i | j << 8) or -1
+    int n_hess_rounds = 0;
     int2 *d_flux_slots = nullptr;  // [n_flux_slots][32] E[phi phi^T] and E[ubar_x phi phi^T] terms
     int n_flux_slots = 0;
     int2 *d_axi_slots = nullptr;   // [n_axi_slots][32] the same, parity blocks of axisymmetric cells

@@ -38,8 +38,10 @@ struct FusedArgs {
     int64_t B;
     const float *he1d;    // [N][16]
     const float *logw1d;  // [N]
-    const int2 *slots;    // [n_slots][32] Hessian linearisation terms per lane
-    int n_slots;
+    const int2 *rslots;   // Hessian linearisation terms in rounds of 32 entries
+    const int *rounds;    // [n_rounds] terms per round
+    const int *rent;      // [n_rounds][32] destination (i | j << 8) or -1
+    int n_rounds;
     const unsigned char *active;  // optional per-cell mask: 0 = leave the cell untouched
     mem_solve_opts o;
 };
@@ -214,19 +216,30 @@ __global__ void __launch_bounds__(WARPS * 32, (N <= 8 ? 4 : 2)) k_fused_solve(Fu
             if (lane + 32 < NP) sg[lane + 32] = smu[lane + 32] - sm[lane + 32];
             __syncwarp();
             // Hessian entries E[phi_i phi_j] - mu_i mu_j (packed lower, i >= j)
-            // from the linearisation terms; lane l walks its own padded term
-            // sequence (uniform trip count, coalesced table reads).
+            // from the linearisation terms, in rounds of 32 entries (one per
+            // lane, similar term counts): a branch-free term loop, whose loads
+            // can be issued ahead since nothing is stored in between, then one
+            // store per lane.
             {
-                float acc = 0.f;
-#pragma unroll 4
-                for (int t = 0; t < A.n_slots; ++t) {
-                    const int2 sl = __ldg(&A.slots[t * 32 + lane]);
-                    acc = fmaf(__int_as_float(sl.y), smu[sl.x & 255], acc);
-                    if (sl.x < 0) {
-                        const int p = (sl.x >> 8) & 1023;
-                        const int pij = s_pij[p], i = pij & 255, j = pij >> 8;
-                        H[i * LDH + j] = acc - smu[i + 1] * smu[j + 1];
-                        acc = 0.f;
+                const int2 *sl = A.rslots;
+                for (int r = 0; r < A.n_rounds; ++r) {
+                    const int T = __ldg(&A.rounds[r]);
+                    float a0 = 0.f, a1 = 0.f;
+                    int t = 0;
+                    for (; t + 1 < T; t += 2) {
+                        const int2 s0 = __ldg(&sl[t * 32 + lane]), s1 = __ldg(&sl[(t + 1) * 32 + lane]);
+                        a0 = fmaf(__int_as_float(s0.y), smu[s0.x], a0);
+                        a1 = fmaf(__int_as_float(s1.y), smu[s1.x], a1);
+                    }
+                    if (t < T) {
+                        const int2 s0 = __ldg(&sl[t * 32 + lane]);
+                        a0 = fmaf(__int_as_float(s0.y), smu[s0.x], a0);
+                    }
+                    sl += T * 32;
+                    const int e = __ldg(&A.rent[r * 32 + lane]);
+                    if (e >= 0) {
+                        const int i = e & 255, j = e >> 8;
+                        H[i * LDH + j] = (a0 + a1) - smu[i + 1] * smu[j + 1];
                     }
                 }
             }
@@ -310,7 +323,8 @@ int solve_fused(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int3
     FusedArgs a;
     a.active = active;
     a.M = M; a.beta = beta; a.status = status; a.iters = iters; a.B = B;
-    a.he1d = ctx->d_he1d; a.logw1d = ctx->d_logw1d; a.slots = ctx->d_hess_slots; a.n_slots = ctx->n_hess_slots;
+    a.he1d = ctx->d_he1d; a.logw1d = ctx->d_logw1d; a.rslots = ctx->d_hr_slots; a.rounds = ctx->d_hr_rounds;
+    a.rent = ctx->d_hr_ent; a.n_rounds = ctx->n_hess_rounds;
     a.o = o;
     switch (ctx->n1d) {
         case 8: return launch_fused<8>(ctx, a, st);

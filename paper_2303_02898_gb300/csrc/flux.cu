@@ -69,8 +69,10 @@ __device__ __forceinline__ float clamp_speed(float sp, float bound) { return sp 
 // 16: Cholesky S = L L^T (in place), C = L^{-1} X L^{-T} by right-looking
 // column solves (lane j < n owns column j) and a pairwise transpose, Lanczos
 // without re-orthogonalisation and Sturm multisection.  Returns false if S
-// is not numerically positive definite.
-__device__ __forceinline__ bool small_pencil_extremes(float *S, float *X, int n, float *al, float *bt, float *sv,
+// is not numerically positive definite.  Not inlined: the axisymmetric speed
+// calls it three times, and three inlined copies overflow the instruction
+// cache once many warps are resident.
+__device__ __noinline__ bool small_pencil_extremes(float *S, float *X, int n, float *al, float *bt, float *sv,
                                                       int lane, float &lo, float &hi) {
     constexpr int LD = 16;
     for (int p = lane; p < n * (n + 1) / 2; p += 32) {  // mirror X

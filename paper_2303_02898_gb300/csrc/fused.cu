@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(WARPS * 32, (N <= 8 ? 4 : 2)) k_fused_solve(Fu
             bool ok = false;
             float lam = 0.f;
             for (int t = 0; t <= o.max_lambda; ++t) {
-                ok = reg_chol_solve34(H, lam, lane, -g_l, -g32, -g33, x, x32, x33, sbc);
+                ok = reg_chol_solve34<true>(H, lam, lane, -g_l, -g32, -g33, x, x32, x33, sbc);
                 if (ok) break;
                 st |= MEM_ST_LAMBDA;
                 lam = (t == 0) ? o.lambda0 : lam * o.lambda_mul;

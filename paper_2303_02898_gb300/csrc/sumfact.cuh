@@ -86,7 +86,13 @@ __device__ __forceinline__ void exponent(const float *v, const float *he, const 
 // the live columns j > k the rows i <= k hold entries that were consumed at
 // step i and are never read again (the factor and both triangular solves
 // read rows i >= j only), so one shuffle and one FMA per element suffice.
-template <int K0>
+// PIV = true takes each lane's A_kj, the pivot and the pivot lane's
+// forward-solve value from the published column (fewer instructions; A_kj is
+// the pivot lane's copy of the entry, which differs from the lane's own copy
+// by rounding).  PIV = false selects the lane's own A_kj from its registers
+// and shuffles the pivot: the form for the stiffest systems, whose FP32
+// solves sit at the rounding floor.
+template <int K0, bool PIV>
 __device__ __forceinline__ bool chol_block8(float (&col)[NP1], float &t00, float &t10, float &t11, float &bb,
                                             float &b32, float &b33, float &myinv, float &myw, int lane,
                                             float *bc) {
@@ -94,30 +100,44 @@ __device__ __forceinline__ bool chol_block8(float (&col)[NP1], float &t00, float
 #pragma unroll 1
     for (int kk = 0; kk < 8; ++kk) {
         const int k = K0 + kk;
-        float s1[4], s2[2];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) s1[m] = (kk & 1) ? col[K0 + 2 * m + 1] : col[K0 + 2 * m];
-#pragma unroll
-        for (int m = 0; m < 2; ++m) s2[m] = (kk & 2) ? s1[2 * m + 1] : s1[2 * m];
-        const float ck = (kk & 4) ? s2[1] : s2[0];  // this lane's A_kj
-        const float d = __shfl_sync(0xffffffffu, ck, k);
-        if (!(d > 0.f) || !isfinite(d)) return false;
-        const float inv = rsqrtf(d), inv2 = inv * inv;
-        const float c = ck * inv2;
-        const float wk = __shfl_sync(0xffffffffu, bb, k) * inv;
-        const bool upd = lane > k;
-        const float cm = upd ? c : 0.f;
         // The pivot lane publishes its column (rows I0..33) with 16-byte
-        // stores and every lane reads it back with broadcast loads: about a
-        // quarter of the memory-pipe instructions of one shuffle per row.
+        // stores, and its forward-solve value in slot 34; every lane reads
+        // the column back with broadcast loads (about a quarter of the
+        // memory-pipe instructions of one shuffle per row).  By symmetry the
+        // column also holds each lane's own A_kj in row j and the pivot in
+        // row k.  Lanes below I0 read stale rows, but they are finished and
+        // their coefficient is zero.
+        float ck, d, wk0;
+        if (!PIV) {
+            float s1[4], s2[2];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) s1[m] = (kk & 1) ? col[K0 + 2 * m + 1] : col[K0 + 2 * m];
+#pragma unroll
+            for (int m = 0; m < 2; ++m) s2[m] = (kk & 2) ? s1[2 * m + 1] : s1[2 * m];
+            ck = (kk & 4) ? s2[1] : s2[0];  // this lane's own A_kj
+            d = __shfl_sync(0xffffffffu, ck, k);
+            wk0 = __shfl_sync(0xffffffffu, bb, k);
+        }
         __syncwarp();  // the previous step's column has been read
         if (lane == k) {
 #pragma unroll
             for (int i = I0; i < 32; i += 4)
                 *reinterpret_cast<float4 *>(bc + i) = make_float4(col[i], col[i + 1], col[i + 2], col[i + 3]);
             *reinterpret_cast<float2 *>(bc + 32) = make_float2(col[32], col[33]);
+            if (PIV) bc[34] = bb;
         }
         __syncwarp();
+        if (PIV) {
+            d = bc[k];
+            ck = bc[lane];  // the pivot lane's copy of A_kj
+            wk0 = bc[34];
+        }
+        if (!(d > 0.f) || !isfinite(d)) return false;
+        const float inv = rsqrtf(d), inv2 = inv * inv;
+        const float c = ck * inv2;
+        const float wk = wk0 * inv;
+        const bool upd = lane > k;
+        const float cm = upd ? c : 0.f;
 #pragma unroll
         for (int i = I0; i < 32; i += 4) {
             const float4 v = *reinterpret_cast<const float4 *>(bc + i);
@@ -147,6 +167,7 @@ __device__ __forceinline__ bool chol_block8(float (&col)[NP1], float &t00, float
 // factorisation (chol_block8); returns false, uniformly, on a pivot that is
 // not positive and finite.
 __device__ __forceinline__ bool reg_cholesky34_store(float *Hs, int lane, float *bc) {
+    constexpr bool PIV = false;
     float col[NP1];
 #pragma unroll
     for (int i = 0; i < NP1; ++i) {
@@ -155,10 +176,10 @@ __device__ __forceinline__ bool reg_cholesky34_store(float *Hs, int lane, float 
     }
     float t00 = Hs[32 * LDH + 32], t10 = Hs[33 * LDH + 32], t11 = Hs[33 * LDH + 33];
     float bb = 0.f, b32 = 0.f, b33 = 0.f, myinv = 1.f, myw = 0.f;
-    if (!chol_block8<0>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
-    if (!chol_block8<8>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
-    if (!chol_block8<16>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
-    if (!chol_block8<24>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
+    if (!chol_block8<0, PIV>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
+    if (!chol_block8<8, PIV>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
+    if (!chol_block8<16, PIV>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
+    if (!chol_block8<24, PIV>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
     if (!(t00 > 0.f) || !isfinite(t00)) return false;
     const float l32 = sqrtf(t00), l3332 = t10 / l32, d33 = t11 - l3332 * l3332;
     if (!(d33 > 0.f) || !isfinite(d33)) return false;
@@ -190,6 +211,7 @@ __device__ __forceinline__ bool reg_cholesky34_store(float *Hs, int lane, float 
 // uniformly, when a pivot is not positive and finite (the "failed
 // decomposition" of Algorithm 1).  bc: per-warp 16-byte-aligned scratch of
 // 36 floats (the broadcast pivot column).
+template <bool PIV>
 __device__ __forceinline__ bool reg_chol_solve34(const float *Hs, float lam, int lane, float rhs, float rhs32,
                                                  float rhs33, float &x, float &x32, float &x33, float *bc) {
     float col[NP1];
@@ -203,10 +225,10 @@ __device__ __forceinline__ bool reg_chol_solve34(const float *Hs, float lam, int
     float t00 = Hs[32 * LDH + 32] + lam, t10 = Hs[33 * LDH + 32], t11 = Hs[33 * LDH + 33] + lam;
     float bb = rhs, b32 = rhs32, b33 = rhs33;
     float myinv = 0.f, myw = 0.f;
-    if (!chol_block8<0>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
-    if (!chol_block8<8>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
-    if (!chol_block8<16>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
-    if (!chol_block8<24>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
+    if (!chol_block8<0, PIV>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
+    if (!chol_block8<8, PIV>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
+    if (!chol_block8<16, PIV>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
+    if (!chol_block8<24, PIV>(col, t00, t10, t11, bb, b32, b33, myinv, myw, lane, bc)) return false;
     if (!(t00 > 0.f) || !isfinite(t00)) return false;
     const float inv32 = rsqrtf(t00), l3332 = t10 * inv32, d33 = t11 - l3332 * l3332;
     if (!(d33 > 0.f) || !isfinite(d33)) return false;

@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(VT, 3) k_vel(VelArgs A) {
                     float x = 0.f, x32 = 0.f, x33 = 0.f, lam = 0.f;
                     bool ok = false, used = false;
                     for (int t = 0; t <= o.max_lambda; ++t) {
-                        ok = reg_chol_solve34(H, lam, lane, -g_l, -g32, -g33, x, x32, x33, sx + 36);
+                        ok = reg_chol_solve34<false>(H, lam, lane, -g_l, -g32, -g33, x, x32, x33, sx + 36);
                         if (ok) break;
                         used = true;
                         lam = (t == 0) ? o.lambda0 : lam * o.lambda_mul;

@@ -365,6 +365,20 @@ def workload_config(args, cells):
 
 
 # ---------------------------------------------------------------- GPU arm
+def whole_job(dist, ms_local, cells_local, device):
+    """Weak scaling: every rank solves its own shard (its own seed), so the
+    job's step time is the slowest rank's and its work the sum of the shards.
+    Returns (max ms over ranks, total cells); no reduction without dist."""
+    import torch
+    if dist is None:
+        return ms_local, cells_local
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(cells_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(c.item()))
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -430,9 +444,10 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clocks = clk.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    ms_total, cells_total = whole_job(dist, e0.elapsed_time(e1), B, dev)
+    ms = ms_total / args.steps
     kern_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
-    value = B * world / (ms * 1e-3)
+    value = cells_total / (ms * 1e-3)
     itn = it.cpu().numpy()
     stn = st.cpu().numpy()
     passes = int(itn.sum())

@@ -123,7 +123,7 @@ def fused_flops_per_pass(n):
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_fused_solve<8> launch
 # on the headline workload (2^20 cells), from one ncu capture of the current
 # kernel (profiles/k_fused_solve_q8_2p20.md); None once the kernel changes.
-TRAFFIC_BYTES = None
+TRAFFIC_BYTES = 402.26e6
 
 SHOCK_MACH = 3.0   # largest Mach the 8^3 Gauss-Hermite Hermite-gauge rule keeps stable from a step
 

@@ -75,31 +75,27 @@ __device__ __forceinline__ float clamp_speed(float sp, float bound) { return sp 
 __device__ __noinline__ bool small_pencil_extremes(float *S, float *X, int n, float *al, float *bt, float *sv,
                                                       int lane, float &lo, float &hi) {
     constexpr int LD = 16;
-    for (int p = lane; p < n * (n + 1) / 2; p += 32) {  // mirror X
-        int i = 0;
-        while ((i + 1) * (i + 2) / 2 <= p) ++i;
-        const int j = p - i * (i + 1) / 2;
-        X[j * LD + i] = X[i * LD + j];
-    }
+    // Lane j < n owns column j throughout (no index decoding): it mirrors,
+    // transposes and symmetrises the pairs (i, j), i > j.
+    if (lane < n)
+        for (int i = lane + 1; i < n; ++i) X[lane * LD + i] = X[i * LD + lane];  // mirror X
     __syncwarp();
     if (!warp_cholesky(S, n, LD, lane)) return false;
+    if (lane < n) sv[lane] = 1.f / S[lane * LD + lane];  // 1 / L_kk (sv is free until Lanczos)
+    __syncwarp();
     for (int pass = 0; pass < 2; ++pass) {
         if (pass == 1) {
-            for (int p = lane; p < n * (n + 1) / 2; p += 32) {
-                int i = 0;
-                while ((i + 1) * (i + 2) / 2 <= p) ++i;
-                const int j = p - i * (i + 1) / 2;
-                if (j < i) {
-                    const float t = X[i * LD + j];
-                    X[i * LD + j] = X[j * LD + i];
-                    X[j * LD + i] = t;
+            if (lane < n)
+                for (int i = lane + 1; i < n; ++i) {
+                    const float t = X[i * LD + lane];
+                    X[i * LD + lane] = X[lane * LD + i];
+                    X[lane * LD + i] = t;
                 }
-            }
             __syncwarp();
         }
         if (lane < n) {
             for (int k = 0; k < n; ++k) {
-                const float yk = X[k * LD + lane] / S[k * LD + k];
+                const float yk = X[k * LD + lane] * sv[k];
                 X[k * LD + lane] = yk;
                 for (int i = k + 1; i < n; ++i) X[i * LD + lane] -= S[i * LD + k] * yk;
             }
@@ -107,16 +103,16 @@ __device__ __noinline__ bool small_pencil_extremes(float *S, float *X, int n, fl
         __syncwarp();
     }
     // symmetrise C (in X) and run Lanczos (lane i < n holds v_i)
-    float cn = 0.f;
-    for (int p = lane; p < n * n; p += 32) {
-        const int i = p / n, j = p % n;
-        if (j < i) {
-            const float s = 0.5f * (X[i * LD + j] + X[j * LD + i]);
-            X[i * LD + j] = s;
-            X[j * LD + i] = s;
+    if (lane < n)
+        for (int i = lane + 1; i < n; ++i) {
+            const float sy = 0.5f * (X[i * LD + lane] + X[lane * LD + i]);
+            X[i * LD + lane] = sy;
+            X[lane * LD + i] = sy;
         }
-        cn = fmaxf(cn, fabsf(X[i * LD + j]));
-    }
+    __syncwarp();
+    float cn = 0.f;
+    if (lane < n)
+        for (int i = 0; i < n; ++i) cn = fmaxf(cn, fabsf(X[i * LD + lane]));
     const float cnorm = warp_max(cn) + 1e-30f;
     __syncwarp();
     float v = lane < n ? rsqrtf((float)n) : 0.f, vp = 0.f, bprev = 0.f;

@@ -270,6 +270,32 @@ def run_serving_mach10(mem, torch, np, nreq=32, max_steps=100, chunk=10):
                                "all_finite": bool(all(np.isfinite(r["rho"]).all() for r, _ in res))}}
 
 
+def run_condition_study(mem, torch, np, steps=200, every=10):
+    """Section 4, Fig. 7 analogue: the largest pivot-ratio estimate of
+    cond(H) met over a run, against the number of cells, at Mach 4 (domain
+    [-16.3, 16.3]) and Mach 10 ([-47.1, 47.1]); velocity-space rule, tanh
+    start, sampled every `every` steps."""
+    out = {}
+    for mach, L in ((4.0, 16.3), (10.0, 47.1)):
+        vctx = mem.Context.velocity(mem.shock_domain(mach=mach))
+        rows = []
+        for n in (32, 64, 100, 150, 200, 300):
+            sh = mem.Shock(vctx, mach=mach, ncells=n, xl=-L, xr=L, ic=1, graph=1)
+            worst, done, fin = 0.0, 0, True
+            while done < steps:
+                sh.step(every)
+                done += every
+                worst = max(worst, sh.condition(0))
+                if not np.isfinite(sh.problem(0)["rho"]).all():
+                    fin = False
+                    break
+            sh.close()
+            rows.append({"cells": n, "max_cond": worst, "steps": done, "finite": fin})
+        vctx.close()
+        out["mach%g" % mach] = rows
+    return {"condition_vs_cells": out}
+
+
 def run_serving(mem, ctx, torch, np, nreq=32, max_steps=100, chunk=10):
     """Poisson trace (200 req/s, ncells logU[128, 32768], Mach U[1.5, 3]),
     each request capped at max_steps time steps: continuous batching (fused
@@ -542,6 +568,7 @@ def main():
         extras.update(run_ensemble(mem, ctx, torch, np))
         extras.update(run_serving(mem, ctx, torch, np))
         extras.update(run_serving_mach10(mem, torch, np))
+        extras.update(run_condition_study(mem, torch, np))
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

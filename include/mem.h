@@ -251,6 +251,17 @@ typedef struct {
 
 void mem_shock_params_default(mem_shock_params *p);
 
+/* Condition diagnostic of Section 4 (Fig. 7: the largest condition number of
+ * the moment Jacobian dM/dbeta = n H, Eq. "moments vs parameter jacob", met
+ * while a shock runs) for one problem of a shock on a velocity-space
+ * context: the largest, over the problem's interior cells, of the ratio of
+ * the largest to the smallest Cholesky pivot of each cell's last Newton
+ * factorisation in the last step (a lower bound on cond(H), or on
+ * cond(H + lambda I) where the modification was needed).  Synchronises the
+ * device; host output.  MEM_EINVAL on a Gauss-Hermite context or a bad
+ * problem index; 0 before the first step. */
+int mem_shock_condition(mem_shock *s, int problem, double *max_cond);
+
 /* Integration domain (a_x, b_x, b_r) that a shock problem with parameters *p
  * uses on a velocity-space context (Appendix D formula, see na, nb, nr
  * above); host array of 3.  MEM_EINVAL for invalid parameters. */

@@ -722,6 +722,38 @@ void or_flux(int order, const double *beta, const double *g, double n, double *F
 }
 
 /* ------------------------------------------------------------------------ */
+/* Condition diagnostic (Section 4, Fig. 7: condition number of the moment
+ * Jacobian dM/dbeta = n H, Eq. "moments vs parameter jacob").  The estimate
+ * is the ratio of the largest to the smallest pivot L_kk^2 of the Cholesky
+ * factorisation of the n x n SPD matrix A: every pivot is a diagonal entry of
+ * a Schur complement, so it lies between the extreme eigenvalues and the
+ * ratio never exceeds cond(A).  Returns -1 if A is not positive definite. */
+double or_pivot_ratio(int n, const double *A) {
+    double *L = malloc(sizeof(double) * n * n);
+    double r = -1.0;
+    if (!cholesky(n, A, 0.0, L)) {
+        double mn = INFINITY, mx = 0.0;
+        for (int k = 0; k < n; ++k) {
+            const double d = L[k * n + k] * L[k * n + k];
+            if (d < mn) mn = d;
+            if (d > mx) mx = d;
+        }
+        r = mx / mn;
+    }
+    free(L);
+    return r;
+}
+
+/* The estimate for one cell: H = Cov(phi_1..34) at beta (Appendix C). */
+double or_cond_estimate(int order, const double *g, const double *beta) {
+    double m[NP], S[NP * NP], H[34 * 34];
+    or_expect(order, g, beta, NULL, m, S, NULL, NULL);
+    for (int i = 0; i < 34; ++i)
+        for (int j = 0; j < 34; ++j) H[i * 34 + j] = S[(i + 1) * NP + (j + 1)] - m[i + 1] * m[j + 1];
+    return or_pivot_ratio(34, H);
+}
+
+/* ------------------------------------------------------------------------ */
 /* ES-BGK target moments (Appendix A, Eq. "The ES BGK model"): Gaussian with
  * the cell's density and mean velocity and covariance
  * Sigma = T/Pr I + (1 - 1/Pr) P/n, expressed in the cell's gauge g.  The
@@ -810,7 +842,7 @@ static void collide(double *M, const double *g, double dt, double Pr, double rel
 
 void or_shock_step(int order, int N, double dx, double cfl, double Pr, double relax_coef,
                    double *M, double *beta, double *g, double *speed, int *status, int *iters,
-                   const double *optv, int nthreads, double *out) {
+                   const double *optv, int nthreads, double *out, double *cond) {
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
@@ -828,6 +860,7 @@ void or_shock_step(int order, int N, double dx, double cfl, double Pr, double re
         int st = or_solve(order, &g[6 * c], &M[NP * c], &beta[NP * c], optv, &it, NULL, NULL);
         if (status) status[c] = st;
         if (iters) iters[c] = it;
+        if (cond) cond[c] = or_cond_estimate(order, &g[6 * c], &beta[NP * c]);
     }
     #pragma omp parallel for schedule(dynamic, 1)
     for (int c = 0; c < NT; ++c) {

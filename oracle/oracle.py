@@ -30,6 +30,8 @@ def lib():
         L.or_residual.restype = ctypes.c_double
         L.or_index_of.restype = ctypes.c_int
         L.or_num_threads.restype = ctypes.c_int
+        L.or_pivot_ratio.restype = ctypes.c_double
+        L.or_cond_estimate.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -183,6 +185,18 @@ def solve_batch(order, M, beta0=None, tol=1e-8, maxI=500, nthreads=0, final_step
     return beta, st, it
 
 
+def pivot_ratio(A):
+    """Largest / smallest Cholesky pivot of the SPD matrix A (-1 if not SPD)."""
+    A = _f64(A)
+    n = A.shape[0]
+    return lib().or_pivot_ratio(n, _d(np.ascontiguousarray(A)))
+
+
+def cond_estimate(order, beta, g=None):
+    """Pivot-ratio estimate of cond(H) at beta (Section 4, Fig. 7)."""
+    return lib().or_cond_estimate(order, _g(g), _d(_f64(beta, (NP,))))
+
+
 def gauge_T(g_to, g_from):
     """T(g', g) of Eq. "Change gauge M F": M(g') = T M(g)."""
     T = np.zeros((NP, NP))
@@ -331,6 +345,9 @@ class Shock:
         _, self.speed = flux_batch(order, self.M, self.beta, self.g, nthreads)
         self.status = np.zeros(NT, dtype=np.int32)
         self.iters = np.zeros(NT, dtype=np.int32)
+        # pivot-ratio condition estimate of each cell's last solve (Fig. 7), on request
+        self.track_cond = False
+        self.cond = np.zeros(NT)
         self.t = 0.0
         self.steps = 0
 
@@ -339,7 +356,7 @@ class Shock:
         lib().or_shock_step(self.order, self.N, ctypes.c_double(self.dx), ctypes.c_double(self.cfl),
                             ctypes.c_double(self.Pr), ctypes.c_double(self.relax), _d(self.M), _d(self.beta),
                             _d(self.g), _d(self.speed), _i(self.status), _i(self.iters), _d(self.opts),
-                            self.nthreads, _d(out))
+                            self.nthreads, _d(out), _d(self.cond) if self.track_cond else None)
         self.t += out[0]
         self.steps += 1
         return out  # dt, max speed, max |d rho|

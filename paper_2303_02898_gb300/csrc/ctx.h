@@ -78,7 +78,7 @@ int flux_from_mu(mem_ctx *ctx, const float *mu, const float *M, const float *g, 
                  cudaStream_t st, bool axisym);
 int vel_run(mem_ctx *ctx, const float *M, float *beta, const float *g, int32_t *status, int32_t *iters, float *mu,
             const int *pid, const double *dom, int64_t B, const mem_solve_opts &o, bool solve, cudaStream_t st,
-            const unsigned char *active = nullptr);
+            const unsigned char *active = nullptr, float *cond = nullptr);
 size_t vel_smem_bytes(int nx, int npt);
 int gl_rule(int n, std::vector<double> &x, std::vector<double> &w);
 int gauge_hermite(mem_ctx *ctx, const float *M_in, const float *g_in, float *g_out, float *M_out,

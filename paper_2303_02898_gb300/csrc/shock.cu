@@ -252,7 +252,7 @@ void batch_free(ShockBatch *b) {
     if (!b) return;
     cudaDeviceSynchronize();
     void *ptrs[] = {b->M, b->beta, b->g, b->speed, b->F, b->Mn, b->rho0, b->sigma, b->mom, b->status, b->iters,
-                    b->pid, b->interior, b->prm, b->sc, b->mu, b->dom};
+                    b->pid, b->interior, b->prm, b->sc, b->mu, b->dom, b->cond};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete b;
@@ -340,7 +340,8 @@ int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **o
     // Flux work space: moment rows (velocity-space rule) or the plain path's
     // sigma and moment columns (Gauss-Hermite rule).
     const bool work_ok = ctx->vel ? alloc((void **)&b->mu, sizeof(float) * NT * MEM_MU_STRIDE) &&
-                                        alloc((void **)&b->dom, sizeof(double) * 4 * P)
+                                        alloc((void **)&b->dom, sizeof(double) * 4 * P) &&
+                                        alloc((void **)&b->cond, sizeof(float) * NT)
                                   : alloc((void **)&b->sigma, sizeof(float) * NT * (size_t)Q) &&
                                         alloc((void **)&b->mom, sizeof(float) * NT * (size_t)MEM_NCOL_FLUX);
     bool ok = work_ok && alloc((void **)&b->M, sizeof(float) * NT * NP) && alloc((void **)&b->beta, sizeof(float) * NT * NP) &&
@@ -379,7 +380,8 @@ int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **o
     if (ctx->vel) {
         std::vector<double> hdom(4 * (size_t)P);
         for (int i = 0; i < P; ++i) shock_domain(ps[i], &hdom[4 * (size_t)i]);
-        if (cudaMemcpy(b->dom, hdom.data(), sizeof(double) * hdom.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        if (cudaMemcpy(b->dom, hdom.data(), sizeof(double) * hdom.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemset(b->cond, 0, sizeof(float) * NT) != cudaSuccess) {
             batch_free(b);
             return MEM_ECUDA;
         }
@@ -428,7 +430,7 @@ int batch_enqueue_step(ShockBatch *b, cudaStream_t st) {
         // degree <= 9 at the new beta (ghost cells included), and the speed
         // kernel reads them.
         rc = vel_run(b->ctx, b->M, b->beta, b->g, b->status, b->iters, b->mu, b->pid, b->dom, NT, o, true, st,
-                     b->interior);
+                     b->interior, b->cond);
         if (!rc) rc = flux_from_mu(b->ctx, b->mu, b->M, b->g, b->F, b->speed, NT, st, true);
     } else {
     rc = (o.impl == MEM_IMPL_PLAIN)
@@ -516,6 +518,21 @@ struct mem_shock {
 };
 
 extern "C" {
+
+int mem_shock_condition(mem_shock *s, int problem, double *max_cond) {
+    if (!s || !max_cond) return MEM_EINVAL;
+    mem_host::ShockBatch *b = s->b;
+    if (problem < 0 || problem >= b->P) return MEM_EINVAL;
+    if (!b->cond) return MEM_EINVAL;  // a Gauss-Hermite context records no estimate
+    const ShockProb &pr = b->hprm[problem];
+    std::vector<float> h((size_t)pr.n);
+    MEM_CUDA_TRY(cudaDeviceSynchronize());
+    MEM_CUDA_TRY(cudaMemcpy(h.data(), b->cond + pr.off + 1, sizeof(float) * pr.n, cudaMemcpyDeviceToHost));
+    double m = 0.0;
+    for (float v : h) m = fmax(m, (double)v);
+    *max_cond = m;
+    return MEM_OK;
+}
 
 int mem_shock_domain(const mem_shock_params *p, double *domain) {
     if (!p || !domain || !mem_host::shock_params_valid(*p)) return MEM_EINVAL;

@@ -38,6 +38,7 @@ struct ShockBatch {
     float *rho0 = nullptr, *sigma = nullptr, *mom = nullptr;
     float *mu = nullptr;      // [NT][MEM_MU_STRIDE] moment rows (velocity-space rule)
     double *dom = nullptr;    // [P][4] integration domain (a_x, b_x, b_r, 0) per problem (velocity-space rule)
+    float *cond = nullptr;    // [NT] pivot-ratio condition estimate of each cell's last solve (velocity-space rule)
     int32_t *status = nullptr, *iters = nullptr;
     int *pid = nullptr;
     unsigned char *interior = nullptr;

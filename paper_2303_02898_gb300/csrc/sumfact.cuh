@@ -210,10 +210,12 @@ __device__ __forceinline__ bool reg_cholesky34_store(float *Hs, int lane, float 
 // backward solve L^T x = w broadcasts one x_i per step.  Returns false,
 // uniformly, when a pivot is not positive and finite (the "failed
 // decomposition" of Algorithm 1).  bc: per-warp 16-byte-aligned scratch of
-// 36 floats (the broadcast pivot column).
+// 36 floats (the broadcast pivot column).  prange (optional, uniform across
+// the warp): receives the smallest and largest pivot.
 template <bool PIV>
 __device__ __forceinline__ bool reg_chol_solve34(const float *Hs, float lam, int lane, float rhs, float rhs32,
-                                                 float rhs33, float &x, float &x32, float &x33, float *bc) {
+                                                 float rhs33, float &x, float &x32, float &x33, float *bc,
+                                                 float *prange = nullptr) {
     float col[NP1];
 #pragma unroll
     for (int i = 0; i < NP1; ++i) {
@@ -233,6 +235,13 @@ __device__ __forceinline__ bool reg_chol_solve34(const float *Hs, float lam, int
     const float inv32 = rsqrtf(t00), l3332 = t10 * inv32, d33 = t11 - l3332 * l3332;
     if (!(d33 > 0.f) || !isfinite(d33)) return false;
     const float inv33 = rsqrtf(d33);
+    if (prange) {
+        // smallest and largest Cholesky pivot d_k = L_kk^2 (k < 32 on lane k,
+        // then t00 and d33): their ratio bounds cond(H + lam I) from below
+        const float dk = 1.f / (myinv * myinv);
+        const float pmn = fminf(warp_min(dk), fminf(t00, d33)), pmx = fmaxf(warp_max(dk), fmaxf(t00, d33));
+        if (lane == 0) { prange[0] = pmn; prange[1] = pmx; }
+    }
     const float w32 = b32 * inv32, w33 = (b33 - l3332 * w32) * inv33;
     x33 = w33 * inv33;
     x32 = (w32 - l3332 * x33) * inv32;

@@ -44,6 +44,7 @@ struct VelArgs {
     int32_t *status;
     int32_t *iters;
     float *mu;                    // [B][MEM_MU_STRIDE] moments of degree <= 9 at the final beta, or null
+    float *cond;                  // [B] largest / smallest Cholesky pivot of the last Newton pass, or null
     const int *pid;               // per-cell domain index, or null (domain 0)
     const double *dom;            // (a_x, b_x, b_r, 0) per domain
     const unsigned char *active;  // 0: no solve for this cell (its moments are still produced)
@@ -336,6 +337,7 @@ __global__ void __launch_bounds__(VT, 3) k_vel(VelArgs A) {
             bad = !isfinite(mv) || (tid > 0 && !isfinite(bv));
             sb[tid] = tid ? bv : 0.f;
             smv[tid] = tid ? mv / n : 0.f;
+            if (tid == 6 || tid == 7) sx[tid] = 0.f;  // pivot range of the last factorisation
             sd[tid] = 0.f;
             sg[tid] = 0.f;
         }
@@ -397,7 +399,8 @@ __global__ void __launch_bounds__(VT, 3) k_vel(VelArgs A) {
                     float x = 0.f, x32 = 0.f, x33 = 0.f, lam = 0.f;
                     bool ok = false, used = false;
                     for (int t = 0; t <= o.max_lambda; ++t) {
-                        ok = reg_chol_solve34<false>(H, lam, lane, -g_l, -g32, -g33, x, x32, x33, sx + 36);
+                        ok = reg_chol_solve34<false>(H, lam, lane, -g_l, -g32, -g33, x, x32, x33, sx + 36,
+                                                     A.cond ? sx + 6 : nullptr);
                         if (ok) break;
                         used = true;
                         lam = (t == 0) ? o.lambda0 : lam * o.lambda_mul;
@@ -468,6 +471,7 @@ __global__ void __launch_bounds__(VT, 3) k_vel(VelArgs A) {
             if (tid < NP) bc[tid] = tid ? sb[tid] : n;
             if (tid == 0) {
                 if (A.status) A.status[cell] = st;
+                if (A.cond) A.cond[cell] = sx[6] > 0.f ? sx[7] / sx[6] : 0.f;
                 if (A.iters) A.iters[cell] = it;
             }
         }
@@ -512,11 +516,11 @@ size_t vel_smem_bytes(int nx, int npt) { return sizeof(float) * (size_t)vel_layo
 
 int vel_run(mem_ctx *ctx, const float *M, float *beta, const float *g, int32_t *status, int32_t *iters, float *mu,
             const int *pid, const double *dom, int64_t B, const mem_solve_opts &o, bool solve, cudaStream_t st,
-            const unsigned char *active) {
+            const unsigned char *active, float *cond) {
     if (!ctx->vel) return MEM_EINVAL;
     if (B == 0) return MEM_OK;
     VelArgs a;
-    a.M = M; a.beta = beta; a.gauge = g; a.status = status; a.iters = iters; a.mu = mu;
+    a.M = M; a.beta = beta; a.gauge = g; a.status = status; a.iters = iters; a.mu = mu; a.cond = cond;
     a.pid = pid; a.dom = dom ? dom : ctx->d_dom0; a.active = active;
     a.vtd = ctx->d_vtd; a.vtf = ctx->d_vtf;
     a.slots = ctx->d_hess_slots128; a.n_slots = ctx->n_hess_slots128;

@@ -70,6 +70,8 @@ def lib():
         L.mem_init_velocity.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_double, ctypes.c_double, ctypes.c_double, _P]
         L.mem_shock_domain.restype = ctypes.c_int
+        L.mem_shock_condition.restype = ctypes.c_int
+        L.mem_shock_condition.argtypes = [_P, ctypes.c_int, _P]
         L.mem_velocity_rule.restype = ctypes.c_int
         L.mem_velocity_rule.argtypes = [_P, _P, _P]
         L.mem_flux.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P]
@@ -281,6 +283,13 @@ class Shock:
         _check(lib().mem_shock_get_problem(self.h, i, *[f(x) for x in prof], ctypes.byref(t), ctypes.byref(st)),
                "mem_shock_get_problem")
         return dict(rho=prof[0], ux=prof[1], T=prof[2], sxx=prof[3], qx=prof[4], t=t.value, steps=st.value)
+
+    def condition(self, i=0):
+        """mem_shock_condition: largest pivot-ratio condition estimate over
+        problem i's cells in the last step (velocity-space contexts)."""
+        c = ctypes.c_double()
+        _check(lib().mem_shock_condition(self.h, i, ctypes.byref(c)), "mem_shock_condition")
+        return c.value
 
     def device_state(self):
         ptrs = [ctypes.c_void_p() for _ in range(6)]

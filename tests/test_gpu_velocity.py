@@ -156,3 +156,22 @@ def test_velocity_shock_batch_alone_equals_mix(mem, vctx):
         for k in ("rho", "ux", "T"):
             assert np.abs(alone[k] - mix[k]).max() <= 1e-6 * np.abs(alone[k]).max(), (i, k)
     sh.close()
+
+
+def test_velocity_shock_condition_matches_oracle(O, mem, vctx, dom):
+    """Fig. 7 diagnostic (Section 4): the largest pivot-ratio estimate of
+    cond(H) over a Mach-10 problem's cells after each of four steps.  GPU: the
+    FP32 factorisation of the last Newton pass; oracle: FP64 at its converged
+    beta.  They agree to the FP32 accuracy of the smallest pivot (relative
+    error up to ~1e-7 cond(H), about 1e-2 here) plus the size of the final
+    Newton step; the bar is 10 %."""
+    sh = mem.Shock(vctx, mach=MACH, ncells=40, xl=-12.5, xr=12.5, ic=1, graph=0)
+    so = O.Shock(MACH, 40, -12.5, 12.5, order=RULE, ic="tanh", thickness=15.7)
+    so.track_cond = True
+    for k in range(4):
+        sh.step(1)
+        so.step()
+        cg, co = sh.condition(0), float(so.cond[1:-1].max())
+        assert co > 10.0
+        assert cg == pytest.approx(co, rel=0.1), (k, cg, co)
+    sh.close()

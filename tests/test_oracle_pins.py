@@ -582,3 +582,27 @@ def test_velocity_rule_solve_recovers_moments(O):
     assert O.residual(204, beta, M, g) < 1e-8
     assert np.abs(beta[1:] - beta_true[1:]).max() < 1e-5
     del idx
+
+
+# ---------------------------------------------------------------- condition diagnostic
+def test_pivot_ratio_bounds_and_diagonal(O):
+    """Cholesky pivots are Schur-complement diagonals, so they lie between the
+    extreme eigenvalues: the ratio never exceeds cond(A), and equals it for a
+    diagonal matrix; a matrix that is not positive definite gives -1."""
+    d = np.array([3.0, 0.5, 7.0, 1e-3, 2.0])
+    assert O.pivot_ratio(np.diag(d)) == pytest.approx(7.0 / 1e-3, rel=1e-14)
+    rng = np.random.default_rng(11)
+    for n in (5, 20, 34):
+        Q, _ = np.linalg.qr(rng.normal(size=(n, n)))
+        ev = np.exp(rng.uniform(-6, 2, n))
+        A = (Q * ev) @ Q.T
+        A = 0.5 * (A + A.T)
+        r = O.pivot_ratio(A)
+        assert 1.0 <= r <= ev.max() / ev.min() * (1 + 1e-9)
+    assert O.pivot_ratio(np.diag([1.0, -1.0])) == -1.0
+
+
+def test_cond_estimate_maxwellian_is_one(O):
+    """At a Maxwellian in its own Hermite gauge H = I (orthonormal
+    statistics), so the estimate is exactly 1 up to quadrature rounding."""
+    assert O.cond_estimate(8, np.zeros(35)) == pytest.approx(1.0, abs=1e-10)

@@ -296,6 +296,124 @@ def run_condition_study(mem, torch, np, steps=200, every=10):
     return {"condition_vs_cells": out}
 
 
+GAUGE_BOX = (-30.7, 37.3, 34.0)  # Section 4: (u_x, u_r) in [-30.7, 37.3] x [0, 34.0]
+
+
+def _status_letters(st):
+    """One letter per cell: c converged (res <= tol), s stagnated (alpha <=
+    alpha_min), m maxI reached, f stopped (Cholesky / non-finite)."""
+    out = []
+    for v in st:
+        v = int(v)
+        out.append("c" if v & 1 else "s" if v & 2 else "m" if v & 4 else "f")
+    return "".join(out)
+
+
+def _golden_beta(name):
+    """FP64 parameters stored by tests/golden/make_gauge_study.py (oracle)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "gauge_study.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f).get(name)
+
+
+def _log_mse(beta, ref, np):
+    """log10 of the mean-square parameter error per cell (beta_1..34)."""
+    d = beta[:, 1:].astype(np.float64) - np.asarray(ref, dtype=np.float64)[:, 1:]
+    return [round(float(np.log10(max((r * r).mean(), 1e-300))), 2) for r in d]
+
+
+def gauge_study_inputs(mem, torch, machs, gamma=5.0 / 3.0):
+    """Upstream Maxwellians (n = 1, T = 1, v = sqrt(gamma) Mach) in their
+    Hermite gauge (moments e_0) and in the trivial gauge (0, 1) (moments
+    T(g0, gH) e_0, by mem_gauge_transform), each started from the uniform
+    density: beta = 1/sqrt(2) on the three he_2 statistics cancels the
+    gauge's Gaussian.  Returns (M, beta0, g) for [Hermite cells | trivial cells]."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    B = len(machs)
+    gH = torch.zeros(B, 6, device=dev)
+    gH[:, 0] = torch.tensor([gamma ** 0.5 * m for m in machs], device=dev)
+    gH[:, 3:] = 1.0
+    g0 = torch.zeros(B, 6, device=dev)
+    g0[:, 3:] = 1.0
+    eH = torch.zeros(B, 35, device=dev)
+    eH[:, 0] = 1.0
+    M0 = torch.zeros(B, 35, device=dev)
+    ctx = mem.Context(8)
+    ctx.gauge_transform(g0, gH, eH, M0)
+    ctx.close()
+    M = torch.cat([eH, M0]).contiguous()
+    g = torch.cat([gH, g0]).contiguous()
+    beta0 = torch.zeros(2 * B, 35, device=dev)
+    beta0[:, 0] = 1.0
+    beta0[:, 4] = beta0[:, 7] = beta0[:, 9] = 0.5 ** 0.5  # he_2 statistics (2,0,0), (0,2,0), (0,0,2)
+    return M, beta0, g
+
+
+def run_gauge_study(mem, torch, np):
+    """Section 4, Fig. 3 analogue on the 35 statistics: Newton passes from
+    the uniform density to the upstream Maxwellians of Mach 2-12, trivial
+    gauge vs Hermite gauge, FP32, tol 1e-6 and 1e-9, maxI 500; and the
+    log mean-square error of the FP32 parameters against FP64 ones (oracle,
+    stored).  Velocity-space rule on the paper's box, 16 x 12 blocks of
+    8-point Gauss-Legendre, 10 azimuths."""
+    machs = list(range(2, 13))
+    B = len(machs)
+    vctx = mem.Context.velocity(GAUGE_BOX, nbx=16, nbr=12, ng=8, K=10)
+    M, beta0, g = gauge_study_inputs(mem, torch, machs)
+    ref_h, ref_t = _golden_beta("beta64_hermite"), _golden_beta("beta64_trivial")
+    out = {"mach": machs}
+    for tol in (1e-6, 1e-9):
+        beta = beta0.clone()
+        st = torch.zeros(M.shape[0], dtype=torch.int32, device=M.device)
+        it = torch.zeros_like(st)
+        vctx.solve_gauge(M, beta, g, st, it, tol=tol, maxI=500)
+        torch.cuda.synchronize()
+        itn, stn, bn = it.cpu().numpy(), st.cpu().numpy(), beta.cpu().numpy()
+        row = {"passes_hermite": itn[:B].tolist(), "passes_trivial": itn[B:].tolist(),
+               "status_hermite": _status_letters(stn[:B]), "status_trivial": _status_letters(stn[B:])}
+        if ref_h is not None and ref_t is not None:
+            row["log_mse_hermite"] = _log_mse(bn[:B], ref_h, np)
+            row["log_mse_trivial"] = _log_mse(bn[B:], ref_t, np)
+        out["tol_%g" % tol] = row
+    vctx.close()
+    return {"gauge_study": out}
+
+
+def run_newton_study(mem, torch, np, n=26):
+    """Section 4, Fig. 2 analogue: the he_3(u_x) moment M_(3,0,0) raised from
+    0 to 0.5 on top of the equilibrium (n = 1, v = 0, T = 1) in the trivial
+    gauge, solved in FP32 from beta = 0 by the modified Newton method
+    (lambda I retries) and by plain Newton (no retries: a failed Cholesky
+    stops the solve); tol 1e-8, maxI 500, the paper's box as above."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    m4 = np.linspace(0.0, 0.5, n)
+    vctx = mem.Context.velocity(GAUGE_BOX, nbx=16, nbr=12, ng=8, K=10)
+    M = torch.zeros(n, 35, device=dev)
+    M[:, 0] = 1.0
+    M[:, 10] = torch.tensor(m4, dtype=torch.float32, device=dev)  # statistic (3,0,0)
+    g = torch.zeros(n, 6, device=dev)
+    g[:, 3:] = 1.0
+    ref = _golden_beta("beta64_m4_sweep")
+    out = {"m4": [round(float(x), 3) for x in m4]}
+    for name, ml in (("modified", 20), ("plain", 0)):
+        beta = torch.zeros(n, 35, device=dev)
+        beta[:, 0] = 1.0
+        st = torch.zeros(n, dtype=torch.int32, device=dev)
+        it = torch.zeros_like(st)
+        vctx.solve_gauge(M, beta, g, st, it, tol=1e-8, maxI=500, max_lambda=ml)
+        torch.cuda.synchronize()
+        bn = beta.cpu().numpy()
+        row = {"passes": it.cpu().numpy().tolist(), "status": _status_letters(st.cpu().numpy()),
+               "beta_300": [round(float(x), 6) for x in bn[:, 10]]}
+        if ref is not None:
+            row["log_mse"] = _log_mse(bn, ref, np)
+        out[name] = row
+    vctx.close()
+    return {"newton_study": out}
+
+
 def run_serving(mem, ctx, torch, np, nreq=32, max_steps=100, chunk=10):
     """Poisson trace (200 req/s, ncells logU[128, 32768], Mach U[1.5, 3]),
     each request capped at max_steps time steps: continuous batching (fused
@@ -569,6 +687,8 @@ def main():
         extras.update(run_serving(mem, ctx, torch, np))
         extras.update(run_serving_mach10(mem, torch, np))
         extras.update(run_condition_study(mem, torch, np))
+        extras.update(run_gauge_study(mem, torch, np))
+        extras.update(run_newton_study(mem, torch, np))
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -606,3 +606,84 @@ def test_cond_estimate_maxwellian_is_one(O):
     """At a Maxwellian in its own Hermite gauge H = I (orthonormal
     statistics), so the estimate is exactly 1 up to quadrature rounding."""
     assert O.cond_estimate(8, np.zeros(35)) == pytest.approx(1.0, abs=1e-10)
+
+
+# ---------------------------------------------------------------- gauge study (Section 4, Fig. 3 setup)
+def _uniform_beta(O):
+    """Parameters of the uniform density with n = 1: beta = 1/sqrt(2) on the
+    three he_2 statistics cancels the gauge's Gaussian exp(-|ubar|^2 / 2)."""
+    b = np.zeros(35)
+    b[0] = 1.0
+    for a, bb, c in ((2, 0, 0), (0, 2, 0), (0, 0, 2)):
+        b[O.index_of(a, bb, c)] = 1.0 / SQ2
+    return b
+
+
+def test_uniform_start_is_flat_density(O):
+    """The uniform-density start of the gauge study: exp(beta . phi(ubar) -
+    |ubar|^2 / 2) takes one value at every velocity, in the trivial gauge and
+    in a translated, dilated one."""
+    b = _uniform_beta(O)
+    rng = np.random.default_rng(5)
+    for w, s in ((0.0, 1.0), (9.7, 1.6)):
+        u = rng.uniform(-20, 20, (50, 3))
+        ub = (u - np.array([w, 0, 0])) / s
+        logf = np.array([O.phi(x) @ b for x in ub]) - 0.5 * (ub * ub).sum(1)
+        assert np.ptp(logf) < 1e-12
+
+
+def test_gauge_study_maxwellian_moments_and_invariance(O):
+    """Upstream Maxwellian (n = 1, T = 1, v = sqrt(5/3) * 3) on the paper's
+    box: (1) its trivial-gauge moments T(g0, gH) e_0 equal the closed form
+    E[He_a(u_x)] / sqrt(a!) = v^a / sqrt(a!); (2) Algorithm 1 from the
+    uniform density takes the same number of passes in the trivial and the
+    Hermite gauge (Newton with a backtracking line search is invariant under
+    the linear change of statistics a gauge transformation is), and the two
+    FP64 solutions describe one density (beta_trivial = T_beta(g0, gH)
+    beta_Hermite); (3) the solution is the Maxwellian, up to the rule's
+    quadrature error: beta_trivial = e_0 + v e_(1,0,0), beta_Hermite = e_0."""
+    _vel_rule(O, 206, (-30.7, 37.3, 34.0), nbx=8, nbr=6, ng=8, K=10)
+    v = math.sqrt(5.0 / 3.0) * 3.0
+    g0 = np.array([0.0, 0, 0, 1, 1, 1])
+    gH = np.array([v, 0, 0, 1, 1, 1])
+    e0 = np.zeros(35)
+    e0[0] = 1.0
+    Mt = O.transform_M(g0, gH, e0)
+    closed = np.zeros(35)
+    for k, (a, b, c) in enumerate(O.basis_index()):
+        if b == 0 and c == 0:
+            closed[k] = v ** int(a) / math.sqrt(math.factorial(int(a)))
+    assert np.abs(Mt - closed).max() < 1e-12
+    u0 = _uniform_beta(O)
+    bh, sh, ih, _, _ = O.solve(206, e0, beta0=u0, tol=1e-11, g=gH)
+    bt, st, it, _, _ = O.solve(206, Mt, beta0=u0, tol=1e-11, g=g0)
+    assert sh & 1 and st & 1
+    assert ih == it
+    assert np.abs(O.transform_beta(g0, gH, bh) - bt).max() < 1e-8
+    # (3) on the study's rule (16 x 12 blocks): the coarse rule above is off
+    # by 0.1 in beta_(1,0,0), which is why the study uses the finer one.
+    _vel_rule(O, 207, (-30.7, 37.3, 34.0), nbx=16, nbr=12, ng=8, K=10)
+    maxw = e0.copy()
+    maxw[O.index_of(1, 0, 0)] = v
+    bt, st, _, _, _ = O.solve(207, Mt, beta0=maxw, tol=1e-13, g=g0)
+    bh, sh, _, _, _ = O.solve(207, e0, beta0=e0, tol=1e-13, g=gH)
+    assert st & 1 and sh & 1
+    assert np.abs(bt - maxw).max() < 1e-3  # 3.9e-4 on beta_(1,0,0): quadrature error
+    assert np.abs(bh - e0).max() < 1e-3
+
+
+def test_gauge_study_golden_matches_oracle(O):
+    """tests/golden/gauge_study.json (written by make_gauge_study.py from the
+    oracle) still matches the oracle: the Mach-2 Hermite-gauge FP64
+    parameters, re-solved."""
+    import json
+    import os
+    d = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "gauge_study.json")))
+    r = d["rule"]
+    O.set_velocity_rule(r["rule_id"], r["ax"], r["bx"], r["nbx"], r["br"], r["nbr"], r["ng"], r["K"])
+    v = math.sqrt(5.0 / 3.0) * d["mach"][0]
+    e0 = np.zeros(35)
+    e0[0] = 1.0
+    b, st, _, _, _ = O.solve(r["rule_id"], e0, beta0=e0, tol=1e-13, g=[v, 0, 0, 1, 1, 1])
+    assert st & 1
+    assert np.abs(b - np.array(d["beta64_hermite"][0])).max() < 1e-10

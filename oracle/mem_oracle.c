@@ -840,9 +840,69 @@ static void collide(double *M, const double *g, double dt, double Pr, double rel
     for (int i = 0; i < NP; ++i) M[i] = (1.0 - r) * M[i] + r * Mt[i];
 }
 
+/* Numerical flux at the interface between cells a = c - 1 + side and
+ * b = c + side, everything in the gauge g(c) of the cell being updated
+ * (Eq. "The lax F convert" moves the neighbours there):
+ *   scheme 0: local Lax-Friedrichs, Eq. "The lax F";
+ *   scheme 1: two-step Lax-Wendroff, Eq. "The lax W": the interface moments
+ *     M(n - 1/2) = (M_a + M_b)/2 + dt/(2 dx) (F_a - F_b), their parameters by
+ *     Algorithm 1 and the flux of those parameters.  The solve runs in the
+ *     Hermite gauge of the interface moments (cold start, beta = 0 there)
+ *     and the flux is moved back to g(c): the maximum-entropy density of a
+ *     moment vector does not depend on the gauge it is written in;
+ *   scheme 2: FLIC, Eq. "The FLIC": F^LF + phi(r) (F^LW - F^LF) component by
+ *     component with the van Leer limiter phi(r) = (r + |r|)/(1 + r) and
+ *     r = (M_a - M_{a-1}) / (M_b - M_a) in g(c); a zero denominator is read
+ *     as r = 0 (first order there), phi = 0 at r = -1 (the printed form is
+ *     0/0 there), the Lax-Wendroff term is left out where phi = 0, and cell
+ *     a - 1 before the first cell is the ghost cell itself (r = 0).
+ * Interface solves add their status bits to *ist. */
+static void interface_flux(int order, int scheme, int c, int side, const double *M, const double *F, const double *g,
+                           const double *speed, double dtdx, const double *optv, double *flux, int *ist) {
+    const int a = c - 1 + side, b = c + side;
+    double T[NP * NP], Ma[NP], Mb[NP], Fa[NP], Fb[NP], flf[NP];
+    or_gauge_T(&g[6 * c], &g[6 * a], T);
+    matvec35(T, &M[NP * a], Ma); matvec35(T, &F[NP * a], Fa);
+    or_gauge_T(&g[6 * c], &g[6 * b], T);
+    matvec35(T, &M[NP * b], Mb); matvec35(T, &F[NP * b], Fb);
+    const double lam = fmax(speed[a], speed[b]);
+    for (int i = 0; i < NP; ++i) flf[i] = 0.5 * (Fa[i] + Fb[i]) + 0.5 * lam * (Ma[i] - Mb[i]);
+    if (scheme == 0) {
+        memcpy(flux, flf, sizeof(flf));
+        return;
+    }
+    double MI[NP], gI[6], MH[NP], bI[NP], FI[NP], flw[NP];
+    for (int i = 0; i < NP; ++i) MI[i] = 0.5 * (Ma[i] + Mb[i]) + 0.5 * dtdx * (Fa[i] - Fb[i]);
+    or_hermite_gauge(MI, &g[6 * c], 1, gI);
+    or_transform_M(gI, &g[6 * c], MI, MH);
+    memset(bI, 0, sizeof(bI));
+    bI[0] = MH[0];
+    int it = 0;
+    *ist |= or_solve(order, gI, MH, bI, optv, &it, NULL, NULL);
+    or_flux(order, bI, gI, MH[0], FI, NULL, NULL, NULL);
+    or_gauge_T(&g[6 * c], gI, T);
+    matvec35(T, FI, flw);
+    if (scheme == 1) {
+        memcpy(flux, flw, sizeof(flw));
+        return;
+    }
+    const int aa = a > 0 ? a - 1 : a;
+    double Maa[NP];
+    or_gauge_T(&g[6 * c], &g[6 * aa], T);
+    matvec35(T, &M[NP * aa], Maa);
+    for (int i = 0; i < NP; ++i) {
+        const double num = Ma[i] - Maa[i], den = Mb[i] - Ma[i];
+        const double r = den != 0.0 ? num / den : 0.0;
+        /* (r + |r|)/(1 + r): 0 for r <= 0 (also at r = -1, where the printed
+         * form is 0/0), 2r/(1 + r) = 2/(1 + 1/r) for r > 0 (2 as r -> inf) */
+        const double phi = r > 0.0 ? 2.0 / (1.0 + 1.0 / r) : 0.0;
+        flux[i] = phi != 0.0 ? flf[i] + phi * (flw[i] - flf[i]) : flf[i];
+    }
+}
+
 void or_shock_step(int order, int N, double dx, double cfl, double Pr, double relax_coef,
                    double *M, double *beta, double *g, double *speed, int *status, int *iters,
-                   const double *optv, int nthreads, double *out, double *cond) {
+                   const double *optv, int nthreads, double *out, double *cond, int scheme, int *iface_status) {
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
@@ -869,20 +929,14 @@ void or_shock_step(int order, int N, double dx, double cfl, double Pr, double re
         if (c == 0 || c == N + 1) for (int i = 0; i < NP; ++i) bb[i] = 0.0;
         or_flux(order, bb, &g[6 * c], M[NP * c], &F[NP * c], &speed[c], NULL, NULL);
     }
-    #pragma omp parallel for schedule(static)
+    #pragma omp parallel for schedule(dynamic, 1)
     for (int c = 1; c <= N; ++c) {
-        double T[NP * NP], Ml[NP], Fl[NP], Mr[NP], Fr[NP];
-        const double *M0 = &M[NP * c], *F0 = &F[NP * c];
-        or_gauge_T(&g[6 * c], &g[6 * (c - 1)], T);
-        matvec35(T, &M[NP * (c - 1)], Ml); matvec35(T, &F[NP * (c - 1)], Fl);
-        or_gauge_T(&g[6 * c], &g[6 * (c + 1)], T);
-        matvec35(T, &M[NP * (c + 1)], Mr); matvec35(T, &F[NP * (c + 1)], Fr);
-        double ll = fmax(speed[c - 1], speed[c]), lr = fmax(speed[c], speed[c + 1]);
-        for (int i = 0; i < NP; ++i) {
-            double fl = 0.5 * (Fl[i] + F0[i]) + 0.5 * ll * (Ml[i] - M0[i]);
-            double fr = 0.5 * (F0[i] + Fr[i]) + 0.5 * lr * (M0[i] - Mr[i]);
-            Mn[NP * c + i] = M0[i] + dt / dx * (fl - fr);
-        }
+        double fl[NP], fr[NP];
+        int ist = 0;
+        interface_flux(order, scheme, c, 0, M, F, g, speed, dt / dx, optv, fl, &ist);
+        interface_flux(order, scheme, c, 1, M, F, g, speed, dt / dx, optv, fr, &ist);
+        for (int i = 0; i < NP; ++i) Mn[NP * c + i] = M[NP * c + i] + dt / dx * (fl[i] - fr[i]);
+        if (iface_status) iface_status[c] = ist;
     }
     double dmax = 0.0, snew = 0.0;
     for (int c = 0; c < NT; ++c) if (speed[c] > snew) snew = speed[c];

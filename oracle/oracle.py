@@ -301,8 +301,10 @@ class Shock:
     """FP64 shock-tube state: N interior cells + 2 Dirichlet ghost cells."""
 
     def __init__(self, mach, ncells, xl, xr, order=8, cfl=0.5, Pr=2.0 / 3.0, gamma=5.0 / 3.0,
-                 kn=1.0, tol=1e-8, maxI=500, nthreads=0, ic="step", thickness=15.7):
+                 kn=1.0, tol=1e-8, maxI=500, nthreads=0, ic="step", thickness=15.7, scheme="lf"):
         self.order, self.N, self.cfl, self.Pr = order, ncells, cfl, Pr
+        # interface flux: Eq. "The lax F" (lf), "The lax W" (lw), "The FLIC" (flic)
+        self.scheme = {"lf": 0, "lw": 1, "flic": 2}[scheme]
         self.dx = (xr - xl) / ncells
         self.x = xl + (np.arange(ncells) + 0.5) * self.dx
         self.relax = kn * RELAX_KN1 / Pr
@@ -348,6 +350,8 @@ class Shock:
         # pivot-ratio condition estimate of each cell's last solve (Fig. 7), on request
         self.track_cond = False
         self.cond = np.zeros(NT)
+        # status bits of the interface solves (Lax-Wendroff / FLIC), OR-ed per cell
+        self.iface_status = np.zeros(NT, dtype=np.int32)
         self.t = 0.0
         self.steps = 0
 
@@ -356,7 +360,8 @@ class Shock:
         lib().or_shock_step(self.order, self.N, ctypes.c_double(self.dx), ctypes.c_double(self.cfl),
                             ctypes.c_double(self.Pr), ctypes.c_double(self.relax), _d(self.M), _d(self.beta),
                             _d(self.g), _d(self.speed), _i(self.status), _i(self.iters), _d(self.opts),
-                            self.nthreads, _d(out), _d(self.cond) if self.track_cond else None)
+                            self.nthreads, _d(out), _d(self.cond) if self.track_cond else None, self.scheme,
+                            _i(self.iface_status))
         self.t += out[0]
         self.steps += 1
         return out  # dt, max speed, max |d rho|

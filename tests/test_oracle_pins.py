@@ -377,31 +377,49 @@ def test_rankine_hugoniot_values_and_conservation(O):
         assert v1 * (v1 ** 2 / 2 + 2.5) == pytest.approx(r * v2 * (v2 ** 2 / 2 + 2.5 * t))  # energy
 
 
-def test_shock_conserves_mass_momentum_energy(O):
-    sh = O.Shock(1.5, 64, -20.0, 20.0)
+@pytest.mark.parametrize("scheme", ["lf", "lw", "flic"])
+def test_shock_conserves_mass_momentum_energy(O, scheme):
+    """Flux form with Rankine-Hugoniot boundary states: the boundary fluxes
+    balance (that is what the RH conditions say), so interior mass, momentum
+    and energy do not change.  Local Lax-Friedrichs and Lax-Wendroff fluxes
+    commute with the change of gauge, so the two cells of an interface see
+    one flux and the totals hold to rounding.  FLIC's limiter acts component
+    by component in each cell's own gauge (all quantities of cell n in g(n)),
+    which does not commute with the change of gauge: the two sides of an
+    interface get slightly different fluxes.  Mass (phi_0 = 1, the same in
+    every gauge) still holds to rounding; momentum and energy drift by
+    ~1e-5 and ~2e-4 of their totals over these 10 steps."""
+    sh = O.Shock(1.5, 64, -20.0, 20.0, scheme=scheme)
     tot0 = sum(physical_totals(O, sh.M[c], sh.g[c]) for c in range(1, 65))
     for _ in range(10):
         sh.step()
     tot1 = sum(physical_totals(O, sh.M[c], sh.g[c]) for c in range(1, 65))
-    assert np.abs(tot1 - tot0).max() < 1e-11 * np.abs(tot0).max()
+    rel = np.abs(tot1 - tot0) / np.abs(tot0)
+    if scheme == "flic":
+        assert rel[0] < 1e-12
+        assert 0 < rel[1:].max() < 1e-3
+    else:
+        assert np.abs(tot1 - tot0).max() < 1e-11 * np.abs(tot0).max()
     # the boundary cells are still the RH states
     rho, ux, T = sh.profile()
     assert rho[0] == pytest.approx(1.0, abs=1e-12) and rho[-1] == pytest.approx(sh.n_dn, abs=1e-12)
     assert T[-1] == pytest.approx(sh.T_dn, abs=1e-12)
 
 
-def test_uniform_state_is_steady(O):
-    sh = O.Shock(1.5, 16, 1.0, 11.0)   # every cell on the downstream side
+@pytest.mark.parametrize("scheme", ["lf", "lw", "flic"])
+def test_uniform_state_is_steady(O, scheme):
+    sh = O.Shock(1.5, 16, 1.0, 11.0, scheme=scheme)   # every cell on the downstream side
     M0 = sh.M.copy()
     for _ in range(3):
         sh.step()
     assert np.abs(sh.M - M0).max() < 1e-12
 
 
-def test_shock_symmetry_zeros(O):
+@pytest.mark.parametrize("scheme", ["lf", "flic"])
+def test_shock_symmetry_zeros(O, scheme):
     """y -> -y and y <-> z leave the 1D shock invariant: parameters odd in u_y
     or u_z stay zero."""
-    sh = O.Shock(1.5, 32, -10.0, 10.0)
+    sh = O.Shock(1.5, 32, -10.0, 10.0, scheme=scheme)
     for _ in range(4):
         sh.step()
     idx = O.basis_index()
@@ -417,6 +435,31 @@ def test_shock_step_dt_from_cfl(O):
     assert dt == pytest.approx(0.5 * sh.dx / smax)
     r = math.sqrt(5 + math.sqrt(10))
     assert smax == pytest.approx(max(sh.v_up + r, sh.v_dn + r * math.sqrt(sh.T_dn)))
+
+
+def _shock_density_at(O, N, scheme, t_end=2.0):
+    """Smooth Mach-1.5 tanh profile (thickness 12 on [-20, 20]), collisions
+    made negligible (Kn = 100: the explicit source update of Eq. "source
+    update" is first order in dt), advanced to exactly t_end (the last step's
+    CFL number is cut to land there)."""
+    s = O.Shock(1.5, N, -20.0, 20.0, order=8, ic="tanh", thickness=12.0, kn=100.0, scheme=scheme)
+    while s.t < t_end - 1e-12:
+        if s.t + s.cfl * s.dx / s.speed.max() > t_end:
+            s.cfl = (t_end - s.t) * s.speed.max() / s.dx
+        s.step()
+    return s.profile()[0]
+
+
+def test_interface_fluxes_convergence_order(O):
+    """Self-convergence on a smooth profile: e(N) = L1 distance between the
+    N-cell density and the 2N-cell one averaged onto the N cells.  Local
+    Lax-Friedrichs is first order (e(N)/e(2N) -> 2), the two-step
+    Lax-Wendroff flux of Eq. "The lax W" and FLIC (Eq. "The FLIC", van Leer
+    limiter) are second order (-> 4; measured 3.5 and 3.6 at N = 64)."""
+    for scheme, lo, hi in (("lf", 1.5, 2.3), ("lw", 3.0, 4.6), ("flic", 3.0, 4.6)):
+        r = {N: _shock_density_at(O, N, scheme) for N in (32, 64, 128)}
+        e = [np.abs(r[N] - r[2 * N].reshape(-1, 2).mean(1)).mean() for N in (32, 64)]
+        assert lo < e[0] / e[1] < hi, (scheme, e)
 
 
 # ---------------------------------------------------------------- targets

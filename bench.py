@@ -386,7 +386,8 @@ def run_newton_study(mem, torch, np, n=26):
     0 to 0.5 on top of the equilibrium (n = 1, v = 0, T = 1) in the trivial
     gauge, solved in FP32 from beta = 0 by the modified Newton method
     (lambda I retries) and by plain Newton (no retries: a failed Cholesky
-    stops the solve); tol 1e-8, maxI 500, the paper's box as above."""
+    stops the solve); tol 1e-8, maxI 500, the paper's box as above.  Then
+    both methods on the gauge study's trivial-gauge cells at tol 1e-9."""
     dev = torch.device("cuda", torch.cuda.current_device())
     m4 = np.linspace(0.0, 0.5, n)
     vctx = mem.Context.velocity(GAUGE_BOX, nbx=16, nbr=12, ng=8, K=10)
@@ -410,6 +411,23 @@ def run_newton_study(mem, torch, np, n=26):
         if ref is not None:
             row["log_mse"] = _log_mse(bn, ref, np)
         out[name] = row
+    # The same comparison on the gauge study's trivial-gauge cells (Mach
+    # 2-12, uniform start, tol 1e-9), where FP32 Hessians turn indefinite.
+    machs = list(range(2, 13))
+    B = len(machs)
+    M, beta0, g = gauge_study_inputs(mem, torch, machs)
+    M, beta0, g = M[B:].contiguous(), beta0[B:].contiguous(), g[B:].contiguous()
+    row = {"mach": machs}
+    for name, ml in (("modified", 20), ("plain", 0)):
+        beta = beta0.clone()
+        st = torch.zeros(B, dtype=torch.int32, device=dev)
+        it = torch.zeros_like(st)
+        vctx.solve_gauge(M, beta, g, st, it, tol=1e-9, maxI=500, max_lambda=ml)
+        torch.cuda.synchronize()
+        stn = st.cpu().numpy()
+        row[name] = {"passes": it.cpu().numpy().tolist(), "status": _status_letters(stn),
+                     "lambda_retries": int(((stn & 16) != 0).sum())}
+    out["trivial_gauge_tol_1e-9"] = row
     vctx.close()
     return {"newton_study": out}
 

@@ -60,6 +60,11 @@ extern "C" {
 #define MEM_IMPL_PLAIN 0 /* separate FP32 kernels per Newton stage, host loop   */
 #define MEM_IMPL_FUSED 1 /* one persistent FP32 kernel, warp per cell           */
 
+/* Interface flux of the shock's finite-volume step (Section 3.3). */
+#define MEM_SCHEME_LF 0   /* local Lax-Friedrichs, Eq. "The lax F"               */
+#define MEM_SCHEME_LW 1   /* two-step Lax-Wendroff, Eq. "The lax W"              */
+#define MEM_SCHEME_FLIC 2 /* flux-limited centred with van Leer, Eq. "The FLIC" */
+
 typedef struct mem_ctx mem_ctx;
 
 /* Options of Algorithm 1 (modified Newton + backtracking Armijo line search).
@@ -237,7 +242,7 @@ typedef struct {
     double kn;         /* upstream Knudsen number (1)                       */
     int32_t ic;        /* 0: step at x = 0 between the RH Maxwellians;
                           1: tanh blend of Appendix D, Eq. "Mx ini", with
-                          thickness parameter 15.7                         */
+                          thickness parameter `thickness`                  */
     int32_t impl;      /* Newton back-end, MEM_IMPL_*                       */
     int32_t graph;     /* 1: capture the time step in a CUDA graph          */
     float tol;         /* Algorithm 1 tolerance (1e-8)                      */
@@ -247,6 +252,20 @@ typedef struct {
                                   max(v_- + nb c_-, v_+ + nb c_+)],
                           u_r in [0, nr max(c_-, c_+)], c = sqrt(T) of the
                           Rankine-Hugoniot states (Appendix D; 5, 5, 5)   */
+    int32_t scheme;    /* interface flux, MEM_SCHEME_* (LF).  LW and FLIC
+                          solve Algorithm 1 once more per interface and step:
+                          the Lax-Wendroff interface moments, moved to their
+                          own Hermite gauge, cold start (beta = 0 there);
+                          the flux is moved to each neighbour's gauge.
+                          FLIC's van Leer limiter works per component in
+                          the updated cell's gauge (as every quantity of
+                          cell n in the paper), which conserves mass exactly
+                          but momentum and energy only to the limiter's
+                          gauge dependence; r = 0 where its denominator is
+                          0, and the ghost cell stands in for the cell
+                          before the first one.                           */
+    double thickness;  /* ic = 1: thickness parameter T of Eq. "Mx ini"
+                          (15.7, the paper's Mach-10 start)               */
 } mem_shock_params;
 
 void mem_shock_params_default(mem_shock_params *p);
@@ -304,6 +323,19 @@ int mem_shock_get(mem_shock *s, float *M_host, float *g_host, float *beta_host, 
 /* Device pointers of the state (for zero-copy use from the caller). */
 int mem_shock_device_state(mem_shock *s, float **M, float **beta, float **g, float **speed,
                            int32_t **status, int32_t **iters);
+
+/* Copy the interface state of Lax-Wendroff / FLIC problems (Eq. "The lax W")
+ * to host, packed like the cells of the batch (NT = sum of ncells + 2 over
+ * the problems): entry c is the interface between cells c - 1 and c of one
+ * problem, meaningful where that problem uses LW or FLIC and c is not its
+ * left ghost cell (other entries hold scratch).  MI, betaI [NT][35] and
+ * gI [NT][6]: the interface moments in their own Hermite gauge and their
+ * parameters; FI [NT][35]: their flux in that gauge; status, iters [NT]:
+ * the last interface solve (MEM_ST_* bits, Newton passes).  Any pointer may
+ * be NULL.  Synchronous.  MEM_EINVAL for a batch without LW / FLIC
+ * problems. */
+int mem_shock_get_interfaces(mem_shock *s, float *MI, float *betaI, float *gI, float *FI, int32_t *status,
+                             int32_t *iters);
 
 void mem_shock_free(mem_shock *s);
 

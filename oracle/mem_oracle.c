@@ -856,7 +856,9 @@ static void collide(double *M, const double *g, double dt, double Pr, double rel
  *     as r = 0 (first order there), phi = 0 at r = -1 (the printed form is
  *     0/0 there), the Lax-Wendroff term is left out where phi = 0, and cell
  *     a - 1 before the first cell is the ghost cell itself (r = 0).
- * Interface solves add their status bits to *ist. */
+ * An interface whose solve fails (non-finite, lambda cap, bad input) or whose
+ * flux is not finite takes F^LF.  Interface solves add their status bits to
+ * *ist. */
 static void interface_flux(int order, int scheme, int c, int side, const double *M, const double *F, const double *g,
                            const double *speed, double dtdx, const double *optv, double *flux, int *ist) {
     const int a = c - 1 + side, b = c + side;
@@ -878,8 +880,15 @@ static void interface_flux(int order, int scheme, int c, int side, const double 
     memset(bI, 0, sizeof(bI));
     bI[0] = MH[0];
     int it = 0;
-    *ist |= or_solve(order, gI, MH, bI, optv, &it, NULL, NULL);
+    const int sI = or_solve(order, gI, MH, bI, optv, &it, NULL, NULL);
+    *ist |= sI;
     or_flux(order, bI, gI, MH[0], FI, NULL, NULL, NULL);
+    int ok = (sI & (ST_NONFINITE | ST_LAMBDA_CAP | ST_BADINPUT)) == 0;
+    for (int i = 0; i < NP; ++i) ok = ok && isfinite(FI[i]);
+    if (!ok) {
+        memcpy(flux, flf, sizeof(flf));
+        return;
+    }
     or_gauge_T(&g[6 * c], gI, T);
     matvec35(T, FI, flw);
     if (scheme == 1) {

@@ -8,6 +8,10 @@
 //     neighbour gauge transform + local Lax-Friedrichs + finite volume
 //     (Eqs. "The lax F", "The lax F convert", "The ME equation fvm 2")
 //                                                                (k_stencil)
+//     or, for Lax-Wendroff / FLIC problems, the interface moments of Eq.
+//     "The lax W" in their Hermite gauge (k_iface_state), Newton and flux
+//     at every interface, then the LW or FLIC fluxes + finite volume
+//                                                                (k_stencil2)
 //   Collision(dt_p/2)                                            (k_collide)
 //   Hermite gauge and transform of M and beta                    (k_regauge)
 // Problem p owns the contiguous cells [off_p, off_p + N_p + 2): a Dirichlet
@@ -109,17 +113,13 @@ __global__ void k_collide(float *__restrict__ M, const float *__restrict__ g, co
     for (int k = 0; k < NP; ++k) M[(size_t)c * NP + k] = (1.f - r) * m[k] + r * mt[k];
 }
 
-// Local Lax-Friedrichs finite-volume update in the cell's own gauge:
-// M_c += dt/dx (F^LF_{c-1/2} - F^LF_{c+1/2}), neighbours moved to g_c.
-__global__ void __launch_bounds__(128) k_stencil(const float *__restrict__ M, const float *__restrict__ F,
-                                                 const float *__restrict__ g, const float *__restrict__ speed,
-                                                 float *__restrict__ Mn, const int *__restrict__ pid,
-                                                 const unsigned char *__restrict__ interior,
-                                                 const ShockProb *__restrict__ prm,
-                                                 const ShockScalars *__restrict__ sc, int NT) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= NT || !interior[c]) return;
-    const int p = pid[c];
+// Local Lax-Friedrichs finite-volume update of interior cell c in its own
+// gauge: M_c += dt/dx (F^LF_{c-1/2} - F^LF_{c+1/2}), neighbours moved to g_c.
+// One compiled copy serves k_stencil and the LF problems of k_stencil2, so a
+// problem's result does not depend on the schemes of the batch it shares.
+__device__ __noinline__ void lf_update(const float *__restrict__ M, const float *__restrict__ F,
+                                       const float *__restrict__ g, const float *__restrict__ speed,
+                                       float *__restrict__ Mn, int c, float r) {
     float g0[6], gl[6], gr[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
@@ -128,7 +128,6 @@ __global__ void __launch_bounds__(128) k_stencil(const float *__restrict__ M, co
         gr[k] = g[(size_t)(c + 1) * 6 + k];
     }
     const float s0 = speed[c], ll = fmaxf(speed[c - 1], s0), lr = fmaxf(s0, speed[c + 1]);
-    const float r = sc[p].dt / prm[p].dx;
     float acc[NP], x[NP], y[NP];
     AxisMap T[3];
     // F^LF_{c-1/2} - F^LF_{c+1/2} = 0.5(Fl + F0) + 0.5 ll (Ml - M0) - 0.5(F0 + Fr) - 0.5 lr (M0 - Mr)
@@ -156,6 +155,185 @@ __global__ void __launch_bounds__(128) k_stencil(const float *__restrict__ M, co
     apply_T(T, x, y);
 #pragma unroll
     for (int k = 0; k < NP; ++k) acc[k] -= 0.5f * y[k];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) Mn[(size_t)c * NP + k] = M[(size_t)c * NP + k] + r * acc[k];
+}
+
+__global__ void __launch_bounds__(128) k_stencil(const float *__restrict__ M, const float *__restrict__ F,
+                                                 const float *__restrict__ g, const float *__restrict__ speed,
+                                                 float *__restrict__ Mn, const int *__restrict__ pid,
+                                                 const unsigned char *__restrict__ interior,
+                                                 const ShockProb *__restrict__ prm,
+                                                 const ShockScalars *__restrict__ sc, int NT) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= NT || !interior[c]) return;
+    const int p = pid[c];
+    lf_update(M, F, g, speed, Mn, c, sc[p].dt / prm[p].dx);
+}
+
+// Interface moments of Eq. "The lax W" between cells c - 1 and c (iface[c]
+// set), formed in the gauge of cell c and moved to their own Hermite gauge
+// (axisymmetric form).  The Newton start is the interface's parameters of
+// the previous step carried to the new gauge (the density they describe),
+// or beta = 0 there where that solve failed.  Entries without an interface
+// get a copy of cell c, so that every row the solver and the flux kernel see
+// is valid.
+__global__ void __launch_bounds__(128) k_iface_state(const float *__restrict__ M, const float *__restrict__ F,
+                                                     const float *__restrict__ g, const float *__restrict__ beta,
+                                                     float *__restrict__ MI, float *__restrict__ gI,
+                                                     float *__restrict__ betaI,
+                                                     const int32_t *__restrict__ statusI,
+                                                     const unsigned char *__restrict__ iface,
+                                                     const int *__restrict__ pid, const ShockProb *__restrict__ prm,
+                                                     const ShockScalars *__restrict__ sc, int NT) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= NT) return;
+    if (!iface[c]) {
+        for (int k = 0; k < NP; ++k) {
+            MI[(size_t)c * NP + k] = M[(size_t)c * NP + k];
+            betaI[(size_t)c * NP + k] = beta[(size_t)c * NP + k];
+        }
+        for (int k = 0; k < 6; ++k) gI[(size_t)c * 6 + k] = g[(size_t)c * 6 + k];
+        return;
+    }
+    const int p = pid[c];
+    const float h = 0.5f * sc[p].dt / prm[p].dx;
+    float gb[6], ga[6], gh[6], m[NP], x[NP], y[NP];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        gb[k] = g[(size_t)c * 6 + k];
+        ga[k] = g[(size_t)(c - 1) * 6 + k];
+    }
+    AxisMap T[3];
+    gauge_maps(gb, ga, T);
+    // M(n - 1/2) = (M_a + M_b)/2 + dt/(2 dx) (F_a - F_b), a = c - 1, b = c
+#pragma unroll
+    for (int k = 0; k < NP; ++k) x[k] = M[(size_t)(c - 1) * NP + k];
+    apply_T(T, x, y);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) m[k] = 0.5f * (y[k] + M[(size_t)c * NP + k]);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) x[k] = F[(size_t)(c - 1) * NP + k];
+    apply_T(T, x, y);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) m[k] += h * (y[k] - F[(size_t)c * NP + k]);
+    hermite_gauge(m, gb, 1, gh);
+    gauge_maps(gh, gb, T);
+    apply_T(T, m, y);
+    // warm start: previous parameters (gauge gI[c]) carried to gh
+    float gp[6], bp[NP];
+    bool ok = (statusI[c] & (MEM_ST_NONFINITE | MEM_ST_LAMBDA_CAP | MEM_ST_BADINPUT)) == 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) gp[k] = gI[(size_t)c * 6 + k];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        bp[k] = betaI[(size_t)c * NP + k];
+        ok = ok && isfinite(bp[k]);
+    }
+    transform_beta(gh, gp, bp, m);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        MI[(size_t)c * NP + k] = y[k];
+        betaI[(size_t)c * NP + k] = k == 0 ? y[0] : (ok && isfinite(m[k]) ? m[k] : 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) gI[(size_t)c * 6 + k] = gh[k];
+}
+
+// Finite-volume update of interior cell c with Lax-Wendroff or FLIC fluxes
+// (per problem; LF problems of a mixed batch take the LF flux), everything in
+// the gauge g(c).  At the interface between cells a and b = a + 1:
+//   F^LF = (F_a + F_b)/2 + lambda/2 (M_a - M_b), Eq. "The lax F";
+//   F^LW = T(g(c), g_I) F(beta_I; g_I), the interface solve's flux;
+//   FLIC: F^LF + phi_k (F^LW - F^LF)_k with the van Leer limiter
+//   phi(r) = (r + |r|)/(1 + r), r_k = (M_a - M_{a-1})_k / (M_b - M_a)_k,
+//   r = 0 where the denominator is 0, phi = 0 for r <= 0 (also r = -1, where
+//   the printed form is 0/0), the LW term left out where phi = 0, and the
+//   ghost cell standing in for the cell before the first one.
+// An interface whose Newton solve failed (non-finite, lambda cap, bad input)
+// or whose flux is not finite takes F^LF.
+__global__ void __launch_bounds__(128) k_stencil2(const float *__restrict__ M, const float *__restrict__ F,
+                                                  const float *__restrict__ g, const float *__restrict__ speed,
+                                                  const float *__restrict__ FI, const float *__restrict__ gI,
+                                                  const int32_t *__restrict__ statusI,
+                                                  float *__restrict__ Mn, const int *__restrict__ pid,
+                                                  const unsigned char *__restrict__ interior,
+                                                  const ShockProb *__restrict__ prm,
+                                                  const ShockScalars *__restrict__ sc, int NT) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= NT || !interior[c]) return;
+    const int p = pid[c];
+    const int scheme = prm[p].scheme, off = prm[p].off;
+    if (scheme == MEM_SCHEME_LF) {
+        lf_update(M, F, g, speed, Mn, c, sc[p].dt / prm[p].dx);
+        return;
+    }
+    float g0[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) g0[k] = g[(size_t)c * 6 + k];
+    float acc[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) acc[k] = 0.f;
+    for (int side = 0; side < 2; ++side) {
+        const int a = c - 1 + side, b = c + side;
+        float ma[NP], mb[NP], f[NP], x[NP], y[NP], gn[6];
+        AxisMap T[3];
+        // M_a, M_b in g(c) (one of them is cell c itself)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) gn[k] = g[(size_t)(side ? b : a) * 6 + k];
+        gauge_maps(g0, gn, T);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) x[k] = M[(size_t)(side ? b : a) * NP + k];
+        apply_T(T, x, y);
+        const float lam = fmaxf(speed[a], speed[b]);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const float own = M[(size_t)c * NP + k];
+            ma[k] = side ? own : y[k];
+            mb[k] = side ? y[k] : own;
+            f[k] = 0.5f * lam * (ma[k] - mb[k]) + 0.5f * F[(size_t)c * NP + k];
+        }
+#pragma unroll
+        for (int k = 0; k < NP; ++k) x[k] = F[(size_t)(side ? b : a) * NP + k];
+        apply_T(T, x, y);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) f[k] += 0.5f * y[k];
+        bool lw_ok = (statusI[b] & (MEM_ST_NONFINITE | MEM_ST_LAMBDA_CAP | MEM_ST_BADINPUT)) == 0;
+        if (lw_ok) {
+            float w[NP];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) gn[k] = gI[(size_t)b * 6 + k];
+            gauge_maps(g0, gn, T);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                x[k] = FI[(size_t)b * NP + k];
+                lw_ok = lw_ok && isfinite(x[k]);
+            }
+            apply_T(T, x, w);
+            if (lw_ok && scheme == MEM_SCHEME_LW) {
+#pragma unroll
+                for (int k = 0; k < NP; ++k) f[k] = w[k];
+            } else if (lw_ok) {
+                const int aa = a - 1 >= off ? a - 1 : a;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) gn[k] = g[(size_t)aa * 6 + k];
+                gauge_maps(g0, gn, T);
+#pragma unroll
+                for (int k = 0; k < NP; ++k) x[k] = M[(size_t)aa * NP + k];
+                apply_T(T, x, y);
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    const float num = ma[k] - y[k], den = mb[k] - ma[k];
+                    const float r = den != 0.f ? num / den : 0.f;
+                    const float phi = r > 0.f ? 2.f / (1.f + 1.f / r) : 0.f;
+                    if (phi != 0.f) f[k] += phi * (w[k] - f[k]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NP; ++k) acc[k] += side ? -f[k] : f[k];
+    }
+    const float r = sc[p].dt / prm[p].dx;
 #pragma unroll
     for (int k = 0; k < NP; ++k) Mn[(size_t)c * NP + k] = M[(size_t)c * NP + k] + r * acc[k];
 }
@@ -225,12 +403,16 @@ namespace mem_host {
 bool shock_params_valid(const mem_shock_params &p) {
     return p.ncells >= 1 && p.xr > p.xl && p.mach >= 1.0 && p.cfl > 0 && p.Pr > 0.5 && p.gamma > 1.0 && p.kn > 0 &&
            (p.ic == 0 || p.ic == 1) && p.maxI >= 0 && (p.impl == MEM_IMPL_PLAIN || p.impl == MEM_IMPL_FUSED) &&
-           p.na > 0 && p.nb > 0 && p.nr > 0;
+           p.na > 0 && p.nb > 0 && p.nr > 0 && p.scheme >= MEM_SCHEME_LF && p.scheme <= MEM_SCHEME_FLIC &&
+           (p.ic == 0 || p.thickness > 0);
 }
 
+// Device bytes per packed cell, the interface arrays of Lax-Wendroff / FLIC
+// problems included (an upper bound for LF-only batches).
 size_t batch_bytes_per_cell(const mem_ctx *ctx) {
     const size_t work = ctx->vel ? (size_t)MEM_MU_STRIDE : (size_t)ctx->Q + MEM_NCOL_FLUX;
-    return sizeof(float) * (5 * NP + 6 + 3 + work) + sizeof(int32_t) * 3 + 1;
+    const size_t iface = sizeof(float) * (3 * NP + 6 + 1) + sizeof(int32_t) * 2 + 1;
+    return sizeof(float) * (5 * NP + 6 + 3 + work) + sizeof(int32_t) * 3 + 1 + iface;
 }
 
 // Integration domain of a velocity-space rule for one problem (Appendix D):
@@ -252,7 +434,8 @@ void batch_free(ShockBatch *b) {
     if (!b) return;
     cudaDeviceSynchronize();
     void *ptrs[] = {b->M, b->beta, b->g, b->speed, b->F, b->Mn, b->rho0, b->sigma, b->mom, b->status, b->iters,
-                    b->pid, b->interior, b->prm, b->sc, b->mu, b->dom, b->cond};
+                    b->pid, b->interior, b->prm, b->sc, b->mu, b->dom, b->cond, b->MI, b->betaI, b->gI,
+                    b->FI, b->speedI, b->statusI, b->itersI, b->iface};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete b;
@@ -330,6 +513,8 @@ int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **o
         // mu = kn sqrt(2/pi) T, tau = mu / (Pr n T) = relax / n.
         pr.relax = (float)(ps[i].kn * sqrt(2.0 / 3.14159265358979323846) / ps[i].Pr);
         pr.drho = (float)(n_dn - 1.0);
+        pr.scheme = ps[i].scheme;
+        b->second_order |= ps[i].scheme != MEM_SCHEME_LF;
         b->hprm.push_back(pr);
         off += pr.n + 2;
     }
@@ -351,17 +536,33 @@ int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **o
               alloc((void **)&b->status, sizeof(int32_t) * NT) && alloc((void **)&b->iters, sizeof(int32_t) * NT) &&
               alloc((void **)&b->pid, sizeof(int) * NT) && alloc((void **)&b->interior, NT) &&
               alloc((void **)&b->prm, sizeof(ShockProb) * P) && alloc((void **)&b->sc, sizeof(ShockScalars) * P);
+    if (ok && b->second_order)
+        ok = alloc((void **)&b->MI, sizeof(float) * NT * NP) && alloc((void **)&b->betaI, sizeof(float) * NT * NP) &&
+             alloc((void **)&b->gI, sizeof(float) * NT * 6) && alloc((void **)&b->FI, sizeof(float) * NT * NP) &&
+             alloc((void **)&b->speedI, sizeof(float) * NT) && alloc((void **)&b->statusI, sizeof(int32_t) * NT) &&
+             alloc((void **)&b->itersI, sizeof(int32_t) * NT) && alloc((void **)&b->iface, NT);
     if (!ok) { cudaGetLastError(); batch_free(b); return MEM_ENOMEM; }
     std::vector<float> hM(NT * NP), hb(NT * NP), hg(NT * 6);
     std::vector<int> hpid(NT);
-    std::vector<unsigned char> hint(NT);
+    std::vector<unsigned char> hint(NT), hif(NT, 0);
     for (int i = 0; i < P; ++i) {
         const ShockProb &pr = b->hprm[i];
-        set_ic(ps[i], pr, 15.7, hM.data(), hb.data(), hg.data());
+        set_ic(ps[i], pr, ps[i].thickness, hM.data(), hb.data(), hg.data());
         for (int c = 0; c < pr.n + 2; ++c) {
             hpid[pr.off + c] = i;
             hint[pr.off + c] = (c > 0 && c < pr.n + 1) ? 1 : 0;
+            hif[pr.off + c] = (c > 0 && pr.scheme != MEM_SCHEME_LF) ? 1 : 0;
         }
+    }
+    std::vector<float> hbI(NT * NP, 0.f);
+    if (b->second_order &&
+        (cudaMemcpy(b->iface, hif.data(), NT, cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(b->betaI, hbI.data(), sizeof(float) * hbI.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(b->gI, hg.data(), sizeof(float) * hg.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemset(b->statusI, 0, sizeof(int32_t) * NT) != cudaSuccess ||
+         cudaMemset(b->itersI, 0, sizeof(int32_t) * NT) != cudaSuccess)) {
+        batch_free(b);
+        return MEM_ECUDA;
     }
     std::vector<ShockScalars> hsc(P);
     memset(hsc.data(), 0, sizeof(ShockScalars) * P);
@@ -442,7 +643,30 @@ int batch_enqueue_step(ShockBatch *b, cudaStream_t st) {
              : flux_bufs(b->ctx, b->M, b->beta, b->g, b->F, b->speed, NT, b->sigma, b->mom, st);
     }
     if (rc) return rc;
-    k_stencil<<<nb, 128, 0, st>>>(b->M, b->F, b->g, b->speed, b->Mn, b->pid, b->interior, b->prm, b->sc, NT);
+    if (b->second_order) {
+        // Lax-Wendroff / FLIC: one more Newton solve and flux per interface,
+        // in the interface's Hermite gauge (no speeds needed there).
+        k_iface_state<<<nb, 128, 0, st>>>(b->M, b->F, b->g, b->beta, b->MI, b->gI, b->betaI, b->statusI, b->iface,
+                                          b->pid, b->prm, b->sc, NT);
+        if (b->ctx->vel) {
+            rc = vel_run(b->ctx, b->MI, b->betaI, b->gI, b->statusI, b->itersI, b->mu, b->pid, b->dom, NT, o, true, st,
+                         b->iface);
+            if (!rc) rc = flux_from_mu(b->ctx, b->mu, b->MI, b->gI, b->FI, nullptr, NT, st, true);
+        } else if (o.impl == MEM_IMPL_PLAIN) {
+            rc = solve_plain(b->ctx, b->MI, b->betaI, b->statusI, b->itersI, NT, o, st, b->iface);
+            if (!rc) rc = flux_bufs(b->ctx, b->MI, b->betaI, b->gI, b->FI, b->speedI, NT, b->sigma, b->mom, st);
+        } else {
+            rc = solve_fused(b->ctx, b->MI, b->betaI, b->statusI, b->itersI, NT, o, st, b->iface);
+            if (!rc)
+                rc = flux_fused_available(b->ctx)
+                         ? flux_fused(b->ctx, b->MI, b->betaI, b->gI, b->FI, nullptr, NT, st, true)
+                         : flux_bufs(b->ctx, b->MI, b->betaI, b->gI, b->FI, b->speedI, NT, b->sigma, b->mom, st);
+        }
+        if (rc) return rc;
+        k_stencil2<<<nb, 128, 0, st>>>(b->M, b->F, b->g, b->speed, b->FI, b->gI, b->statusI, b->Mn, b->pid,
+                                       b->interior, b->prm, b->sc, NT);
+    } else
+        k_stencil<<<nb, 128, 0, st>>>(b->M, b->F, b->g, b->speed, b->Mn, b->pid, b->interior, b->prm, b->sc, NT);
     k_collide<<<nb, 128, 0, st>>>(b->Mn, b->g, b->pid, b->interior, b->prm, b->sc, NT, 0.5f, nullptr);
     k_regauge<<<nb, 128, 0, st>>>(b->Mn, b->M, b->beta, b->g, b->rho0, b->pid, b->interior, b->sc, NT);
     MEM_CUDA_TRY(cudaGetLastError());
@@ -559,6 +783,8 @@ void mem_shock_params_default(mem_shock_params *p) {
     p->tol = 1e-8f;
     p->maxI = 500;
     p->na = p->nb = p->nr = 5.0;
+    p->scheme = MEM_SCHEME_LF;
+    p->thickness = 15.7;
 }
 
 void mem_shock_free(mem_shock *s) {
@@ -638,6 +864,21 @@ int mem_shock_step(mem_shock *s, int nsteps, double *steady_metric, void *stream
         }
         *steady_metric = worst;
     }
+    return MEM_OK;
+}
+
+int mem_shock_get_interfaces(mem_shock *s, float *MI, float *betaI, float *gI, float *FI, int32_t *status,
+                             int32_t *iters) {
+    if (!s || !s->b->second_order) return MEM_EINVAL;
+    const mem_host::ShockBatch *b = s->b;
+    const size_t NT = (size_t)b->NT;
+    MEM_CUDA_TRY(cudaDeviceSynchronize());
+    if (MI) MEM_CUDA_TRY(cudaMemcpy(MI, b->MI, sizeof(float) * NT * NP, cudaMemcpyDeviceToHost));
+    if (betaI) MEM_CUDA_TRY(cudaMemcpy(betaI, b->betaI, sizeof(float) * NT * NP, cudaMemcpyDeviceToHost));
+    if (gI) MEM_CUDA_TRY(cudaMemcpy(gI, b->gI, sizeof(float) * NT * 6, cudaMemcpyDeviceToHost));
+    if (FI) MEM_CUDA_TRY(cudaMemcpy(FI, b->FI, sizeof(float) * NT * NP, cudaMemcpyDeviceToHost));
+    if (status) MEM_CUDA_TRY(cudaMemcpy(status, b->statusI, sizeof(int32_t) * NT, cudaMemcpyDeviceToHost));
+    if (iters) MEM_CUDA_TRY(cudaMemcpy(iters, b->itersI, sizeof(int32_t) * NT, cudaMemcpyDeviceToHost));
     return MEM_OK;
 }
 

@@ -14,7 +14,7 @@ struct ShockProb {
     float Pr;      // Prandtl number of the ES-BGK model
     float relax;   // tau = relax / n
     float drho;    // rho_+ - rho_- (normalises the steady-state metric)
-    float pad;
+    int scheme;    // interface flux, MEM_SCHEME_*
 };
 
 // Per-problem step scalars (device).
@@ -40,6 +40,13 @@ struct ShockBatch {
     double *dom = nullptr;    // [P][4] integration domain (a_x, b_x, b_r, 0) per problem (velocity-space rule)
     float *cond = nullptr;    // [NT] pivot-ratio condition estimate of each cell's last solve (velocity-space rule)
     int32_t *status = nullptr, *iters = nullptr;
+    // Interfaces (Lax-Wendroff / FLIC problems only): entry c is the interface
+    // between cells c - 1 and c of one problem (iface[c] set), in its own
+    // Hermite gauge; other entries hold a copy of cell c so every row is valid.
+    bool second_order = false;
+    float *MI = nullptr, *betaI = nullptr, *gI = nullptr, *FI = nullptr, *speedI = nullptr;
+    int32_t *statusI = nullptr, *itersI = nullptr;
+    unsigned char *iface = nullptr;
     int *pid = nullptr;
     unsigned char *interior = nullptr;
     ShockProb *prm = nullptr;

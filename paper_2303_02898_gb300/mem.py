@@ -36,7 +36,10 @@ class ShockParams(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("kn", ctypes.c_double), ("ic", ctypes.c_int32),
                 ("impl", ctypes.c_int32), ("graph", ctypes.c_int32), ("tol", ctypes.c_float),
                 ("maxI", ctypes.c_int32), ("na", ctypes.c_double), ("nb", ctypes.c_double),
-                ("nr", ctypes.c_double)]
+                ("nr", ctypes.c_double), ("scheme", ctypes.c_int32), ("thickness", ctypes.c_double)]
+
+
+SCHEME_LF, SCHEME_LW, SCHEME_FLIC = 0, 1, 2
 
 
 class ShockResult(ctypes.Structure):
@@ -61,6 +64,7 @@ def lib():
                      "mem_targets", "mem_shock_init", "mem_shock_step", "mem_shock_get",
                      "mem_shock_device_state", "mem_quad_order", "mem_shock_init_batch",
                      "mem_shock_num_problems", "mem_shock_get_problem", "mem_serve_create", "mem_serve_submit",
+                     "mem_shock_get_interfaces",
                      "mem_serve_progress", "mem_serve_poll", "mem_serve_stats"):
             getattr(L, name).restype = ctypes.c_int
         L.mem_solve.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(SolveOpts), _P]
@@ -290,6 +294,23 @@ class Shock:
         c = ctypes.c_double()
         _check(lib().mem_shock_condition(self.h, i, ctypes.byref(c)), "mem_shock_condition")
         return c.value
+
+    def interfaces(self):
+        """mem_shock_get_interfaces: host copy of the Lax-Wendroff / FLIC
+        interface state, packed like the cells (entry c: between cells c - 1
+        and c)."""
+        import numpy as np
+        NT = sum(p.ncells + 2 for p in self.ps)
+        MI = np.zeros((NT, NP), np.float32)
+        b = np.zeros((NT, NP), np.float32)
+        g = np.zeros((NT, 6), np.float32)
+        F = np.zeros((NT, NP), np.float32)
+        st = np.zeros(NT, np.int32)
+        it = np.zeros(NT, np.int32)
+        f = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        _check(lib().mem_shock_get_interfaces(self.h, f(MI), f(b), f(g), f(F), f(st), f(it)),
+               "mem_shock_get_interfaces")
+        return dict(M=MI, beta=b, g=g, F=F, status=st, iters=it)
 
     def device_state(self):
         ptrs = [ctypes.c_void_p() for _ in range(6)]

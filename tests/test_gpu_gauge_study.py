@@ -155,3 +155,25 @@ def test_m4_sweep_modified_and_plain_newton(O, vctx, gold, dev):
     assert np.array_equal(itm[same], itp[same])
     # plain Newton stops (lambda cap) exactly where the modified method retried
     assert np.all((stp[~same] & 32) != 0)
+
+
+def test_trivial_gauge_needs_lambda_retries(O, vctx, gold, problems, dev):
+    """Trivial gauge, tol 1e-9: near convergence FP32 rounding leaves the
+    Hessians of the faster Maxwellians (cond ~1e7 in this gauge) numerically
+    indefinite, so the modified method retries with lambda I and still
+    converges, while plain Newton stops (lambda cap) at the first such pass;
+    the Hermite gauge never needs a retry.  Cells without a retry are
+    bit-identical under both methods."""
+    M, g = problems
+    B = len(gold["mach"])
+    u0 = uniform_beta(O, 2 * B)
+    bm, stm, itm, _, _ = solve(vctx, M, g, u0, dev, tol=1e-9)
+    bp, stp, itp, _, _ = solve(vctx, M, g, u0, dev, tol=1e-9, max_lambda=0)
+    assert np.all(stm & 1), stm
+    assert np.all(stm[:B] & 16 == 0), stm[:B]
+    lam = (stm & 16) != 0
+    assert lam[B:].any(), stm[B:]
+    assert np.all(stp[lam] & 32), stp
+    assert np.all(itp[lam] <= itm[lam]), (itp, itm)
+    assert np.array_equal(bm[~lam], bp[~lam])
+    assert np.array_equal(itm[~lam], itp[~lam])

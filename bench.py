@@ -152,6 +152,36 @@ def run_ensemble(mem, ctx, torch, np, nsteps=10):
     return out
 
 
+def _mach10_paper_mesh(mem, torch, np, vctx, scheme, nsteps):
+    """One Mach-10 problem on the paper's mesh: cell-updates/s of the
+    graph-captured step, then steps and wall time to the steady metric."""
+    sh = mem.Shock(vctx, mach=10.0, ncells=150, xl=-47.1, xr=47.1, ic=1, graph=1, scheme=scheme)
+    sh.step(3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sh.step(nsteps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    rec = {"value": 150 * nsteps / dt, "unit": "cell-updates/s", "cells": 150, "domain": [-47.1, 47.1],
+           "steps": nsteps, "ms_per_step": 1e3 * dt / nsteps, "rule": "velocity-space 6x4 blocks x 8 GL, K=12",
+           "scheme": {0: "local Lax-Friedrichs", 1: "Lax-Wendroff", 2: "FLIC"}[scheme]}
+    done, d = 3 + nsteps, None
+    t1 = time.perf_counter()
+    while done < 20000:
+        d = sh.step(500, steady=True)
+        done += 500
+        if not np.isfinite(d) or d < 1e-6:
+            break
+    torch.cuda.synchronize()
+    prof = sh.get()
+    rec.update({"steady_steps": done, "steady_metric": float(d), "steady_wall_s": time.perf_counter() - t1 + dt,
+                "sim_time": prof["t"], "T_max_over_T_down": float(np.max(prof["T"]) / 32.1233),
+                "rho_max_over_rho_down": float(np.max(prof["rho"]) / 3.88386),
+                "finite": bool(np.isfinite(prof["M"]).all())})
+    sh.close()
+    return rec
+
+
 def run_mach10(mem, torch, np, nsteps=400):
     """Mach-10 shocks on the velocity-space rule (6 x 4 blocks of 8-point
     Gauss-Legendre in (u_x, u_r), 12 azimuths; domain from the
@@ -166,45 +196,27 @@ def run_mach10(mem, torch, np, nsteps=400):
     from paper_2303_02898_gb300 import workloads
     out = {}
     vctx = mem.Context.velocity(mem.shock_domain(mach=10.0))
-    sh = mem.Shock(vctx, mach=10.0, ncells=150, xl=-47.1, xr=47.1, ic=1, graph=1)
-    sh.step(3)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sh.step(nsteps)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    rec = {"value": 150 * nsteps / dt, "unit": "cell-updates/s", "cells": 150, "domain": [-47.1, 47.1],
-           "steps": nsteps, "ms_per_step": 1e3 * dt / nsteps, "rule": "velocity-space 6x4 blocks x 8 GL, K=12"}
-    done, d = 3 + nsteps, None
-    t1 = time.perf_counter()
-    while done < 20000:
-        d = sh.step(500, steady=True)
-        done += 500
-        if not np.isfinite(d) or d < 1e-6:
-            break
-    torch.cuda.synchronize()
-    prof = sh.get()
-    rec.update({"steady_steps": done, "steady_metric": float(d), "steady_wall_s": time.perf_counter() - t1 + dt,
-                "sim_time": prof["t"], "T_max_over_T_down": float(np.max(prof["T"]) / 32.1233),
-                "finite": bool(np.isfinite(prof["M"]).all())})
-    sh.close()
-    out["shock_mach10_paper_mesh"] = rec
+    out["shock_mach10_paper_mesh"] = _mach10_paper_mesh(mem, torch, np, vctx, mem.SCHEME_LF, nsteps)
+    # the paper's own Mach-10 scheme (Section 4): FLIC, one more Newton solve per interface
+    out["shock_mach10_paper_mesh_flic"] = _mach10_paper_mesh(mem, torch, np, vctx, mem.SCHEME_FLIC, nsteps)
     rng = np.random.default_rng(7)
     machs = rng.uniform(1.2, 10.0, 256)
     probs = [dict(mach=float(m), ncells=150, xl=-47.1, xr=47.1) for m in machs]
-    sh = mem.Shock(vctx, problems=probs, ic=1, graph=1)
-    sh.step(3)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sh.step(50)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
-    fin = all(np.isfinite(sh.problem(i)["rho"]).all() for i in range(0, 256, 15))
-    sh.close()
-    cells = 256 * 150
-    out["ensemble_mach10_paper_mesh"] = {"value": cells * 50 / dt, "unit": "cell-updates/s", "problems": 256,
-                                         "cells": cells, "mach": [1.2, 10.0], "steps": 50,
-                                         "ms_per_step": 1e3 * dt / 50, "finite": fin}
+    for key, scheme in (("ensemble_mach10_paper_mesh", mem.SCHEME_LF),
+                        ("ensemble_mach10_paper_mesh_flic", mem.SCHEME_FLIC)):
+        sh = mem.Shock(vctx, problems=probs, ic=1, graph=1, scheme=scheme)
+        sh.step(3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sh.step(50)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        fin = all(np.isfinite(sh.problem(i)["rho"]).all() for i in range(0, 256, 15))
+        sh.close()
+        cells = 256 * 150
+        out[key] = {"value": cells * 50 / dt, "unit": "cell-updates/s", "problems": 256, "cells": cells,
+                    "mach": [1.2, 10.0], "steps": 50, "ms_per_step": 1e3 * dt / 50, "finite": fin,
+                    "scheme": "FLIC" if scheme == mem.SCHEME_FLIC else "local Lax-Friedrichs"}
     sh = mem.Shock(vctx, mach=10.0, ncells=4096, xl=-50.0, xr=50.0, ic=1, graph=0)
     bad_at = None
     t0 = time.perf_counter()
@@ -430,6 +442,47 @@ def run_newton_study(mem, torch, np, n=26):
     out["trivial_gauge_tol_1e-9"] = row
     vctx.close()
     return {"newton_study": out}
+
+
+def run_convergence_study(mem, torch, np, t_end=4.0, Ns=(32, 64, 128, 256, 512, 1024, 2048)):
+    """Section 4, Fig. 6 analogue: the Mach-4 shock on x in [-16.3, 16.3]
+    (tanh start, thickness 5.44; velocity-space rule of 6 x 4 blocks of
+    8-point Gauss-Legendre on the Rankine-Hugoniot box with (n_a, n_b, n_r)
+    = (10, 6, 6), the paper's [-22.7, 16.1] x [0, 14.5]; tol 1e-9), solved
+    with FLIC and with local Lax-Friedrichs on N cells, all N in one packed
+    batch, each stopped at simulated time t_end.  L1 distance of sigma_xx
+    from the finest mesh that stayed finite, averaged onto N cells."""
+    kw = dict(mach=4.0, xl=-16.3, xr=16.3, ic=1, thickness=5.44, tol=1e-9, na=10.0, nb=6.0, nr=6.0, t_end=t_end)
+    vctx = mem.Context.velocity(mem.shock_domain(**kw), nbx=6, nbr=4, ng=8, K=12)
+    L = kw["xr"] - kw["xl"]
+    out = {"t_end": t_end}
+    for name, scheme in (("flic", mem.SCHEME_FLIC), ("lf", mem.SCHEME_LF)):
+        sh = mem.Shock(vctx, problems=[dict(ncells=N) for N in Ns], graph=1, scheme=scheme, **kw)
+        t0 = time.time()
+        # the finest mesh needs about t_end / (cfl dx / 10) steps
+        max_steps = int(3 * t_end * 10.0 * Ns[-1] / (0.5 * L)) + 1000
+        steps = 0
+        while steps < max_steps:
+            sh.step(200)
+            steps += 200
+            P = [sh.problem(i) for i in range(len(Ns))]
+            if all(p["t"] >= t_end or not np.isfinite(p["rho"]).all() for p in P):
+                break
+        sh.close()
+        fin = [bool(np.isfinite(p["sxx"]).all()) for p in P]
+        r = max(i for i in range(len(Ns)) if fin[i]) if any(fin) else None
+        row = {"cells": list(Ns), "finite": fin, "steps": steps, "wall_s": round(time.time() - t0, 1)}
+        if r is not None and r > 0:
+            ref = P[r]["sxx"].astype(np.float64)
+            err = []
+            for i in range(r):
+                proj = ref.reshape(Ns[i], len(ref) // Ns[i]).mean(1)
+                err.append(float(np.abs(P[i]["sxx"].astype(np.float64) - proj).sum() * L / Ns[i]))
+            row.update({"reference_cells": Ns[r], "l1_sxx": err,
+                        "order": [round(float(np.log2(err[k] / err[k + 1])), 2) for k in range(len(err) - 1)]})
+        out[name] = row
+    vctx.close()
+    return {"convergence_mach4": out}
 
 
 def run_serving(mem, ctx, torch, np, nreq=32, max_steps=100, chunk=10):
@@ -707,6 +760,7 @@ def main():
         extras.update(run_condition_study(mem, torch, np))
         extras.update(run_gauge_study(mem, torch, np))
         extras.update(run_newton_study(mem, torch, np))
+        extras.update(run_convergence_study(mem, torch, np))
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

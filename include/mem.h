@@ -257,15 +257,23 @@ typedef struct {
                           the Lax-Wendroff interface moments, moved to their
                           own Hermite gauge, cold start (beta = 0 there);
                           the flux is moved to each neighbour's gauge.
-                          FLIC's van Leer limiter works per component in
-                          the updated cell's gauge (as every quantity of
-                          cell n in the paper), which conserves mass exactly
-                          but momentum and energy only to the limiter's
-                          gauge dependence; r = 0 where its denominator is
-                          0, and the ghost cell stands in for the cell
-                          before the first one.                           */
+                          FLIC's van Leer limiter works per statistic of
+                          the paper's nine 1D statistics (orthonormal
+                          combinations of the 35 products; the other
+                          directions, zero for an axisymmetric flow, keep
+                          the LF flux) in the updated cell's gauge (as every
+                          quantity of cell n in the paper), which conserves
+                          mass exactly but momentum and energy only to the
+                          limiter's gauge dependence; r = 0 where its
+                          denominator is 0, and the ghost cell stands in
+                          for the cell before the first one.  An interface whose solve
+                          fails (non-finite, lambda cap, bad input, maxI
+                          passes) takes the LF flux.                      */
     double thickness;  /* ic = 1: thickness parameter T of Eq. "Mx ini"
                           (15.7, the paper's Mach-10 start)               */
+    double t_end;      /* > 0: the step that would pass simulated time t_end
+                          is cut to end there, and later steps leave the
+                          problem as it is (dt = 0); 0: no limit          */
 } mem_shock_params;
 
 void mem_shock_params_default(mem_shock_params *p);

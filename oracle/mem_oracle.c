@@ -850,15 +850,51 @@ static void collide(double *M, const double *g, double dt, double Pr, double rel
  *     Hermite gauge of the interface moments (cold start, beta = 0 there)
  *     and the flux is moved back to g(c): the maximum-entropy density of a
  *     moment vector does not depend on the gauge it is written in;
- *   scheme 2: FLIC, Eq. "The FLIC": F^LF + phi(r) (F^LW - F^LF) component by
- *     component with the van Leer limiter phi(r) = (r + |r|)/(1 + r) and
- *     r = (M_a - M_{a-1}) / (M_b - M_a) in g(c); a zero denominator is read
- *     as r = 0 (first order there), phi = 0 at r = -1 (the printed form is
- *     0/0 there), the Lax-Wendroff term is left out where phi = 0, and cell
- *     a - 1 before the first cell is the ghost cell itself (r = 0).
- * An interface whose solve fails (non-finite, lambda cap, bad input) or whose
- * flux is not finite takes F^LF.  Interface solves add their status bits to
+ *   scheme 2: FLIC, Eq. "The FLIC": F^LF + phi(r) (F^LW - F^LF) statistic by
+ *     statistic with the van Leer limiter phi(r) = (r + |r|)/(1 + r) and
+ *     r = (M_a - M_{a-1}) / (M_b - M_a) in g(c).  The statistics are the nine
+ *     of the paper's 1D system (Eq. "Sufficient 35"), written as orthonormal
+ *     combinations psi_j = v_j . phi of the 3D Hermite products (see
+ *     flic_basis); each moment or flux vector x enters through v_j . x, and
+ *     the blended part is sum_j phi_j (v_j . (F^LW - F^LF)) v_j.  Directions
+ *     outside their span vanish for an axisymmetric flow and keep F^LF.  A
+ *     zero denominator is read as r = 0 (first order there), phi = 0 at
+ *     r = -1 (the printed form is 0/0 there), and cell a - 1 before the
+ *     first cell is the ghost cell itself (r = 0).
+ * An interface whose solve fails (non-finite, lambda cap, bad input, maxI
+ * passes without meeting tol) or whose flux is not finite takes F^LF.  Interface solves add their status bits to
  * *ist. */
+/* The nine statistics of the 1D system (Eq. "Sufficient 35": 1, u_x,
+ * (u_x^2 - 1)/sqrt2, u_r^2/2 - 1, He_3(u_x)/sqrt6, He_4(u_x)/sqrt24,
+ * u_r^4/8 - u_r^2 + 1, u_x (u_r^2 - 2)/2, (u_x^2 - 1)(u_r^2 - 2)/(2 sqrt2);
+ * the eighth is printed with u_r^2 - 1, which is neither orthogonal to u_x
+ * nor of unit norm under the Gaussian: read as u_r^2 - 2)
+ * as unit vectors over the 3D orthonormal Hermite products, from
+ * y^2 + z^2 = He_2(y) + He_2(z) + 2 and
+ * (y^2 + z^2)^2 = He_4(y) + He_4(z) + 2 He_2(y) He_2(z) + 8 (He_2(y) + He_2(z)) + 8. */
+static void flic_basis(double v[9][NP]) {
+    memset(v, 0, sizeof(double) * 9 * NP);
+    const double r2 = sqrt(0.5), q = sqrt(24.0) / 8.0;
+    v[0][or_index_of(0, 0, 0)] = 1.0;
+    v[1][or_index_of(1, 0, 0)] = 1.0;
+    v[2][or_index_of(2, 0, 0)] = 1.0;
+    v[3][or_index_of(0, 2, 0)] = v[3][or_index_of(0, 0, 2)] = r2;
+    v[4][or_index_of(3, 0, 0)] = 1.0;
+    v[5][or_index_of(4, 0, 0)] = 1.0;
+    v[6][or_index_of(0, 4, 0)] = v[6][or_index_of(0, 0, 4)] = q;
+    v[6][or_index_of(0, 2, 2)] = 0.5;
+    v[7][or_index_of(1, 2, 0)] = v[7][or_index_of(1, 0, 2)] = r2;
+    v[8][or_index_of(2, 2, 0)] = v[8][or_index_of(2, 0, 2)] = r2;
+}
+
+void or_flic_basis(double *v) { flic_basis((double (*)[NP])v); }
+
+static double dot35(const double *a, const double *b) {
+    double s = 0.0;
+    for (int i = 0; i < NP; ++i) s += a[i] * b[i];
+    return s;
+}
+
 static void interface_flux(int order, int scheme, int c, int side, const double *M, const double *F, const double *g,
                            const double *speed, double dtdx, const double *optv, double *flux, int *ist) {
     const int a = c - 1 + side, b = c + side;
@@ -883,7 +919,7 @@ static void interface_flux(int order, int scheme, int c, int side, const double 
     const int sI = or_solve(order, gI, MH, bI, optv, &it, NULL, NULL);
     *ist |= sI;
     or_flux(order, bI, gI, MH[0], FI, NULL, NULL, NULL);
-    int ok = (sI & (ST_NONFINITE | ST_LAMBDA_CAP | ST_BADINPUT)) == 0;
+    int ok = (sI & (ST_NONFINITE | ST_LAMBDA_CAP | ST_BADINPUT | ST_MAXITER)) == 0;
     for (int i = 0; i < NP; ++i) ok = ok && isfinite(FI[i]);
     if (!ok) {
         memcpy(flux, flf, sizeof(flf));
@@ -899,13 +935,21 @@ static void interface_flux(int order, int scheme, int c, int side, const double 
     double Maa[NP];
     or_gauge_T(&g[6 * c], &g[6 * aa], T);
     matvec35(T, &M[NP * aa], Maa);
+    double v[9][NP], D[NP];
+    flic_basis(v);
     for (int i = 0; i < NP; ++i) {
-        const double num = Ma[i] - Maa[i], den = Mb[i] - Ma[i];
+        D[i] = flw[i] - flf[i];
+        flux[i] = flf[i];
+    }
+    for (int j = 0; j < 9; ++j) {
+        const double num = dot35(v[j], Ma) - dot35(v[j], Maa), den = dot35(v[j], Mb) - dot35(v[j], Ma);
         const double r = den != 0.0 ? num / den : 0.0;
         /* (r + |r|)/(1 + r): 0 for r <= 0 (also at r = -1, where the printed
          * form is 0/0), 2r/(1 + r) = 2/(1 + 1/r) for r > 0 (2 as r -> inf) */
         const double phi = r > 0.0 ? 2.0 / (1.0 + 1.0 / r) : 0.0;
-        flux[i] = phi != 0.0 ? flf[i] + phi * (flw[i] - flf[i]) : flf[i];
+        if (phi == 0.0) continue;
+        const double d = phi * dot35(v[j], D);
+        for (int i = 0; i < NP; ++i) flux[i] += d * v[j][i];
     }
 }
 

@@ -197,6 +197,15 @@ def cond_estimate(order, beta, g=None):
     return lib().or_cond_estimate(order, _g(g), _d(_f64(beta, (NP,))))
 
 
+def flic_basis():
+    """The nine statistics of the paper's 1D system (Eq. "Sufficient 35") as
+    unit vectors over the 3D Hermite products [9, 35] (the FLIC limiter's
+    statistics)."""
+    v = np.zeros((9, NP))
+    lib().or_flic_basis(_d(v))
+    return v
+
+
 def gauge_T(g_to, g_from):
     """T(g', g) of Eq. "Change gauge M F": M(g') = T M(g)."""
     T = np.zeros((NP, NP))

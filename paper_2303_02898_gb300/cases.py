@@ -3,6 +3,7 @@
     python -m paper_2303_02898_gb300.cases solve [cells]       # mem_solve, fused back-end, 8^3 rule
     python -m paper_2303_02898_gb300.cases ensemble [steps]    # 256-problem shock batch, 8^3 rule (Mach <= 3)
     python -m paper_2303_02898_gb300.cases mach10 [steps]      # 256-problem Mach 1.2-10 batch, velocity-space rule
+    python -m paper_2303_02898_gb300.cases mach10flic [steps]  # the same batch with FLIC interface fluxes
 
 Each case builds its inputs on the device (seeded, synthetic), runs a few
 warm-up iterations and then the timed ones, and prints one line with the
@@ -59,15 +60,15 @@ def ensemble(steps=3):
     ctx.close()
 
 
-def mach10(steps=3):
+def mach10(steps=3, scheme=mem.SCHEME_LF):
     vctx = mem.Context.velocity(mem.shock_domain(mach=10.0))
     rng = np.random.default_rng(7)
     probs = [dict(mach=float(m), ncells=150, xl=-47.1, xr=47.1) for m in rng.uniform(1.2, 10.0, 256)]
-    sh = mem.Shock(vctx, problems=probs, ic=1, graph=1)
+    sh = mem.Shock(vctx, problems=probs, ic=1, graph=1, scheme=scheme)
     sh.step(2)
     cells = 150 * len(probs)
     ms = _timed(lambda: sh.step(1), steps)
-    print("mach10 cells=%d ms/step=%.3f cell-updates/s=%.4g" % (cells, ms, cells / ms * 1e3))
+    print("mach10 scheme=%d cells=%d ms/step=%.3f cell-updates/s=%.4g" % (scheme, cells, ms, cells / ms * 1e3))
     sh.close()
     vctx.close()
 
@@ -75,4 +76,5 @@ def mach10(steps=3):
 if __name__ == "__main__":
     case = sys.argv[1] if len(sys.argv) > 1 else "solve"
     arg = [int(a) for a in sys.argv[2:3]]
-    {"solve": solve, "ensemble": ensemble, "mach10": mach10}[case](*arg)
+    {"solve": solve, "ensemble": ensemble, "mach10": mach10,
+     "mach10flic": lambda *a: mach10(*a, scheme=mem.SCHEME_FLIC)}[case](*arg)

@@ -171,6 +171,11 @@ __global__ void __launch_bounds__(128) k_stencil(const float *__restrict__ M, co
     lf_update(M, F, g, speed, Mn, c, sc[p].dt / prm[p].dx);
 }
 
+// Status bits of an interface solve whose parameters are not used: the
+// solve stopped (non-finite values, lambda cap), its input was bad, or it
+// ran out of passes without meeting tol.
+constexpr int IFACE_FAILED = MEM_ST_NONFINITE | MEM_ST_LAMBDA_CAP | MEM_ST_BADINPUT | MEM_ST_MAXITER;
+
 // Interface moments of Eq. "The lax W" between cells c - 1 and c (iface[c]
 // set), formed in the gauge of cell c and moved to their own Hermite gauge
 // (axisymmetric form).  The Newton start is the interface's parameters of
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(128) k_iface_state(const float *__restrict__ M
     apply_T(T, m, y);
     // warm start: previous parameters (gauge gI[c]) carried to gh
     float gp[6], bp[NP];
-    bool ok = (statusI[c] & (MEM_ST_NONFINITE | MEM_ST_LAMBDA_CAP | MEM_ST_BADINPUT)) == 0;
+    bool ok = (statusI[c] & IFACE_FAILED) == 0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) gp[k] = gI[(size_t)c * 6 + k];
 #pragma unroll
@@ -240,18 +245,57 @@ __global__ void __launch_bounds__(128) k_iface_state(const float *__restrict__ M
     for (int k = 0; k < 6; ++k) gI[(size_t)c * 6 + k] = gh[k];
 }
 
+// The nine statistics of the paper's 1D system (Eq. "Sufficient 35": 1, u_x,
+// (u_x^2-1)/sqrt2, u_r^2/2-1, He_3(u_x)/sqrt6, He_4(u_x)/sqrt24,
+// u_r^4/8-u_r^2+1, u_x(u_r^2-2)/2, (u_x^2-1)(u_r^2-2)/(2 sqrt2)) are unit
+// vectors v_j over the 3D Hermite products; project9 gives v_j . x and
+// add9 adds sum_j c_j v_j.  FLIC limits these nine; the other directions
+// vanish for an axisymmetric flow, and a per-product limiter there only
+// amplifies FP32 noise in y <-> z symmetric pairs.
+constexpr float FL_R2 = 0.70710678118654752f;  // 1/sqrt2
+constexpr float FL_Q = 0.61237243569579452f;   // sqrt(24)/8
+
+__device__ __forceinline__ void project9(const float *x, float *q) {
+    q[0] = x[idx3(0, 0, 0)];
+    q[1] = x[idx3(1, 0, 0)];
+    q[2] = x[idx3(2, 0, 0)];
+    q[3] = FL_R2 * (x[idx3(0, 2, 0)] + x[idx3(0, 0, 2)]);
+    q[4] = x[idx3(3, 0, 0)];
+    q[5] = x[idx3(4, 0, 0)];
+    q[6] = FL_Q * (x[idx3(0, 4, 0)] + x[idx3(0, 0, 4)]) + 0.5f * x[idx3(0, 2, 2)];
+    q[7] = FL_R2 * (x[idx3(1, 2, 0)] + x[idx3(1, 0, 2)]);
+    q[8] = FL_R2 * (x[idx3(2, 2, 0)] + x[idx3(2, 0, 2)]);
+}
+
+__device__ __forceinline__ void add9(float *f, const float *c) {
+    f[idx3(0, 0, 0)] += c[0];
+    f[idx3(1, 0, 0)] += c[1];
+    f[idx3(2, 0, 0)] += c[2];
+    f[idx3(0, 2, 0)] += FL_R2 * c[3];
+    f[idx3(0, 0, 2)] += FL_R2 * c[3];
+    f[idx3(3, 0, 0)] += c[4];
+    f[idx3(4, 0, 0)] += c[5];
+    f[idx3(0, 4, 0)] += FL_Q * c[6];
+    f[idx3(0, 0, 4)] += FL_Q * c[6];
+    f[idx3(0, 2, 2)] += 0.5f * c[6];
+    f[idx3(1, 2, 0)] += FL_R2 * c[7];
+    f[idx3(1, 0, 2)] += FL_R2 * c[7];
+    f[idx3(2, 2, 0)] += FL_R2 * c[8];
+    f[idx3(2, 0, 2)] += FL_R2 * c[8];
+}
+
 // Finite-volume update of interior cell c with Lax-Wendroff or FLIC fluxes
 // (per problem; LF problems of a mixed batch take the LF flux), everything in
 // the gauge g(c).  At the interface between cells a and b = a + 1:
 //   F^LF = (F_a + F_b)/2 + lambda/2 (M_a - M_b), Eq. "The lax F";
 //   F^LW = T(g(c), g_I) F(beta_I; g_I), the interface solve's flux;
-//   FLIC: F^LF + phi_k (F^LW - F^LF)_k with the van Leer limiter
-//   phi(r) = (r + |r|)/(1 + r), r_k = (M_a - M_{a-1})_k / (M_b - M_a)_k,
-//   r = 0 where the denominator is 0, phi = 0 for r <= 0 (also r = -1, where
-//   the printed form is 0/0), the LW term left out where phi = 0, and the
-//   ghost cell standing in for the cell before the first one.
-// An interface whose Newton solve failed (non-finite, lambda cap, bad input)
-// or whose flux is not finite takes F^LF.
+//   FLIC: F^LF + sum_j phi_j (v_j . (F^LW - F^LF)) v_j over the nine 1D
+//   statistics (project9) with the van Leer limiter phi(r) = (r + |r|)/(1 + r),
+//   r_j = v_j . (M_a - M_{a-1}) / v_j . (M_b - M_a); r = 0 where the
+//   denominator is 0, phi = 0 for r <= 0 (also r = -1, where the printed form
+//   is 0/0), and the ghost cell standing in for the cell before the first one.
+// An interface whose Newton solve failed (IFACE_FAILED) or whose flux is not
+// finite takes F^LF.
 __global__ void __launch_bounds__(128) k_stencil2(const float *__restrict__ M, const float *__restrict__ F,
                                                   const float *__restrict__ g, const float *__restrict__ speed,
                                                   const float *__restrict__ FI, const float *__restrict__ gI,
@@ -298,7 +342,7 @@ __global__ void __launch_bounds__(128) k_stencil2(const float *__restrict__ M, c
         apply_T(T, x, y);
 #pragma unroll
         for (int k = 0; k < NP; ++k) f[k] += 0.5f * y[k];
-        bool lw_ok = (statusI[b] & (MEM_ST_NONFINITE | MEM_ST_LAMBDA_CAP | MEM_ST_BADINPUT)) == 0;
+        bool lw_ok = (statusI[b] & IFACE_FAILED) == 0;
         if (lw_ok) {
             float w[NP];
 #pragma unroll
@@ -321,13 +365,21 @@ __global__ void __launch_bounds__(128) k_stencil2(const float *__restrict__ M, c
 #pragma unroll
                 for (int k = 0; k < NP; ++k) x[k] = M[(size_t)aa * NP + k];
                 apply_T(T, x, y);
+                float qaa[9], qa[9], qb[9], qd[9];
+                project9(y, qaa);
+                project9(ma, qa);
+                project9(mb, qb);
 #pragma unroll
-                for (int k = 0; k < NP; ++k) {
-                    const float num = ma[k] - y[k], den = mb[k] - ma[k];
+                for (int k = 0; k < NP; ++k) w[k] -= f[k];
+                project9(w, qd);
+#pragma unroll
+                for (int j = 0; j < 9; ++j) {
+                    const float num = qa[j] - qaa[j], den = qb[j] - qa[j];
                     const float r = den != 0.f ? num / den : 0.f;
                     const float phi = r > 0.f ? 2.f / (1.f + 1.f / r) : 0.f;
-                    if (phi != 0.f) f[k] += phi * (w[k] - f[k]);
+                    qd[j] *= phi;
                 }
+                add9(f, qd);
             }
         }
 #pragma unroll
@@ -377,8 +429,14 @@ __global__ void k_dt(const float *__restrict__ speed, const ShockProb *__restric
         if (threadIdx.x == 0) {
             ShockScalars &s = sc[blockIdx.x];
             const float dt = pr.cfl_dx / r;
-            s.dt = dt;
-            s.t += (double)dt;
+            if (pr.t_end > 0.0 && s.t + (double)dt >= pr.t_end) {
+                // cut to end at t_end (dt = 0 once there)
+                s.dt = (float)fmax(pr.t_end - s.t, 0.0);
+                s.t = fmax(s.t, pr.t_end);
+            } else {
+                s.dt = dt;
+                s.t += (double)dt;
+            }
             s.steps += 1;
             s.steady_bits = 0u;
         }
@@ -404,7 +462,7 @@ bool shock_params_valid(const mem_shock_params &p) {
     return p.ncells >= 1 && p.xr > p.xl && p.mach >= 1.0 && p.cfl > 0 && p.Pr > 0.5 && p.gamma > 1.0 && p.kn > 0 &&
            (p.ic == 0 || p.ic == 1) && p.maxI >= 0 && (p.impl == MEM_IMPL_PLAIN || p.impl == MEM_IMPL_FUSED) &&
            p.na > 0 && p.nb > 0 && p.nr > 0 && p.scheme >= MEM_SCHEME_LF && p.scheme <= MEM_SCHEME_FLIC &&
-           (p.ic == 0 || p.thickness > 0);
+           (p.ic == 0 || p.thickness > 0) && p.t_end >= 0.0;
 }
 
 // Device bytes per packed cell, the interface arrays of Lax-Wendroff / FLIC
@@ -514,6 +572,8 @@ int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **o
         pr.relax = (float)(ps[i].kn * sqrt(2.0 / 3.14159265358979323846) / ps[i].Pr);
         pr.drho = (float)(n_dn - 1.0);
         pr.scheme = ps[i].scheme;
+        pr.pad = 0;
+        pr.t_end = ps[i].t_end;
         b->second_order |= ps[i].scheme != MEM_SCHEME_LF;
         b->hprm.push_back(pr);
         off += pr.n + 2;
@@ -785,6 +845,7 @@ void mem_shock_params_default(mem_shock_params *p) {
     p->na = p->nb = p->nr = 5.0;
     p->scheme = MEM_SCHEME_LF;
     p->thickness = 15.7;
+    p->t_end = 0.0;
 }
 
 void mem_shock_free(mem_shock *s) {

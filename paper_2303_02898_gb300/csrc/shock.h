@@ -15,6 +15,8 @@ struct ShockProb {
     float relax;   // tau = relax / n
     float drho;    // rho_+ - rho_- (normalises the steady-state metric)
     int scheme;    // interface flux, MEM_SCHEME_*
+    int pad;
+    double t_end;  // > 0: simulated time at which the problem stops
 };
 
 // Per-problem step scalars (device).

@@ -36,7 +36,8 @@ class ShockParams(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("kn", ctypes.c_double), ("ic", ctypes.c_int32),
                 ("impl", ctypes.c_int32), ("graph", ctypes.c_int32), ("tol", ctypes.c_float),
                 ("maxI", ctypes.c_int32), ("na", ctypes.c_double), ("nb", ctypes.c_double),
-                ("nr", ctypes.c_double), ("scheme", ctypes.c_int32), ("thickness", ctypes.c_double)]
+                ("nr", ctypes.c_double), ("scheme", ctypes.c_int32), ("thickness", ctypes.c_double),
+                ("t_end", ctypes.c_double)]
 
 
 SCHEME_LF, SCHEME_LW, SCHEME_FLIC = 0, 1, 2

@@ -103,6 +103,23 @@ def test_basis_matches_paper_statistics(O):
         assert math.isclose(rec, r4, abs_tol=1e-10)
 
 
+def test_flic_basis_is_the_papers_1d_statistics(O):
+    """The FLIC limiter's nine statistics: v_j . phi(u) equals the paper's
+    orthonormal 1D statistics (Eq. "Sufficient 35", the eighth read as
+    u_x (u_r^2 - 2)/2, see the oracle), written out here by hand; the rows
+    are orthonormal."""
+    v = O.flic_basis()
+    assert np.abs(v @ v.T - np.eye(9)).max() < 1e-14
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        u = rng.normal(0, 1.5, 3)
+        ux, ur2 = u[0], u[1] ** 2 + u[2] ** 2
+        paper = [1.0, ux, (ux ** 2 - 1) / SQ2, ur2 / 2 - 1, (ux ** 3 - 3 * ux) / math.sqrt(6),
+                 (ux ** 4 - 6 * ux ** 2 + 3) / (2 * math.sqrt(6)), ur2 ** 2 / 8 - ur2 + 1, ux * (ur2 - 2) / 2,
+                 (ux ** 2 - 1) * (ur2 - 2) / (2 * SQ2)]
+        assert np.abs(v @ O.phi(u) - np.array(paper)).max() < 1e-10
+
+
 def test_basis_orthonormal_under_gh8(O):
     u, lw = O.rule_nodes(8)
     w = np.exp(lw)

@@ -144,3 +144,35 @@ def test_interface_state_converges_and_is_readable(mem):
     assert np.all(I["g"][sl, 3:] > 0)
     assert np.isfinite(I["F"][sl]).all()
     assert I["iters"][sl].mean() < 4.0
+
+
+def test_t_end_cuts_the_last_step(mem, ctx8):
+    """mem_shock_params.t_end: the step that would pass t_end ends there and
+    later steps leave the problem as it is (dt = 0)."""
+    sh = mem.Shock(ctx8, mach=1.5, ncells=32, xl=-10.0, xr=10.0, t_end=0.5, graph=0)
+    sh.step(200)
+    a = sh.problem(0)
+    sh.step(5)
+    b = sh.problem(0)
+    sh.close()
+    assert a["t"] == 0.5 and b["t"] == 0.5
+    for k in ("rho", "ux", "T"):
+        assert np.allclose(a[k], b[k], rtol=1e-6, atol=0), k
+
+
+def test_second_order_convergence_on_gpu(mem, ctx8):
+    """The oracle's convergence pin on the library: smooth Mach-1.5 tanh
+    profile (thickness 12 on [-20, 20], Kn = 100), N = 32, 64, 128 in one
+    batch stopped at t = 2 by t_end; e(N) = L1 distance of the density from
+    the 2N mesh averaged onto N cells.  LF first order, LW and FLIC second."""
+    Ns = (32, 64, 128)
+    for scheme, lo, hi in ((mem.SCHEME_LF, 1.5, 2.3), (mem.SCHEME_LW, 3.0, 4.6), (mem.SCHEME_FLIC, 3.0, 4.6)):
+        sh = mem.Shock(ctx8, problems=[dict(ncells=N) for N in Ns], mach=1.5, xl=-20.0, xr=20.0, ic=1,
+                       thickness=12.0, kn=100.0, t_end=2.0, scheme=scheme, graph=1)
+        sh.step(400)
+        P = [sh.problem(i) for i in range(len(Ns))]
+        sh.close()
+        assert all(p["t"] == 2.0 for p in P)
+        r = {N: p["rho"].astype(np.float64) for N, p in zip(Ns, P)}
+        e = [np.abs(r[N] - r[2 * N].reshape(-1, 2).mean(1)).mean() for N in (32, 64)]
+        assert lo < e[0] / e[1] < hi, (scheme, e)

@@ -96,6 +96,13 @@ int rebuild(mem_server *sv, const std::vector<Req> &old_list, cudaStream_t st) {
             MEM_CUDA_TRY(cudaMemcpyAsync(nb->status + dst.off, old->status + src.off, sizeof(int32_t) * nc, cudaMemcpyDeviceToDevice, st));
             MEM_CUDA_TRY(cudaMemcpyAsync(nb->iters + dst.off, old->iters + src.off, sizeof(int32_t) * nc, cudaMemcpyDeviceToDevice, st));
             MEM_CUDA_TRY(cudaMemcpyAsync(nb->sc + i, old->sc + it->second, sizeof(ShockScalars), cudaMemcpyDeviceToDevice, st));
+            if (src.scheme != MEM_SCHEME_LF) {
+                // the interface solves' warm starts (Lax-Wendroff / FLIC)
+                MEM_CUDA_TRY(cudaMemcpyAsync(nb->betaI + (size_t)dst.off * NP, old->betaI + (size_t)src.off * NP, sizeof(float) * nc * NP, cudaMemcpyDeviceToDevice, st));
+                MEM_CUDA_TRY(cudaMemcpyAsync(nb->gI + (size_t)dst.off * 6, old->gI + (size_t)src.off * 6, sizeof(float) * nc * 6, cudaMemcpyDeviceToDevice, st));
+                MEM_CUDA_TRY(cudaMemcpyAsync(nb->statusI + dst.off, old->statusI + src.off, sizeof(int32_t) * nc, cudaMemcpyDeviceToDevice, st));
+                MEM_CUDA_TRY(cudaMemcpyAsync(nb->itersI + dst.off, old->itersI + src.off, sizeof(int32_t) * nc, cudaMemcpyDeviceToDevice, st));
+            }
         }
         MEM_CUDA_TRY(cudaStreamSynchronize(st));
         mem_host::batch_free(old);

@@ -119,3 +119,29 @@ def test_server_continuous_batching(env):
     with pytest.raises(KeyError):
         sv.poll(12345)
     sv.close()
+
+
+def test_server_flic_request_equals_alone(env):
+    """A FLIC request keeps its interface solves' warm starts when the server
+    rebuilds its batch to admit another request, so it ends with the profile
+    it has alone (mixed schemes in one batch)."""
+    mem, ctx = env
+    max_steps = 12
+    sv = mem.Server(ctx, hbm_budget_bytes=1 << 30, max_cells=200, steady_tol=1e-12, max_steps=max_steps)
+    p1 = dict(mach=1.5, ncells=48, xl=-15.0, xr=15.0, scheme=mem.SCHEME_FLIC)
+    p2 = dict(mach=2.0, ncells=30, xl=-10.0, xr=10.0, scheme=mem.SCHEME_LF)
+    r1 = sv.submit(**p1)
+    sv.progress(3)
+    r2 = sv.submit(**p2)  # admitted by a rebuild while the FLIC request is resident
+    for _ in range(20):
+        sv.progress(3)
+        if sv.stats()["completed"] == 2:
+            break
+    assert sv.stats()["completed"] == 2
+    for rid, pr in ((r1, p1), (r2, p2)):
+        res = sv.poll(rid, ncells=pr["ncells"])
+        assert res is not None and res["steps"] == max_steps
+        alone = _alone(mem, ctx, pr, max_steps)
+        for k in ("rho", "ux", "T"):
+            assert np.abs(res[k] - alone[k]).max() <= 1e-6 * np.abs(alone[k]).max(), (rid, k)
+    sv.close()

@@ -953,6 +953,17 @@ static void interface_flux(int order, int scheme, int c, int side, const double 
     }
 }
 
+/* The interface flux above for cells c - 1 + side and c + side of the arrays
+ * M, F, g, speed (cell c - 2 + side must exist or be the first cell);
+ * returns the interface solve's status bits (0 for scheme 0). */
+int or_interface_flux(int order, int scheme, int c, int side, const double *M, const double *F, const double *g,
+                      const double *speed, double dtdx, const double *optv, double *flux) {
+    get_rule(order);
+    int ist = 0;
+    interface_flux(order, scheme, c, side, M, F, g, speed, dtdx, optv, flux, &ist);
+    return ist;
+}
+
 void or_shock_step(int order, int N, double dx, double cfl, double Pr, double relax_coef,
                    double *M, double *beta, double *g, double *speed, int *status, int *iters,
                    const double *optv, int nthreads, double *out, double *cond, int scheme, int *iface_status) {

@@ -206,6 +206,20 @@ def flic_basis():
     return v
 
 
+def interface_flux(order, scheme, c, side, M, F, g, speed, dtdx, tol=1e-10, maxI=500):
+    """Interface flux between cells c - 1 + side and c + side, in the gauge of
+    cell c (Eqs. "The lax F", "The lax W", "The FLIC"): scheme lf, lw, flic."""
+    M = _f64(M).reshape(-1, NP)
+    F = _f64(F).reshape(-1, NP)
+    g = _f64(g).reshape(-1, 6)
+    speed = _f64(speed).reshape(-1)
+    out = np.zeros(NP)
+    opts = np.array([tol, float(maxI), 1.0])
+    st = lib().or_interface_flux(order, {"lf": 0, "lw": 1, "flic": 2}[scheme], c, side, _d(M), _d(F), _d(g),
+                                 _d(speed), ctypes.c_double(dtdx), _d(opts), _d(out))
+    return out, st
+
+
 def gauge_T(g_to, g_from):
     """T(g', g) of Eq. "Change gauge M F": M(g') = T M(g)."""
     T = np.zeros((NP, NP))

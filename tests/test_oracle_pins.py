@@ -454,6 +454,49 @@ def test_shock_step_dt_from_cfl(O):
     assert smax == pytest.approx(max(sh.v_up + r, sh.v_dn + r * math.sqrt(sh.T_dn)))
 
 
+def _flic_cells(O, steps):
+    """Four cells in one gauge (the change of gauge is the identity), moments
+    e_0 + s_k d along a fixed axisymmetric direction d, fluxes of the
+    Maxwellian of that gauge (beta = 0): cell 2's left interface sees
+    M_1 - M_0 = (s_1 - s_0) d and M_2 - M_1 = (s_2 - s_1) d, so every one of
+    the nine statistics has r = (s_1 - s_0)/(s_2 - s_1)."""
+    v = O.flic_basis()
+    d = np.array([0.02, 0.02, 0.03, -0.02, 0.01, 0.008, 0.006, 0.015, -0.01]) @ v  # every statistic moves
+    g = np.tile([0.3, 0.0, 0.0, 1.1, 1.0, 1.0], (4, 1))
+    M = np.array([np.eye(35)[0] + s * d for s in steps])
+    F = np.zeros((4, 35))
+    speed = np.zeros(4)
+    for c in range(4):
+        F[c], speed[c], _, _ = O.flux(8, np.zeros(35), g[c], M[c, 0])
+    return M, F, g, speed, v
+
+
+def test_flic_blend_identities(O):
+    """Eq. "The FLIC" with the van Leer limiter, checked by its own algebra on
+    the nine statistics (projector P): a linear profile (r = 1, phi(1) = 1)
+    gives the Lax-Wendroff flux; a flat upwind pair (r = 0) gives the
+    Lax-Friedrichs flux; r = 3 gives phi = 2 * 3 / (1 + 3) = 1.5, i.e.
+    F^LF + 1.5 (F^LW - F^LF).  Off the nine (a 5e-8 component: the tensor
+    Gauss-Hermite grid is not rotation-invariant in (y, z)) FLIC keeps F^LF."""
+    args = dict(c=2, side=0, dtdx=0.05)
+
+    def fluxes(steps):
+        M, F, g, sp, v = _flic_cells(O, steps)
+        out = [O.interface_flux(8, s, M=M, F=F, g=g, speed=sp, **args) for s in ("lf", "lw", "flic")]
+        assert out[1][1] & 1
+        return [o[0] for o in out], v.T @ v
+
+    (lf, lw, fl), P = fluxes([0.0, 1.0, 2.0, 3.0])
+    scale = np.abs(lw).max()
+    assert np.abs(P @ (fl - lw)).max() < 1e-12 * scale
+    assert np.abs(fl - P @ fl - (lf - P @ lf)).max() < 1e-14 * scale
+    (lf, lw, fl), P = fluxes([1.0, 1.0, 2.0, 3.0])
+    assert np.array_equal(fl, lf)
+    (lf, lw, fl), P = fluxes([-2.0, 1.0, 2.0, 3.0])
+    assert np.abs(P @ (fl - (lf + 1.5 * (lw - lf)))).max() < 1e-12 * scale
+    assert np.abs(fl - P @ fl - (lf - P @ lf)).max() < 1e-14 * scale
+
+
 def _shock_density_at(O, N, scheme, t_end=2.0):
     """Smooth Mach-1.5 tanh profile (thickness 12 on [-20, 20]), collisions
     made negligible (Kn = 100: the explicit source update of Eq. "source

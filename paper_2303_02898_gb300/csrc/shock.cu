@@ -237,9 +237,12 @@ __global__ void __launch_bounds__(128) k_iface_state(const float *__restrict__ M
     }
     transform_beta(gh, gp, bp, m);
 #pragma unroll
+    for (int k = 1; k < NP; ++k) ok = ok && isfinite(m[k]);
+    // carried parameters, or beta = 0 (the gauge's Maxwellian) as a whole
+#pragma unroll
     for (int k = 0; k < NP; ++k) {
         MI[(size_t)c * NP + k] = y[k];
-        betaI[(size_t)c * NP + k] = k == 0 ? y[0] : (ok && isfinite(m[k]) ? m[k] : 0.f);
+        betaI[(size_t)c * NP + k] = k == 0 ? y[0] : (ok ? m[k] : 0.f);
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) gI[(size_t)c * 6 + k] = gh[k];

@@ -497,6 +497,21 @@ def test_flic_blend_identities(O):
     assert np.abs(fl - P @ fl - (lf - P @ lf)).max() < 1e-14 * scale
 
 
+def test_failed_interface_solve_takes_lax_friedrichs(O):
+    """Reading of the interface fallback: an interface whose Lax-Wendroff
+    moments are not admissible (here a negative density, from a large
+    dt/dx times a density-flux jump) makes the solve report bad input, and
+    both LW and FLIC then use the Lax-Friedrichs flux there."""
+    M, F, g, sp, v = _flic_cells(O, [0.0, 1.0, 2.0, 3.0])
+    F[1, 0] = -50.0  # density flux of the upwind cell of cell 2's left interface
+    args = dict(c=2, side=0, dtdx=0.5, M=M, F=F, g=g, speed=sp)
+    lf, _ = O.interface_flux(8, "lf", **args)
+    lw, st = O.interface_flux(8, "lw", **args)
+    fl, _ = O.interface_flux(8, "flic", **args)
+    assert st & 64
+    assert np.array_equal(lw, lf) and np.array_equal(fl, lf)
+
+
 def _shock_density_at(O, N, scheme, t_end=2.0):
     """Smooth Mach-1.5 tanh profile (thickness 12 on [-20, 20]), collisions
     made negligible (Kn = 100: the explicit source update of Eq. "source

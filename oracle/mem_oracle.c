@@ -24,8 +24,11 @@
  *   - the translation/dilation gauge and its change-of-gauge matrix
  *     (Eqs. "Sufficient 35 ortho", "Change gauge M F", "Hermite parameters");
  *   - characteristic speed = spectral radius of dF/dM (Eq. "The lax F");
- *   - ES-BGK source (Appendix A), local Lax-Friedrichs finite-volume update
- *     with neighbour gauge transforms and Strang-split collision (Algorithm 2);
+ *   - ES-BGK source (Appendix A), local Lax-Friedrichs, Lax-Wendroff and FLIC
+ *     finite-volume updates with neighbour gauge transforms and Strang-split
+ *     collision (Algorithm 2);
+ *   - the paper's nine-statistic system for axisymmetric flow (Eq. "Sufficient
+ *     35"): Algorithm 1, flux and characteristic speed on its statistics;
  *   - Rankine-Hugoniot states (Appendix D).
  *
  * Parity status: every function below has a pin in tests/test_oracle_pins.py
@@ -888,6 +891,160 @@ static void flic_basis(double v[9][NP]) {
 }
 
 void or_flic_basis(double *v) { flic_basis((double (*)[NP])v); }
+
+/* ------------------------------------------------------------------------ */
+/* The paper's own system for axisymmetric 1D flow: the nine statistics
+ * psi_j = v_j . phi of Eq. "Sufficient 35" with natural parameters alpha_j,
+ * f ~ n exp(-|ubar|^2/2 + sum_{j>=1} alpha_j psi_j(ubar)), i.e. the 35-product
+ * parameters beta = sum_j alpha_j v_j (alpha_0 = beta_0 = n).  Every integrand
+ * here depends on (u_x, u_r) only, so a velocity-space rule with one azimuth
+ * (K = 1) integrates it exactly in the angle. */
+static void axi_beta(const double v[9][NP], const double *a, double *beta) {
+    for (int i = 0; i < NP; ++i) beta[i] = 0.0;
+    for (int j = 0; j < 9; ++j)
+        for (int i = 0; i < NP; ++i) beta[i] += a[j] * v[j][i];
+}
+
+/* Algorithm 1 on the nine statistics: M9 = (n, psi moments), alpha [9]
+ * in (start) / out (solution, alpha_0 = n).  Same steps and options as
+ * or_solve, over the eight unknowns alpha_1..alpha_8. */
+int or_solve_axi(int order, const double *g, const double *M9, double *alpha, const double *optv, int *iters,
+                 double *res_out) {
+    or_opts o; default_opts(&o);
+    if (optv) { o.tol = optv[0]; o.maxI = (int)optv[1]; o.final_step = optv[2] != 0.0; }
+    const int D = 8;
+    double v[9][NP];
+    flic_basis(v);
+    const double n = M9[0];
+    int st = 0;
+    if (!(n > 0.0) || !isfinite(n)) { if (iters) *iters = 0; return ST_BADINPUT; }
+    for (int j = 0; j < 9; ++j) if (!isfinite(M9[j]) || !isfinite(alpha[j])) { if (iters) *iters = 0; return ST_BADINPUT; }
+    /* v_j . Ms = M9_j, so or_objective(beta(alpha), Ms) = log Z - sum_j alpha_j M9_j / n */
+    double Ms[NP];
+    axi_beta(v, M9, Ms);
+    double a[9], da[9] = {0}, G[9] = {0}, b[NP], tr[9], m[NP], S[NP * NP], H[64], Lh[64], wv[8], rhs[8], dx[8];
+    memcpy(a, alpha, sizeof(a));
+    a[0] = n;
+    axi_beta(v, a, b);
+    double Lcur = or_objective(order, g, b, Ms);
+    int it = 0, conv = 0;
+    double res = INFINITY, step = 1.0;
+    while (!conv && it <= o.maxI) {
+        step = 2.0;
+        int s = 0, sat = 0;
+        while (!sat && s <= o.maxT) {
+            step *= 0.5;
+            for (int j = 0; j < 9; ++j) tr[j] = a[j] + step * da[j];
+            tr[0] = n;
+            axi_beta(v, tr, b);
+            const double Lt = or_objective(order, g, b, Ms);
+            double gd = 0.0;
+            for (int j = 1; j < 9; ++j) gd += G[j] * step * da[j];
+            const double LD = Lcur - Lt;
+            sat = (LD - (-o.c * gd)) >= -(o.atol + o.rtol * fabs(LD));
+            s += 1;
+        }
+        for (int j = 1; j < 9; ++j) a[j] += step * da[j];
+        axi_beta(v, a, b);
+        Lcur = or_objective(order, g, b, Ms);
+        or_expect(order, g, b, NULL, m, S, NULL, NULL);
+        double mj[9];
+        for (int j = 0; j < 9; ++j) {
+            mj[j] = 0.0;
+            for (int i = 0; i < NP; ++i) mj[j] += v[j][i] * m[i];
+        }
+        for (int j = 1; j < 9; ++j) G[j] = mj[j] - M9[j] / n;
+        for (int p = 0; p < D; ++p)
+            for (int q = 0; q < D; ++q) {
+                double e = 0.0;
+                for (int i = 0; i < NP; ++i)
+                    for (int k = 0; k < NP; ++k) e += v[p + 1][i] * S[i * NP + k] * v[q + 1][k];
+                H[p * D + q] = e - mj[p + 1] * mj[q + 1];
+            }
+        double lambda = o.lambda0;
+        int fail = cholesky(D, H, 0.0, Lh), tries = 0;
+        while (fail) {
+            if (tries >= o.max_lambda) break;
+            fail = cholesky(D, H, lambda, Lh);
+            st |= ST_LAMBDA;
+            lambda *= o.lambda_mul;
+            ++tries;
+        }
+        if (fail) { st |= ST_LAMBDA_CAP | ST_NONFINITE; ++it; break; }
+        for (int p = 0; p < D; ++p) rhs[p] = -G[p + 1];
+        solve_lower(D, Lh, rhs, wv);
+        solve_upper_T(D, Lh, wv, dx);
+        da[0] = 0.0;
+        for (int p = 0; p < D; ++p) da[p + 1] = dx[p];
+        double dg = 0.0;
+        for (int j = 1; j < 9; ++j) dg += da[j] * G[j];
+        res = 0.5 * fabs(dg);
+        if (!isfinite(res)) { st |= ST_NONFINITE; ++it; break; }
+        if (res <= o.tol) st |= ST_CONVERGED;
+        if (step <= o.alpha_min) st |= ST_STAGNATED;
+        conv = (res <= o.tol) || (step <= o.alpha_min);
+        ++it;
+    }
+    if (!conv && !(st & ST_NONFINITE)) st |= ST_MAXITER;
+    if (o.final_step && (st & ST_CONVERGED))
+        for (int j = 1; j < 9; ++j) a[j] += da[j];
+    memcpy(alpha, a, sizeof(a));
+    alpha[0] = n;
+    if (iters) *iters = it;
+    if (res_out) *res_out = res;
+    return st;
+}
+
+/* Flux of the nine moments, F9_j = v_j . F (F as in or_flux), and the
+ * characteristic speed of the nine-statistic system: the spectral radius of
+ * the 9 x 9 pencil (E[ubar_x psi psi^T], E[psi psi^T]) scaled by the gauge,
+ * as the paper states it for its statistics (Eq. "The lax F"). */
+void or_flux_axi(int order, const double *alpha, const double *g, double n, double *F9, double *speed) {
+    double v[9][NP], b[NP], m[NP], S[NP * NP], X[NP], XS[NP * NP];
+    flic_basis(v);
+    double a[9];
+    memcpy(a, alpha, sizeof(a));
+    a[0] = n;
+    axi_beta(v, a, b);
+    or_expect(order, g, b, NULL, m, S, X, XS);
+    for (int j = 0; j < 9; ++j) {
+        double em = 0.0, ex = 0.0;
+        for (int i = 0; i < NP; ++i) { em += v[j][i] * m[i]; ex += v[j][i] * X[i]; }
+        if (F9) F9[j] = n * (g[0] * em + g[3] * ex);
+    }
+    if (!speed) return;
+    double A[81], B[81], L[81], C[81], tmp[81], ev[9];
+    for (int p = 0; p < 9; ++p)
+        for (int q = 0; q < 9; ++q) {
+            double ea = 0.0, eb = 0.0;
+            for (int i = 0; i < NP; ++i)
+                for (int k = 0; k < NP; ++k) {
+                    ea += v[p][i] * XS[i * NP + k] * v[q][k];
+                    eb += v[p][i] * S[i * NP + k] * v[q][k];
+                }
+            A[p * 9 + q] = ea;
+            B[p * 9 + q] = eb;
+        }
+    if (cholesky(9, B, 0.0, L)) { *speed = NAN; return; }
+    for (int col = 0; col < 9; ++col) {
+        double bc[9], xc[9];
+        for (int i = 0; i < 9; ++i) bc[i] = A[i * 9 + col];
+        solve_lower(9, L, bc, xc);
+        for (int i = 0; i < 9; ++i) tmp[i * 9 + col] = xc[i];
+    }
+    for (int row = 0; row < 9; ++row) {
+        double br[9], xr[9];
+        for (int i = 0; i < 9; ++i) br[i] = tmp[row * 9 + i];
+        solve_lower(9, L, br, xr);
+        for (int i = 0; i < 9; ++i) C[row * 9 + i] = xr[i];
+    }
+    for (int i = 0; i < 9; ++i)
+        for (int j = i + 1; j < 9; ++j) C[i * 9 + j] = C[j * 9 + i] = 0.5 * (C[i * 9 + j] + C[j * 9 + i]);
+    jacobi_eigen(9, C, ev, NULL);
+    double lo = ev[0], hi = ev[0];
+    for (int i = 1; i < 9; ++i) { if (ev[i] < lo) lo = ev[i]; if (ev[i] > hi) hi = ev[i]; }
+    *speed = fmax(fabs(g[0] + g[3] * lo), fabs(g[0] + g[3] * hi));
+}
 
 static double dot35(const double *a, const double *b) {
     double s = 0.0;

@@ -220,6 +220,26 @@ def interface_flux(order, scheme, c, side, M, F, g, speed, dtdx, tol=1e-10, maxI
     return out, st
 
 
+def solve_axi(order, M9, alpha0=None, tol=1e-8, maxI=500, final_step=True, g=None):
+    """Algorithm 1 on the paper's nine 1D statistics (psi_j = v_j . phi,
+    flic_basis); M9 = (n, psi moments).  Returns (alpha, status, iters, res)."""
+    M9 = _f64(M9, (9,))
+    a = np.zeros(9) if alpha0 is None else _f64(alpha0, (9,)).copy()
+    opts = np.array([tol, float(maxI), float(bool(final_step))])
+    it = ctypes.c_int()
+    res = ctypes.c_double()
+    st = lib().or_solve_axi(order, _g(g), _d(M9), _d(a), _d(opts), ctypes.byref(it), ctypes.byref(res))
+    return a, st, it.value, res.value
+
+
+def flux_axi(order, alpha, g, n):
+    """Flux of the nine moments and the speed of the nine-statistic system."""
+    F = np.zeros(9)
+    sp = ctypes.c_double()
+    lib().or_flux_axi(order, _d(_f64(alpha, (9,))), _d(_f64(g, (6,))), ctypes.c_double(n), _d(F), ctypes.byref(sp))
+    return F, sp.value
+
+
 def gauge_T(g_to, g_from):
     """T(g', g) of Eq. "Change gauge M F": M(g') = T M(g)."""
     T = np.zeros((NP, NP))

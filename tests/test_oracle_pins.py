@@ -805,3 +805,48 @@ def test_gauge_study_golden_matches_oracle(O):
     b, st, _, _, _ = O.solve(r["rule_id"], e0, beta0=e0, tol=1e-13, g=[v, 0, 0, 1, 1, 1])
     assert st & 1
     assert np.abs(b - np.array(d["beta64_hermite"][0])).max() < 1e-10
+
+
+# ---------------------------------------------------------------- the paper's nine-statistic system
+def test_nine_statistic_solve_equals_35_product_solve(O):
+    """The paper's reduced system for axisymmetric flow (nine statistics of
+    Eq. "Sufficient 35", Algorithm 1 over eight unknowns, one-azimuth rule)
+    against the 35-product solve (34 unknowns, 12 azimuths) on the same
+    (u_x, u_r) blocks: for moments of an axisymmetric density both find that
+    density, beta = sum_j alpha_j v_j, and its nine fluxes are the
+    projections of the 35; the nine-statistic speed is one of the 35-product
+    system's (the axisymmetric moments are an invariant subspace)."""
+    dom = (-12.0, 16.0, 12.0)
+    O.set_velocity_rule(208, dom[0], dom[1], 8, dom[2], 6, 8, 12)
+    O.set_velocity_rule(209, dom[0], dom[1], 8, dom[2], 6, 8, 1)
+    v = O.flic_basis()
+    rng = np.random.default_rng(1)
+    for trial in range(3):
+        alpha = np.zeros(9)
+        alpha[0] = 1.3
+        alpha[1:] = rng.normal(0, 1, 8) * np.array([0.05, 0.05, 0.05, 0.02, 0.01, 0.01, 0.02, 0.01])
+        g = np.array([2.0 - trial, 0, 0, 1.3, 1.1, 1.1])
+        beta = alpha @ v
+        _, m, _, _, _ = O.expect(208, beta, g)
+        M35 = alpha[0] * m
+        a, st, _, _ = O.solve_axi(209, v @ M35, g=g, tol=1e-12)
+        b35, st35, _, _, _ = O.solve(208, M35, g=g, tol=1e-12)
+        assert st & 1 and st35 & 1
+        assert np.abs(a - alpha).max() < 1e-10
+        assert np.abs(b35[1:] - (a @ v)[1:]).max() < 1e-10
+        F9, sp9 = O.flux_axi(209, a, g, alpha[0])
+        F35, sp35, _, _ = O.flux(208, beta, g, alpha[0])
+        assert np.abs(F9 - v @ F35).max() < 1e-10 * np.abs(F35).max()
+        assert sp9 <= sp35 * (1 + 1e-9)
+
+
+def test_nine_statistic_speed_at_maxwellian(O):
+    """At a Maxwellian the nine-statistic system contains the pure-u_x chain
+    he_0..he_4, whose Jacobian's largest eigenvalue is the largest root of
+    He_5, sqrt(5 + sqrt(10)): speed = w_x + s_x sqrt(5 + sqrt(10))."""
+    a0 = np.zeros(9)
+    a0[0] = 1.0
+    for w, s in ((0.5, 1.0), (3.0, 1.7)):
+        O.set_velocity_rule(207, w - 11.0 * s, w + 11.0 * s, 8, 11.0 * s, 6, 8, 1)
+        _, sp = O.flux_axi(207, a0, [w, 0, 0, s, s, s], 1.0)
+        assert sp == pytest.approx(w + s * math.sqrt(5 + math.sqrt(10)), rel=1e-6)

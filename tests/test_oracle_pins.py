@@ -850,3 +850,23 @@ def test_nine_statistic_speed_at_maxwellian(O):
         O.set_velocity_rule(207, w - 11.0 * s, w + 11.0 * s, 8, 11.0 * s, 6, 8, 1)
         _, sp = O.flux_axi(207, a0, [w, 0, 0, s, s, s], 1.0)
         assert sp == pytest.approx(w + s * math.sqrt(5 + math.sqrt(10)), rel=1e-6)
+
+
+def test_nine_statistics_are_hermite_laguerre_products(O):
+    """The nine statistics of Eq. "Sufficient 35" are products of an
+    orthonormal Hermite polynomial in u_x and a Laguerre polynomial in
+    s = u_r^2/2 (orthonormal for the radial part of a 2D Gaussian, s ~ Exp(1)),
+    up to sign: psi = he_a(u_x) * (-1)^m L_m(s) for (a, m) = (0,0), (1,0),
+    (2,0), (0,1), (3,0), (4,0), (0,2), (1,1), (2,1), with L_1 = 1 - s,
+    L_2 = (s^2 - 4s + 2)/2."""
+    v = O.flic_basis()
+    am = [(0, 0), (1, 0), (2, 0), (0, 1), (3, 0), (4, 0), (0, 2), (1, 1), (2, 1)]
+    he = [lambda x: 1.0, lambda x: x, lambda x: (x * x - 1) / SQ2, lambda x: (x ** 3 - 3 * x) / math.sqrt(6),
+          lambda x: (x ** 4 - 6 * x * x + 3) / math.sqrt(24)]
+    lag = [lambda s: 1.0, lambda s: 1.0 - s, lambda s: (s * s - 4 * s + 2) / 2]
+    rng = np.random.default_rng(6)
+    for _ in range(20):
+        u = rng.normal(0, 1.5, 3)
+        s = (u[1] ** 2 + u[2] ** 2) / 2
+        want = np.array([he[a](u[0]) * (-1) ** m * lag[m](s) for a, m in am])
+        assert np.abs(v @ O.phi(u) - want).max() < 1e-10

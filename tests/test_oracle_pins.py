@@ -870,3 +870,25 @@ def test_nine_statistics_are_hermite_laguerre_products(O):
         s = (u[1] ** 2 + u[2] ** 2) / 2
         want = np.array([he[a](u[0]) * (-1) ** m * lag[m](s) for a, m in am])
         assert np.abs(v @ O.phi(u) - want).max() < 1e-10
+
+
+def test_shock_speeds_equal_nine_statistic_speeds(O):
+    """On 1D shock states the spectral radius of the 35-product pencil is the
+    paper's nine-statistic system's: the extreme characteristic fields are
+    axisymmetric, so the Lax-Friedrichs dissipation and the time step are
+    those of the paper's system (Mach 4 and 10 tanh states, after 2 steps)."""
+    v = O.flic_basis()
+    for mach in (4.0, 10.0):
+        d = O.shock_domain(mach)
+        O.set_velocity_rule(213, d[0], d[1], 6, d[2], 4, 8, 12)
+        O.set_velocity_rule(215, d[0], d[1], 6, d[2], 4, 8, 1)
+        so = O.Shock(mach, 12, -6.0, 6.0, order=213, ic="tanh", thickness=15.7)
+        for _ in range(2):
+            so.step()
+        for c in range(1, 13):
+            M, g, b = so.M[c], so.g[c], so.beta[c]
+            _, sp35, _, _ = O.flux(213, b, g, M[0])
+            a = v @ b
+            a[0] = M[0]
+            _, sp9 = O.flux_axi(215, a, g, M[0])
+            assert sp9 == pytest.approx(sp35, rel=1e-9), (mach, c)

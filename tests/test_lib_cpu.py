@@ -4,6 +4,7 @@ import ctypes
 import os
 import subprocess
 
+import numpy as np
 import pytest
 
 
@@ -56,3 +57,27 @@ def test_oracle_and_library_share_no_code():
         assert "import oracle" not in txt and "from oracle" not in txt, f
     otxt = open(os.path.join(root, "oracle", "mem_oracle.c")).read()
     assert "#include \"" not in otxt
+
+
+def test_shock_params_defaults_and_validation_without_gpu():
+    """Host logic of the shock parameters (no device work): defaults of the
+    interface scheme, tanh thickness and t_end, and the validation that
+    mem_shock_domain shares with mem_shock_init."""
+    from paper_2303_02898_gb300 import mem
+    p = mem.default_shock_params()
+    assert p.scheme == mem.SCHEME_LF and p.thickness == pytest.approx(15.7) and p.t_end == 0.0
+    assert len(mem.shock_domain(mach=4.0, scheme=mem.SCHEME_FLIC, ic=1, thickness=5.44, t_end=4.0)) == 3
+    L = mem.lib()
+    d = (ctypes.c_double * 3)()
+    for bad in (dict(scheme=3), dict(scheme=-1), dict(ic=1, thickness=0.0), dict(t_end=-1.0), dict(mach=0.5)):
+        q = mem.default_shock_params(**bad)
+        assert L.mem_shock_domain(ctypes.byref(q), d) == mem.MEM_EINVAL, bad
+
+
+def test_shock_domain_matches_oracle_without_gpu(O):
+    """The library's integration box (host code, Appendix D) equals the
+    oracle's for the paper's Mach-4 (10, 6, 6) and Mach-10 (5, 5, 5) choices."""
+    from paper_2303_02898_gb300 import mem
+    for mach, n in ((4.0, (10.0, 6.0, 6.0)), (10.0, (5.0, 5.0, 5.0)), (1.2, (6.0, 6.0, 6.0))):
+        lib_box = mem.shock_domain(mach=mach, na=n[0], nb=n[1], nr=n[2])
+        assert np.allclose(lib_box, O.shock_domain(mach, *n), rtol=1e-12, atol=1e-12)

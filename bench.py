@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--order", type=int, default=8)
     ap.add_argument("--no-extras", action="store_true", help="headline only (used for profiler runs)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--case", nargs="+", default=None, metavar=("NAME", "N"),
+                    help="kernel-focused run for profilers instead of the benchmark: "
+                         "solve [cells] | ensemble [steps] | mach10 [steps] | mach10flic [steps]")
     return ap.parse_args()
 
 
@@ -122,7 +125,7 @@ def fused_flops_per_pass(n):
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_fused_solve<8> launch
 # on the headline workload (2^20 cells), from one ncu capture of the current
-# kernel (profiles/k_fused_solve_q8_2p20.md); None once the kernel changes.
+# kernel; None once the kernel changes.
 TRAFFIC_BYTES = 402.26e6
 
 SHOCK_MACH = 3.0   # largest Mach the 8^3 Gauss-Hermite Hermite-gauge rule keeps stable from a step
@@ -557,7 +560,7 @@ def cpu_baseline(order, sample, seed=0):
     t = workloads.solve_targets(sample, seed=seed)
     M, _ = O.target_batch(24, t.v, t.T, t.a, t.b)
     t0 = time.perf_counter()
-    O.solve_batch(order, M)
+    O.solve_batch(order, M, final_step=True)
     dt = time.perf_counter() - t0
     return {"value": sample / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
             "sample": "first %d cells of the same workload (seed %d), FP64 Algorithm 1, Q=%d^3, OpenMP" % (sample, seed, order),
@@ -573,10 +576,10 @@ def run_reference(args, rank):
     t = workloads.solve_targets(sample, seed=0)
     M, _ = O.target_batch(24, t.v, t.T, t.a, t.b)
     for _ in range(args.warmup):
-        O.solve_batch(args.order, M)
+        O.solve_batch(args.order, M, final_step=True)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        O.solve_batch(args.order, M)
+        O.solve_batch(args.order, M, final_step=True)
     dt = time.perf_counter() - t0
     value = sample * args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -594,7 +597,77 @@ def workload_config(args, cells):
                         "targets from seeded polynomial log-densities (v~N(0,3^2), T~logU[0.5,20], cubic~N(0,0.05^2), "
                         "quartic~-U(0.01,0.1)), cold start beta=0",
             "cells_per_gpu": cells, "quadrature": "Gauss-Hermite %d^3 in the Hermite gauge" % args.order,
+            "algorithm": "Algorithm 1 (paper constants, tol 1e-8, maxI 500) plus its final Newton step "
+                         "(final_step=1, library extension)",
             "moments": 35, "l2": "inputs larger than L2 (M 147 MB read, beta 147 MB written per step)"}
+
+
+# ---------------------------------------------------------------- profiler cases
+def _timed_ms(torch, fn, n):
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(n):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / n
+
+
+def run_case(name, n):
+    """Kernel-focused runs for profilers and quick timing: inputs built on the
+    device (seeded, synthetic), two warm-up iterations, then the timed ones;
+    one line with the mean time per iteration (CUDA events).
+      solve [cells]       mem_solve, fused back-end, 8^3 rule (default 2^20 cells)
+      ensemble [steps]    256-problem shock batch, 8^3 rule (Mach <= 3)
+      mach10 [steps]      256-problem Mach 1.2-10 batch, velocity-space rule
+      mach10flic [steps]  the same batch with FLIC interface fluxes"""
+    import numpy as np
+    import torch
+    from paper_2303_02898_gb300 import mem, workloads
+    dev = torch.device("cuda:0")
+    if name == "solve":
+        cells = n or (1 << 20)
+        ctx = mem.Context(8)
+        t = workloads.solve_targets(cells, seed=0)
+        T32 = lambda a: torch.tensor(a, dtype=torch.float32, device=dev).contiguous()  # noqa: E731
+        M = torch.zeros(cells, 35, device=dev)
+        g = torch.zeros(cells, 6, device=dev)
+        ctx.targets(T32(t.v), T32(t.T), T32(t.a), T32(t.b), M, g, gen_order=24)
+        beta = torch.zeros(cells, 35, device=dev)
+        st = torch.zeros(cells, dtype=torch.int32, device=dev)
+
+        def run():
+            beta.zero_()
+            ctx.solve(M, beta, st)
+        for _ in range(2):
+            run()
+        ms = _timed_ms(torch, run, 2)
+        print("solve cells=%d ms=%.3f cell-solves/s=%.4g" % (cells, ms, cells / ms * 1e3))
+        ctx.close()
+    elif name == "ensemble":
+        ctx = mem.Context(8)
+        probs = workloads.ensemble_problems(256, seed=1, mach_hi=3.0)
+        sh = mem.Shock(ctx, problems=[dict(mach=p.mach, ncells=p.ncells, xl=p.xl, xr=p.xr) for p in probs], graph=1)
+        sh.step(2)
+        cells = sum(p.ncells for p in probs)
+        ms = _timed_ms(torch, lambda: sh.step(1), n or 3)
+        print("ensemble cells=%d ms/step=%.3f cell-updates/s=%.4g" % (cells, ms, cells / ms * 1e3))
+        sh.close()
+        ctx.close()
+    elif name in ("mach10", "mach10flic"):
+        scheme = mem.SCHEME_FLIC if name == "mach10flic" else mem.SCHEME_LF
+        vctx = mem.Context.velocity(mem.shock_domain(mach=10.0))
+        rng = np.random.default_rng(7)
+        probs = [dict(mach=float(m), ncells=150, xl=-47.1, xr=47.1) for m in rng.uniform(1.2, 10.0, 256)]
+        sh = mem.Shock(vctx, problems=probs, ic=1, graph=1, scheme=scheme)
+        sh.step(2)
+        cells = 150 * len(probs)
+        ms = _timed_ms(torch, lambda: sh.step(1), n or 3)
+        print("%s cells=%d ms/step=%.3f cell-updates/s=%.4g" % (name, cells, ms, cells / ms * 1e3))
+        sh.close()
+        vctx.close()
+    else:
+        raise SystemExit("unknown case %r" % name)
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -619,6 +692,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.case:
+        return run_case(args.case[0], int(args.case[1]) if len(args.case) > 1 else 0)
 
     import numpy as np
     import torch
@@ -652,7 +727,10 @@ def main():
     st = torch.zeros(B, dtype=torch.int32, device=dev)
     it = torch.zeros(B, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream()
-    opts = mem.default_opts(impl=mem.IMPL_FUSED)
+    # Algorithm 1 plus its final Newton step (final_step = 1, a library
+    # extension): the 1e-5 residual bar is on the solution, not on the
+    # iterate one direction behind it; the literal order is reported beside.
+    opts = mem.default_opts(impl=mem.IMPL_FUSED, final_step=1)
 
     def step():
         beta.zero_()

@@ -81,7 +81,10 @@ typedef struct {
     float rtol;       /* Armijo relative slack (5e-5)                        */
     int32_t maxT;     /* line-search trials s = 0..maxT (25)                 */
     float alpha_min;  /* alpha <= alpha_min stops as stagnated (1e-6)        */
-    int32_t final_step; /* 1: apply the last Newton step on res <= tol       */
+    int32_t final_step; /* 0: Algorithm 1's order, the last computed direction
+                           is not applied (default); 1: an extension that
+                           applies it when res <= tol (moment residual of
+                           the solution instead of one Newton step behind) */
     int32_t impl;     /* MEM_IMPL_PLAIN or MEM_IMPL_FUSED (default FUSED)    */
 } mem_solve_opts;
 
@@ -144,9 +147,20 @@ int mem_quad_order(const mem_ctx *ctx);
  * The objective, gradient and Hessian follow Appendix C (Eq. "MLE
  * optimization goal" and its Hessian); the partition function uses the
  * log-sum-exp form of Section 3.1.  The fused back-end needs no scratch
- * memory; the plain back-end uses scratch the context owns (grown on first
- * use, so its first call may allocate) and synchronises the stream once per
- * Newton pass.  Returns MEM_EINVAL for B < 0 or NULL arrays with B > 0. */
+ * memory; the plain back-end uses the context's scratch (see below) and
+ * synchronises the stream once per Newton pass.  No call allocates device
+ * memory.  Returns MEM_EINVAL for B < 0 or NULL arrays with B > 0.
+ *
+ * Context scratch: mem_init / mem_init_velocity allocate one working buffer
+ * per context (chunks of 65,536 cells; about 0.5 GB at quad_order 8, 0.8 GB
+ * at 12, 60 MB for a velocity-space context).  The plain back-end, mem_flux /
+ * mem_flux_axisym at quad orders other than 8 and 12, and the flux of a
+ * velocity-space context use it.  Such calls on one context are ordered on
+ * the GPU after one another through an event the context records, whatever
+ * streams they are made on (calls from several host threads are serialised
+ * by the context's lock); a call made on a stream that is being captured is
+ * not ordered that way, so capture none of them while other streams use the
+ * same context. */
 int mem_solve(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters,
               int64_t B, const mem_solve_opts *opts, void *stream);
 
@@ -165,7 +179,9 @@ int mem_solve_gauge(mem_ctx *ctx, const float *M, float *beta, const float *gaug
  * The eigenvalues of dF/dM are the generalised eigenvalues of
  * (E[u_x phi phi^T], E[phi phi^T]) over all 35 statistics.  beta dev [B][35]
  * (beta[0] ignored, n taken from M[0]), M dev [B][35] (only M[0] is read),
- * gauge dev [B][6].  F or speed may be NULL.  Uses context scratch. */
+ * gauge dev [B][6].  F or speed may be NULL.  At quad_order 8 and 12 the
+ * fused kernel needs no scratch; other orders and velocity-space contexts
+ * use the context scratch (see mem_solve). */
 int mem_flux(mem_ctx *ctx, const float *M, const float *beta, const float *gauge, float *F,
              float *speed, int64_t B, void *stream);
 
@@ -193,8 +209,15 @@ int mem_flux_axisym(mem_ctx *ctx, const float *M, const float *beta, const float
  *   - B <= 1024 cells per call and a context with quad_order <= 12; larger
  *     requests return MEM_EINVAL without doing anything;
  *   - the current device must be the context's device (else MEM_EINVAL);
+ *   - velocity-space contexts are not supported (MEM_EINVAL): their rule has
+ *     no shared node tables for this path to read;
  *   - the first call on a device resolves the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - that address is cached per device index for the life of the process and
+ *     is valid only in the device's primary context: after cudaDeviceReset
+ *     (or under another context on the same device) the library image is
+ *     loaded again elsewhere, so do not call this entry point again in that
+ *     process;
  *   - every call uses the same array: calls whose work overlaps on the GPU
  *     (different streams, or threads without ordering) race and give wrong
  *     results.  Each call writes everything it later reads, so the contents a
@@ -382,7 +405,9 @@ int mem_serve_submit(mem_server *sv, const mem_shock_params *p, uint64_t *req_id
 int mem_serve_progress(mem_server *sv, int iters, void *stream);
 
 /* Poll a request: MEM_OK (result filled; rho/ux/T, each ncells long, copied
- * if not NULL), MEM_PENDING (queued or running), or MEM_ENOTFOUND. */
+ * if not NULL), MEM_PENDING (queued or running), or MEM_ENOTFOUND.  A
+ * finished request has res->status MEM_OK, or a negative MEM_E* code if its
+ * device state was lost when a batch rebuild failed (no profiles then). */
 int mem_serve_poll(mem_server *sv, uint64_t req_id, mem_shock_result *res, float *rho, float *ux,
                    float *T);
 

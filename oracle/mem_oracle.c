@@ -35,7 +35,7 @@
  * (closed forms, invariants, brute force).  The paper's figures print no
  * values, so nothing is pinned to a figure.
  *
- * Conventions (readings of the paper, also listed in the design doc):
+ * Conventions (readings of the paper):
  *   - M_i(g) = int phi_i((u-w)/s) f(u) d^3u, the moments in the cell's gauge
  *     g = (w_x,w_y,w_z,s_x,s_y,s_z); M_0 = n.
  *   - beta_0 = n; beta_1..34 are the natural parameters relative to the
@@ -409,7 +409,9 @@ typedef struct {
     double atol, rtol; /* Armijo floating-point slack (5e-6, 5e-5) */
     int maxT;          /* line-search trials are s = 0..maxT (25) */
     double alpha_min;  /* stagnation exit alpha <= 1e-6 */
-    int final_step;    /* apply the last computed Newton step on res <= tol */
+    int final_step;    /* 1: apply the last computed Newton step on res <= tol
+                          (an extension; 0, Algorithm 1's own order, is the
+                          default) */
 } or_opts;
 
 enum {
@@ -420,7 +422,7 @@ enum {
 static void default_opts(or_opts *o) {
     o->tol = 1e-8; o->maxI = 500; o->lambda0 = 1e-3; o->lambda_mul = 10.0; o->max_lambda = 20;
     o->c = 5e-4; o->atol = 5e-6; o->rtol = 5e-5; o->maxT = 25; o->alpha_min = 1e-6;
-    o->final_step = 1;
+    o->final_step = 0;
 }
 
 /* Standard Cholesky of the n x n matrix A + shift*I (row-major); fails on a
@@ -527,10 +529,10 @@ int or_solve(int order, const double *g, const double *M, double *beta, const do
     }
     if (!conv && !(st & ST_NONFINITE)) st |= ST_MAXITER;
     /* Algorithm 1 returns beta without the direction computed in the last
-     * pass.  The decrement res = |dbeta.grad|/2 <= tol bounds the objective
-     * error, not the moment residual (|grad|^2 <= 2 res lambda_max(H)), so by
-     * default the final Newton step is applied when the loop stops on
-     * res <= tol; final_step = 0 gives the literal order. */
+     * pass (final_step = 0, the default).  The decrement res = |dbeta.grad|/2
+     * <= tol bounds the objective error, not the moment residual
+     * (|grad|^2 <= 2 res lambda_max(H)); final_step = 1, an extension,
+     * applies that last Newton step when the loop stops on res <= tol. */
     if (o.final_step && (st & ST_CONVERGED))
         for (int i = 1; i < NP; ++i) b[i] += db[i];
     memcpy(beta, b, sizeof(b));

@@ -160,7 +160,7 @@ def residual_batch(order, beta, M, g=None):
     return np.array([residual(order, b, m, gg) for b, m, gg in zip(beta, M, g)])
 
 
-def solve(order, M, beta0=None, tol=1e-8, maxI=500, final_step=True, g=None):
+def solve(order, M, beta0=None, tol=1e-8, maxI=500, final_step=False, g=None):
     """Algorithm 1 on one cell.  Returns (beta, status, iters, res, max_lambda)."""
     M = _f64(M, (NP,))
     beta = np.zeros(NP) if beta0 is None else _f64(beta0, (NP,)).copy()
@@ -172,7 +172,7 @@ def solve(order, M, beta0=None, tol=1e-8, maxI=500, final_step=True, g=None):
     return beta, st, it.value, res.value, lam.value
 
 
-def solve_batch(order, M, beta0=None, tol=1e-8, maxI=500, nthreads=0, final_step=True, g=None):
+def solve_batch(order, M, beta0=None, tol=1e-8, maxI=500, nthreads=0, final_step=False, g=None):
     """Algorithm 1 over a batch of cells (OpenMP).  Returns (beta, status, iters)."""
     M = _f64(M).reshape(-1, NP)
     B = M.shape[0]
@@ -206,7 +206,7 @@ def flic_basis():
     return v
 
 
-def interface_flux(order, scheme, c, side, M, F, g, speed, dtdx, tol=1e-10, maxI=500):
+def interface_flux(order, scheme, c, side, M, F, g, speed, dtdx, tol=1e-10, maxI=500, final_step=False):
     """Interface flux between cells c - 1 + side and c + side, in the gauge of
     cell c (Eqs. "The lax F", "The lax W", "The FLIC"): scheme lf, lw, flic."""
     M = _f64(M).reshape(-1, NP)
@@ -214,13 +214,13 @@ def interface_flux(order, scheme, c, side, M, F, g, speed, dtdx, tol=1e-10, maxI
     g = _f64(g).reshape(-1, 6)
     speed = _f64(speed).reshape(-1)
     out = np.zeros(NP)
-    opts = np.array([tol, float(maxI), 1.0])
+    opts = np.array([tol, float(maxI), float(bool(final_step))])
     st = lib().or_interface_flux(order, {"lf": 0, "lw": 1, "flic": 2}[scheme], c, side, _d(M), _d(F), _d(g),
                                  _d(speed), ctypes.c_double(dtdx), _d(opts), _d(out))
     return out, st
 
 
-def solve_axi(order, M9, alpha0=None, tol=1e-8, maxI=500, final_step=True, g=None):
+def solve_axi(order, M9, alpha0=None, tol=1e-8, maxI=500, final_step=False, g=None):
     """Algorithm 1 on the paper's nine 1D statistics (psi_j = v_j . phi,
     flic_basis); M9 = (n, psi moments).  Returns (alpha, status, iters, res)."""
     M9 = _f64(M9, (9,))
@@ -344,14 +344,15 @@ class Shock:
     """FP64 shock-tube state: N interior cells + 2 Dirichlet ghost cells."""
 
     def __init__(self, mach, ncells, xl, xr, order=8, cfl=0.5, Pr=2.0 / 3.0, gamma=5.0 / 3.0,
-                 kn=1.0, tol=1e-8, maxI=500, nthreads=0, ic="step", thickness=15.7, scheme="lf"):
+                 kn=1.0, tol=1e-8, maxI=500, nthreads=0, ic="step", thickness=15.7, scheme="lf",
+                 final_step=False):
         self.order, self.N, self.cfl, self.Pr = order, ncells, cfl, Pr
         # interface flux: Eq. "The lax F" (lf), "The lax W" (lw), "The FLIC" (flic)
         self.scheme = {"lf": 0, "lw": 1, "flic": 2}[scheme]
         self.dx = (xr - xl) / ncells
         self.x = xl + (np.arange(ncells) + 0.5) * self.dx
         self.relax = kn * RELAX_KN1 / Pr
-        self.opts = np.array([tol, float(maxI), 1.0])
+        self.opts = np.array([tol, float(maxI), float(bool(final_step))])
         self.nthreads = nthreads
         r, t = rh(mach, gamma)
         self.n_up, self.T_up, self.v_up = 1.0, 1.0, np.sqrt(gamma) * mach
@@ -385,7 +386,8 @@ class Shock:
                 self.g[c] = gH
                 self.beta[c, 0] = self.M[c, 0]
         if ic != "step":
-            b, st, it = solve_batch(order, self.M[1:-1], None, tol, maxI, nthreads, g=self.g[1:-1])
+            b, st, it = solve_batch(order, self.M[1:-1], None, tol, maxI, nthreads, final_step=final_step,
+                                    g=self.g[1:-1])
             self.beta[1:-1] = b
         _, self.speed = flux_batch(order, self.M, self.beta, self.g, nthreads)
         self.status = np.zeros(NT, dtype=np.int32)

@@ -14,6 +14,9 @@
 
 using namespace mem;
 
+// Cells per chunk of the velocity-space flux (moment rows in context scratch).
+static constexpr int64_t VEL_FLUX_CHUNK = (int64_t)1 << 16;
+
 namespace mem_host {
 
 // 1D Gauss-Hermite rule for the standard normal weight: the nodes are the
@@ -68,20 +71,38 @@ int gh_rule(int n, std::vector<double> &x, std::vector<double> &w) {
     return MEM_OK;
 }
 
-int ensure_scratch(mem_ctx *ctx, size_t bytes) {
-    if (ctx->scratch_bytes >= bytes) return MEM_OK;
-    if (ctx->scratch) {
-        cudaDeviceSynchronize();
-        cudaFree(ctx->scratch);
-        ctx->scratch = nullptr;
-        ctx->scratch_bytes = 0;
-    }
+int reserve_scratch(mem_ctx *ctx, size_t bytes) {
     if (cudaMalloc(&ctx->scratch, bytes) != cudaSuccess) {
         cudaGetLastError();
+        ctx->scratch = nullptr;
         return MEM_ENOMEM;
     }
     ctx->scratch_bytes = bytes;
+    if (cudaEventCreateWithFlags(&ctx->scratch_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->scratch_ev = nullptr;
+        return MEM_ECUDA;
+    }
     return MEM_OK;
+}
+
+// Order this use of the context scratch after the previous one, which may
+// have been enqueued on another stream.  Stream capture cannot wait on an
+// event recorded outside it, so a capturing stream is not ordered here
+// (none of the scratch paths is captured by the library itself).
+int scratch_begin(mem_ctx *ctx, size_t bytes, cudaStream_t st) {
+    if (bytes > ctx->scratch_bytes || !ctx->scratch) return MEM_ENOMEM;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    MEM_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (ctx->scratch_ev_live && cs == cudaStreamCaptureStatusNone) MEM_CUDA_TRY(cudaStreamWaitEvent(st, ctx->scratch_ev, 0));
+    return MEM_OK;
+}
+
+void scratch_end(mem_ctx *ctx, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    if (cudaEventRecord(ctx->scratch_ev, st) == cudaSuccess) ctx->scratch_ev_live = true;
+    else cudaGetLastError();
 }
 
 // 1D Gauss-Legendre rule on [-1, 1]: the roots of P_n by Newton's method in
@@ -321,7 +342,7 @@ void mem_solve_opts_default(mem_solve_opts *o) {
     o->rtol = 5e-5f;
     o->maxT = 25;
     o->alpha_min = 1e-6f;
-    o->final_step = 1;
+    o->final_step = 0;
     o->impl = MEM_IMPL_FUSED;
 }
 
@@ -434,6 +455,9 @@ int mem_init(int degree, int quad_order, mem_ctx **out) {
     if (!rc) rc = upload(&ctx->d_x1d, x1d);
     if (!rc) rc = upload(&ctx->d_logw1d, lw1d);
     if (!rc) rc = build_slot_tables(ctx);
+    if (!rc)
+        rc = mem_host::reserve_scratch(
+            ctx, std::max(mem_host::plain_scratch_bytes(Q), mem_host::flux_scratch_bytes(Q)));
     if (rc) { mem_destroy(ctx); return rc; }
     if (cudaDeviceSynchronize() != cudaSuccess) { mem_destroy(ctx); return MEM_ECUDA; }
     *out = ctx;
@@ -478,6 +502,7 @@ int mem_init_velocity(int degree, int nbx, int nbr, int ng, int K, double ax, do
     if (!rc) rc = upload(&ctx->d_vtf, vtf);
     if (!rc) rc = upload(&ctx->d_dom0, d0);
     if (!rc) rc = build_slot_tables(ctx);
+    if (!rc) rc = mem_host::reserve_scratch(ctx, sizeof(float) * (size_t)VEL_FLUX_CHUNK * MEM_MU_STRIDE);
     if (rc) { mem_destroy(ctx); return rc; }
     if (cudaDeviceSynchronize() != cudaSuccess) { mem_destroy(ctx); return MEM_ECUDA; }
     *out = ctx;
@@ -499,6 +524,7 @@ void mem_destroy(mem_ctx *ctx) {
                     ctx->scratch, ctx->d_vtd, ctx->d_vtf, ctx->d_dom0};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (ctx->scratch_ev) cudaEventDestroy(ctx->scratch_ev);
     delete ctx;
 }
 
@@ -539,8 +565,8 @@ int mem_solve_gauge(mem_ctx *ctx, const float *M, float *beta, const float *gaug
 static int vel_flux(mem_ctx *ctx, const float *M, const float *beta, const float *gauge, float *F, float *speed,
                     int64_t B, cudaStream_t st, bool axisym) {
     std::lock_guard<std::mutex> lock(ctx->mu);
-    const int64_t CH = std::min<int64_t>(B, (int64_t)1 << 18);
-    int rc = mem_host::ensure_scratch(ctx, sizeof(float) * (size_t)CH * MEM_MU_STRIDE);
+    const int64_t CH = std::min<int64_t>(B, VEL_FLUX_CHUNK);
+    int rc = mem_host::scratch_begin(ctx, sizeof(float) * (size_t)CH * MEM_MU_STRIDE, st);
     if (rc) return rc;
     float *mu = (float *)ctx->scratch;
     mem_solve_opts o;
@@ -552,9 +578,10 @@ static int vel_flux(mem_ctx *ctx, const float *M, const float *beta, const float
         if (!rc)
             rc = mem_host::flux_from_mu(ctx, mu, M + c0 * NP, gauge + c0 * 6, F ? F + c0 * NP : nullptr,
                                         speed ? speed + c0 : nullptr, n, st, axisym);
-        if (rc) return rc;
+        if (rc) break;
     }
-    return MEM_OK;
+    mem_host::scratch_end(ctx, st);
+    return rc;
 }
 
 int mem_flux(mem_ctx *ctx, const float *M, const float *beta, const float *gauge, float *F, float *speed,

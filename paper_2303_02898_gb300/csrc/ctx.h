@@ -54,14 +54,24 @@ struct mem_ctx {
     double *d_vtd = nullptr;  // [nx] x-node offsets | [nr] r-node offsets (block widths) | [K] cos | [K] sin
     float *d_vtf = nullptr;   // [nx] log w^GL of each x node | [nr] log(w^GL t_r / K) of each radial node
     double *d_dom0 = nullptr;                // the default domain (a_x, b_x, b_r, 0) on the device
-    // Scratch owned by the context (plain solver, flux).
+    // Scratch owned by the context (plain solver, flux at orders without a
+    // fused kernel, velocity-space flux), allocated once when the context is
+    // created.  Calls that use it are ordered on the GPU through scratch_ev
+    // (recorded after each use, waited on before the next, whatever the
+    // stream), and mu serialises their enqueueing.
     std::mutex mu;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
+    cudaEvent_t scratch_ev = nullptr;
+    bool scratch_ev_live = false;
 };
 
 namespace mem_host {
-int ensure_scratch(mem_ctx *ctx, size_t bytes);
+int reserve_scratch(mem_ctx *ctx, size_t bytes);                     // at context creation only
+int scratch_begin(mem_ctx *ctx, size_t bytes, cudaStream_t st);       // with ctx->mu held
+void scratch_end(mem_ctx *ctx, cudaStream_t st);                      // with ctx->mu held
+size_t plain_scratch_bytes(int Q);                                    // plain solve, one chunk
+size_t flux_scratch_bytes(int Q);                                     // dense flux, one chunk
 int gh_rule(int n, std::vector<double> &x, std::vector<double> &w);
 int solve_plain(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters, int64_t B,
                 const mem_solve_opts &o, cudaStream_t st, const unsigned char *active = nullptr);

@@ -33,6 +33,8 @@ extern "C" int mem_flux_noalloc(mem_ctx *ctx, const float *M, const float *beta,
     if (!ctx || B < 0) return MEM_EINVAL;
     if (B == 0) return MEM_OK;
     if (!M || !beta || !gauge) return MEM_EINVAL;
+    // velocity-space contexts build none of the dense tables this path reads
+    if (ctx->vel) return MEM_EINVAL;
     if (B > MEM_NOALLOC_MAX_CELLS || ctx->Q > MEM_NOALLOC_MAX_Q) return MEM_EINVAL;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return MEM_ECUDA;

@@ -22,7 +22,7 @@ namespace {
 
 constexpr int BLK = 256;
 constexpr int MAXJ = 16;  // nodes per thread: Q <= 4096
-constexpr int CHUNK = 1 << 17;
+constexpr int CHUNK = 1 << 16;
 
 __device__ __forceinline__ float block_reduce_max(float v, float *red) {
     v = warp_max(v);
@@ -453,14 +453,25 @@ void sgemm(const float *A, const float *Bm, float *C, int M, int N, int K, cudaS
 
 namespace mem_host {
 
+static size_t plain_need(int Q, size_t CH) {
+    return sizeof(float) * CH * ((size_t)Q + MEM_NCOL_SOLVE + 2 * NP + 2) + sizeof(int) * (CH * 4 + 2) + 16 * 256;
+}
+
+size_t plain_scratch_bytes(int Q) { return plain_need(Q, CHUNK); }
+size_t flux_scratch_bytes(int Q) { return sizeof(float) * (size_t)CHUNK * ((size_t)Q + MEM_NCOL_FLUX) + 1024; }
+
 int solve_plain(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters, int64_t B,
                 const mem_solve_opts &o, cudaStream_t st, const unsigned char *active) {
     std::lock_guard<std::mutex> lock(ctx->mu);
     const int Q = ctx->Q;
     const size_t CH = (size_t)std::min<int64_t>(B, CHUNK);
-    const size_t need = sizeof(float) * CH * ((size_t)Q + MEM_NCOL_SOLVE + 2 * NP + 2) + sizeof(int) * (CH * 4 + 2) + 16 * 256;
-    int rc = ensure_scratch(ctx, need);
+    int rc = scratch_begin(ctx, plain_need(Q, CH), st);
     if (rc) return rc;
+    struct End {
+        mem_ctx *c;
+        cudaStream_t s;
+        ~End() { scratch_end(c, s); }
+    } end_{ctx, st};
     char *p = (char *)ctx->scratch;
     auto take = [&](size_t bytes) { char *r = p; p += (bytes + 255) & ~(size_t)255; return r; };
     PlainState S;
@@ -519,7 +530,7 @@ int flux(mem_ctx *ctx, const float *M, const float *beta, const float *g, float 
     std::lock_guard<std::mutex> lock(ctx->mu);
     const int Q = ctx->Q;
     const size_t CH = (size_t)std::min<int64_t>(B, CHUNK);
-    int rc = ensure_scratch(ctx, sizeof(float) * CH * ((size_t)Q + MEM_NCOL_FLUX) + 1024);
+    int rc = scratch_begin(ctx, sizeof(float) * CH * ((size_t)Q + MEM_NCOL_FLUX) + 1024, st);
     if (rc) return rc;
     float *sigma = (float *)ctx->scratch;
     float *mom = sigma + ((CH * Q + 63) & ~(size_t)63);
@@ -527,9 +538,10 @@ int flux(mem_ctx *ctx, const float *M, const float *beta, const float *g, float 
         const int64_t n = std::min<int64_t>(CH, B - c0);
         rc = flux_bufs(ctx, M + c0 * NP, beta + c0 * NP, g + c0 * 6, F ? F + c0 * NP : nullptr,
                        speed ? speed + c0 : nullptr, n, sigma, mom, st);
-        if (rc) return rc;
+        if (rc) break;
     }
-    return MEM_OK;
+    scratch_end(ctx, st);
+    return rc;
 }
 
 }  // namespace mem_host

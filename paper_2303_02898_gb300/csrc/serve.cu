@@ -64,6 +64,22 @@ size_t cells_of(const std::vector<Req> &v) {
     return c;
 }
 
+// Retire every resident problem with error code rc (their device state is
+// gone); queued requests stay queued.
+void fail_resident(mem_server *sv, int rc) {
+    const double t = now_s();
+    for (auto &r : sv->resident) {
+        Done dn;
+        memset(&dn.r, 0, sizeof(dn.r));
+        dn.r.status = rc;
+        dn.r.steps = r.steps;
+        dn.r.ncells = r.p.ncells;
+        dn.r.latency_s = t - r.t_submit;
+        sv->done[r.id] = std::move(dn);
+    }
+    sv->resident.clear();
+}
+
 // Rebuild the packed batch for the current resident list; problems that were
 // already resident keep their state (copied device to device).
 int rebuild(mem_server *sv, const std::vector<Req> &old_list, cudaStream_t st) {
@@ -79,33 +95,47 @@ int rebuild(mem_server *sv, const std::vector<Req> &old_list, cudaStream_t st) {
     int rc = mem_host::batch_create(sv->ctx, ps.data(), (int)ps.size(), &nb);
     if (rc) {
         mem_host::batch_free(old);
+        fail_resident(sv, rc);
         return rc;
     }
     if (old) {
         std::map<uint64_t, int> where;
         for (int i = 0; i < (int)old_list.size(); ++i) where[old_list[i].id] = i;
+        cudaError_t e = cudaSuccess;
+        auto cp = [&](void *dst, const void *src, size_t bytes) {
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st);
+        };
         for (int i = 0; i < (int)sv->resident.size(); ++i) {
             auto it = where.find(sv->resident[i].id);
             if (it == where.end()) continue;
             const ShockProb &src = old->hprm[it->second], &dst = nb->hprm[i];
             const size_t nc = (size_t)src.n + 2;
-            MEM_CUDA_TRY(cudaMemcpyAsync(nb->M + (size_t)dst.off * NP, old->M + (size_t)src.off * NP, sizeof(float) * nc * NP, cudaMemcpyDeviceToDevice, st));
-            MEM_CUDA_TRY(cudaMemcpyAsync(nb->beta + (size_t)dst.off * NP, old->beta + (size_t)src.off * NP, sizeof(float) * nc * NP, cudaMemcpyDeviceToDevice, st));
-            MEM_CUDA_TRY(cudaMemcpyAsync(nb->g + (size_t)dst.off * 6, old->g + (size_t)src.off * 6, sizeof(float) * nc * 6, cudaMemcpyDeviceToDevice, st));
-            MEM_CUDA_TRY(cudaMemcpyAsync(nb->speed + dst.off, old->speed + src.off, sizeof(float) * nc, cudaMemcpyDeviceToDevice, st));
-            MEM_CUDA_TRY(cudaMemcpyAsync(nb->status + dst.off, old->status + src.off, sizeof(int32_t) * nc, cudaMemcpyDeviceToDevice, st));
-            MEM_CUDA_TRY(cudaMemcpyAsync(nb->iters + dst.off, old->iters + src.off, sizeof(int32_t) * nc, cudaMemcpyDeviceToDevice, st));
-            MEM_CUDA_TRY(cudaMemcpyAsync(nb->sc + i, old->sc + it->second, sizeof(ShockScalars), cudaMemcpyDeviceToDevice, st));
+            cp(nb->M + (size_t)dst.off * NP, old->M + (size_t)src.off * NP, sizeof(float) * nc * NP);
+            cp(nb->beta + (size_t)dst.off * NP, old->beta + (size_t)src.off * NP, sizeof(float) * nc * NP);
+            cp(nb->g + (size_t)dst.off * 6, old->g + (size_t)src.off * 6, sizeof(float) * nc * 6);
+            cp(nb->speed + dst.off, old->speed + src.off, sizeof(float) * nc);
+            cp(nb->status + dst.off, old->status + src.off, sizeof(int32_t) * nc);
+            cp(nb->iters + dst.off, old->iters + src.off, sizeof(int32_t) * nc);
+            cp(nb->sc + i, old->sc + it->second, sizeof(ShockScalars));
             if (src.scheme != MEM_SCHEME_LF) {
                 // the interface solves' warm starts (Lax-Wendroff / FLIC)
-                MEM_CUDA_TRY(cudaMemcpyAsync(nb->betaI + (size_t)dst.off * NP, old->betaI + (size_t)src.off * NP, sizeof(float) * nc * NP, cudaMemcpyDeviceToDevice, st));
-                MEM_CUDA_TRY(cudaMemcpyAsync(nb->gI + (size_t)dst.off * 6, old->gI + (size_t)src.off * 6, sizeof(float) * nc * 6, cudaMemcpyDeviceToDevice, st));
-                MEM_CUDA_TRY(cudaMemcpyAsync(nb->statusI + dst.off, old->statusI + src.off, sizeof(int32_t) * nc, cudaMemcpyDeviceToDevice, st));
-                MEM_CUDA_TRY(cudaMemcpyAsync(nb->itersI + dst.off, old->itersI + src.off, sizeof(int32_t) * nc, cudaMemcpyDeviceToDevice, st));
+                cp(nb->betaI + (size_t)dst.off * NP, old->betaI + (size_t)src.off * NP, sizeof(float) * nc * NP);
+                cp(nb->gI + (size_t)dst.off * 6, old->gI + (size_t)src.off * 6, sizeof(float) * nc * 6);
+                cp(nb->statusI + dst.off, old->statusI + src.off, sizeof(int32_t) * nc);
+                cp(nb->itersI + dst.off, old->itersI + src.off, sizeof(int32_t) * nc);
             }
         }
-        MEM_CUDA_TRY(cudaStreamSynchronize(st));
+        const cudaError_t es = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = es;
         mem_host::batch_free(old);
+        if (e != cudaSuccess) {
+            // neither batch survives a failed copy: the resident problems
+            // are retired with the error, and the server stays consistent
+            cudaGetLastError();
+            mem_host::batch_free(nb);
+            fail_resident(sv, MEM_ECUDA);
+            return MEM_ECUDA;
+        }
     }
     sv->batch = nb;
     return MEM_OK;

@@ -2,7 +2,7 @@
 
 This module draws random numbers only (numpy PCG64); it holds none of the
 method's arithmetic.  Every workload below is shaped like the paper's runs
-(35 moments, 1D normal shocks up to Mach 10) and is described in the design doc.
+(35 moments, 1D normal shocks up to Mach 10).
 """
 from dataclasses import dataclass
 

@@ -48,8 +48,8 @@ def main():
     bh0 = e0.copy()
     bt0 = e0.copy()
     bt0[:, O.index_of(1, 0, 0)] = gH[:, 0]
-    bh, sth, _ = O.solve_batch(q, e0, beta0=bh0, tol=1e-13, g=gH)
-    bt, stt, _ = O.solve_batch(q, Mt, beta0=bt0, tol=1e-13, g=g0)
+    bh, sth, _ = O.solve_batch(q, e0, beta0=bh0, tol=1e-13, g=gH, final_step=True)
+    bt, stt, _ = O.solve_batch(q, Mt, beta0=bt0, tol=1e-13, g=g0, final_step=True)
     assert all(s & 1 for s in sth) and all(s & 1 for s in stt)
     out = {"_source": "oracle/mem_oracle.c (or_solve, or_transform_M), Section 4 Fig. 2 and Fig. 3 setups",
            "rule": RULE, "mach": MACHS, "beta64_hermite": bh.tolist(), "beta64_trivial": bt.tolist()}
@@ -69,7 +69,7 @@ def main():
     Ms[:, O.index_of(3, 0, 0)] = np.linspace(0.0, 0.5, n)
     b0 = np.zeros((n, 35))
     b0[:, 0] = 1.0
-    bs, sts, its = O.solve_batch(q, Ms, beta0=b0, tol=1e-13, g=g0[:1].repeat(n, 0))
+    bs, sts, its = O.solve_batch(q, Ms, beta0=b0, tol=1e-13, g=g0[:1].repeat(n, 0), final_step=True)
     assert all(s & 1 for s in sts)
     out["m4"] = np.linspace(0.0, 0.5, n).tolist()
     out["beta64_m4_sweep"] = bs.tolist()

@@ -16,6 +16,12 @@ pytestmark = pytest.mark.gpu
 
 RES_TOL = 1e-5
 PROFILE_TOL = 1e-3
+# Algorithm 1 returns beta one Newton direction behind its last pass (the
+# default on both sides); final_step = 1 applies that direction, which the
+# 1e-5 residual bar needs (the FP64 oracle leaves up to 2.5e-4 on the
+# standalone targets in the literal order).  Acceptance tests use the
+# extension on both sides; the literal order has its own tests below.
+EXT = dict(final_step=1)
 
 
 @pytest.fixture(scope="module")
@@ -127,12 +133,12 @@ def _solve(mem, ctx, M, dev, impl, beta0=None, **kw):
 def test_solve_perturbed_moments(O, mem, ctx8, dev, impl):
     from paper_2303_02898_gb300 import workloads
     M = workloads.perturbed_hermite_moments(1003, seed=3, scale=0.04)   # ragged: not a multiple of 4 or 32
-    Mf, b, st, it = _solve(mem, ctx8, M, dev, impl)
+    Mf, b, st, it = _solve(mem, ctx8, M, dev, impl, **EXT)
     ok = (st & (mem.ST_CONVERGED | mem.ST_STAGNATED)) != 0
     assert ok.all(), np.unique(st, return_counts=True)
     assert (it >= 1).all() and (it <= 20).all()
     assert np.all(b[:, 0] == Mf[:, 0])
-    bo, sto, ito = O.solve_batch(8, Mf)
+    bo, sto, ito = O.solve_batch(8, Mf, final_step=True)
     res = O.residual_batch(8, b, Mf)
     assert res.max() <= RES_TOL, res.max()
     assert np.abs(b[:, 1:] - bo[:, 1:]).max() <= 1e-4
@@ -154,12 +160,12 @@ def test_targets_and_solve_match_oracle(O, mem, dev, order, ctx8, ctx12):
     assert np.abs(Mgn - Mo).max() <= 2e-5, np.abs(Mgn - Mo).max()
     assert np.abs(ggn - go).max() <= 2e-5 * (1 + np.abs(go).max())
     for impl in (0, 1):
-        _, b, st, it = _solve(mem, ctx, Mg, dev, impl)
+        _, b, st, it = _solve(mem, ctx, Mg, dev, impl, **EXT)
         ok = (st & (mem.ST_CONVERGED | mem.ST_STAGNATED)) != 0
         assert ok.all(), (impl, np.unique(st, return_counts=True))
         res = O.residual_batch(order, b, Mgn)
         assert res.max() <= RES_TOL, (impl, res.max(), np.argmax(res))
-        bo, _, _ = O.solve_batch(order, Mgn)
+        bo, _, _ = O.solve_batch(order, Mgn, final_step=True)
         assert np.abs(b[:, 1:] - bo[:, 1:]).max() <= 5e-3, (impl, np.abs(b[:, 1:] - bo[:, 1:]).max())
 
 
@@ -179,12 +185,52 @@ def test_solve_edge_cases(O, mem, ctx8, dev):
     # warm start at the solution takes one pass
     from paper_2303_02898_gb300 import workloads
     Mw = workloads.perturbed_hermite_moments(64, seed=9, scale=0.03)
-    Mf, b1, _, _ = _solve(mem, ctx8, Mw, dev, 1)
-    _, b2, st2, it2 = _solve(mem, ctx8, Mf, dev, 1, beta0=b1)
+    Mf, b1, _, _ = _solve(mem, ctx8, Mw, dev, 1, **EXT)
+    _, b2, st2, it2 = _solve(mem, ctx8, Mf, dev, 1, beta0=b1, **EXT)
     assert (it2 <= 2).all() and np.abs(b2 - b1).max() < 1e-4
-    # the literal order of Algorithm 1 (no final step) is one option away
-    _, b3, st3, it3 = _solve(mem, ctx8, Mf, dev, 1, final_step=0)
-    assert (st3 & mem.ST_CONVERGED).all()
+    # the default is the literal order of Algorithm 1 (no final step): the
+    # same passes, beta one Newton direction behind
+    _, b3, st3, it3 = _solve(mem, ctx8, Mf, dev, 1)
+    _, b4, st4, it4 = _solve(mem, ctx8, Mf, dev, 1, **EXT)
+    assert (st3 & mem.ST_CONVERGED).all() and np.array_equal(it3, it4)
+    assert 0.0 < np.abs(b3 - b4).max() < 1e-3
+
+
+@pytest.mark.parametrize("impl", [0, 1])
+@pytest.mark.parametrize("order", [8, 12])
+@pytest.mark.parametrize("workload", ["perturbed", "targets"])
+def test_literal_order_matches_oracle(O, mem, dev, ctx8, ctx12, impl, order, workload):
+    """Algorithm 1 as printed (beta returned without the last direction), on
+    both sides.  Where the GPU and the oracle take the same number of passes
+    they return the same iterate, so beta agrees element-wise; the moment
+    residual of that iterate, evaluated by the oracle in FP64, is one Newton
+    step's worth and matches the oracle's own literal-order residual."""
+    from paper_2303_02898_gb300 import workloads
+    ctx = ctx8 if order == 8 else ctx12
+    if workload == "perturbed":
+        M = workloads.perturbed_hermite_moments(517, seed=31, scale=0.04)
+        Mt = T32(M, dev)
+    else:
+        t = workloads.solve_targets(257, seed=13)
+        Mt = torch.zeros(len(t.T), 35, device=dev)
+        gg = torch.zeros(len(t.T), 6, device=dev)
+        ctx.targets(T32(t.v, dev), T32(t.T, dev), T32(t.a, dev), T32(t.b, dev), Mt, gg, gen_order=24)
+    Mf, b, st, it = _solve(mem, ctx, Mt, dev, impl, final_step=0)
+    assert ((st & (mem.ST_CONVERGED | mem.ST_STAGNATED)) != 0).all()
+    bo, sto, ito = O.solve_batch(order, Mf, final_step=False)
+    same = it == ito
+    assert same.mean() > 0.85, same.mean()
+    scale = 1.0 + np.abs(bo[:, 1:]).max(axis=1)
+    err = np.abs(b[:, 1:] - bo[:, 1:]).max(axis=1) / scale
+    assert err[same].max() <= (1e-4 if workload == "perturbed" else 5e-3), err[same].max()
+    res, res_o = O.residual_batch(order, b, Mf), O.residual_batch(order, bo, Mf)
+    # the literal order's residual is set by the last direction, the same
+    # on both sides where the pass counts agree
+    assert np.all(res[same] <= 1.5 * res_o[same] + RES_TOL), np.max(res[same] - 1.5 * res_o[same])
+    print("literal order %s q%d impl %d: passes equal on %.3f; residual median %.2e p99 %.2e max %.2e "
+          "(oracle max %.2e); cells above 1e-5: %d of %d" % (
+              workload, order, impl, same.mean(), np.median(res), np.percentile(res, 99), res.max(), res_o.max(),
+              int((res > RES_TOL).sum()), len(res)))
 
 
 def test_plain_and_fused_agree(O, mem, ctx8, dev):
@@ -361,3 +407,40 @@ def test_full_size_solve_sampled(O, mem, ctx8, dev):
     res = O.residual_batch(8, b, M)
     ok = conv[idx]
     assert res[ok].max() <= RES_TOL, res.max()
+
+
+def test_context_scratch_ordered_across_streams(O, mem, dev):
+    """The dense flux path (and the plain back-end) share the context's
+    scratch.  Calls made on two streams of one context are ordered on the GPU
+    by the context's event, so each result equals the same call made alone."""
+    from paper_2303_02898_gb300 import workloads
+    ctx = mem.Context(10)   # no fused kernel at order 10: the flux uses the scratch
+    rng = np.random.default_rng(43)
+    Ms, bs, gs = [], [], []
+    for k, B in enumerate((3000, 2000, 2500)):
+        M = workloads.perturbed_hermite_moments(B, seed=44 + k, scale=0.04)
+        Mt = T32(M, dev)
+        b = torch.zeros_like(Mt)
+        ctx.solve(Mt, b, impl=mem.IMPL_PLAIN)
+        Ms.append(Mt)
+        bs.append(b)
+        gs.append(T32(np.concatenate([rng.normal(0, 1.0, (B, 3)), np.exp(rng.uniform(-0.5, 0.5, (B, 3)))], 1), dev))
+    torch.cuda.synchronize()
+
+    def run(streams):
+        outs = [(torch.zeros_like(M), torch.zeros(M.shape[0], device=dev)) for M in Ms]
+        for s in streams:
+            s.wait_stream(torch.cuda.current_stream())
+        for k in range(3):   # flux 0 and 2 on the first stream, flux 1 on the second
+            st = streams[k % 2]
+            with torch.cuda.stream(st):
+                ctx.flux(Ms[k], bs[k], gs[k], outs[k][0], outs[k][1], stream=st)
+        torch.cuda.synchronize()
+        return [np64(x) for o in outs for x in o]
+
+    s0 = torch.cuda.current_stream()
+    alone = run([s0, s0])
+    both = run([torch.cuda.Stream(), torch.cuda.Stream()])
+    for x, y in zip(alone, both):
+        assert np.array_equal(x, y)
+    ctx.close()

@@ -54,7 +54,7 @@ def vctx(mem, dom):
 def states(O, dom):
     """Interior cells of the oracle's Mach-10 tanh initial state (two-Maxwellian
     mixtures in their Hermite gauges) with their FP64 parameters."""
-    so = O.Shock(MACH, 24, -15.0, 15.0, order=RULE, ic="tanh", thickness=15.7)
+    so = O.Shock(MACH, 24, -15.0, 15.0, order=RULE, ic="tanh", thickness=15.7, final_step=True)
     return so.M[1:-1].copy(), so.g[1:-1].copy(), so.beta[1:-1].copy()
 
 
@@ -80,12 +80,14 @@ def test_velocity_solve_matches_oracle(O, mem, vctx, states, dev):
     beta = torch.zeros(B, 35, device=dev)
     st = torch.zeros(B, dtype=torch.int32, device=dev)
     it = torch.zeros(B, dtype=torch.int32, device=dev)
-    vctx.solve_gauge(Mt, beta, gt, st, it)
+    # the acceptance bar is on the solution: the final Newton step applied
+    vctx.solve_gauge(Mt, beta, gt, st, it, final_step=1)
     stn, bn = np64(st).astype(int), np64(beta)
     assert np.all(stn & 3), stn
     assert np.all(stn & 8 == 0)
     Mf, gf = np64(Mt), np64(gt)
     _, _, beta_o = states
+    relaxed = 0
     for c in range(B):
         res = O.residual(RULE, bn[c], Mf[c], gf[c])
         # Storing the exact (FP64) solution in FP32 already leaves this
@@ -93,6 +95,10 @@ def test_velocity_solve_matches_oracle(O, mem, vctx, states, dev):
         # 1e-5, so no FP32 beta can meet 1e-5 there.
         floor = O.residual(RULE, beta_o[c].astype(np.float32).astype(np.float64), Mf[c], gf[c])
         assert res <= max(RES_TOL, 4.0 * floor), (c, res, floor)
+        relaxed += int(res > RES_TOL)
+    # cells that needed the relaxed bar (above 1e-5, below 4x the floor)
+    print("velocity solve: %d of %d cells above 1e-5 (within 4x their FP32 floor)" % (relaxed, B))
+    assert relaxed <= B // 4, relaxed
 
 
 def test_velocity_solve_rejects_plain_entry(mem, vctx, dev):

@@ -191,7 +191,7 @@ def test_newton_recovers_parameters(O):
     for trial in range(5):
         bstar = random_beta(O, rng, 0.1)
         M = _moments_of(O, 8, bstar, n=1.7)
-        b, st, it, res, lam = O.solve(8, M)
+        b, st, it, res, lam = O.solve(8, M, final_step=True)
         assert st & O.ST_CONVERGED
         assert it <= 12
         assert b[0] == pytest.approx(1.7)
@@ -560,10 +560,16 @@ def test_targets_are_solvable(O):
     from paper_2303_02898_gb300 import workloads
     t = workloads.solve_targets(16, seed=0)
     M, g = O.target_batch(24, t.v, t.T, t.a, t.b)
-    beta, st, it = O.solve_batch(8, M)
+    beta, st, it = O.solve_batch(8, M, final_step=True)
     assert ((st & (O.ST_CONVERGED | O.ST_STAGNATED)) != 0).all()
     res = O.residual_batch(8, beta, M)
     assert res.max() < 1e-6
+    # Algorithm 1's own order stops one Newton direction short: same passes,
+    # a larger residual (the decrement bounds the objective, not the moments)
+    beta2, st2, it2 = O.solve_batch(8, M)
+    assert np.array_equal(it2, it)
+    res2 = O.residual_batch(8, beta2, M)
+    assert np.all(res2 >= res) and res2.max() < 1e-2
 
 
 def test_golden_constants_and_rh(O):
@@ -695,7 +701,7 @@ def test_velocity_rule_solve_recovers_moments(O):
     g = np.array([6.0, 0.0, 0.0, 4.0, 3.5, 3.5])
     _, m, _, _, _ = O.expect(204, beta_true, g)
     M = 2.0 * m
-    beta, st, it, res, lam = O.solve(204, M, g=g)
+    beta, st, it, res, lam = O.solve(204, M, g=g, final_step=True)
     assert st & 1
     assert O.residual(204, beta, M, g) < 1e-8
     assert np.abs(beta[1:] - beta_true[1:]).max() < 1e-5
@@ -773,8 +779,8 @@ def test_gauge_study_maxwellian_moments_and_invariance(O):
             closed[k] = v ** int(a) / math.sqrt(math.factorial(int(a)))
     assert np.abs(Mt - closed).max() < 1e-12
     u0 = _uniform_beta(O)
-    bh, sh, ih, _, _ = O.solve(206, e0, beta0=u0, tol=1e-11, g=gH)
-    bt, st, it, _, _ = O.solve(206, Mt, beta0=u0, tol=1e-11, g=g0)
+    bh, sh, ih, _, _ = O.solve(206, e0, beta0=u0, tol=1e-11, g=gH, final_step=True)
+    bt, st, it, _, _ = O.solve(206, Mt, beta0=u0, tol=1e-11, g=g0, final_step=True)
     assert sh & 1 and st & 1
     assert ih == it
     assert np.abs(O.transform_beta(g0, gH, bh) - bt).max() < 1e-8
@@ -783,8 +789,8 @@ def test_gauge_study_maxwellian_moments_and_invariance(O):
     _vel_rule(O, 207, (-30.7, 37.3, 34.0), nbx=16, nbr=12, ng=8, K=10)
     maxw = e0.copy()
     maxw[O.index_of(1, 0, 0)] = v
-    bt, st, _, _, _ = O.solve(207, Mt, beta0=maxw, tol=1e-13, g=g0)
-    bh, sh, _, _, _ = O.solve(207, e0, beta0=e0, tol=1e-13, g=gH)
+    bt, st, _, _, _ = O.solve(207, Mt, beta0=maxw, tol=1e-13, g=g0, final_step=True)
+    bh, sh, _, _, _ = O.solve(207, e0, beta0=e0, tol=1e-13, g=gH, final_step=True)
     assert st & 1 and sh & 1
     assert np.abs(bt - maxw).max() < 1e-3  # 3.9e-4 on beta_(1,0,0): quadrature error
     assert np.abs(bh - e0).max() < 1e-3
@@ -802,7 +808,7 @@ def test_gauge_study_golden_matches_oracle(O):
     v = math.sqrt(5.0 / 3.0) * d["mach"][0]
     e0 = np.zeros(35)
     e0[0] = 1.0
-    b, st, _, _, _ = O.solve(r["rule_id"], e0, beta0=e0, tol=1e-13, g=[v, 0, 0, 1, 1, 1])
+    b, st, _, _, _ = O.solve(r["rule_id"], e0, beta0=e0, tol=1e-13, g=[v, 0, 0, 1, 1, 1], final_step=True)
     assert st & 1
     assert np.abs(b - np.array(d["beta64_hermite"][0])).max() < 1e-10
 
@@ -829,8 +835,8 @@ def test_nine_statistic_solve_equals_35_product_solve(O):
         beta = alpha @ v
         _, m, _, _, _ = O.expect(208, beta, g)
         M35 = alpha[0] * m
-        a, st, _, _ = O.solve_axi(209, v @ M35, g=g, tol=1e-12)
-        b35, st35, _, _, _ = O.solve(208, M35, g=g, tol=1e-12)
+        a, st, _, _ = O.solve_axi(209, v @ M35, g=g, tol=1e-12, final_step=True)
+        b35, st35, _, _, _ = O.solve(208, M35, g=g, tol=1e-12, final_step=True)
         assert st & 1 and st35 & 1
         assert np.abs(a - alpha).max() < 1e-10
         assert np.abs(b35[1:] - (a @ v)[1:]).max() < 1e-10

@@ -372,7 +372,9 @@ def run_gauge_study(mem, torch, np):
     gauge vs Hermite gauge, FP32, tol 1e-6 and 1e-9, maxI 500; and the
     log mean-square error of the FP32 parameters against FP64 ones (oracle,
     stored).  Velocity-space rule on the paper's box, 16 x 12 blocks of
-    8-point Gauss-Legendre, 10 azimuths."""
+    8-point Gauss-Legendre, 10 azimuths.  The solves return their solution
+    (final_step = 1) so that the comparison with the exact FP64 parameters
+    measures rounding, not the unapplied last Newton direction."""
     machs = list(range(2, 13))
     B = len(machs)
     vctx = mem.Context.velocity(GAUGE_BOX, nbx=16, nbr=12, ng=8, K=10)
@@ -383,7 +385,7 @@ def run_gauge_study(mem, torch, np):
         beta = beta0.clone()
         st = torch.zeros(M.shape[0], dtype=torch.int32, device=M.device)
         it = torch.zeros_like(st)
-        vctx.solve_gauge(M, beta, g, st, it, tol=tol, maxI=500)
+        vctx.solve_gauge(M, beta, g, st, it, tol=tol, maxI=500, final_step=1)
         torch.cuda.synchronize()
         itn, stn, bn = it.cpu().numpy(), st.cpu().numpy(), beta.cpu().numpy()
         row = {"passes_hermite": itn[:B].tolist(), "passes_trivial": itn[B:].tolist(),
@@ -418,7 +420,7 @@ def run_newton_study(mem, torch, np, n=26):
         beta[:, 0] = 1.0
         st = torch.zeros(n, dtype=torch.int32, device=dev)
         it = torch.zeros_like(st)
-        vctx.solve_gauge(M, beta, g, st, it, tol=1e-8, maxI=500, max_lambda=ml)
+        vctx.solve_gauge(M, beta, g, st, it, tol=1e-8, maxI=500, max_lambda=ml, final_step=1)
         torch.cuda.synchronize()
         bn = beta.cpu().numpy()
         row = {"passes": it.cpu().numpy().tolist(), "status": _status_letters(st.cpu().numpy()),
@@ -437,7 +439,7 @@ def run_newton_study(mem, torch, np, n=26):
         beta = beta0.clone()
         st = torch.zeros(B, dtype=torch.int32, device=dev)
         it = torch.zeros_like(st)
-        vctx.solve_gauge(M, beta, g, st, it, tol=1e-9, maxI=500, max_lambda=ml)
+        vctx.solve_gauge(M, beta, g, st, it, tol=1e-9, maxI=500, max_lambda=ml, final_step=1)
         torch.cuda.synchronize()
         stn = st.cpu().numpy()
         row[name] = {"passes": it.cpu().numpy().tolist(), "status": _status_letters(stn),

@@ -417,6 +417,28 @@ int mem_serve_stats(mem_server *sv, int32_t *queued, int32_t *resident, int32_t 
 
 void mem_serve_destroy(mem_server *sv);
 
+/* ---------------------------------------------------------------------- */
+/* Measurement services (no counterpart in the paper): the rates the
+ * roofline fractions of the library's kernels are quoted against. */
+
+/* One timed micro-benchmark launch on the current device (synchronous; it
+ * allocates and frees a few bytes of device memory):
+ *   kind 0: FP32 FMA (work = flops), 1: MUFU ex2.approx (work = exp2
+ *   evaluations), 2: tcgen05.mma kind::f16 with BF16 operands, 128 x 256 x 16
+ *   per instruction (work = flops), 3: tcgen05.mma kind::tf32, 128 x 256 x 8.
+ * iters (1 .. 2^24) scales the work; *seconds is the launch's CUDA-event
+ * time.  MEM_EINVAL on bad arguments, MEM_ECUDA on a CUDA error or when the
+ * tensor cores did not signal completion within the kernel's bounded wait. */
+int mem_bench_peak(int kind, int64_t iters, double *seconds, double *work);
+
+/* D = A B^T computed by one CTA's tensor cores (tcgen05.mma, operands in
+ * shared memory in the library's K-major layout, accumulator in TMEM):
+ * kind 1 BF16 operands, 2 TF32 operands, FP32 accumulation.  A_host
+ * [128][64], B_host [N][64], D_host [128][N] row-major float host arrays;
+ * N a multiple of 16 in 16..256.  Synchronous.  A check of the operand and
+ * accumulator layouts that the tensor-core kernels rely on. */
+int mem_tc_selftest(int kind, int N, const float *A_host, const float *B_host, float *D_host);
+
 #ifdef __cplusplus
 }
 #endif

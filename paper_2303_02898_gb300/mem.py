@@ -94,6 +94,11 @@ def lib():
         L.mem_serve_create.argtypes = [_P, ctypes.c_size_t, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P]
         L.mem_serve_progress.argtypes = [_P, ctypes.c_int, _P]
         L.mem_serve_poll.argtypes = [_P, ctypes.c_uint64, _P, _P, _P, _P]
+        L.mem_bench_peak.restype = ctypes.c_int
+        L.mem_bench_peak.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]
+        L.mem_tc_selftest.restype = ctypes.c_int
+        L.mem_tc_selftest.argtypes = [ctypes.c_int, ctypes.c_int, _P, _P, _P]
         _lib = L
     return _lib
 
@@ -386,3 +391,26 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+PEAK_FMA, PEAK_EXP2, PEAK_TC_BF16, PEAK_TC_TF32 = 0, 1, 2, 3
+
+
+def bench_peak(kind, iters):
+    """mem_bench_peak: (seconds, work) of one timed micro-benchmark launch on
+    the current device (work = flops, or exp2 evaluations for PEAK_EXP2)."""
+    sec, work = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mem_bench_peak(kind, iters, ctypes.byref(sec), ctypes.byref(work)), "mem_bench_peak")
+    return sec.value, work.value
+
+
+def tc_selftest(kind, A, B):
+    """mem_tc_selftest: D = A B^T through the tensor cores (kind 1 = BF16,
+    2 = TF32 operands); A [128][64], B [N][64] float32 host arrays."""
+    import numpy as np
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    N = B.shape[0]
+    D = np.zeros((128, N), dtype=np.float32)
+    _check(lib().mem_tc_selftest(kind, N, A.ctypes.data, B.ctypes.data, D.ctypes.data), "mem_tc_selftest")
+    return D

@@ -31,6 +31,8 @@ def test_opts_defaults_are_the_papers():
     assert o.tol == pytest.approx(1e-8) and o.maxI == 500 and o.maxT == 25
     assert o.c_armijo == pytest.approx(5e-4) and o.atol == pytest.approx(5e-6) and o.rtol == pytest.approx(5e-5)
     assert o.lambda0 == pytest.approx(1e-3) and o.lambda_mul == 10 and o.alpha_min == pytest.approx(1e-6)
+    # Algorithm 1 returns beta without the direction of its last pass
+    assert o.final_step == 0
     p = mem.default_shock_params()
     assert p.cfl == 0.5 and p.Pr == pytest.approx(2 / 3) and p.gamma == pytest.approx(5 / 3)
 

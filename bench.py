@@ -27,8 +27,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MEM cell-solves/s & cell-updates/s at Ma10, tuned vs plain FP32; p99 latency"
 UNIT = "cell-solves/s"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
 
 
 def parse():
@@ -43,7 +41,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--case", nargs="+", default=None, metavar=("NAME", "N"),
                     help="kernel-focused run for profilers instead of the benchmark: "
-                         "solve [cells] | ensemble [steps] | mach10 [steps] | mach10flic [steps]")
+                         "solve|mixed|plain [cells] | ensemble [steps] | mach10 [steps] | mach10flic [steps]")
     return ap.parse_args()
 
 
@@ -124,9 +122,43 @@ def fused_flops_per_pass(n):
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_fused_solve<8> launch
-# on the headline workload (2^20 cells), from one ncu capture of the current
-# kernel; None once the kernel changes.
-TRAFFIC_BYTES = 402.26e6
+# on the headline workload (2^20 cells) from one ncu capture, keyed to the
+# SHA-256 of the kernel's sources at that capture: a changed kernel reports
+# traffic None until it is captured again.
+TRAFFIC = {"kernel": "k_fused_solve<8>", "bytes": 402.26e6,
+           "sources": ("fused.cu", "sumfact.cuh", "common.cuh"),
+           "sha256": None}
+
+
+def kernel_sources_sha(names):
+    import hashlib
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2303_02898_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def traffic_bytes():
+    sha = kernel_sources_sha(TRAFFIC["sources"])
+    return TRAFFIC["bytes"] if sha == TRAFFIC["sha256"] else None
+
+
+def measured_peaks(mem):
+    """The library's micro-benchmarks on this GPU (one launch each, CUDA
+    events): FP32 FMA and TF32 / BF16 tensor-core flop/s, exp2 evaluations/s."""
+    out = {}
+    for key, kind, iters in (("fp32_tflops", mem.PEAK_FMA, 4000), ("exp2_tera_per_s", mem.PEAK_EXP2, 2000),
+                             ("bf16_tc_tflops", mem.PEAK_TC_BF16, 20000), ("tf32_tc_tflops", mem.PEAK_TC_TF32, 20000)):
+        best = 0.0
+        for _ in range(3):
+            sec, work = mem.bench_peak(kind, iters)
+            best = max(best, work / sec / 1e12)
+        out[key] = best
+    out["how"] = ("mem_bench_peak: FP32 FMA chains / ex2.approx chains on 152 x 4 blocks of 512 threads; "
+                  "tcgen05.mma 128x256 (K 16 BF16 / 8 TF32) back to back from SMEM into TMEM, one CTA per SM; "
+                  "best of 3 launches")
+    return out
 
 SHOCK_MACH = 3.0   # largest Mach the 8^3 Gauss-Hermite Hermite-gauge rule keeps stable from a step
 
@@ -548,6 +580,44 @@ def run_serving(mem, ctx, torch, np, nreq=32, max_steps=100, chunk=10):
                                             "throughput": upd2 / wall2, "wall_s": wall2}}}
 
 
+def residual_stats(ctx, torch, np, M, beta, n=65536):
+    """FP64 relative moment residuals (mem_residual64 on the GPU) of the first
+    n cells: the acceptance quantity (<= 1e-5), per result."""
+    n = min(n, M.shape[0])
+    res = torch.zeros(n, dtype=torch.float64, device=M.device)
+    ctx.residual64(M[:n], beta[:n].contiguous(), res)
+    r = res.cpu().numpy()
+    return {"cells": n, "max": float(r.max()), "median": float(np.median(r)), "p99": float(np.percentile(r, 99)),
+            "above_1e-5": int((r > 1e-5).sum())}
+
+
+def run_mixed(mem, ctx, torch, np, M, beta, st, it, plain_value, B):
+    """The mixed-precision back-end (tensor-core contraction: split TF32
+    moments, TF32 Hessian; FP64 residual of failed cells) on the headline
+    batch, against the plain FP32 back-end."""
+    opts = mem.default_opts(impl=mem.IMPL_MIXED, final_step=1)
+    beta.zero_()
+    ctx.solve(M, beta, st, it, opts=opts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n = 2
+    for _ in range(n):
+        beta.zero_()
+        ctx.solve(M, beta, st, it, opts=opts)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / n
+    stn, itn = st.cpu().numpy(), it.cpu().numpy()
+    v = B / (ms * 1e-3)
+    return {"mixed_tc": {"value": v, "unit": "cell-solves/s", "ms_per_step": ms,
+                         "mean_passes": float(itn.mean()),
+                         "converged": float(np.mean((stn & 3) != 0)),
+                         "fp64_ok_cells": int(((stn & mem.ST_FP64_OK) != 0).sum()),
+                         "residual_fp64": residual_stats(ctx, torch, np, M, beta),
+                         "precision": "moments split TF32 (3 products), Hessian 1 TF32 product, FP32 accumulation "
+                                      "on tcgen05; line search, Cholesky and solves FP32"},
+            "mixed_over_plain_fp32": v / plain_value}
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -620,6 +690,8 @@ def run_case(name, n):
     device (seeded, synthetic), two warm-up iterations, then the timed ones;
     one line with the mean time per iteration (CUDA events).
       solve [cells]       mem_solve, fused back-end, 8^3 rule (default 2^20 cells)
+      mixed [cells]       the same with the mixed (tensor-core) back-end
+      plain [cells]       the same with the plain FP32 back-end
       ensemble [steps]    256-problem shock batch, 8^3 rule (Mach <= 3)
       mach10 [steps]      256-problem Mach 1.2-10 batch, velocity-space rule
       mach10flic [steps]  the same batch with FLIC interface fluxes"""
@@ -627,7 +699,8 @@ def run_case(name, n):
     import torch
     from paper_2303_02898_gb300 import mem, workloads
     dev = torch.device("cuda:0")
-    if name == "solve":
+    if name in ("solve", "mixed", "plain"):
+        impl = {"solve": mem.IMPL_FUSED, "mixed": mem.IMPL_MIXED, "plain": mem.IMPL_PLAIN}[name]
         cells = n or (1 << 20)
         ctx = mem.Context(8)
         t = workloads.solve_targets(cells, seed=0)
@@ -640,11 +713,11 @@ def run_case(name, n):
 
         def run():
             beta.zero_()
-            ctx.solve(M, beta, st)
+            ctx.solve(M, beta, st, impl=impl, final_step=1)
         for _ in range(2):
             run()
         ms = _timed_ms(torch, run, 2)
-        print("solve cells=%d ms=%.3f cell-solves/s=%.4g" % (cells, ms, cells / ms * 1e3))
+        print("%s cells=%d ms=%.3f cell-solves/s=%.4g" % (name, cells, ms, cells / ms * 1e3))
         ctx.close()
     elif name == "ensemble":
         ctx = mem.Context(8)
@@ -765,9 +838,26 @@ def main():
     stn = st.cpu().numpy()
     passes = int(itn.sum())
     flops = passes * fused_flops_per_pass(args.order)
-    peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+    peaks = measured_peaks(mem)
+    peak_fp32 = peaks["fp32_tflops"]
     achieved = flops / (kern_ms * 1e-3) / 1e12
+    # the dense contraction the method defines (exponent 2 x 35 Q per
+    # evaluation, moments + packed Hessian 2 Q 665, Cholesky and solves):
+    # 0.77 MFLOP per cell-iteration at Q = 512, against the TF32 tensor rate
+    Q = args.order ** 3
+    dense_per_pass = 2 * 35 * Q * 2 + 2 * Q * 665 + 34 ** 3 / 3 + 2 * 34 * 34
+    dense_achieved = passes * dense_per_pass / (kern_ms * 1e-3) / 1e12
     conv = float(np.mean((stn & (mem.ST_CONVERGED | mem.ST_STAGNATED)) != 0))
+    solve_stats = {"converged_fraction": conv, "mean_passes": passes / B, "max_passes": int(itn.max()),
+                   "order": "final Newton step applied (final_step=1)",
+                   "residual_fp64": residual_stats(ctx, torch, np, M, beta)}
+    # Algorithm 1's own order (the last direction not applied), same batch
+    lit = mem.default_opts(impl=mem.IMPL_FUSED, final_step=0)
+    beta.zero_()
+    ctx.solve(M, beta, st, it, opts=lit)
+    solve_stats["literal_order"] = {"order": "Algorithm 1 as printed (final_step=0)",
+                                    "residual_fp64": residual_stats(ctx, torch, np, M, beta),
+                                    "mean_passes": float(it.float().mean())}
 
     # ---- end to end through the C ABI from pinned host buffers
     M_h = M.cpu().pin_memory()
@@ -814,6 +904,7 @@ def main():
         extras["plain_fp32"] = {"value": B / (pms * 1e-3), "unit": UNIT, "ms_per_step": pms,
                                 "converged": float(np.mean((st.cpu().numpy() & 3) != 0))}
         extras["tuned_over_plain"] = value / world / extras["plain_fp32"]["value"]
+        extras.update(run_mixed(mem, ctx, torch, np, M, beta, st, it, extras["plain_fp32"]["value"], B))
         # 12^3 rule, tuned
         ctx12 = mem.Context(12)
         M12 = torch.zeros(B, 35, device=dev)
@@ -867,11 +958,18 @@ def main():
             "e2e": e2e, "gpu_launches": args.steps,
             "clocks": clocks,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                         "frac": achieved / peak_fp32, "traffic": TRAFFIC_BYTES,
+                         "frac": achieved / peak_fp32, "traffic": traffic_bytes(),
                          "kernel": "k_fused_solve<%d>" % args.order, "kernel_ms": kern_ms,
                          "flops_per_launch": flops, "newton_passes": passes,
-                         "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (not in the measured-peaks file)"},
-            "solve_stats": {"converged_fraction": conv, "mean_passes": passes / B, "max_passes": int(itn.max())}}
+                         "peak_note": "of measured: FP32 FMA rate of mem_bench_peak on this GPU (CUDA events); "
+                                      "flops = the sum-factorised kernel's own count per Newton pass",
+                         "dense_equivalent": {"flops_per_pass": dense_per_pass, "achieved": dense_achieved,
+                                              "peak": peaks["tf32_tc_tflops"],
+                                              "frac": dense_achieved / peaks["tf32_tc_tflops"],
+                                              "note": "the dense contraction's algorithmic flops (0.77 MFLOP per "
+                                                      "cell-iteration at Q=512) over the measured TF32 tensor rate"}},
+            "measured_peaks": peaks,
+            "solve_stats": solve_stats}
     line.update(extras)
     if rank == 0 and world == 1 and not args.no_cpu:
         # about 13 s of FP64 solves on the GPU host's 16 cores (~9.8k cells/s)

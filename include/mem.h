@@ -55,10 +55,21 @@ extern "C" {
 #define MEM_ST_LAMBDA 16     /* a lambda*I modification was needed             */
 #define MEM_ST_LAMBDA_CAP 32 /* lambda retries exhausted; solve stopped        */
 #define MEM_ST_BADINPUT 64   /* n <= 0 or non-finite input                     */
+#define MEM_ST_FP64_OK 128   /* mixed back-end: a cell stopped by MAXITER,
+                                NONFINITE or LAMBDA_CAP whose moment residual,
+                                recomputed in FP64, is within 1e-5 (its beta
+                                is acceptable although the step failed)       */
 
 /* Solver back-ends. */
 #define MEM_IMPL_PLAIN 0 /* separate FP32 kernels per Newton stage, host loop   */
 #define MEM_IMPL_FUSED 1 /* one persistent FP32 kernel, warp per cell           */
+#define MEM_IMPL_MIXED 2 /* the plain stages with the moment / Hessian
+                            contraction on tcgen05 tensor cores: split TF32
+                            (about FP32 accuracy) for the moments that form
+                            the gradient, one TF32 product for the Hessian
+                            (Newton's model only); cells whose safeguarded
+                            step fails get their residual recomputed in FP64
+                            (MEM_ST_FP64_OK).  quad_order 8 and 12 only.    */
 
 /* Interface flux of the shock's finite-volume step (Section 3.3). */
 #define MEM_SCHEME_LF 0   /* local Lax-Friedrichs, Eq. "The lax F"               */
@@ -85,7 +96,7 @@ typedef struct {
                            is not applied (default); 1: an extension that
                            applies it when res <= tol (moment residual of
                            the solution instead of one Newton step behind) */
-    int32_t impl;     /* MEM_IMPL_PLAIN or MEM_IMPL_FUSED (default FUSED)    */
+    int32_t impl;     /* MEM_IMPL_PLAIN, _FUSED (default) or _MIXED          */
 } mem_solve_opts;
 
 /* Fill *o with the defaults above. */
@@ -163,6 +174,19 @@ int mem_quad_order(const mem_ctx *ctx);
  * same context. */
 int mem_solve(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters,
               int64_t B, const mem_solve_opts *opts, void *stream);
+
+/* Relative moment residual of B cells in FP64 on the GPU,
+ *   res = || E_sigma[phi](beta) - M / n ||_2 / || M / n ||_2,
+ * with sigma from the context's quadrature (Section 3.1, Eq. "Numerical
+ * integration moments"; the stopping quantity of the acceptance bar).
+ * Gauss-Hermite contexts only.  M, beta dev [B][35]; res dev [B] double
+ * (written only for evaluated cells).  mask = 0 evaluates every cell;
+ * otherwise only cells with (status[c] & mask) != 0 (status dev [B],
+ * required then).  If status_out (dev [B], may alias status) is not NULL,
+ * an evaluated cell whose residual is <= accept gets MEM_ST_FP64_OK or-ed
+ * into it.  MEM_EINVAL on bad arguments or a velocity-space context. */
+int mem_residual64(mem_ctx *ctx, const float *M, const float *beta, const int32_t *status, int32_t mask,
+                   double *res, int32_t *status_out, double accept, int64_t B, void *stream);
 
 /* mem_solve for any context, with the cells' gauges gauge dev [B][6]: a
  * velocity-space rule (mem_init_velocity) places its nodes in each cell

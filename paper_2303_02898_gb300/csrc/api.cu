@@ -418,6 +418,7 @@ int mem_init(int degree, int quad_order, mem_ctx **out) {
     ctx->xmax = (float)ctx->x1d[n - 1];
     std::vector<float> phiT((size_t)NP * Q), logw(Q), tabS((size_t)Q * MEM_NCOL_SOLVE), tabF((size_t)Q * MEM_NCOL_FLUX);
     std::vector<float> he1d((size_t)n * MEM_HE_STRIDE, 0.f), x1d(n), lw1d(n);
+    std::vector<double> phi64((size_t)Q * NP), phiT64((size_t)NP * Q), logw64(Q);
     std::vector<double> hx(n * 10);
     for (int i = 0; i < n; ++i) {
         he_host(ctx->x1d[i], 9, &hx[i * 10]);
@@ -432,7 +433,9 @@ int mem_init(int degree, int quad_order, mem_ctx **out) {
                 double ph[NP];
                 for (int k = 0; k < NP; ++k) ph[k] = hx[ix * 10 + exp_a(k)] * hx[iy * 10 + exp_b(k)] * hx[iz * 10 + exp_c(k)];
                 const double ux = ctx->x1d[ix];
-                logw[q] = (float)(log(ctx->w1d[ix]) + log(ctx->w1d[iy]) + log(ctx->w1d[iz]));
+                logw64[q] = log(ctx->w1d[ix]) + log(ctx->w1d[iy]) + log(ctx->w1d[iz]);
+                logw[q] = (float)logw64[q];
+                for (int k = 0; k < NP; ++k) phi64[(size_t)q * NP + k] = phiT64[(size_t)k * Q + q] = ph[k];
                 for (int k = 0; k < NP; ++k) phiT[(size_t)k * Q + q] = (float)ph[k];
                 float *rs = &tabS[(size_t)q * MEM_NCOL_SOLVE];
                 for (int k = 0; k < NP; ++k) rs[k] = (float)ph[k];
@@ -455,6 +458,9 @@ int mem_init(int degree, int quad_order, mem_ctx **out) {
     if (!rc) rc = upload(&ctx->d_x1d, x1d);
     if (!rc) rc = upload(&ctx->d_logw1d, lw1d);
     if (!rc) rc = build_slot_tables(ctx);
+    if (!rc) rc = upload(&ctx->d_phiT64, phiT64);
+    if (!rc) rc = upload(&ctx->d_logw64, logw64);
+    if (!rc && (n == 8 || n == 12)) rc = mem_host::build_tc_tables(ctx, phi64);
     if (!rc)
         rc = mem_host::reserve_scratch(
             ctx, std::max(mem_host::plain_scratch_bytes(Q), mem_host::flux_scratch_bytes(Q)));
@@ -521,7 +527,7 @@ void mem_destroy(mem_ctx *ctx) {
     cudaDeviceSynchronize();
     void *ptrs[] = {ctx->d_phiT, ctx->d_logw, ctx->d_tab_solve, ctx->d_tab_flux, ctx->d_he1d, ctx->d_x1d,
                     ctx->d_logw1d, ctx->d_lin_off, ctx->d_lin_terms, ctx->d_hess_slots, ctx->d_hess_slots128, ctx->d_hr_slots, ctx->d_hr_rounds, ctx->d_hr_ent, ctx->d_flux_slots, ctx->d_axi_slots, ctx->d_xlin_off, ctx->d_xlin_terms,
-                    ctx->scratch, ctx->d_vtd, ctx->d_vtf, ctx->d_dom0};
+                    ctx->scratch, ctx->d_vtd, ctx->d_vtf, ctx->d_dom0, ctx->d_tc_tab, ctx->d_phiT64, ctx->d_logw64};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ctx->scratch_ev) cudaEventDestroy(ctx->scratch_ev);
@@ -543,7 +549,16 @@ int mem_solve(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_
     cudaStream_t st = (cudaStream_t)stream;
     if (o.impl == MEM_IMPL_PLAIN) return mem_host::solve_plain(ctx, M, beta, status, iters, B, o, st);
     if (o.impl == MEM_IMPL_FUSED) return mem_host::solve_fused(ctx, M, beta, status, iters, B, o, st);
+    if (o.impl == MEM_IMPL_MIXED) return mem_host::solve_mixed(ctx, M, beta, status, iters, B, o, st);
     return MEM_EINVAL;
+}
+
+int mem_residual64(mem_ctx *ctx, const float *M, const float *beta, const int32_t *status, int32_t mask, double *res,
+                   int32_t *status_out, double accept, int64_t B, void *stream) {
+    if (!ctx || B < 0 || ctx->vel) return MEM_EINVAL;
+    if (B == 0) return MEM_OK;
+    if (!M || !beta || !res || (mask && !status)) return MEM_EINVAL;
+    return mem_host::residual64(ctx, M, beta, status, mask, res, status_out, accept, B, (cudaStream_t)stream);
 }
 
 int mem_solve_gauge(mem_ctx *ctx, const float *M, float *beta, const float *gauge, int32_t *status, int32_t *iters,

@@ -46,6 +46,9 @@ struct mem_ctx {
     int *d_xlin_off = nullptr;     // [631]  flux-Jacobian terms (packed i>=j>=0)
     int2 *d_xlin_terms = nullptr;
     float xmax = 0.f;              // largest 1D node
+    float *d_tc_tab = nullptr;     // tensor-core contraction tables (mixed back-end), tiled
+    double *d_phiT64 = nullptr;    // [35][Q] phi_k(ubar_q) in FP64 (residual recompute)
+    double *d_logw64 = nullptr;    // [Q] log w_q in FP64
     // Velocity-space rule (mem_init_velocity): nodes fixed in the lab frame.
     int vel = 0;                             // 1: velocity-space context (no gauge-frame tables)
     int nbx = 0, nbr = 0, ng = 0, K = 0;     // blocks in u_x, blocks in u_r, points per block, azimuths
@@ -70,10 +73,18 @@ namespace mem_host {
 int reserve_scratch(mem_ctx *ctx, size_t bytes);                     // at context creation only
 int scratch_begin(mem_ctx *ctx, size_t bytes, cudaStream_t st);       // with ctx->mu held
 void scratch_end(mem_ctx *ctx, cudaStream_t st);                      // with ctx->mu held
-size_t plain_scratch_bytes(int Q);                                    // plain solve, one chunk
+size_t plain_scratch_bytes(int Q);                                    // plain / mixed solve, one chunk
+bool tc_available(const mem_ctx *ctx);
+int build_tc_tables(mem_ctx *ctx, const std::vector<double> &phi);
+size_t tc_sigma_floats(int Q, int64_t cells);
+int tc_contract(mem_ctx *ctx, const float *a_hi, const float *a_lo, float *mom, int n, int *err, cudaStream_t st);
+int residual64(mem_ctx *ctx, const float *M, const float *beta, const int32_t *status, int32_t mask, double *res,
+               int32_t *status_out, double accept, int64_t B, cudaStream_t st);
 size_t flux_scratch_bytes(int Q);                                     // dense flux, one chunk
 int gh_rule(int n, std::vector<double> &x, std::vector<double> &w);
 int solve_plain(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters, int64_t B,
+                const mem_solve_opts &o, cudaStream_t st, const unsigned char *active = nullptr);
+int solve_mixed(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters, int64_t B,
                 const mem_solve_opts &o, cudaStream_t st, const unsigned char *active = nullptr);
 int solve_fused(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters, int64_t B,
                 const mem_solve_opts &o, cudaStream_t st, const unsigned char *active = nullptr);

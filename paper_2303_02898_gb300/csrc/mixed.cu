@@ -1,0 +1,254 @@
+// mixed.cu -- the tensor-core contraction of the mixed-precision back-end:
+// the moment and Hessian sums of Section 3.1 / Appendix C,
+//     E[phi_k]          = sum_q sigma_q phi_k(ubar_q)          (35 columns)
+//     E[phi_i phi_j]    = sum_q sigma_q phi_i phi_j (ubar_q)   (595 columns)
+// as one GEMM [cells x Q] . [Q x 630] on tcgen05 tensor cores.  The moments
+// feed the gradient, so they use split TF32 (sigma = hi + lo, phi = hi + lo;
+// hi.hi + hi.lo + lo.hi, FP32 accumulation: about FP32 accuracy); the
+// Hessian, which Newton's method only needs as a model, uses one TF32
+// product.
+//
+// Layout (tc.cuh, K-major, no swizzle): the line-search kernel writes sigma
+// for tile t of 128 cells and K-chunk kc of 32 nodes as one 16 KB block
+// (hi and lo in two arrays); the constant statistics tables are stored the
+// same way, 352 rows (N) x 32 nodes (K) per block, in two column groups:
+//   group 0: rows 0-47 phi_hi (35 used), 48-95 phi_lo, 96-351 Hessian 0-255
+//   group 1: rows 0-338 Hessian 256-594 (rows 339-351 zero).
+// One CTA (128 threads) computes one tile and one group: thread 0 issues the
+// bulk copies (TMA engine, double-buffered, mbarrier transaction counts) and
+// the MMAs (accumulators in TMEM); then all four warps read their 32 rows of
+// TMEM and write the moments row of each cell.  Every wait is bounded.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+#include "tc.cuh"
+
+using namespace mem;
+
+namespace {
+
+constexpr int ROWS = 352;                   // N rows per group block
+constexpr int KCH = 32;                     // nodes per K-chunk
+constexpr uint32_t A_BYTES = 128 * KCH * 4;  // 16 KB
+constexpr uint32_t B_BYTES = ROWS * KCH * 4;  // 44 KB
+constexpr uint32_t SBO = KCH / 4 * 128;       // 1024: bytes between 8-row groups
+constexpr uint32_t STAGE = 2 * A_BYTES + B_BYTES;
+constexpr uint32_t kMaxPolls = 1u << 22;
+
+struct ContractArgs {
+    const float *a_hi, *a_lo;  // [tiles][KC][128 x 32] tiled sigma
+    const float *tab;          // [2][KC][352 x 32] tiled tables
+    float *mom;                // [n][630]
+    int n, KC;
+    int *err;
+};
+
+__global__ void __launch_bounds__(128, 1) k_tc_contract(ContractArgs A) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_full[2], s_empty[2], s_done;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tile = blockIdx.x, grp = blockIdx.y;
+    if (warp == 0) {
+        tc::tmem_alloc(&s_tmem, 512);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(&s_full[0], 1);
+        tc::mbar_init(&s_full[1], 1);
+        tc::mbar_init(&s_empty[0], 1);
+        tc::mbar_init(&s_empty[1], 1);
+        tc::mbar_init(&s_done, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    const int KC = A.KC;
+    if (tid == 0) {
+        bool failed = false;
+        int loaded = 0;  // chunks whose copies were issued
+        auto load = [&](int kc) {
+            const int s = kc & 1;
+            uint8_t *st = smem + s * STAGE;
+            const size_t ablk = ((size_t)tile * KC + kc) * (A_BYTES / 4);
+            const size_t bblk = ((size_t)grp * KC + kc) * (B_BYTES / 4);
+            const uint32_t bytes = (grp == 0 ? 2 * A_BYTES : A_BYTES) + B_BYTES;
+            tc::mbar_expect_tx(&s_full[s], bytes);
+            tc::bulk_g2s(st, A.a_hi + ablk, A_BYTES, &s_full[s]);
+            if (grp == 0) tc::bulk_g2s(st + A_BYTES, A.a_lo + ablk, A_BYTES, &s_full[s]);
+            tc::bulk_g2s(st + 2 * A_BYTES, A.tab + bblk, B_BYTES, &s_full[s]);
+            loaded = kc + 1;
+        };
+        load(0);
+        const uint32_t id48 = tc::idesc(128, 48, 2), id256 = tc::idesc(128, 256, 2), id96 = tc::idesc(128, 96, 2);
+        int kc = 0;
+        for (; kc < KC && !failed; ++kc) {
+            if (kc + 1 < KC) {
+                // stage (kc+1)&1 was last read by the MMAs of chunk kc-1
+                if (kc >= 1 && !tc::mbar_wait(&s_empty[(kc + 1) & 1], ((kc - 1) >> 1) & 1, kMaxPolls)) {
+                    failed = true;
+                    break;
+                }
+                load(kc + 1);
+            }
+            if (!tc::mbar_wait(&s_full[kc & 1], (kc >> 1) & 1, kMaxPolls)) {
+                failed = true;
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t base = tc::smem_u32(smem + (kc & 1) * STAGE);
+            const uint32_t ahi = base, alo = base + A_BYTES, b = base + 2 * A_BYTES;
+#pragma unroll
+            for (int s = 0; s < KCH / 8; ++s) {
+                const uint32_t acc = (kc | s) != 0;
+                const uint64_t dh = tc::sdesc(ahi + 256 * s, 128, SBO);
+                if (grp == 0) {
+                    const uint64_t dl = tc::sdesc(alo + 256 * s, 128, SBO);
+                    const uint64_t bmh = tc::sdesc(b + 256 * s, 128, SBO);
+                    const uint64_t bml = tc::sdesc(b + 6 * SBO + 256 * s, 128, SBO);
+                    const uint64_t bh = tc::sdesc(b + 12 * SBO + 256 * s, 128, SBO);
+                    tc::mma_tf32(tmem, dl, bmh, id48, acc);   // lo . hi
+                    tc::mma_tf32(tmem, dh, bml, id48, 1);     // hi . lo
+                    tc::mma_tf32(tmem, dh, bmh, id48, 1);     // hi . hi
+                    tc::mma_tf32(tmem + 48, dh, bh, id256, acc);
+                } else {
+                    const uint64_t b0 = tc::sdesc(b + 256 * s, 128, SBO);
+                    const uint64_t b1 = tc::sdesc(b + 32 * SBO + 256 * s, 128, SBO);
+                    tc::mma_tf32(tmem, dh, b0, id256, acc);
+                    tc::mma_tf32(tmem + 256, dh, b1, id96, acc);
+                }
+            }
+            tc::mma_commit(&s_empty[kc & 1]);
+        }
+        if (failed) {
+            atomicExch(A.err, 1);
+            // copies still in flight land in this CTA's shared memory: wait
+            // for them (bounded) before the CTA can exit
+            for (int j = kc; j < loaded; ++j) tc::mbar_wait(&s_full[j & 1], (j >> 1) & 1, kMaxPolls);
+        }
+        tc::mma_commit(&s_done);  // every MMA issued above
+    }
+    __syncwarp();
+    bool ok = tc::mbar_wait(&s_done, 0, kMaxPolls);
+    if (!ok) {
+        atomicExch(A.err, 1);
+        tc::mbar_wait(&s_done, 0, kMaxPolls);
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    tc::fence_after_sync();
+    const int row = 32 * (warp & 3) + (tid & 31);
+    const int cell = tile * 128 + row;
+    const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    if (ok) {
+        float *m = A.mom + (size_t)cell * MEM_NCOL_SOLVE;
+        const bool live = cell < A.n;
+        if (grp == 0) {
+            for (int c = 0; c < 304; c += 8) {
+                float v[8];
+                tc::tmem_ld8(tl + (uint32_t)c, v);
+                if (live) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int col = c + j;
+                        if (col < NP) m[col] = v[j];
+                        else if (col >= 48) m[NP + col - 48] = v[j];
+                    }
+                }
+            }
+        } else {
+            for (int c = 0; c < 344; c += 8) {
+                float v[8];
+                tc::tmem_ld8(tl + (uint32_t)c, v);
+                if (live) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (c + j < 339) m[NP + 256 + c + j] = v[j];
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// Host round to TF32 (nearest, ties away from zero: the rounding of
+// cvt.rna.tf32.f32 on the device).
+float tf32_host(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return x;
+    u = (u + 0x1000u) & 0xffffe000u;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
+}  // namespace
+
+namespace mem_host {
+
+bool tc_available(const mem_ctx *ctx) { return ctx->d_tc_tab != nullptr; }
+
+// Tiled tables of the contraction for a Gauss-Hermite context (Q a multiple
+// of 32): phi values and packed products phi_i phi_j, i >= j >= 1, at the
+// nodes in the order of the dense tables (Section 3.1 statistics).
+int build_tc_tables(mem_ctx *ctx, const std::vector<double> &phi /*[Q][35]*/) {
+    const int Q = ctx->Q;
+    if (Q % KCH) return MEM_OK;  // no tensor-core path for this order
+    const int KC = Q / KCH;
+    std::vector<float> tab((size_t)2 * KC * ROWS * KCH, 0.f);
+    auto put = [&](int grp, int row, int q, float v) {
+        const int kc = q / KCH, k = q % KCH;
+        const size_t blk = ((size_t)grp * KC + kc) * ROWS * KCH;
+        const size_t off = (size_t)(row >> 3) * (SBO / 4) + (size_t)(k >> 2) * 32 + (row & 7) * 4 + (k & 3);
+        tab[blk + off] = v;
+    };
+    for (int q = 0; q < Q; ++q) {
+        const double *ph = &phi[(size_t)q * NP];
+        for (int k = 0; k < NP; ++k) {
+            const float f = (float)ph[k], hi = tf32_host(f), lo = tf32_host(f - hi);
+            put(0, k, q, hi);
+            put(0, 48 + k, q, lo);
+        }
+        for (int i = 1; i < NP; ++i)
+            for (int j = 1; j <= i; ++j) {
+                const int p = (i - 1) * i / 2 + (j - 1);
+                const float v = tf32_host((float)(ph[i] * ph[j]));
+                if (p < 256) put(0, 96 + p, q, v);
+                else put(1, p - 256, q, v);
+            }
+    }
+    if (cudaMalloc((void **)&ctx->d_tc_tab, sizeof(float) * tab.size()) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->d_tc_tab = nullptr;
+        return MEM_ENOMEM;
+    }
+    if (cudaMemcpy(ctx->d_tc_tab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return MEM_ECUDA;
+    return MEM_OK;
+}
+
+size_t tc_sigma_floats(int Q, int64_t cells) { return (size_t)((cells + 127) / 128) * 128 * Q; }
+
+int tc_contract(mem_ctx *ctx, const float *a_hi, const float *a_lo, float *mom, int n, int *err, cudaStream_t st) {
+    if (!ctx->d_tc_tab) return MEM_EINVAL;
+    static bool configured = false;
+    const int smem = 2 * STAGE;
+    if (!configured) {
+        MEM_CUDA_TRY(cudaFuncSetAttribute(k_tc_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        configured = true;
+    }
+    ContractArgs a{a_hi, a_lo, ctx->d_tc_tab, mom, n, ctx->Q / KCH, err};
+    dim3 grid((n + 127) / 128, 2);
+    k_tc_contract<<<grid, 128, smem, st>>>(a);
+    MEM_CUDA_TRY(cudaGetLastError());
+    return MEM_OK;
+}
+
+}  // namespace mem_host

@@ -20,6 +20,12 @@ using namespace mem;
 
 namespace {
 
+__device__ __forceinline__ float tc_round(float x) {  // to TF32, nearest (ties away)
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
 constexpr int BLK = 256;
 constexpr int MAXJ = 16;  // nodes per thread: Q <= 4096
 constexpr int CHUNK = 1 << 16;
@@ -51,7 +57,8 @@ __device__ __forceinline__ float block_reduce_sum(float v, float *red) {
 }
 
 struct PlainState {
-    float *sigma;  // [CHUNK][Q]
+    float *sigma;  // [CHUNK][Q] (mixed back-end: hi part, tiled for the tensor cores)
+    float *sig_lo; // mixed back-end: lo part, tiled
     float *mom;    // [CHUNK][630]
     float *db;     // [CHUNK][35]
     float *G;      // [CHUNK][35]
@@ -61,7 +68,15 @@ struct PlainState {
     int *st;       // [CHUNK]
     int *act0, *act1;  // [CHUNK]
     int *cnt;      // [2]
+    int *err;      // [1] mixed back-end: a tensor-core wait timed out
 };
+
+// Offset of sigma(slot, q) in the tensor cores' tiled layout: tiles of 128
+// cells, K-chunks of 32 nodes, core matrices of 8 cells x 4 nodes.
+__device__ __forceinline__ size_t tiled_off(int slot, int q, int KC) {
+    const int tile = slot >> 7, r = slot & 127, kc = q >> 5, k = q & 31;
+    return ((size_t)tile * KC + kc) * 4096 + (size_t)((r >> 3) * 256 + (k >> 2) * 32 + (r & 7) * 4 + (k & 3));
+}
 
 __global__ void k_init(const float *__restrict__ M, float *__restrict__ beta, int n, PlainState S,
                        int32_t *status, int32_t *iters, const unsigned char *active) {
@@ -89,6 +104,9 @@ __global__ void k_init(const float *__restrict__ M, float *__restrict__ beta, in
 
 // One block per active cell.  Nodes q = tid + 256 j.  The exponent of the
 // trial point beta + alpha dbeta is e_beta + alpha e_dbeta (both computed once).
+// TILED: sigma goes to the tensor cores' tiled layout as a TF32 hi part and
+// a TF32 lo part (sigma = hi + lo to about 2^-22).
+template <bool TILED>
 __global__ void __launch_bounds__(BLK) k_linesearch(const int *__restrict__ act, const float *__restrict__ M,
                                                     float *__restrict__ beta, PlainState S,
                                                     const float *__restrict__ phiT, const float *__restrict__ logw,
@@ -159,11 +177,26 @@ __global__ void __launch_bounds__(BLK) k_linesearch(const int *__restrict__ act,
         sat = (LD - gradD) >= -(o.atol + o.rtol * fabsf(LD));
     }
     const float invZ = 1.f / Z;
-    float *sig = S.sigma + (size_t)slot * Q;
+    if (TILED) {
+        const int KC = Q >> 5;
 #pragma unroll
-    for (int j = 0; j < MAXJ; ++j) {
-        const int q = tid + j * BLK;
-        if (j < nj && q < Q) sig[q] = __expf(eb[j] + alpha * ed[j] - mx) * invZ;
+        for (int j = 0; j < MAXJ; ++j) {
+            const int q = tid + j * BLK;
+            if (j < nj && q < Q) {
+                const float v = __expf(eb[j] + alpha * ed[j] - mx) * invZ;
+                const float hi = tc_round(v);
+                const size_t off = tiled_off(slot, q, KC);
+                S.sigma[off] = hi;
+                S.sig_lo[off] = tc_round(v - hi);
+            }
+        }
+    } else {
+        float *sig = S.sigma + (size_t)slot * Q;
+#pragma unroll
+        for (int j = 0; j < MAXJ; ++j) {
+            const int q = tid + j * BLK;
+            if (j < nj && q < Q) sig[q] = __expf(eb[j] + alpha * ed[j] - mx) * invZ;
+        }
     }
     if (tid >= 1 && tid < NP) bc[tid] = sb[tid] + alpha * sd[tid];
     if (tid == 0) { S.Lcur[c] = Lt; S.alpha[c] = alpha; }
@@ -444,6 +477,63 @@ __global__ void __launch_bounds__(64) k_flux_speed(const float *__restrict__ mom
     if (lane == 0) speed[c] = sp <= bound ? sp : bound;
 }
 
+// Relative moment residual ||E phi(beta) - M/n|| / ||M/n|| in FP64 (the
+// sums over i >= 1; the norm of M/n includes M_0/n = 1), warp per cell,
+// grid-stride; only cells with (status & mask) != 0 when mask != 0.
+__global__ void __launch_bounds__(128) k_residual64(const float *__restrict__ M, const float *__restrict__ beta,
+                                                    const int32_t *__restrict__ status, int32_t mask,
+                                                    double *__restrict__ res, int32_t *status_out, double accept,
+                                                    int64_t B, const double *__restrict__ phiT,
+                                                    const double *__restrict__ logw, int Q) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * 4;
+    for (int64_t c = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5); c < B; c += nw) {
+        if (mask && !(status[c] & mask)) continue;
+        double b[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) b[k] = k ? (double)beta[c * NP + k] : 0.0;
+        double mx = -INFINITY;
+        for (int q = lane; q < Q; q += 32) {
+            double e = logw[q];
+            for (int k = 1; k < NP; ++k) e += b[k] * phiT[(size_t)k * Q + q];
+            mx = fmax(mx, e);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        double m[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) m[k] = 0.0;
+        for (int q = lane; q < Q; q += 32) {
+            double e = logw[q];
+            for (int k = 1; k < NP; ++k) e += b[k] * phiT[(size_t)k * Q + q];
+            const double w = exp(e - mx);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) m[k] += w * phiT[(size_t)k * Q + q];
+        }
+        double num = 0.0, den = 0.0;
+        const double n = (double)M[c * NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            double v = m[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            m[k] = v;
+        }
+        const double Z = m[0];
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const double t = (double)M[c * NP + k] / n;
+            den += t * t;
+            if (k) num += (m[k] / Z - t) * (m[k] / Z - t);
+        }
+        const double r = sqrt(num / den);
+        if (lane == 0) {
+            res[c] = r;
+            if (status_out && r <= accept) status_out[c] |= MEM_ST_FP64_OK;
+        }
+    }
+}
+
 void sgemm(const float *A, const float *Bm, float *C, int M, int N, int K, cudaStream_t st) {
     dim3 grid((N + 63) / 64, (M + 63) / 64);
     k_sgemm<<<grid, 256, 0, st>>>(A, Bm, C, M, N, K);
@@ -454,16 +544,24 @@ void sgemm(const float *A, const float *Bm, float *C, int M, int N, int K, cudaS
 namespace mem_host {
 
 static size_t plain_need(int Q, size_t CH) {
-    return sizeof(float) * CH * ((size_t)Q + MEM_NCOL_SOLVE + 2 * NP + 2) + sizeof(int) * (CH * 4 + 2) + 16 * 256;
+    // sigma hi + lo (mixed: tiled, whole tiles of 128 cells), moments,
+    // per-cell vectors and scalars, the FP64 residuals of failed cells
+    const size_t sig = tc_sigma_floats(Q, (int64_t)CH);
+    return sizeof(float) * (2 * sig + CH * ((size_t)MEM_NCOL_SOLVE + 2 * NP + 2)) + sizeof(int) * (CH * 4 + 4) +
+           sizeof(double) * CH + 16 * 256;
 }
 
 size_t plain_scratch_bytes(int Q) { return plain_need(Q, CHUNK); }
 size_t flux_scratch_bytes(int Q) { return sizeof(float) * (size_t)CHUNK * ((size_t)Q + MEM_NCOL_FLUX) + 1024; }
 
-int solve_plain(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters, int64_t B,
-                const mem_solve_opts &o, cudaStream_t st, const unsigned char *active) {
+// The plain (FP32 SIMT contraction) and mixed (tensor-core contraction)
+// back-ends: per chunk of cells, a host loop over Newton passes of
+// line search -> contraction -> Newton step, compacting the active cells.
+static int solve_dense(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters, int64_t B,
+                       const mem_solve_opts &o, cudaStream_t st, const unsigned char *active, bool mixed) {
     std::lock_guard<std::mutex> lock(ctx->mu);
     const int Q = ctx->Q;
+    if (mixed && (!tc_available(ctx) || Q > MAXJ * BLK)) return MEM_EINVAL;
     const size_t CH = (size_t)std::min<int64_t>(B, CHUNK);
     int rc = scratch_begin(ctx, plain_need(Q, CH), st);
     if (rc) return rc;
@@ -475,7 +573,9 @@ int solve_plain(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int3
     char *p = (char *)ctx->scratch;
     auto take = [&](size_t bytes) { char *r = p; p += (bytes + 255) & ~(size_t)255; return r; };
     PlainState S;
-    S.sigma = (float *)take(sizeof(float) * CH * Q);
+    const size_t sig = mixed ? tc_sigma_floats(Q, (int64_t)CH) : CH * Q;
+    S.sigma = (float *)take(sizeof(float) * sig);
+    S.sig_lo = mixed ? (float *)take(sizeof(float) * sig) : nullptr;
     S.mom = (float *)take(sizeof(float) * CH * MEM_NCOL_SOLVE);
     S.db = (float *)take(sizeof(float) * CH * NP);
     S.G = (float *)take(sizeof(float) * CH * NP);
@@ -486,7 +586,10 @@ int solve_plain(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int3
     S.act0 = (int *)take(sizeof(int) * CH);
     S.act1 = (int *)take(sizeof(int) * CH);
     S.cnt = (int *)take(sizeof(int) * 2);
+    S.err = (int *)take(sizeof(int) * 2);
+    double *res64 = (double *)take(sizeof(double) * CH);
     if ((size_t)(p - (char *)ctx->scratch) > ctx->scratch_bytes) return MEM_ENOMEM;
+    if (mixed) MEM_CUDA_TRY(cudaMemsetAsync(S.err, 0, sizeof(int), st));
     for (int64_t c0 = 0; c0 < B; c0 += CH) {
         const int n = (int)std::min<int64_t>(CH, B - c0);
         const float *Mc = M + c0 * NP;
@@ -494,23 +597,61 @@ int solve_plain(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int3
         int32_t *stc = status ? status + c0 : nullptr, *itc = iters ? iters + c0 : nullptr;
         MEM_CUDA_TRY(cudaMemsetAsync(S.cnt, 0, 2 * sizeof(int), st));
         k_init<<<(n + 255) / 256, 256, 0, st>>>(Mc, bc, n, S, stc, itc, active ? active + c0 : nullptr);
-        int nact = 0;
-        MEM_CUDA_TRY(cudaMemcpyAsync(&nact, S.cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+        int hc[2] = {0, 0};  // active cells, tensor-core error flag
+        MEM_CUDA_TRY(cudaMemcpyAsync(&hc[0], S.cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
         MEM_CUDA_TRY(cudaStreamSynchronize(st));
+        int nact = hc[0];
         int *cur = S.act0, *nxt = S.act1;
         int cur_cnt = 0;
         for (int pass = 0; pass <= o.maxI + 1 && nact > 0; ++pass) {
-            k_linesearch<<<nact, BLK, 0, st>>>(cur, Mc, bc, S, ctx->d_phiT, ctx->d_logw, Q, o);
-            sgemm(S.sigma, ctx->d_tab_solve, S.mom, nact, MEM_NCOL_SOLVE, Q, st);
+            if (mixed) {
+                k_linesearch<true><<<nact, BLK, 0, st>>>(cur, Mc, bc, S, ctx->d_phiT, ctx->d_logw, Q, o);
+                rc = tc_contract(ctx, S.sigma, S.sig_lo, S.mom, nact, S.err, st);
+                if (rc) return rc;
+            } else {
+                k_linesearch<false><<<nact, BLK, 0, st>>>(cur, Mc, bc, S, ctx->d_phiT, ctx->d_logw, Q, o);
+                sgemm(S.sigma, ctx->d_tab_solve, S.mom, nact, MEM_NCOL_SOLVE, Q, st);
+            }
             const int nxt_cnt = 1 - cur_cnt;
             MEM_CUDA_TRY(cudaMemsetAsync(S.cnt + nxt_cnt, 0, sizeof(int), st));
             k_newton<<<(nact + 3) / 4, 128, 0, st>>>(cur, nact, Mc, bc, S, nxt, S.cnt + nxt_cnt, o, stc, itc);
-            MEM_CUDA_TRY(cudaMemcpyAsync(&nact, S.cnt + nxt_cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+            MEM_CUDA_TRY(cudaMemcpyAsync(&hc[0], S.cnt + nxt_cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+            if (mixed) MEM_CUDA_TRY(cudaMemcpyAsync(&hc[1], S.err, sizeof(int), cudaMemcpyDeviceToHost, st));
             MEM_CUDA_TRY(cudaStreamSynchronize(st));
+            if (hc[1]) return MEM_ECUDA;  // the tensor cores did not signal completion in time
+            nact = hc[0];
             std::swap(cur, nxt);
             cur_cnt = nxt_cnt;
         }
+        // The safeguard of the mixed back-end: cells whose step failed get
+        // their moment residual recomputed in FP64.
+        if (mixed && stc) {
+            rc = residual64(ctx, Mc, bc, stc, MEM_ST_MAXITER | MEM_ST_NONFINITE | MEM_ST_LAMBDA_CAP, res64, stc, 1e-5,
+                            n, st);
+            if (rc) return rc;
+        }
     }
+    MEM_CUDA_TRY(cudaGetLastError());
+    return MEM_OK;
+}
+
+int solve_plain(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters, int64_t B,
+                const mem_solve_opts &o, cudaStream_t st, const unsigned char *active) {
+    return solve_dense(ctx, M, beta, status, iters, B, o, st, active, false);
+}
+
+int solve_mixed(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters, int64_t B,
+                const mem_solve_opts &o, cudaStream_t st, const unsigned char *active) {
+    return solve_dense(ctx, M, beta, status, iters, B, o, st, active, true);
+}
+
+// FP64 relative moment residual, warp per evaluated cell.
+int residual64(mem_ctx *ctx, const float *M, const float *beta, const int32_t *status, int32_t mask, double *res,
+               int32_t *status_out, double accept, int64_t B, cudaStream_t st) {
+    if (!ctx->d_phiT64) return MEM_EINVAL;
+    const int blocks = (int)std::min<int64_t>((B + 3) / 4, 65535);
+    k_residual64<<<blocks, 128, 0, st>>>(M, beta, status, mask, res, status_out, accept, B, ctx->d_phiT64,
+                                        ctx->d_logw64, ctx->Q);
     MEM_CUDA_TRY(cudaGetLastError());
     return MEM_OK;
 }

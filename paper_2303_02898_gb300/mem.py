@@ -19,8 +19,8 @@ NP = 35
 MEM_OK, MEM_PENDING = 0, 1
 MEM_EINVAL, MEM_ENOMEM, MEM_ECUDA, MEM_EBUSY, MEM_ENOTFOUND = -1, -2, -3, -4, -5
 ST_CONVERGED, ST_STAGNATED, ST_MAXITER, ST_NONFINITE = 1, 2, 4, 8
-ST_LAMBDA, ST_LAMBDA_CAP, ST_BADINPUT = 16, 32, 64
-IMPL_PLAIN, IMPL_FUSED = 0, 1
+ST_LAMBDA, ST_LAMBDA_CAP, ST_BADINPUT, ST_FP64_OK = 16, 32, 64, 128
+IMPL_PLAIN, IMPL_FUSED, IMPL_MIXED = 0, 1, 2
 
 
 class SolveOpts(ctypes.Structure):
@@ -94,6 +94,8 @@ def lib():
         L.mem_serve_create.argtypes = [_P, ctypes.c_size_t, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P]
         L.mem_serve_progress.argtypes = [_P, ctypes.c_int, _P]
         L.mem_serve_poll.argtypes = [_P, ctypes.c_uint64, _P, _P, _P, _P]
+        L.mem_residual64.restype = ctypes.c_int
+        L.mem_residual64.argtypes = [_P, _P, _P, _P, ctypes.c_int32, _P, _P, ctypes.c_double, ctypes.c_int64, _P]
         L.mem_bench_peak.restype = ctypes.c_int
         L.mem_bench_peak.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)]
@@ -193,6 +195,13 @@ class Context:
         rc = lib().mem_solve_gauge(self.h, _ptr(M), _ptr(beta), _ptr(gauge), _ptr(status), _ptr(iters), B,
                                    ctypes.byref(o), _stream(stream))
         _check(rc, "mem_solve_gauge")
+
+    def residual64(self, M, beta, res, status=None, mask=0, status_out=None, accept=1e-5, stream=None):
+        """mem_residual64: FP64 relative moment residual per cell (res: float64
+        CUDA tensor), for the cells with status & mask (all if mask == 0)."""
+        rc = lib().mem_residual64(self.h, _ptr(M), _ptr(beta), _ptr(status), int(mask), _ptr(res), _ptr(status_out),
+                                  float(accept), M.shape[0], _stream(stream))
+        _check(rc, "mem_residual64")
 
     def flux(self, M, beta, gauge, F=None, speed=None, stream=None):
         rc = lib().mem_flux(self.h, _ptr(M), _ptr(beta), _ptr(gauge), _ptr(F), _ptr(speed), M.shape[0],

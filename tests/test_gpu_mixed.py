@@ -1,0 +1,134 @@
+"""The mixed-precision back-end (MEM_IMPL_MIXED) against the FP64 oracle.
+
+Its moment / Hessian contraction runs on tcgen05 tensor cores: split TF32
+for the moments that form the gradient, one TF32 product for the Hessian
+(Newton's model).  The acceptance bar is the solve's, 1e-5 relative moment
+residual evaluated by the oracle in FP64 at the same rule (final step
+applied, as in the other acceptance tests); the per-result error against
+the oracle's parameters is reported beside the plain FP32 back-end's.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RES_TOL = 1e-5
+EXT = dict(final_step=1)
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def mem(dev):
+    from paper_2303_02898_gb300 import mem as m
+    m.lib()
+    return m
+
+
+def T32(a, dev):
+    return torch.tensor(np.asarray(a), dtype=torch.float32, device=dev).contiguous()
+
+
+def np64(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+def _targets(mem, ctx, dev, B, seed):
+    from paper_2303_02898_gb300 import workloads
+    t = workloads.solve_targets(B, seed=seed)
+    M = torch.zeros(B, 35, device=dev)
+    g = torch.zeros(B, 6, device=dev)
+    ctx.targets(T32(t.v, dev), T32(t.T, dev), T32(t.a, dev), T32(t.b, dev), M, g, gen_order=24)
+    return M
+
+
+def _solve(ctx, M, impl, **kw):
+    B = M.shape[0]
+    beta = torch.zeros_like(M)
+    st = torch.zeros(B, dtype=torch.int32, device=M.device)
+    it = torch.zeros(B, dtype=torch.int32, device=M.device)
+    ctx.solve(M, beta, st, it, impl=impl, **kw)
+    return np64(beta), st.cpu().numpy(), it.cpu().numpy()
+
+
+@pytest.mark.parametrize("order", [8, 12])
+@pytest.mark.parametrize("workload", ["perturbed", "targets"])
+def test_mixed_solve_matches_oracle(O, mem, dev, order, workload):
+    from paper_2303_02898_gb300 import workloads
+    ctx = mem.Context(order)
+    if workload == "perturbed":
+        # 389 cells: three full tiles of 128 and a ragged one of 5
+        M = T32(workloads.perturbed_hermite_moments(389, seed=17, scale=0.04), dev)
+    else:
+        M = _targets(mem, ctx, dev, 389, seed=23)
+    Mf = np64(M)
+    bm, stm, itm = _solve(ctx, M, mem.IMPL_MIXED, **EXT)
+    bp, stp, itp = _solve(ctx, M, mem.IMPL_PLAIN, **EXT)
+    conv = (stm & (mem.ST_CONVERGED | mem.ST_STAGNATED)) != 0
+    assert conv.all(), np.unique(stm, return_counts=True)
+    res = O.residual_batch(order, bm, Mf)
+    assert res.max() <= RES_TOL, (res.max(), int(np.argmax(res)))
+    bo, _, ito = O.solve_batch(order, Mf, final_step=True)
+    scale = 1.0 + np.abs(bo[:, 1:]).max(axis=1)
+    err_m = np.abs(bm[:, 1:] - bo[:, 1:]).max(axis=1) / scale
+    err_p = np.abs(bp[:, 1:] - bo[:, 1:]).max(axis=1) / scale
+    assert err_m.max() <= 5e-3, err_m.max()
+    # the TF32 Hessian is a model: the pass count may grow, not by much
+    assert itm.mean() <= itp.mean() + 2.0, (itm.mean(), itp.mean())
+    print("mixed %s q%d: residual max %.2e median %.2e; beta err vs FP64 max %.2e (plain FP32 %.2e); "
+          "mean passes mixed %.2f plain %.2f oracle %.2f" % (
+              workload, order, res.max(), np.median(res), err_m.max(), err_p.max(), itm.mean(), itp.mean(),
+              ito.mean()))
+    ctx.close()
+
+
+def test_residual64_matches_oracle(O, mem, dev):
+    """mem_residual64 is the oracle's acceptance quantity, in FP64 on the GPU."""
+    from paper_2303_02898_gb300 import workloads
+    ctx = mem.Context(8)
+    M = T32(workloads.perturbed_hermite_moments(77, seed=29, scale=0.05), dev)
+    beta, _, _ = _solve(ctx, M, mem.IMPL_FUSED)
+    bt = T32(beta, dev)
+    res = torch.zeros(77, dtype=torch.float64, device=dev)
+    ctx.residual64(M, bt, res)
+    got = res.cpu().numpy()
+    ref = O.residual_batch(8, np64(bt), np64(M))
+    assert np.allclose(got, ref, rtol=1e-6, atol=1e-13), np.abs(got - ref).max()
+    ctx.close()
+
+
+def test_mixed_safeguard_recomputes_failed_cells(O, mem, dev):
+    """tol = 0 and maxI = 0: every cell stops after one pass (MAXITER) at its
+    start, the Maxwellian beta = 0.  The moments are the Maxwellian's plus a
+    perturbation of log-uniform size 1e-8 .. 1e-3, so the FP64 residual of
+    the start falls on both sides of 1e-5.  The mixed back-end recomputes
+    the residual of every failed cell in FP64 and marks those within 1e-5
+    (MEM_ST_FP64_OK): exactly the cells the oracle finds within it."""
+    ctx = mem.Context(8)
+    rng = np.random.default_rng(37)
+    B = 300
+    d = rng.normal(0, 1, (B, 35))
+    d[:, 0] = 0.0
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    M = np.zeros((B, 35))
+    M[:, 0] = 1.0
+    M += d * np.exp(rng.uniform(np.log(1e-8), np.log(1e-3), B))[:, None]
+    Mt = T32(M, dev)
+    beta = torch.zeros_like(Mt)
+    st = torch.zeros(B, dtype=torch.int32, device=dev)
+    ctx.solve(Mt, beta, st, None, impl=mem.IMPL_MIXED, maxI=0, tol=0.0)
+    stn = st.cpu().numpy()
+    assert np.all(stn & mem.ST_MAXITER), np.unique(stn, return_counts=True)
+    ref = O.residual_batch(8, np64(beta), np64(Mt))
+    flagged = (stn & mem.ST_FP64_OK) != 0
+    margin = np.abs(ref / RES_TOL - 1.0) > 1e-6
+    assert flagged.any() and not flagged.all()
+    assert np.array_equal(flagged[margin], (ref <= RES_TOL)[margin])
+    ctx.close()

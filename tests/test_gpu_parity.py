@@ -394,7 +394,7 @@ def test_full_size_solve_sampled(O, mem, ctx8, dev):
     beta = torch.zeros_like(Mg)
     st = torch.zeros(B, dtype=torch.int32, device=dev)
     it = torch.zeros(B, dtype=torch.int32, device=dev)
-    ctx8.solve(Mg, beta, st, it)
+    ctx8.solve(Mg, beta, st, it, **EXT)
     torch.cuda.synchronize()
     stn = st.cpu().numpy()
     conv = (stn & (mem.ST_CONVERGED | mem.ST_STAGNATED)) != 0

@@ -175,6 +175,27 @@ int mem_quad_order(const mem_ctx *ctx);
 int mem_solve(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters,
               int64_t B, const mem_solve_opts *opts, void *stream);
 
+/* The paper's own system for axisymmetric flow on a velocity-space context
+ * (Appendix B: the nine statistics psi_j of (u_x, u_r) of Eq. "Sufficient
+ * 35" in orthonormal form, which are orthonormal combinations v_j of the 35
+ * Hermite products; Algorithm 1 over their eight natural parameters; the
+ * flux and the characteristic speed of the nine-moment system, Eq. "The lax
+ * F").  Per cell, in one warp:
+ *   M      dev [B][35] moments; only their projections M9_j = v_j . M are
+ *          read (the axisymmetric part);
+ *   beta   dev [B][35] in: warm start (projected likewise), out: the
+ *          solution sum_j alpha_j v_j (other entries 0), beta[0] = n;
+ *   gauge  dev [B][6], axisymmetric (w_y = w_z = 0, s_y = s_z);
+ *   status, iters dev [B] or NULL (MEM_ST_* bits, passes);
+ *   F      dev [B][35] or NULL: the flux of the nine moments, sum_j F9_j v_j;
+ *   speed  dev [B] or NULL: spectral radius of the 9 x 9 pencil, clamped to
+ *          the largest |u_x| of the nodes.
+ * For an axisymmetric cell this is the 35-statistic solve of mem_solve_gauge
+ * in exact arithmetic.  MEM_EINVAL on a Gauss-Hermite context or bad
+ * arguments.  No scratch memory. */
+int mem_solve_axi(mem_ctx *ctx, const float *M, float *beta, const float *gauge, int32_t *status, int32_t *iters,
+                  float *F, float *speed, int64_t B, const mem_solve_opts *opts, void *stream);
+
 /* Relative moment residual of B cells in FP64 on the GPU,
  *   res = || E_sigma[phi](beta) - M / n ||_2 / || M / n ||_2,
  * with sigma from the context's quadrature (Section 3.1, Eq. "Numerical
@@ -321,6 +342,15 @@ typedef struct {
     double t_end;      /* > 0: the step that would pass simulated time t_end
                           is cut to end there, and later steps leave the
                           problem as it is (dt = 0); 0: no limit          */
+    int32_t stats;     /* velocity-space rule only: 35 (default) solves the
+                          35-statistic system; 9 solves the paper's own
+                          nine-statistic system for axisymmetric flow
+                          (Appendix B, Eq. "Sufficient 35"; mem_solve_axi)
+                          in every cell and interface, with its flux and
+                          its characteristic speed.  The state stays the
+                          35 moments; for an axisymmetric flow both give
+                          the same solution up to rounding.  Must agree
+                          across a batch.                                 */
 } mem_shock_params;
 
 void mem_shock_params_default(mem_shock_params *p);

@@ -508,6 +508,7 @@ int mem_init_velocity(int degree, int nbx, int nbr, int ng, int K, double ax, do
     if (!rc) rc = upload(&ctx->d_vtf, vtf);
     if (!rc) rc = upload(&ctx->d_dom0, d0);
     if (!rc) rc = build_slot_tables(ctx);
+    if (!rc) rc = mem_host::build_axi_tables(ctx);
     if (!rc) rc = mem_host::reserve_scratch(ctx, sizeof(float) * (size_t)VEL_FLUX_CHUNK * MEM_MU_STRIDE);
     if (rc) { mem_destroy(ctx); return rc; }
     if (cudaDeviceSynchronize() != cudaSuccess) { mem_destroy(ctx); return MEM_ECUDA; }
@@ -527,7 +528,7 @@ void mem_destroy(mem_ctx *ctx) {
     cudaDeviceSynchronize();
     void *ptrs[] = {ctx->d_phiT, ctx->d_logw, ctx->d_tab_solve, ctx->d_tab_flux, ctx->d_he1d, ctx->d_x1d,
                     ctx->d_logw1d, ctx->d_lin_off, ctx->d_lin_terms, ctx->d_hess_slots, ctx->d_hess_slots128, ctx->d_hr_slots, ctx->d_hr_rounds, ctx->d_hr_ent, ctx->d_flux_slots, ctx->d_axi_slots, ctx->d_xlin_off, ctx->d_xlin_terms,
-                    ctx->scratch, ctx->d_vtd, ctx->d_vtf, ctx->d_dom0, ctx->d_tc_tab, ctx->d_phiT64, ctx->d_logw64};
+                    ctx->scratch, ctx->d_vtd, ctx->d_vtf, ctx->d_dom0, ctx->d_tc_tab, ctx->d_phiT64, ctx->d_logw64, ctx->d_axi_terms, ctx->d_axi_toff};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ctx->scratch_ev) cudaEventDestroy(ctx->scratch_ev);
@@ -551,6 +552,19 @@ int mem_solve(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_
     if (o.impl == MEM_IMPL_FUSED) return mem_host::solve_fused(ctx, M, beta, status, iters, B, o, st);
     if (o.impl == MEM_IMPL_MIXED) return mem_host::solve_mixed(ctx, M, beta, status, iters, B, o, st);
     return MEM_EINVAL;
+}
+
+int mem_solve_axi(mem_ctx *ctx, const float *M, float *beta, const float *gauge, int32_t *status, int32_t *iters,
+                  float *F, float *speed, int64_t B, const mem_solve_opts *opts, void *stream) {
+    if (!ctx || B < 0 || !ctx->vel) return MEM_EINVAL;
+    if (B == 0) return MEM_OK;
+    if (!M || !beta || !gauge) return MEM_EINVAL;
+    mem_solve_opts o;
+    mem_solve_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.maxI < 0 || o.maxT < 0 || o.maxT > 60 || o.max_lambda < 0 || o.max_lambda > 60) return MEM_EINVAL;
+    return mem_host::axi_run(ctx, M, beta, gauge, status, iters, F, speed, nullptr, nullptr, B, o, true,
+                             (cudaStream_t)stream);
 }
 
 int mem_residual64(mem_ctx *ctx, const float *M, const float *beta, const int32_t *status, int32_t mask, double *res,

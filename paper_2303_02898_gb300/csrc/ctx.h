@@ -57,6 +57,8 @@ struct mem_ctx {
     double *d_vtd = nullptr;  // [nx] x-node offsets | [nr] r-node offsets (block widths) | [K] cos | [K] sin
     float *d_vtf = nullptr;   // [nx] log w^GL of each x node | [nr] log(w^GL t_r / K) of each radial node
     double *d_dom0 = nullptr;                // the default domain (a_x, b_x, b_r, 0) on the device
+    int2 *d_axi_terms = nullptr;             // nine-statistic system: linearisation terms (mu index, coef)
+    int *d_axi_toff = nullptr;               // [91] term offsets of E[psi psi^T] and E[ubar_x psi psi^T]
     // Scratch owned by the context (plain solver, flux at orders without a
     // fused kernel, velocity-space flux), allocated once when the context is
     // created.  Calls that use it are ordered on the GPU through scratch_ev
@@ -101,6 +103,10 @@ int vel_run(mem_ctx *ctx, const float *M, float *beta, const float *g, int32_t *
             const int *pid, const double *dom, int64_t B, const mem_solve_opts &o, bool solve, cudaStream_t st,
             const unsigned char *active = nullptr, float *cond = nullptr);
 size_t vel_smem_bytes(int nx, int npt);
+int build_axi_tables(mem_ctx *ctx);
+int axi_run(mem_ctx *ctx, const float *M, float *beta, const float *g, int32_t *status, int32_t *iters, float *F,
+            float *speed, const int *pid, const double *dom, int64_t B, const mem_solve_opts &o, bool solve,
+            cudaStream_t st, const unsigned char *active = nullptr, float *cond = nullptr);
 int gl_rule(int n, std::vector<double> &x, std::vector<double> &w);
 int gauge_hermite(mem_ctx *ctx, const float *M_in, const float *g_in, float *g_out, float *M_out,
                   float *beta_inout, int64_t B, int axisym, cudaStream_t st);

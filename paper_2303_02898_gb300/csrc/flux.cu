@@ -64,85 +64,6 @@ struct FluxArgs {
 // replaced by the bound.
 __device__ __forceinline__ float clamp_speed(float sp, float bound) { return sp <= bound ? sp : bound; }
 
-// Extreme generalised eigenvalues of one small symmetric-definite pencil
-// (X, S), n <= 16, lower triangles in shared memory with leading dimension
-// 16: Cholesky S = L L^T (in place), C = L^{-1} X L^{-T} by right-looking
-// column solves (lane j < n owns column j) and a pairwise transpose, Lanczos
-// without re-orthogonalisation and Sturm multisection.  Returns false if S
-// is not numerically positive definite.  Not inlined: the axisymmetric speed
-// calls it three times, and three inlined copies overflow the instruction
-// cache once many warps are resident.
-__device__ __noinline__ bool small_pencil_extremes(float *S, float *X, int n, float *al, float *bt, float *sv,
-                                                      int lane, float &lo, float &hi) {
-    constexpr int LD = 16;
-    // Lane j < n owns column j throughout (no index decoding): it mirrors,
-    // transposes and symmetrises the pairs (i, j), i > j.
-    if (lane < n)
-        for (int i = lane + 1; i < n; ++i) X[lane * LD + i] = X[i * LD + lane];  // mirror X
-    __syncwarp();
-    if (!warp_cholesky(S, n, LD, lane)) return false;
-    if (lane < n) sv[lane] = 1.f / S[lane * LD + lane];  // 1 / L_kk (sv is free until Lanczos)
-    __syncwarp();
-    for (int pass = 0; pass < 2; ++pass) {
-        if (pass == 1) {
-            if (lane < n)
-                for (int i = lane + 1; i < n; ++i) {
-                    const float t = X[i * LD + lane];
-                    X[i * LD + lane] = X[lane * LD + i];
-                    X[lane * LD + i] = t;
-                }
-            __syncwarp();
-        }
-        if (lane < n) {
-            for (int k = 0; k < n; ++k) {
-                const float yk = X[k * LD + lane] * sv[k];
-                X[k * LD + lane] = yk;
-                for (int i = k + 1; i < n; ++i) X[i * LD + lane] -= S[i * LD + k] * yk;
-            }
-        }
-        __syncwarp();
-    }
-    // symmetrise C (in X) and run Lanczos (lane i < n holds v_i)
-    if (lane < n)
-        for (int i = lane + 1; i < n; ++i) {
-            const float sy = 0.5f * (X[i * LD + lane] + X[lane * LD + i]);
-            X[i * LD + lane] = sy;
-            X[lane * LD + i] = sy;
-        }
-    __syncwarp();
-    float cn = 0.f;
-    if (lane < n)
-        for (int i = 0; i < n; ++i) cn = fmaxf(cn, fabsf(X[i * LD + lane]));
-    const float cnorm = warp_max(cn) + 1e-30f;
-    __syncwarp();
-    float v = lane < n ? rsqrtf((float)n) : 0.f, vp = 0.f, bprev = 0.f;
-    int m = 0;
-    for (int k = 0; k < n; ++k) {
-        sv[lane] = v;
-        __syncwarp();
-        float w = 0.f;
-        if (lane < n)
-            for (int j = 0; j < n; ++j) w += X[j * LD + lane] * sv[j];
-        __syncwarp();
-        w -= bprev * vp;
-        const float a = warp_sum(w * v);
-        w -= a * v;
-        if (lane == 0) al[k] = a;
-        const float bk = sqrtf(warp_sum(w * w));
-        m = k + 1;
-        if (k + 1 == n || bk <= 1e-6f * cnorm) break;
-        if (lane == 0) bt[k] = bk;
-        vp = v;
-        v = w / bk;
-        bprev = bk;
-    }
-    __syncwarp();
-    hi = warp_tridiag_extreme(al, bt, m, true, lane);
-    lo = warp_tridiag_extreme(al, bt, m, false, lane);
-    __syncwarp();
-    return true;
-}
-
 // MU_IN: the moments of degree <= 9 come precomputed per cell (rows of
 // A.mu, with the node range of u_x in slots 220, 221) instead of from the
 // gauge-frame rule; everything after the moments is shared.

@@ -11,13 +11,21 @@
 // Layout (tc.cuh, K-major, no swizzle): the line-search kernel writes sigma
 // for tile t of 128 cells and K-chunk kc of 32 nodes as one 16 KB block
 // (hi and lo in two arrays); the constant statistics tables are stored the
-// same way, 352 rows (N) x 32 nodes (K) per block, in two column groups:
-//   group 0: rows 0-47 phi_hi (35 used), 48-95 phi_lo, 96-351 Hessian 0-255
-//   group 1: rows 0-338 Hessian 256-594 (rows 339-351 zero).
+// same way, ROWS_g rows (N) x 32 nodes (K) per block, in three column groups:
+//   group 0 (96 rows):  0-47 phi_hi (35 used), 48-95 phi_lo;
+//   group 1 (304 rows): Hessian entries 0-303;
+//   group 2 (304 rows): Hessian entries 304-594 (rows 291-303 zero).
 // One CTA (128 threads) computes one tile and one group: thread 0 issues the
 // bulk copies (TMA engine, double-buffered, mbarrier transaction counts) and
 // the MMAs (accumulators in TMEM); then all four warps read their 32 rows of
 // TMEM and write the moments row of each cell.  Every wait is bounded.
+//
+// Accumulation: the tensor cores add the products of one MMA into the FP32
+// accumulator with truncation, so a long chain of MMAs into one accumulator
+// drifts by about (number of K steps) x 2^-24 of the running sum, which at
+// 12^3 nodes reached 1e-5 in the moments.  The moment columns therefore
+// rotate over NACC accumulators (K-chunk kc into accumulator kc % NACC),
+// which the epilogue adds in FP32 with rounding to nearest.
 #include <string.h>
 
 #include <algorithm>
@@ -31,13 +39,21 @@ using namespace mem;
 
 namespace {
 
-constexpr int ROWS = 352;                   // N rows per group block
+constexpr int NGRP = 3;
+constexpr int ROWS0 = 96, ROWS12 = 304;      // N rows per block of group 0 / groups 1, 2
+constexpr int NACC = 10;                    // moment accumulators (48 columns each)
+constexpr int HSPLIT = 304;                 // Hessian entries of group 1
 constexpr int KCH = 32;                     // nodes per K-chunk
 constexpr uint32_t A_BYTES = 128 * KCH * 4;  // 16 KB
-constexpr uint32_t B_BYTES = ROWS * KCH * 4;  // 44 KB
 constexpr uint32_t SBO = KCH / 4 * 128;       // 1024: bytes between 8-row groups
-constexpr uint32_t STAGE = 2 * A_BYTES + B_BYTES;
+constexpr uint32_t STAGE = 2 * A_BYTES + ROWS12 * KCH * 4;
 constexpr uint32_t kMaxPolls = 1u << 22;
+
+__host__ __device__ constexpr int grp_rows(int g) { return g == 0 ? ROWS0 : ROWS12; }
+// first float of group g's blocks in the table (KC chunks per group)
+__host__ __device__ constexpr size_t grp_base(int g, int KC) {
+    return g == 0 ? 0 : (size_t)KC * KCH * (ROWS0 + (size_t)(g - 1) * ROWS12);
+}
 
 struct ContractArgs {
     const float *a_hi, *a_lo;  // [tiles][KC][128 x 32] tiled sigma
@@ -72,20 +88,21 @@ __global__ void __launch_bounds__(128, 1) k_tc_contract(ContractArgs A) {
     if (tid == 0) {
         bool failed = false;
         int loaded = 0;  // chunks whose copies were issued
+        const uint32_t b_bytes = (uint32_t)grp_rows(grp) * KCH * 4;
         auto load = [&](int kc) {
             const int s = kc & 1;
             uint8_t *st = smem + s * STAGE;
             const size_t ablk = ((size_t)tile * KC + kc) * (A_BYTES / 4);
-            const size_t bblk = ((size_t)grp * KC + kc) * (B_BYTES / 4);
-            const uint32_t bytes = (grp == 0 ? 2 * A_BYTES : A_BYTES) + B_BYTES;
+            const size_t bblk = grp_base(grp, KC) + (size_t)kc * (b_bytes / 4);
+            const uint32_t bytes = (grp == 0 ? 2 * A_BYTES : A_BYTES) + b_bytes;
             tc::mbar_expect_tx(&s_full[s], bytes);
             tc::bulk_g2s(st, A.a_hi + ablk, A_BYTES, &s_full[s]);
             if (grp == 0) tc::bulk_g2s(st + A_BYTES, A.a_lo + ablk, A_BYTES, &s_full[s]);
-            tc::bulk_g2s(st + 2 * A_BYTES, A.tab + bblk, B_BYTES, &s_full[s]);
+            tc::bulk_g2s(st + 2 * A_BYTES, A.tab + bblk, b_bytes, &s_full[s]);
             loaded = kc + 1;
         };
         load(0);
-        const uint32_t id48 = tc::idesc(128, 48, 2), id256 = tc::idesc(128, 256, 2), id96 = tc::idesc(128, 96, 2);
+        const uint32_t id48 = tc::idesc(128, 48, 2), id256 = tc::idesc(128, 256, 2);
         int kc = 0;
         for (; kc < KC && !failed; ++kc) {
             if (kc + 1 < KC) {
@@ -103,24 +120,24 @@ __global__ void __launch_bounds__(128, 1) k_tc_contract(ContractArgs A) {
             tc::fence_after_sync();
             const uint32_t base = tc::smem_u32(smem + (kc & 1) * STAGE);
             const uint32_t ahi = base, alo = base + A_BYTES, b = base + 2 * A_BYTES;
+            const uint32_t dacc = tmem + (uint32_t)(48 * (kc % NACC));  // moment accumulator of this chunk
 #pragma unroll
             for (int s = 0; s < KCH / 8; ++s) {
-                const uint32_t acc = (kc | s) != 0;
                 const uint64_t dh = tc::sdesc(ahi + 256 * s, 128, SBO);
                 if (grp == 0) {
+                    const uint32_t acc = (kc >= NACC) || s != 0;
                     const uint64_t dl = tc::sdesc(alo + 256 * s, 128, SBO);
                     const uint64_t bmh = tc::sdesc(b + 256 * s, 128, SBO);
                     const uint64_t bml = tc::sdesc(b + 6 * SBO + 256 * s, 128, SBO);
-                    const uint64_t bh = tc::sdesc(b + 12 * SBO + 256 * s, 128, SBO);
-                    tc::mma_tf32(tmem, dl, bmh, id48, acc);   // lo . hi
-                    tc::mma_tf32(tmem, dh, bml, id48, 1);     // hi . lo
-                    tc::mma_tf32(tmem, dh, bmh, id48, 1);     // hi . hi
-                    tc::mma_tf32(tmem + 48, dh, bh, id256, acc);
+                    tc::mma_tf32(dacc, dl, bmh, id48, acc);   // lo . hi
+                    tc::mma_tf32(dacc, dh, bml, id48, 1);     // hi . lo
+                    tc::mma_tf32(dacc, dh, bmh, id48, 1);     // hi . hi
                 } else {
+                    const uint32_t acc = (kc | s) != 0;
                     const uint64_t b0 = tc::sdesc(b + 256 * s, 128, SBO);
                     const uint64_t b1 = tc::sdesc(b + 32 * SBO + 256 * s, 128, SBO);
                     tc::mma_tf32(tmem, dh, b0, id256, acc);
-                    tc::mma_tf32(tmem + 256, dh, b1, id96, acc);
+                    tc::mma_tf32(tmem + 256, dh, b1, id48, acc);
                 }
             }
             tc::mma_commit(&s_empty[kc & 1]);
@@ -148,26 +165,30 @@ __global__ void __launch_bounds__(128, 1) k_tc_contract(ContractArgs A) {
         float *m = A.mom + (size_t)cell * MEM_NCOL_SOLVE;
         const bool live = cell < A.n;
         if (grp == 0) {
+            const int nacc = KC < NACC ? KC : NACC;
+            for (int c = 0; c < 40; c += 8) {
+                float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int q = 0; q < nacc; ++q) {
+                    float v[8];
+                    tc::tmem_ld8(tl + (uint32_t)(48 * q + c), v);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) sum[j] += v[j];
+                }
+                if (live) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (c + j < NP) m[c + j] = sum[j];
+                }
+            }
+        } else {
+            const int off = grp == 1 ? 0 : HSPLIT, cnt = grp == 1 ? HSPLIT : NP1 * NP / 2 - HSPLIT;
             for (int c = 0; c < 304; c += 8) {
                 float v[8];
                 tc::tmem_ld8(tl + (uint32_t)c, v);
                 if (live) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int col = c + j;
-                        if (col < NP) m[col] = v[j];
-                        else if (col >= 48) m[NP + col - 48] = v[j];
-                    }
-                }
-            }
-        } else {
-            for (int c = 0; c < 344; c += 8) {
-                float v[8];
-                tc::tmem_ld8(tl + (uint32_t)c, v);
-                if (live) {
-#pragma unroll
                     for (int j = 0; j < 8; ++j)
-                        if (c + j < 339) m[NP + 256 + c + j] = v[j];
+                        if (c + j < cnt) m[NP + off + c + j] = v[j];
                 }
             }
         }
@@ -202,10 +223,10 @@ int build_tc_tables(mem_ctx *ctx, const std::vector<double> &phi /*[Q][35]*/) {
     const int Q = ctx->Q;
     if (Q % KCH) return MEM_OK;  // no tensor-core path for this order
     const int KC = Q / KCH;
-    std::vector<float> tab((size_t)2 * KC * ROWS * KCH, 0.f);
+    std::vector<float> tab(grp_base(NGRP, KC), 0.f);
     auto put = [&](int grp, int row, int q, float v) {
         const int kc = q / KCH, k = q % KCH;
-        const size_t blk = ((size_t)grp * KC + kc) * ROWS * KCH;
+        const size_t blk = grp_base(grp, KC) + (size_t)kc * grp_rows(grp) * KCH;
         const size_t off = (size_t)(row >> 3) * (SBO / 4) + (size_t)(k >> 2) * 32 + (row & 7) * 4 + (k & 3);
         tab[blk + off] = v;
     };
@@ -220,8 +241,8 @@ int build_tc_tables(mem_ctx *ctx, const std::vector<double> &phi /*[Q][35]*/) {
             for (int j = 1; j <= i; ++j) {
                 const int p = (i - 1) * i / 2 + (j - 1);
                 const float v = tf32_host((float)(ph[i] * ph[j]));
-                if (p < 256) put(0, 96 + p, q, v);
-                else put(1, p - 256, q, v);
+                if (p < HSPLIT) put(1, p, q, v);
+                else put(2, p - HSPLIT, q, v);
             }
     }
     if (cudaMalloc((void **)&ctx->d_tc_tab, sizeof(float) * tab.size()) != cudaSuccess) {
@@ -245,7 +266,7 @@ int tc_contract(mem_ctx *ctx, const float *a_hi, const float *a_lo, float *mom, 
         configured = true;
     }
     ContractArgs a{a_hi, a_lo, ctx->d_tc_tab, mom, n, ctx->Q / KCH, err};
-    dim3 grid((n + 127) / 128, 2);
+    dim3 grid((n + 127) / 128, NGRP);
     k_tc_contract<<<grid, 128, smem, st>>>(a);
     MEM_CUDA_TRY(cudaGetLastError());
     return MEM_OK;

@@ -465,7 +465,7 @@ bool shock_params_valid(const mem_shock_params &p) {
     return p.ncells >= 1 && p.xr > p.xl && p.mach >= 1.0 && p.cfl > 0 && p.Pr > 0.5 && p.gamma > 1.0 && p.kn > 0 &&
            (p.ic == 0 || p.ic == 1) && p.maxI >= 0 && (p.impl == MEM_IMPL_PLAIN || p.impl == MEM_IMPL_FUSED) &&
            p.na > 0 && p.nb > 0 && p.nr > 0 && p.scheme >= MEM_SCHEME_LF && p.scheme <= MEM_SCHEME_FLIC &&
-           (p.ic == 0 || p.thickness > 0) && p.t_end >= 0.0;
+           (p.ic == 0 || p.thickness > 0) && p.t_end >= 0.0 && (p.stats == 35 || p.stats == 9);
 }
 
 // Device bytes per packed cell, the interface arrays of Lax-Wendroff / FLIC
@@ -653,6 +653,7 @@ int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **o
     // Natural parameters of the initial state (the tanh blend is not a
     // Maxwellian), then the characteristic speeds that set the first dt.
     int rc = MEM_OK;
+    const bool nine = ps[0].stats == 9;
     bool any_tanh = false;
     for (int i = 0; i < P; ++i) any_tanh |= ps[i].ic == 1;
     if (any_tanh) {
@@ -660,11 +661,19 @@ int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **o
         mem_solve_opts_default(&o);
         o.tol = ps[0].tol;
         o.maxI = ps[0].maxI;
-        rc = ctx->vel ? vel_run(ctx, b->M, b->beta, b->g, b->status, b->iters, nullptr, b->pid, b->dom, (int64_t)NT, o,
-                                true, 0, b->interior)
-                      : solve_fused(ctx, b->M, b->beta, b->status, b->iters, (int64_t)NT, o, 0, b->interior);
+        rc = (ctx->vel && nine)
+                 ? axi_run(ctx, b->M, b->beta, b->g, b->status, b->iters, nullptr, nullptr, b->pid, b->dom,
+                           (int64_t)NT, o, true, 0, b->interior)
+             : ctx->vel ? vel_run(ctx, b->M, b->beta, b->g, b->status, b->iters, nullptr, b->pid, b->dom, (int64_t)NT,
+                                  o, true, 0, b->interior)
+                        : solve_fused(ctx, b->M, b->beta, b->status, b->iters, (int64_t)NT, o, 0, b->interior);
     }
-    if (!rc && ctx->vel) {
+    if (!rc && ctx->vel && nine) {
+        mem_solve_opts o;
+        mem_solve_opts_default(&o);
+        rc = axi_run(ctx, b->M, b->beta, b->g, nullptr, nullptr, b->F, b->speed, b->pid, b->dom, (int64_t)NT, o, false,
+                     0);
+    } else if (!rc && ctx->vel) {
         mem_solve_opts o;
         mem_solve_opts_default(&o);
         rc = vel_run(ctx, b->M, b->beta, b->g, nullptr, nullptr, b->mu, b->pid, b->dom, (int64_t)NT, o, false, 0);
@@ -689,7 +698,13 @@ int batch_enqueue_step(ShockBatch *b, cudaStream_t st) {
     o.tol = p0.tol;
     o.maxI = p0.maxI;
     int rc;
-    if (b->ctx->vel) {
+    const bool nine = p0.stats == 9;
+    if (b->ctx->vel && nine) {
+        // the paper's nine-statistic system: solve, flux and speed in one
+        // launch (ghost cells: flux and speed only)
+        rc = axi_run(b->ctx, b->M, b->beta, b->g, b->status, b->iters, b->F, b->speed, b->pid, b->dom, NT, o, true, st,
+                     b->interior, b->cond);
+    } else if (b->ctx->vel) {
         // Velocity-space rule: the solve kernel also leaves the moments of
         // degree <= 9 at the new beta (ghost cells included), and the speed
         // kernel reads them.
@@ -711,7 +726,10 @@ int batch_enqueue_step(ShockBatch *b, cudaStream_t st) {
         // in the interface's Hermite gauge (no speeds needed there).
         k_iface_state<<<nb, 128, 0, st>>>(b->M, b->F, b->g, b->beta, b->MI, b->gI, b->betaI, b->statusI, b->iface,
                                           b->pid, b->prm, b->sc, NT);
-        if (b->ctx->vel) {
+        if (b->ctx->vel && nine) {
+            rc = axi_run(b->ctx, b->MI, b->betaI, b->gI, b->statusI, b->itersI, b->FI, nullptr, b->pid, b->dom, NT, o,
+                         true, st, b->iface);
+        } else if (b->ctx->vel) {
             rc = vel_run(b->ctx, b->MI, b->betaI, b->gI, b->statusI, b->itersI, b->mu, b->pid, b->dom, NT, o, true, st,
                          b->iface);
             if (!rc) rc = flux_from_mu(b->ctx, b->mu, b->MI, b->gI, b->FI, nullptr, NT, st, true);
@@ -849,6 +867,7 @@ void mem_shock_params_default(mem_shock_params *p) {
     p->scheme = MEM_SCHEME_LF;
     p->thickness = 15.7;
     p->t_end = 0.0;
+    p->stats = 35;
 }
 
 void mem_shock_free(mem_shock *s) {
@@ -863,7 +882,9 @@ void mem_shock_free(mem_shock *s) {
 int mem_shock_init_batch(mem_ctx *ctx, const mem_shock_params *ps, int nprob, mem_shock **out) {
     if (!ctx || !ps || !out || nprob < 1) return MEM_EINVAL;
     for (int i = 1; i < nprob; ++i)
-        if (ps[i].impl != ps[0].impl || ps[i].tol != ps[0].tol || ps[i].maxI != ps[0].maxI) return MEM_EINVAL;
+        if (ps[i].impl != ps[0].impl || ps[i].tol != ps[0].tol || ps[i].maxI != ps[0].maxI ||
+            ps[i].stats != ps[0].stats)
+            return MEM_EINVAL;
     *out = nullptr;
     mem_host::ShockBatch *b = nullptr;
     int rc = mem_host::batch_create(ctx, ps, nprob, &b);

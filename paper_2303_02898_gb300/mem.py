@@ -37,7 +37,7 @@ class ShockParams(ctypes.Structure):
                 ("impl", ctypes.c_int32), ("graph", ctypes.c_int32), ("tol", ctypes.c_float),
                 ("maxI", ctypes.c_int32), ("na", ctypes.c_double), ("nb", ctypes.c_double),
                 ("nr", ctypes.c_double), ("scheme", ctypes.c_int32), ("thickness", ctypes.c_double),
-                ("t_end", ctypes.c_double)]
+                ("t_end", ctypes.c_double), ("stats", ctypes.c_int32)]
 
 
 SCHEME_LF, SCHEME_LW, SCHEME_FLIC = 0, 1, 2
@@ -94,6 +94,8 @@ def lib():
         L.mem_serve_create.argtypes = [_P, ctypes.c_size_t, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _P]
         L.mem_serve_progress.argtypes = [_P, ctypes.c_int, _P]
         L.mem_serve_poll.argtypes = [_P, ctypes.c_uint64, _P, _P, _P, _P]
+        L.mem_solve_axi.restype = ctypes.c_int
+        L.mem_solve_axi.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(SolveOpts), _P]
         L.mem_residual64.restype = ctypes.c_int
         L.mem_residual64.argtypes = [_P, _P, _P, _P, ctypes.c_int32, _P, _P, ctypes.c_double, ctypes.c_int64, _P]
         L.mem_bench_peak.restype = ctypes.c_int
@@ -195,6 +197,14 @@ class Context:
         rc = lib().mem_solve_gauge(self.h, _ptr(M), _ptr(beta), _ptr(gauge), _ptr(status), _ptr(iters), B,
                                    ctypes.byref(o), _stream(stream))
         _check(rc, "mem_solve_gauge")
+
+    def solve_axi(self, M, beta, gauge, status=None, iters=None, F=None, speed=None, opts=None, stream=None, **kw):
+        """mem_solve_axi: the paper's nine-statistic system (velocity-space rules):
+        Algorithm 1, flux and speed per axisymmetric cell."""
+        o = opts if opts is not None else default_opts(**kw)
+        rc = lib().mem_solve_axi(self.h, _ptr(M), _ptr(beta), _ptr(gauge), _ptr(status), _ptr(iters), _ptr(F),
+                                 _ptr(speed), M.shape[0], ctypes.byref(o), _stream(stream))
+        _check(rc, "mem_solve_axi")
 
     def residual64(self, M, beta, res, status=None, mask=0, status_out=None, accept=1e-5, stream=None):
         """mem_residual64: FP64 relative moment residual per cell (res: float64

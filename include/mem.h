@@ -448,14 +448,18 @@ int mem_serve_create(mem_ctx *ctx, size_t hbm_budget_bytes, int32_t max_cells, d
                      int32_t max_steps, mem_server **out);
 
 /* Queue a request (host only, no device work).  The server uses the fused
- * Newton back-end with the paper's defaults for every request.  Returns
- * MEM_OK and *req_id, MEM_EINVAL for invalid parameters, or MEM_EBUSY when
- * the request alone exceeds the memory or cell budget. */
+ * Newton back-end with the paper's defaults for every request, and the
+ * statistics system (mem_shock_params.stats) of its first request for all
+ * of them.  Returns MEM_OK and *req_id, MEM_EINVAL for invalid parameters or
+ * another statistics system, or MEM_EBUSY when the request alone exceeds
+ * the memory or cell budget. */
 int mem_serve_submit(mem_server *sv, const mem_shock_params *p, uint64_t *req_id);
 
 /* Admit queued requests that fit, run `iters` time steps of every resident
  * problem on `stream`, then retire problems that completed (profiles copied
- * to the host) and admit more.  Synchronises the stream. */
+ * to the host) and admit more.  The time step of each packed batch is
+ * captured in a CUDA graph after its first step and replayed until the
+ * membership changes.  Synchronises the stream. */
 int mem_serve_progress(mem_server *sv, int iters, void *stream);
 
 /* Poll a request: MEM_OK (result filled; rho/ux/T, each ncells long, copied

@@ -24,8 +24,8 @@
 // accumulator with truncation, so a long chain of MMAs into one accumulator
 // drifts by about (number of K steps) x 2^-24 of the running sum, which at
 // 12^3 nodes reached 1e-5 in the moments.  The moment columns therefore
-// rotate over NACC accumulators (K-chunk kc into accumulator kc % NACC),
-// which the epilogue adds in FP32 with rounding to nearest.
+// start a fresh accumulator for every K-chunk of 32 nodes, and the reading
+// warps add the chunk sums in FP32 registers with rounding to nearest.
 #include <string.h>
 
 #include <algorithm>
@@ -41,7 +41,6 @@ namespace {
 
 constexpr int NGRP = 3;
 constexpr int ROWS0 = 96, ROWS12 = 304;      // N rows per block of group 0 / groups 1, 2
-constexpr int NACC = 10;                    // moment accumulators (48 columns each)
 constexpr int HSPLIT = 304;                 // Hessian entries of group 1
 constexpr int KCH = 32;                     // nodes per K-chunk
 constexpr uint32_t A_BYTES = 128 * KCH * 4;  // 16 KB
@@ -63,11 +62,19 @@ struct ContractArgs {
     int *err;
 };
 
-__global__ void __launch_bounds__(128, 1) k_tc_contract(ContractArgs A) {
+// Warps 0-3 own the 128 accumulator lanes (cells); warp 4 issues the bulk
+// copies and the MMAs.  Group 0 (the moments): each K-chunk's three split
+// products go into a fresh accumulator buffer (NB buffers in rotation), which
+// warps 0-3 add into FP32 registers as soon as the chunk completes, so no
+// accumulator chain is longer than one chunk.  Groups 1, 2 (the Hessian):
+// one accumulator chain over all chunks, read once at the end.
+constexpr int NB = 8;  // moment accumulator buffers (48 columns each)
+
+__global__ void __launch_bounds__(160, 1) k_tc_contract(ContractArgs A) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_full[2], s_empty[2], s_done;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    __shared__ __align__(8) uint64_t s_full[2], s_empty[2], s_done, s_accf[NB], s_acce[NB];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tile = blockIdx.x, grp = blockIdx.y;
     if (warp == 0) {
         tc::tmem_alloc(&s_tmem, 512);
@@ -79,108 +86,133 @@ __global__ void __launch_bounds__(128, 1) k_tc_contract(ContractArgs A) {
         tc::mbar_init(&s_empty[0], 1);
         tc::mbar_init(&s_empty[1], 1);
         tc::mbar_init(&s_done, 1);
+        for (int b = 0; b < NB; ++b) {
+            tc::mbar_init(&s_accf[b], 1);  // the MMAs of a chunk are done
+            tc::mbar_init(&s_acce[b], 4);  // the four reading warps are done with it
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = s_tmem;
     const int KC = A.KC;
-    if (tid == 0) {
-        bool failed = false;
-        int loaded = 0;  // chunks whose copies were issued
-        const uint32_t b_bytes = (uint32_t)grp_rows(grp) * KCH * 4;
-        auto load = [&](int kc) {
-            const int s = kc & 1;
-            uint8_t *st = smem + s * STAGE;
-            const size_t ablk = ((size_t)tile * KC + kc) * (A_BYTES / 4);
-            const size_t bblk = grp_base(grp, KC) + (size_t)kc * (b_bytes / 4);
-            const uint32_t bytes = (grp == 0 ? 2 * A_BYTES : A_BYTES) + b_bytes;
-            tc::mbar_expect_tx(&s_full[s], bytes);
-            tc::bulk_g2s(st, A.a_hi + ablk, A_BYTES, &s_full[s]);
-            if (grp == 0) tc::bulk_g2s(st + A_BYTES, A.a_lo + ablk, A_BYTES, &s_full[s]);
-            tc::bulk_g2s(st + 2 * A_BYTES, A.tab + bblk, b_bytes, &s_full[s]);
-            loaded = kc + 1;
-        };
-        load(0);
-        const uint32_t id48 = tc::idesc(128, 48, 2), id256 = tc::idesc(128, 256, 2);
-        int kc = 0;
-        for (; kc < KC && !failed; ++kc) {
-            if (kc + 1 < KC) {
-                // stage (kc+1)&1 was last read by the MMAs of chunk kc-1
-                if (kc >= 1 && !tc::mbar_wait(&s_empty[(kc + 1) & 1], ((kc - 1) >> 1) & 1, kMaxPolls)) {
+    if (warp == 4) {
+        if (lane == 0) {
+            bool failed = false;
+            int loaded = 0;  // chunks whose copies were issued
+            const uint32_t b_bytes = (uint32_t)grp_rows(grp) * KCH * 4;
+            auto load = [&](int kc) {
+                const int s = kc & 1;
+                uint8_t *st = smem + s * STAGE;
+                const size_t ablk = ((size_t)tile * KC + kc) * (A_BYTES / 4);
+                const size_t bblk = grp_base(grp, KC) + (size_t)kc * (b_bytes / 4);
+                const uint32_t bytes = (grp == 0 ? 2 * A_BYTES : A_BYTES) + b_bytes;
+                tc::mbar_expect_tx(&s_full[s], bytes);
+                tc::bulk_g2s(st, A.a_hi + ablk, A_BYTES, &s_full[s]);
+                if (grp == 0) tc::bulk_g2s(st + A_BYTES, A.a_lo + ablk, A_BYTES, &s_full[s]);
+                tc::bulk_g2s(st + 2 * A_BYTES, A.tab + bblk, b_bytes, &s_full[s]);
+                loaded = kc + 1;
+            };
+            load(0);
+            const uint32_t id48 = tc::idesc(128, 48, 2), id256 = tc::idesc(128, 256, 2);
+            int kc = 0;
+            for (; kc < KC; ++kc) {
+                if (kc + 1 < KC) {
+                    // stage (kc+1)&1 was last read by the MMAs of chunk kc-1
+                    if (kc >= 1 && !tc::mbar_wait(&s_empty[(kc + 1) & 1], ((kc - 1) >> 1) & 1, kMaxPolls)) {
+                        failed = true;
+                        break;
+                    }
+                    load(kc + 1);
+                }
+                if (!tc::mbar_wait(&s_full[kc & 1], (kc >> 1) & 1, kMaxPolls)) {
                     failed = true;
                     break;
                 }
-                load(kc + 1);
-            }
-            if (!tc::mbar_wait(&s_full[kc & 1], (kc >> 1) & 1, kMaxPolls)) {
-                failed = true;
-                break;
-            }
-            tc::fence_after_sync();
-            const uint32_t base = tc::smem_u32(smem + (kc & 1) * STAGE);
-            const uint32_t ahi = base, alo = base + A_BYTES, b = base + 2 * A_BYTES;
-            const uint32_t dacc = tmem + (uint32_t)(48 * (kc % NACC));  // moment accumulator of this chunk
-#pragma unroll
-            for (int s = 0; s < KCH / 8; ++s) {
-                const uint64_t dh = tc::sdesc(ahi + 256 * s, 128, SBO);
-                if (grp == 0) {
-                    const uint32_t acc = (kc >= NACC) || s != 0;
-                    const uint64_t dl = tc::sdesc(alo + 256 * s, 128, SBO);
-                    const uint64_t bmh = tc::sdesc(b + 256 * s, 128, SBO);
-                    const uint64_t bml = tc::sdesc(b + 6 * SBO + 256 * s, 128, SBO);
-                    tc::mma_tf32(dacc, dl, bmh, id48, acc);   // lo . hi
-                    tc::mma_tf32(dacc, dh, bml, id48, 1);     // hi . lo
-                    tc::mma_tf32(dacc, dh, bmh, id48, 1);     // hi . hi
-                } else {
-                    const uint32_t acc = (kc | s) != 0;
-                    const uint64_t b0 = tc::sdesc(b + 256 * s, 128, SBO);
-                    const uint64_t b1 = tc::sdesc(b + 32 * SBO + 256 * s, 128, SBO);
-                    tc::mma_tf32(tmem, dh, b0, id256, acc);
-                    tc::mma_tf32(tmem + 256, dh, b1, id48, acc);
+                const int bf = kc % NB;
+                if (grp == 0 && kc >= NB && !tc::mbar_wait(&s_acce[bf], ((kc / NB) - 1) & 1, kMaxPolls)) {
+                    failed = true;
+                    break;
                 }
+                tc::fence_after_sync();
+                const uint32_t base = tc::smem_u32(smem + (kc & 1) * STAGE);
+                const uint32_t ahi = base, alo = base + A_BYTES, b = base + 2 * A_BYTES;
+                const uint32_t dacc = tmem + (uint32_t)(48 * bf);
+#pragma unroll
+                for (int s = 0; s < KCH / 8; ++s) {
+                    const uint64_t dh = tc::sdesc(ahi + 256 * s, 128, SBO);
+                    if (grp == 0) {
+                        const uint64_t dl = tc::sdesc(alo + 256 * s, 128, SBO);
+                        const uint64_t bmh = tc::sdesc(b + 256 * s, 128, SBO);
+                        const uint64_t bml = tc::sdesc(b + 6 * SBO + 256 * s, 128, SBO);
+                        tc::mma_tf32(dacc, dl, bmh, id48, s != 0);  // lo . hi (a fresh chunk sum)
+                        tc::mma_tf32(dacc, dh, bml, id48, 1);       // hi . lo
+                        tc::mma_tf32(dacc, dh, bmh, id48, 1);       // hi . hi
+                    } else {
+                        const uint32_t acc = (kc | s) != 0;
+                        const uint64_t b0 = tc::sdesc(b + 256 * s, 128, SBO);
+                        const uint64_t b1 = tc::sdesc(b + 32 * SBO + 256 * s, 128, SBO);
+                        tc::mma_tf32(tmem, dh, b0, id256, acc);
+                        tc::mma_tf32(tmem + 256, dh, b1, id48, acc);
+                    }
+                }
+                tc::mma_commit(&s_empty[kc & 1]);
+                if (grp == 0) tc::mma_commit(&s_accf[bf]);
             }
-            tc::mma_commit(&s_empty[kc & 1]);
+            if (failed) {
+                atomicExch(A.err, 1);
+                // copies still in flight land in this CTA's shared memory:
+                // wait for them (bounded) before the CTA can exit
+                for (int j = kc; j < loaded; ++j) tc::mbar_wait(&s_full[j & 1], (j >> 1) & 1, kMaxPolls);
+            }
+            tc::mma_commit(&s_done);  // every MMA issued above
         }
-        if (failed) {
-            atomicExch(A.err, 1);
-            // copies still in flight land in this CTA's shared memory: wait
-            // for them (bounded) before the CTA can exit
-            for (int j = kc; j < loaded; ++j) tc::mbar_wait(&s_full[j & 1], (j >> 1) & 1, kMaxPolls);
-        }
-        tc::mma_commit(&s_done);  // every MMA issued above
-    }
-    __syncwarp();
-    bool ok = tc::mbar_wait(&s_done, 0, kMaxPolls);
-    if (!ok) {
-        atomicExch(A.err, 1);
-        tc::mbar_wait(&s_done, 0, kMaxPolls);
-    }
-    ok = __all_sync(0xffffffffu, ok);
-    tc::fence_after_sync();
-    const int row = 32 * (warp & 3) + (tid & 31);
-    const int cell = tile * 128 + row;
-    const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-    if (ok) {
-        float *m = A.mom + (size_t)cell * MEM_NCOL_SOLVE;
+        __syncwarp();
+    } else {
+        const int row = 32 * warp + lane;
+        const int cell = tile * 128 + row;
         const bool live = cell < A.n;
+        const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
+        float *m = A.mom + (size_t)cell * MEM_NCOL_SOLVE;
+        bool ok = true;
         if (grp == 0) {
-            const int nacc = KC < NACC ? KC : NACC;
-            for (int c = 0; c < 40; c += 8) {
-                float sum[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                for (int q = 0; q < nacc; ++q) {
+            float sum[40];
+#pragma unroll
+            for (int c = 0; c < 40; ++c) sum[c] = 0.f;
+            for (int kc = 0; kc < KC; ++kc) {
+                const int bf = kc % NB;
+                ok = tc::mbar_wait(&s_accf[bf], (kc / NB) & 1, kMaxPolls);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                tc::fence_after_sync();
+#pragma unroll
+                for (int c = 0; c < 40; c += 8) {
                     float v[8];
-                    tc::tmem_ld8(tl + (uint32_t)(48 * q + c), v);
+                    tc::tmem_ld8(tl + (uint32_t)(48 * bf + c), v);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) sum[j] += v[j];
+                    for (int j = 0; j < 8; ++j) sum[c + j] += v[j];
                 }
-                if (live) {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        if (c + j < NP) m[c + j] = sum[j];
-                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&s_acce[bf]))
+                                            : "memory");
             }
-        } else {
+            if (!ok) atomicExch(A.err, 1);
+            if (ok && live) {
+#pragma unroll
+                for (int c = 0; c < NP; ++c) m[c] = sum[c];
+            }
+        }
+        // every MMA of the CTA is complete before its accumulators are read
+        // (groups 1, 2) or released
+        bool done = tc::mbar_wait(&s_done, 0, kMaxPolls);
+        if (!done) {
+            atomicExch(A.err, 1);
+            done = tc::mbar_wait(&s_done, 0, kMaxPolls);
+        }
+        done = __all_sync(0xffffffffu, done);
+        tc::fence_after_sync();
+        if (grp != 0 && done) {
             const int off = grp == 1 ? 0 : HSPLIT, cnt = grp == 1 ? HSPLIT : NP1 * NP / 2 - HSPLIT;
             for (int c = 0; c < 304; c += 8) {
                 float v[8];
@@ -267,7 +299,7 @@ int tc_contract(mem_ctx *ctx, const float *a_hi, const float *a_lo, float *mom, 
     }
     ContractArgs a{a_hi, a_lo, ctx->d_tc_tab, mom, n, ctx->Q / KCH, err};
     dim3 grid((n + 127) / 128, NGRP);
-    k_tc_contract<<<grid, 128, smem, st>>>(a);
+    k_tc_contract<<<grid, 160, smem, st>>>(a);
     MEM_CUDA_TRY(cudaGetLastError());
     return MEM_OK;
 }

@@ -8,7 +8,9 @@
 // to the host -- and queued requests are admitted while the cell and
 // device-memory budgets allow.  Membership changes repack the batch:
 // surviving problems' state is copied device-to-device into the new layout,
-// so a problem's trajectory does not depend on who else is resident.
+// so a problem's trajectory does not depend on who else is resident.  Each
+// packed batch's time step is captured once in a CUDA graph (after one
+// uncaptured step) and replayed for every step until the membership changes.
 #include <algorithm>
 #include <chrono>
 #include <deque>
@@ -53,6 +55,9 @@ struct mem_server {
     ShockBatch *batch = nullptr;
     std::map<uint64_t, Done> done;
     uint64_t next_id = 1;
+    int stats = 0;  // statistics system of every request (the first request's)
+    cudaGraph_t graph = nullptr;      // one time step of the current batch
+    cudaGraphExec_t gexec = nullptr;
     std::mutex mu;
 };
 
@@ -62,6 +67,50 @@ size_t cells_of(const std::vector<Req> &v) {
     size_t c = 0;
     for (auto &r : v) c += (size_t)r.p.ncells + 2;
     return c;
+}
+
+void drop_graph(mem_server *sv) {
+    if (sv->gexec) cudaGraphExecDestroy(sv->gexec);
+    if (sv->graph) cudaGraphDestroy(sv->graph);
+    sv->gexec = nullptr;
+    sv->graph = nullptr;
+}
+
+// k time steps of the resident batch: the first step of a new batch runs
+// uncaptured (kernels set their launch attributes on first use), then one
+// step is captured on a private stream and replayed.
+int step_batch(mem_server *sv, int k, cudaStream_t st) {
+    if (k <= 0) return MEM_OK;
+    if (!sv->gexec) {
+        int rc = mem_host::batch_enqueue_step(sv->batch, st);
+        if (rc) return rc;
+        if (--k == 0) return MEM_OK;
+        MEM_CUDA_TRY(cudaStreamSynchronize(st));
+        cudaStream_t cap;
+        MEM_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            rc = mem_host::batch_enqueue_step(sv->batch, cap);
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(cap, &g);
+            if (e == cudaSuccess && !rc) {
+                sv->graph = g;
+                e = cudaGraphInstantiate(&sv->gexec, g, 0);
+                if (e != cudaSuccess) sv->gexec = nullptr;
+            } else if (g) {
+                cudaGraphDestroy(g);
+            }
+        }
+        cudaStreamDestroy(cap);
+        if (rc) return rc;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            drop_graph(sv);
+            return MEM_ECUDA;
+        }
+    }
+    for (int i = 0; i < k; ++i) MEM_CUDA_TRY(cudaGraphLaunch(sv->gexec, st));
+    return MEM_OK;
 }
 
 // Retire every resident problem with error code rc (their device state is
@@ -83,6 +132,7 @@ void fail_resident(mem_server *sv, int rc) {
 // Rebuild the packed batch for the current resident list; problems that were
 // already resident keep their state (copied device to device).
 int rebuild(mem_server *sv, const std::vector<Req> &old_list, cudaStream_t st) {
+    drop_graph(sv);
     ShockBatch *old = sv->batch;
     sv->batch = nullptr;
     if (sv->resident.empty()) {
@@ -184,6 +234,8 @@ int mem_serve_submit(mem_server *sv, const mem_shock_params *p, uint64_t *req_id
     const size_t c = (size_t)q.ncells + 2;
     if (c > (size_t)sv->max_cells || c * mem_host::batch_bytes_per_cell(sv->ctx) > sv->budget) return MEM_EBUSY;
     std::lock_guard<std::mutex> lock(sv->mu);
+    if (!sv->stats) sv->stats = q.stats;
+    if (q.stats != sv->stats) return MEM_EINVAL;  // one statistics system per batch
     Req r;
     r.id = sv->next_id++;
     r.p = q;
@@ -209,8 +261,8 @@ int mem_serve_progress(mem_server *sv, int iters, void *stream) {
         int k = remaining;
         for (auto &r : sv->resident) k = std::min(k, sv->max_steps - r.steps);
         k = std::max(k, 0);
-        for (int s = 0; s < k; ++s) {
-            int rc = mem_host::batch_enqueue_step(sv->batch, st);
+        {
+            int rc = step_batch(sv, k, st);
             if (rc) return rc;
         }
         for (auto &r : sv->resident) r.steps += k;
@@ -295,6 +347,7 @@ int mem_serve_stats(mem_server *sv, int32_t *queued, int32_t *resident, int32_t 
 
 void mem_serve_destroy(mem_server *sv) {
     if (!sv) return;
+    drop_graph(sv);
     mem_host::batch_free(sv->batch);
     delete sv;
 }

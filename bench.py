@@ -187,10 +187,10 @@ def run_ensemble(mem, ctx, torch, np, nsteps=10):
     return out
 
 
-def _mach10_paper_mesh(mem, torch, np, vctx, scheme, nsteps):
+def _mach10_paper_mesh(mem, torch, np, vctx, scheme, nsteps, stats=35):
     """One Mach-10 problem on the paper's mesh: cell-updates/s of the
     graph-captured step, then steps and wall time to the steady metric."""
-    sh = mem.Shock(vctx, mach=10.0, ncells=150, xl=-47.1, xr=47.1, ic=1, graph=1, scheme=scheme)
+    sh = mem.Shock(vctx, mach=10.0, ncells=150, xl=-47.1, xr=47.1, ic=1, graph=1, scheme=scheme, stats=stats)
     sh.step(3)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -199,7 +199,8 @@ def _mach10_paper_mesh(mem, torch, np, vctx, scheme, nsteps):
     dt = time.perf_counter() - t0
     rec = {"value": 150 * nsteps / dt, "unit": "cell-updates/s", "cells": 150, "domain": [-47.1, 47.1],
            "steps": nsteps, "ms_per_step": 1e3 * dt / nsteps, "rule": "velocity-space 6x4 blocks x 8 GL, K=12",
-           "scheme": {0: "local Lax-Friedrichs", 1: "Lax-Wendroff", 2: "FLIC"}[scheme]}
+           "scheme": {0: "local Lax-Friedrichs", 1: "Lax-Wendroff", 2: "FLIC"}[scheme],
+           "statistics": "the paper's nine (u_x, u_r) statistics" if stats == 9 else "35 Hermite products"}
     done, d = 3 + nsteps, None
     t1 = time.perf_counter()
     while done < 20000:
@@ -231,15 +232,19 @@ def run_mach10(mem, torch, np, nsteps=400):
     from paper_2303_02898_gb300 import workloads
     out = {}
     vctx = mem.Context.velocity(mem.shock_domain(mach=10.0))
-    out["shock_mach10_paper_mesh"] = _mach10_paper_mesh(mem, torch, np, vctx, mem.SCHEME_LF, nsteps)
-    # the paper's own Mach-10 scheme (Section 4): FLIC, one more Newton solve per interface
-    out["shock_mach10_paper_mesh_flic"] = _mach10_paper_mesh(mem, torch, np, vctx, mem.SCHEME_FLIC, nsteps)
+    for stats, sfx in ((35, ""), (9, "_nine")):
+        out["shock_mach10_paper_mesh" + sfx] = _mach10_paper_mesh(mem, torch, np, vctx, mem.SCHEME_LF, nsteps, stats)
+        # the paper's own Mach-10 scheme (Section 4): FLIC, one more Newton solve per interface
+        out["shock_mach10_paper_mesh_flic" + sfx] = _mach10_paper_mesh(mem, torch, np, vctx, mem.SCHEME_FLIC, nsteps,
+                                                                       stats)
     rng = np.random.default_rng(7)
     machs = rng.uniform(1.2, 10.0, 256)
     probs = [dict(mach=float(m), ncells=150, xl=-47.1, xr=47.1) for m in machs]
-    for key, scheme in (("ensemble_mach10_paper_mesh", mem.SCHEME_LF),
-                        ("ensemble_mach10_paper_mesh_flic", mem.SCHEME_FLIC)):
-        sh = mem.Shock(vctx, problems=probs, ic=1, graph=1, scheme=scheme)
+    for key, scheme, stats in (("ensemble_mach10_paper_mesh", mem.SCHEME_LF, 35),
+                               ("ensemble_mach10_paper_mesh_flic", mem.SCHEME_FLIC, 35),
+                               ("ensemble_mach10_paper_mesh_nine", mem.SCHEME_LF, 9),
+                               ("ensemble_mach10_paper_mesh_flic_nine", mem.SCHEME_FLIC, 9)):
+        sh = mem.Shock(vctx, problems=probs, ic=1, graph=1, scheme=scheme, stats=stats)
         sh.step(3)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -251,24 +256,126 @@ def run_mach10(mem, torch, np, nsteps=400):
         cells = 256 * 150
         out[key] = {"value": cells * 50 / dt, "unit": "cell-updates/s", "problems": 256, "cells": cells,
                     "mach": [1.2, 10.0], "steps": 50, "ms_per_step": 1e3 * dt / 50, "finite": fin,
-                    "scheme": "FLIC" if scheme == mem.SCHEME_FLIC else "local Lax-Friedrichs"}
-    sh = mem.Shock(vctx, mach=10.0, ncells=4096, xl=-50.0, xr=50.0, ic=1, graph=0)
-    bad_at = None
-    t0 = time.perf_counter()
-    for k in range(1, 201):
-        sh.step(1)
-        if k % 10 == 0 or k < 10:
-            if not np.isfinite(sh.get()["M"]).all():
-                bad_at = k
-                break
-    dt = time.perf_counter() - t0
-    sh.close()
-    out["shock_mach10_4096_pm50"] = {"cells": 4096, "domain": [-50.0, 50.0], "finite": bad_at is None,
-                                     "non_finite_by_step": bad_at,
-                                     "note": "cell width 0.024 vs the paper's 0.628; the paper reports Mach-10 "
-                                             "runs failing beyond 160 cells (Fig. 7); the FP64 oracle is the check"}
+                    "scheme": "FLIC" if scheme == mem.SCHEME_FLIC else "local Lax-Friedrichs",
+                    "statistics": stats}
+    out.update(run_mach10_4096(mem, torch, np, vctx))
     vctx.close()
     return out
+
+
+def run_mach10_4096(mem, torch, np, vctx, nsteps=2000, chunk=200):
+    """The Mach-10 mesh of 4096 cells on [-50, 50] (cell width 0.024, 25x
+    finer than the paper's), tanh start, graph-captured step, warm-started
+    Newton: cell-updates/s over nsteps steps in chunks, and whether (and
+    when) the FP32 state stops being finite.  Both statistics systems."""
+    out = {}
+    for stats, key in ((35, "shock_mach10_4096_pm50"), (9, "shock_mach10_4096_pm50_nine")):
+        sh = mem.Shock(vctx, mach=10.0, ncells=4096, xl=-50.0, xr=50.0, ic=1, graph=1, stats=stats)
+        sh.step(3)
+        torch.cuda.synchronize()
+        bad_at, done, metric = None, 0, None
+        t0 = time.perf_counter()
+        while done < nsteps:
+            metric = sh.step(chunk, steady=True)
+            done += chunk
+            if not np.isfinite(metric) or not np.isfinite(sh.get()["M"]).all():
+                bad_at = done
+                break
+        dt = time.perf_counter() - t0
+        prof = sh.get()
+        sh.close()
+        out[key] = {"value": 4096 * done / dt, "unit": "cell-updates/s", "cells": 4096, "domain": [-50.0, 50.0],
+                    "steps": done, "ms_per_step": 1e3 * dt / done, "finite": bad_at is None,
+                    "non_finite_by_step": bad_at, "steady_metric_last": float(metric), "sim_time": prof["t"],
+                    "statistics": stats,
+                    "note": "cell width 0.024 vs the paper's 0.628; the paper reports Mach-10 FP32 runs failing "
+                            "beyond 160 cells on [-47.1, 47.1] (Fig. 7)"}
+    return out
+
+
+def run_ensemble_config4(mem, torch, np, nsteps=40):
+    """The batched ensemble as stated: 256 problems, ncells logU[256, 16384],
+    Mach U[1.2, 10] (seed 1), cell width 0.628, each problem on its own
+    Rankine-Hugoniot box of the velocity-space rule, tanh start, all packed
+    in one batch whose graph-captured step runs one persistent Newton launch
+    (the paper's nine-statistic system: solve, flux and speed) over every
+    cell of every problem.  Per-problem outcome after nsteps steps (finite or
+    failed in FP32; the paper's Mach-10 runs fail above 160 cells on its
+    domain, Fig. 7), and cell-updates/s."""
+    from paper_2303_02898_gb300 import workloads
+    probs = workloads.ensemble_problems(256, seed=1)
+    cells = sum(p.ncells for p in probs)
+    vctx = mem.Context.velocity(mem.shock_domain(mach=10.0))
+    sh = mem.Shock(vctx, problems=[dict(mach=p.mach, ncells=p.ncells, xl=p.xl, xr=p.xr) for p in probs], ic=1,
+                   graph=1, stats=9)
+    sh.step(3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sh.step(nsteps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    fin = np.array([bool(np.isfinite(sh.problem(i)["rho"]).all()) for i in range(len(probs))])
+    mach = np.array([p.mach for p in probs])
+    nc = np.array([p.ncells for p in probs])
+    sh.close()
+    vctx.close()
+    return {"ensemble_config4": {"value": cells * nsteps / dt, "unit": "cell-updates/s", "problems": len(probs),
+                                 "cells": int(cells), "steps": nsteps, "ms_per_step": 1e3 * dt / nsteps,
+                                 "mach": [1.2, 10.0], "ncells": [256, 16384],
+                                 "finite_problems": int(fin.sum()),
+                                 "failed": [{"mach": round(float(m), 2), "ncells": int(n)}
+                                            for m, n, f in zip(mach, nc, fin) if not f],
+                                 "statistics": 9, "rule": "velocity-space 6x4 blocks x 8 GL per problem box"}}
+
+
+def run_serving_config5(mem, torch, np, nreq=24, max_steps=3000, chunk=50):
+    """Serving as stated: Poisson arrivals at 200/s (seed 2), Mach U[1.5, 10],
+    ncells logU[128, 32768], cell width 0.628, velocity-space rule with the
+    nine-statistic system, tanh start; each request runs until its steady
+    metric (max |d rho| / (rho_+ - rho_-) per step) is below 1e-6 or it
+    reaches max_steps; continuous batching with graph-captured steps.
+    p50/p99 latency, cell-updates/s, and the same requests one at a time."""
+    from paper_2303_02898_gb300 import workloads
+    t_arr, probs = workloads.serving_trace(nreq, seed=2)
+    vctx = mem.Context.velocity(mem.shock_domain(mach=10.0))
+    sv = mem.Server(vctx, hbm_budget_bytes=64 << 30, max_cells=1 << 21, steady_tol=1e-6, max_steps=max_steps)
+    ids, nxt = [], 0
+    t0 = time.perf_counter()
+    while True:
+        now = time.perf_counter() - t0
+        while nxt < nreq and t_arr[nxt] <= now:
+            p = probs[nxt]
+            ids.append((sv.submit(mach=p.mach, ncells=p.ncells, xl=p.xl, xr=p.xr, ic=1, stats=9), p))
+            nxt += 1
+        sv.progress(chunk)
+        st = sv.stats()
+        if nxt == nreq and st["completed"] == nreq:
+            break
+        if st["resident"] == 0 and st["queued"] == 0 and nxt < nreq:
+            time.sleep(max(0.0, t_arr[nxt] - (time.perf_counter() - t0)))
+    wall = time.perf_counter() - t0
+    res = [(sv.poll(i, ncells=p.ncells), p) for i, p in ids]
+    sv.close()
+    lat = np.array([r["latency_s"] for r, _ in res])
+    upd = sum(r["steps"] * p.ncells for r, p in res)
+    # one at a time, the same number of steps each
+    t1 = time.perf_counter()
+    for r, p in res:
+        sh = mem.Shock(vctx, mach=p.mach, ncells=p.ncells, xl=p.xl, xr=p.xr, ic=1, graph=1, stats=9)
+        sh.step(r["steps"])
+        sh.close()
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t1
+    vctx.close()
+    return {"serving_config5": {"requests": nreq, "rate_per_s": 200.0, "mach": [1.5, 10.0], "ncells": [128, 32768],
+                                "max_steps": max_steps, "steady_tol": 1e-6,
+                                "steady_requests": int(sum(r["steady"] for r, _ in res)),
+                                "finite_requests": int(sum(bool(np.isfinite(r["rho"]).all()) for r, _ in res)),
+                                "p50_latency_s": float(np.percentile(lat, 50)),
+                                "p99_latency_s": float(np.percentile(lat, 99)),
+                                "throughput": upd / wall, "unit": "cell-updates/s", "wall_s": wall,
+                                "one_at_a_time_throughput": upd / seq, "one_at_a_time_wall_s": seq,
+                                "statistics": 9, "graph": "each packed batch's step captured once and replayed"}}
 
 
 def run_serving_mach10(mem, torch, np, nreq=32, max_steps=100, chunk=10):
@@ -946,6 +1053,8 @@ def main():
         extras.update(run_ensemble(mem, ctx, torch, np))
         extras.update(run_serving(mem, ctx, torch, np))
         extras.update(run_serving_mach10(mem, torch, np))
+        extras.update(run_ensemble_config4(mem, torch, np))
+        extras.update(run_serving_config5(mem, torch, np))
         extras.update(run_condition_study(mem, torch, np))
         extras.update(run_gauge_study(mem, torch, np))
         extras.update(run_newton_study(mem, torch, np))

@@ -74,18 +74,23 @@ def test_mixed_solve_matches_oracle(O, mem, dev, order, workload):
     conv = (stm & (mem.ST_CONVERGED | mem.ST_STAGNATED)) != 0
     assert conv.all(), np.unique(stm, return_counts=True)
     res = O.residual_batch(order, bm, Mf)
-    assert res.max() <= RES_TOL, (res.max(), int(np.argmax(res)))
     bo, _, ito = O.solve_batch(order, Mf, final_step=True)
+    # the bar: 1e-5, or 1.5 x the oracle's own FP64 residual for the few
+    # cells where Algorithm 1 with its final step stops above 1e-5 in exact
+    # arithmetic too (one of the 389 perturbed cells at 12^3: 1.2e-5)
+    res_o = O.residual_batch(order, bo, Mf)
+    bar = np.maximum(RES_TOL, 1.5 * res_o)
+    assert np.all(res <= bar), (np.max(res / bar), int(np.argmax(res / bar)))
     scale = 1.0 + np.abs(bo[:, 1:]).max(axis=1)
     err_m = np.abs(bm[:, 1:] - bo[:, 1:]).max(axis=1) / scale
     err_p = np.abs(bp[:, 1:] - bo[:, 1:]).max(axis=1) / scale
     assert err_m.max() <= 5e-3, err_m.max()
     # the TF32 Hessian is a model: the pass count may grow, not by much
     assert itm.mean() <= itp.mean() + 2.0, (itm.mean(), itp.mean())
-    print("mixed %s q%d: residual max %.2e median %.2e; beta err vs FP64 max %.2e (plain FP32 %.2e); "
-          "mean passes mixed %.2f plain %.2f oracle %.2f" % (
-              workload, order, res.max(), np.median(res), err_m.max(), err_p.max(), itm.mean(), itp.mean(),
-              ito.mean()))
+    print("mixed %s q%d: residual max %.2e median %.2e (cells on the relaxed bar: %d); beta err vs FP64 max "
+          "%.2e (plain FP32 %.2e); mean passes mixed %.2f plain %.2f oracle %.2f" % (
+              workload, order, res.max(), np.median(res), int((res > RES_TOL).sum()), err_m.max(), err_p.max(),
+              itm.mean(), itp.mean(), ito.mean()))
     ctx.close()
 
 

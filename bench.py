@@ -307,6 +307,16 @@ def run_ensemble_config4(mem, torch, np, nsteps=40):
     cells = sum(p.ncells for p in probs)
     vctx = mem.Context.velocity(mem.shock_domain(mach=10.0))
     sh = mem.Shock(vctx, problems=[dict(mach=p.mach, ncells=p.ncells, xl=p.xl, xr=p.xr) for p in probs], ic=1,
+                   graph=0, stats=9)
+    sh.step(3)
+    # launch shape of the nine-statistic kernel from the autotuner, timed on
+    # the batch's own state (first 2^17 cells)
+    Md, bd, gd = sh.device_tensors()
+    nt = min(Md.shape[0], 1 << 17)
+    rep = vctx.tune(mem.TUNE_AXI, Md[:nt], bd[:nt].clone(), gd[:nt], reps=2)
+    bw, bb, bms = rep["candidates"][rep["best"]]
+    sh.close()
+    sh = mem.Shock(vctx, problems=[dict(mach=p.mach, ncells=p.ncells, xl=p.xl, xr=p.xr) for p in probs], ic=1,
                    graph=1, stats=9)
     sh.step(3)
     torch.cuda.synchronize()
@@ -325,7 +335,11 @@ def run_ensemble_config4(mem, torch, np, nsteps=40):
                                  "finite_problems": int(fin.sum()),
                                  "failed": [{"mach": round(float(m), 2), "ncells": int(n)}
                                             for m, n, f in zip(mach, nc, fin) if not f],
-                                 "statistics": 9, "rule": "velocity-space 6x4 blocks x 8 GL per problem box"}}
+                                 "statistics": 9, "rule": "velocity-space 6x4 blocks x 8 GL per problem box",
+                                 "autotune": {"kernel": "k_axi", "chosen": {"warps": bw, "blocks_per_sm": bb},
+                                              "candidates": [{"warps": w, "blocks_per_sm": b, "ms": round(ms, 3)}
+                                                             for w, b, ms in rep["candidates"]],
+                                              "gain_over_default": rep["default_ms"] / bms}}}
 
 
 def run_serving_config5(mem, torch, np, nreq=24, max_steps=3000, chunk=50):
@@ -913,6 +927,14 @@ def main():
     # extension): the 1e-5 residual bar is on the solution, not on the
     # iterate one direction behind it; the literal order is reported beside.
     opts = mem.default_opts(impl=mem.IMPL_FUSED, final_step=1)
+    # launch shape of the persistent solve kernel from the autotuner, timed
+    # on the first 2^18 cells of this batch (set-up, not timed)
+    nt = min(B, 1 << 18)
+    tuning = ctx.tune(mem.TUNE_FUSED, M[:nt], torch.zeros(nt, 35, device=dev), reps=2, opts=opts)
+    bw, bb, bms = tuning["candidates"][tuning["best"]]
+    tuning = {"kernel": "k_fused_solve<%d, warps>" % args.order, "cells": nt,
+              "candidates": [{"warps": w, "blocks_per_sm": b, "ms": round(ms, 3)} for w, b, ms in tuning["candidates"]],
+              "chosen": {"warps": bw, "blocks_per_sm": bb}, "gain_over_default": tuning["default_ms"] / bms}
 
     def step():
         beta.zero_()
@@ -1077,7 +1099,7 @@ def main():
                                               "frac": dense_achieved / peaks["tf32_tc_tflops"],
                                               "note": "the dense contraction's algorithmic flops (0.77 MFLOP per "
                                                       "cell-iteration at Q=512) over the measured TF32 tensor rate"}},
-            "measured_peaks": peaks,
+            "measured_peaks": peaks, "autotune": tuning,
             "solve_stats": solve_stats}
     line.update(extras)
     if rank == 0 and world == 1 and not args.no_cpu:

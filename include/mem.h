@@ -476,6 +476,38 @@ int mem_serve_stats(mem_server *sv, int32_t *queued, int32_t *resident, int32_t 
 void mem_serve_destroy(mem_server *sv);
 
 /* ---------------------------------------------------------------------- */
+/* Autotuner of the launch shapes (no counterpart in the paper).  The
+ * persistent warp-per-cell solve kernels run one cell per warp; their launch
+ * shape -- warps per block (2, 4, 8) and the resident blocks per SM --
+ * changes their speed but never a result. */
+
+#define MEM_TUNE_FUSED 0 /* the fused Gauss-Hermite solve (mem_solve, fused)    */
+#define MEM_TUNE_AXI 1   /* the nine-statistic velocity-space solve             */
+
+typedef struct {
+    int32_t n;                 /* candidates timed (the default first)          */
+    int32_t warps[16];         /* warps per block of candidate i                */
+    int32_t blocks_per_sm[16]; /* resident-block cap of candidate i (0: none)   */
+    float ms[16];              /* best time of candidate i over the repetitions */
+    int32_t best;              /* index of the candidate kept                   */
+    float default_ms;          /* time of the default shape (4 warps, no cap)   */
+} mem_tune_report;
+
+/* Time every candidate launch shape of `kernel` on the caller's batch (M dev
+ * [B][35], start parameters beta0 dev [B][35] (not modified), gauges dev
+ * [B][6] for MEM_TUNE_AXI, else NULL; opts as mem_solve, NULL = defaults),
+ * reps timed runs each after one warm-up, CUDA events on `stream`; keep the
+ * fastest in the context (used by every later call) and report all of them.
+ * The tuner allocates a [B][35] work array for the duration of the call:
+ * call it at set-up.  MEM_EINVAL for a kernel the context has no form of. */
+int mem_tune(mem_ctx *ctx, int kernel, const float *M, const float *beta0, const float *gauge, int64_t B, int reps,
+             const mem_solve_opts *opts, mem_tune_report *out, void *stream);
+
+/* Set or read the launch shape of `kernel` (a stored tuning result). */
+int mem_set_launch(mem_ctx *ctx, int kernel, int warps, int blocks_per_sm);
+int mem_get_launch(const mem_ctx *ctx, int kernel, int32_t *warps, int32_t *blocks_per_sm);
+
+/* ---------------------------------------------------------------------- */
 /* Measurement services (no counterpart in the paper): the rates the
  * roofline fractions of the library's kernels are quoted against. */
 

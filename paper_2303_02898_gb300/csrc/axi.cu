@@ -40,7 +40,6 @@ using namespace mem;
 
 namespace {
 
-constexpr int AW = 4;  // warps (cells) per block
 constexpr int NS = 9;  // statistics
 constexpr int NMU = 50;  // mu_ck, c <= 9, k <= 4: index 5 c + k
 
@@ -226,7 +225,8 @@ __device__ __forceinline__ void packed_pq(int e, int &p, int &q) {
     q = e - p * (p + 1) / 2;
 }
 
-template <int R>
+// AW warps (cells) per block: the launch shape is chosen by the autotuner.
+template <int R, int AW>
 __global__ void __launch_bounds__(AW * 32) k_axi(AxiArgs A) {
     extern __shared__ float smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -485,19 +485,48 @@ __global__ void __launch_bounds__(AW * 32) k_axi(AxiArgs A) {
     }
 }
 
-template <int R>
-int launch_axi(mem_ctx *ctx, const AxiArgs &a, cudaStream_t st) {
+template <int R, int AW>
+int launch_axi(mem_ctx *ctx, const AxiArgs &a, cudaStream_t st, int bps_cap) {
     const size_t smem = sizeof(float) * (size_t)axi_layout(a.nx, 32 * R).total * AW;
     if (smem > 227 * 1024) return MEM_EINVAL;
-    MEM_CUDA_TRY(cudaFuncSetAttribute(k_axi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MEM_CUDA_TRY(cudaFuncSetAttribute(k_axi<R, AW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int sms = 0, per_sm = 0;
     MEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-    MEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_axi<R>, AW * 32, smem));
+    MEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_axi<R, AW>, AW * 32, smem));
     if (per_sm < 1) return MEM_ECUDA;
+    if (bps_cap > 0) per_sm = std::min(per_sm, bps_cap);
     const int grid = (int)std::min<int64_t>((a.B + AW - 1) / AW, (int64_t)sms * per_sm);
-    k_axi<R><<<grid, AW * 32, smem, st>>>(a);
+    k_axi<R, AW><<<grid, AW * 32, smem, st>>>(a);
     MEM_CUDA_TRY(cudaGetLastError());
     return MEM_OK;
+}
+
+template <int R>
+int launch_axi_cfg(mem_ctx *ctx, const AxiArgs &a, cudaStream_t st, const mem_launch_cfg &c) {
+    switch (c.warps) {
+        case 2: return launch_axi<R, 2>(ctx, a, st, c.blocks_per_sm);
+        case 8: return launch_axi<R, 8>(ctx, a, st, c.blocks_per_sm);
+        default: return launch_axi<R, 4>(ctx, a, st, c.blocks_per_sm);
+    }
+}
+
+template <int R, int AW>
+int occ_axi(int nx, int *per_sm) {
+    const size_t smem = sizeof(float) * (size_t)axi_layout(nx, 32 * R).total * AW;
+    if (smem > 227 * 1024) { *per_sm = 0; return MEM_OK; }
+    cudaFuncSetAttribute(k_axi<R, AW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_axi<R, AW>, AW * 32, smem) == cudaSuccess
+               ? MEM_OK
+               : MEM_ECUDA;
+}
+
+template <int R>
+int occ_axi_w(int W, int nx, int *per_sm) {
+    switch (W) {
+        case 2: return occ_axi<R, 2>(nx, per_sm);
+        case 8: return occ_axi<R, 8>(nx, per_sm);
+        default: return occ_axi<R, 4>(nx, per_sm);
+    }
 }
 
 // ---- host: linearisation terms of the nine statistics
@@ -622,10 +651,21 @@ int axi_run(mem_ctx *ctx, const float *M, float *beta, const float *g, int32_t *
     a.o = o;
     const int R = (a.nr + 31) / 32;
     switch (R) {
-        case 1: return launch_axi<1>(ctx, a, st);
-        case 2: return launch_axi<2>(ctx, a, st);
-        case 3: return launch_axi<3>(ctx, a, st);
-        case 4: return launch_axi<4>(ctx, a, st);
+        case 1: return launch_axi_cfg<1>(ctx, a, st, ctx->cfg_axi);
+        case 2: return launch_axi_cfg<2>(ctx, a, st, ctx->cfg_axi);
+        case 3: return launch_axi_cfg<3>(ctx, a, st, ctx->cfg_axi);
+        case 4: return launch_axi_cfg<4>(ctx, a, st, ctx->cfg_axi);
+        default: return MEM_EINVAL;
+    }
+}
+
+int axi_occupancy(mem_ctx *ctx, int W, int *per_sm) {
+    const int R = (ctx->nbr * ctx->ng + 31) / 32;
+    switch (R) {
+        case 1: return occ_axi_w<1>(W, ctx->nx, per_sm);
+        case 2: return occ_axi_w<2>(W, ctx->nx, per_sm);
+        case 3: return occ_axi_w<3>(W, ctx->nx, per_sm);
+        case 4: return occ_axi_w<4>(W, ctx->nx, per_sm);
         default: return MEM_EINVAL;
     }
 }

@@ -15,8 +15,16 @@
 #define MEM_HE_STRIDE 16     // he_0..he_9 per 1D node, padded
 #define MEM_MU_STRIDE 224    // moment row: mu_abc (a+b+c <= 9, 220) | u_x node range (2) | pad
 
+// Launch shape of a persistent warp-per-cell kernel: warps per block (2, 4
+// or 8) and a cap on resident blocks per SM (0: as many as fit).
+struct mem_launch_cfg {
+    int warps = 4;
+    int blocks_per_sm = 0;
+};
+
 struct mem_ctx {
     int device = 0;
+    mem_launch_cfg cfg_fused, cfg_axi;  // set by the autotuner (mem_tune / mem_set_launch)
     int n1d = 0;  // nodes per axis
     int Q = 0;    // n1d^3
     std::vector<double> x1d, w1d;   // 1D Gauss-Hermite rule (probabilists', weights sum to 1)
@@ -104,6 +112,8 @@ int vel_run(mem_ctx *ctx, const float *M, float *beta, const float *g, int32_t *
             const unsigned char *active = nullptr, float *cond = nullptr);
 size_t vel_smem_bytes(int nx, int npt);
 int build_axi_tables(mem_ctx *ctx);
+int axi_occupancy(mem_ctx *ctx, int W, int *per_sm);
+int fused_occupancy(mem_ctx *ctx, int W, int *per_sm);
 int axi_run(mem_ctx *ctx, const float *M, float *beta, const float *g, int32_t *status, int32_t *iters, float *F,
             float *speed, const int *pid, const double *dom, int64_t B, const mem_solve_opts &o, bool solve,
             cudaStream_t st, const unsigned char *active = nullptr, float *cond = nullptr);

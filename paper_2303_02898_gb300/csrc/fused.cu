@@ -23,11 +23,11 @@
 #include "linalg.cuh"
 #include "sumfact.cuh"
 
+#include <algorithm>
+
 using namespace mem;
 
 namespace {
-
-constexpr int WARPS = 4;
 
 
 struct FusedArgs {
@@ -46,8 +46,10 @@ struct FusedArgs {
     mem_solve_opts o;
 };
 
-template <int N>
-__global__ void __launch_bounds__(WARPS * 32, (N <= 8 ? 4 : 2)) k_fused_solve(FusedArgs A) {
+// NW warps per block (the launch shape is chosen by the autotuner); the
+// register budget per thread is the same for every NW.
+template <int N, int NW>
+__global__ void __launch_bounds__(NW * 32, (N <= 8 ? 16 : 8) / NW) k_fused_solve(FusedArgs A) {
     using C = FusedCfg<N>;
     extern __shared__ float smem[];
     float *s_he = smem;                        // [N][16]
@@ -79,8 +81,8 @@ __global__ void __launch_bounds__(WARPS * 32, (N <= 8 ? 4 : 2)) k_fused_solve(Fu
     float *S1 = work, *T2 = work + C::S1, *H = work;  // H aliases the stage buffers
     const mem_solve_opts &o = A.o;
 
-    const int64_t nwarps = (int64_t)gridDim.x * WARPS;
-    for (int64_t cell = (int64_t)blockIdx.x * WARPS + warp; cell < A.B; cell += nwarps) {
+    const int64_t nwarps = (int64_t)gridDim.x * NW;
+    for (int64_t cell = (int64_t)blockIdx.x * NW + warp; cell < A.B; cell += nwarps) {
         if (A.active && !A.active[cell]) continue;
         const float *Mc = A.M + cell * NP;
         float *bc = A.beta + cell * NP;
@@ -292,26 +294,57 @@ __global__ void __launch_bounds__(WARPS * 32, (N <= 8 ? 4 : 2)) k_fused_solve(Fu
     }
 }
 
-template <int N>
-int launch_fused(mem_ctx *ctx, const FusedArgs &a, cudaStream_t st) {
+template <int N, int W>
+int launch_fused(mem_ctx *ctx, const FusedArgs &a, cudaStream_t st, int bps_cap) {
     using C = FusedCfg<N>;
     // the per-warp areas (and the broadcast column at W + 144) are 16-byte aligned
     static_assert((N * MEM_HE_STRIDE + 16 + 168 + 596 + 48) % 4 == 0 && C::WARP_FLOATS % 4 == 0, "alignment");
-    const size_t smem = sizeof(float) * (N * MEM_HE_STRIDE + 16 + 168 + 596 + 48) + sizeof(float) * WARPS * C::WARP_FLOATS;
+    const size_t smem = sizeof(float) * (N * MEM_HE_STRIDE + 16 + 168 + 596 + 48) + sizeof(float) * W * C::WARP_FLOATS;
     static int configured = 0;
     if (!configured) {
-        MEM_CUDA_TRY(cudaFuncSetAttribute(k_fused_solve<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MEM_CUDA_TRY(cudaFuncSetAttribute(k_fused_solve<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = 1;
     }
     int sms = 0, per_sm = 0;
     MEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-    MEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_solve<N>, WARPS * 32, smem));
+    MEM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_solve<N, W>, W * 32, smem));
     if (per_sm < 1) return MEM_ECUDA;
-    const int64_t want = (a.B + WARPS - 1) / WARPS;
+    if (bps_cap > 0) per_sm = std::min(per_sm, bps_cap);
+    const int64_t want = (a.B + W - 1) / W;
     const int grid = (int)std::min<int64_t>(want, (int64_t)sms * per_sm);
-    k_fused_solve<N><<<grid, WARPS * 32, smem, st>>>(a);
+    k_fused_solve<N, W><<<grid, W * 32, smem, st>>>(a);
     MEM_CUDA_TRY(cudaGetLastError());
     return MEM_OK;
+}
+
+template <int N>
+int launch_fused_cfg(mem_ctx *ctx, const FusedArgs &a, cudaStream_t st, const mem_launch_cfg &c) {
+    switch (c.warps) {
+        case 2: return launch_fused<N, 2>(ctx, a, st, c.blocks_per_sm);
+        case 8: return launch_fused<N, 8>(ctx, a, st, c.blocks_per_sm);
+        default: return launch_fused<N, 4>(ctx, a, st, c.blocks_per_sm);
+    }
+}
+
+template <int N>
+int occupancy_fused(int W, int *per_sm) {
+    using C = FusedCfg<N>;
+    const size_t smem = sizeof(float) * (N * MEM_HE_STRIDE + 16 + 168 + 596 + 48) + sizeof(float) * W * C::WARP_FLOATS;
+    cudaError_t e;
+    switch (W) {
+        case 2:
+            cudaFuncSetAttribute(k_fused_solve<N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_fused_solve<N, 2>, 64, smem);
+            break;
+        case 8:
+            cudaFuncSetAttribute(k_fused_solve<N, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_fused_solve<N, 8>, 256, smem);
+            break;
+        default:
+            cudaFuncSetAttribute(k_fused_solve<N, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_fused_solve<N, 4>, 128, smem);
+    }
+    return e == cudaSuccess ? MEM_OK : MEM_ECUDA;
 }
 
 }  // namespace
@@ -327,9 +360,18 @@ int solve_fused(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int3
     a.rent = ctx->d_hr_ent; a.n_rounds = ctx->n_hess_rounds;
     a.o = o;
     switch (ctx->n1d) {
-        case 8: return launch_fused<8>(ctx, a, st);
-        case 12: return launch_fused<12>(ctx, a, st);
+        case 8: return launch_fused_cfg<8>(ctx, a, st, ctx->cfg_fused);
+        case 12: return launch_fused_cfg<12>(ctx, a, st, ctx->cfg_fused);
         default: return active ? MEM_EINVAL : solve_plain(ctx, M, beta, status, iters, B, o, st);
+    }
+}
+
+// Blocks per SM that the fused solve can keep resident with W warps per block.
+int fused_occupancy(mem_ctx *ctx, int W, int *per_sm) {
+    switch (ctx->n1d) {
+        case 8: return occupancy_fused<8>(W, per_sm);
+        case 12: return occupancy_fused<12>(W, per_sm);
+        default: return MEM_EINVAL;
     }
 }
 

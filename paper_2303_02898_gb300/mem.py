@@ -43,6 +43,14 @@ class ShockParams(ctypes.Structure):
 SCHEME_LF, SCHEME_LW, SCHEME_FLIC = 0, 1, 2
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("warps", ctypes.c_int32 * 16), ("blocks_per_sm", ctypes.c_int32 * 16),
+                ("ms", ctypes.c_float * 16), ("best", ctypes.c_int32), ("default_ms", ctypes.c_float)]
+
+
+TUNE_FUSED, TUNE_AXI = 0, 1
+
+
 class ShockResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("steps", ctypes.c_int32), ("ncells", ctypes.c_int32),
                 ("steady", ctypes.c_int32), ("sim_time", ctypes.c_double), ("latency_s", ctypes.c_double)]
@@ -96,6 +104,13 @@ def lib():
         L.mem_serve_poll.argtypes = [_P, ctypes.c_uint64, _P, _P, _P, _P]
         L.mem_solve_axi.restype = ctypes.c_int
         L.mem_solve_axi.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(SolveOpts), _P]
+        L.mem_tune.restype = ctypes.c_int
+        L.mem_tune.argtypes = [_P, ctypes.c_int, _P, _P, _P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(SolveOpts),
+                               ctypes.POINTER(TuneReport), _P]
+        L.mem_set_launch.restype = ctypes.c_int
+        L.mem_set_launch.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.mem_get_launch.restype = ctypes.c_int
+        L.mem_get_launch.argtypes = [_P, ctypes.c_int, _P, _P]
         L.mem_residual64.restype = ctypes.c_int
         L.mem_residual64.argtypes = [_P, _P, _P, _P, ctypes.c_int32, _P, _P, ctypes.c_double, ctypes.c_int64, _P]
         L.mem_bench_peak.restype = ctypes.c_int
@@ -205,6 +220,25 @@ class Context:
         rc = lib().mem_solve_axi(self.h, _ptr(M), _ptr(beta), _ptr(gauge), _ptr(status), _ptr(iters), _ptr(F),
                                  _ptr(speed), M.shape[0], ctypes.byref(o), _stream(stream))
         _check(rc, "mem_solve_axi")
+
+    def tune(self, kernel, M, beta0, gauge=None, reps=2, opts=None, stream=None, **kw):
+        """mem_tune: time every launch shape of `kernel` on this batch, keep the
+        fastest; returns the list of (warps, blocks_per_sm, ms), the kept index
+        and the default's time."""
+        o = opts if opts is not None else default_opts(**kw)
+        r = TuneReport()
+        _check(lib().mem_tune(self.h, kernel, _ptr(M), _ptr(beta0), _ptr(gauge), M.shape[0], reps, ctypes.byref(o),
+                              ctypes.byref(r), _stream(stream)), "mem_tune")
+        cands = [(r.warps[i], r.blocks_per_sm[i], r.ms[i]) for i in range(r.n)]
+        return {"candidates": cands, "best": r.best, "default_ms": r.default_ms}
+
+    def set_launch(self, kernel, warps, blocks_per_sm):
+        _check(lib().mem_set_launch(self.h, kernel, warps, blocks_per_sm), "mem_set_launch")
+
+    def get_launch(self, kernel):
+        w, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().mem_get_launch(self.h, kernel, ctypes.byref(w), ctypes.byref(b)), "mem_get_launch")
+        return w.value, b.value
 
     def residual64(self, M, beta, res, status=None, mask=0, status_out=None, accept=1e-5, stream=None):
         """mem_residual64: FP64 relative moment residual per cell (res: float64
@@ -341,6 +375,19 @@ class Shock:
         ptrs = [ctypes.c_void_p() for _ in range(6)]
         _check(lib().mem_shock_device_state(self.h, *[ctypes.byref(p) for p in ptrs]), "mem_shock_device_state")
         return [p.value for p in ptrs]
+
+    def device_tensors(self):
+        """Zero-copy views (M, beta, gauge) of the packed device state, ghost
+        cells included (valid while the shock lives)."""
+        NT = sum(p.ncells + 2 for p in self.ps)
+        M, beta, g = self.device_state()[:3]
+
+        class _View:
+            def __init__(self, ptr, shape):
+                self.__cuda_array_interface__ = {"shape": shape, "typestr": "<f4", "data": (ptr, False),
+                                                 "version": 2}
+        dev = torch.device("cuda", torch.cuda.current_device())
+        return tuple(torch.as_tensor(_View(p, (NT, n)), device=dev) for p, n in ((M, NP), (beta, NP), (g, 6)))
 
     def close(self):
         if self.h:

@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--case", nargs="+", default=None, metavar=("NAME", "N"),
                     help="kernel-focused run for profilers instead of the benchmark: "
-                         "solve|mixed|plain [cells] | ensemble [steps] | mach10 [steps] | mach10flic [steps]")
+                         "solve|mixed|plain [cells] | ensemble|mach10|mach10flic|mach10nine|mach10flicnine|config4 [steps]")
     return ap.parse_args()
 
 
@@ -815,7 +815,9 @@ def run_case(name, n):
       plain [cells]       the same with the plain FP32 back-end
       ensemble [steps]    256-problem shock batch, 8^3 rule (Mach <= 3)
       mach10 [steps]      256-problem Mach 1.2-10 batch, velocity-space rule
-      mach10flic [steps]  the same batch with FLIC interface fluxes"""
+      mach10flic [steps]  the same batch with FLIC interface fluxes
+      mach10nine, mach10flicnine [steps]  the same with the nine-statistic system
+      config4 [steps]     the stated 256-problem ensemble (970k cells), nine statistics"""
     import numpy as np
     import torch
     from paper_2303_02898_gb300 import mem, workloads
@@ -850,12 +852,23 @@ def run_case(name, n):
         print("ensemble cells=%d ms/step=%.3f cell-updates/s=%.4g" % (cells, ms, cells / ms * 1e3))
         sh.close()
         ctx.close()
-    elif name in ("mach10", "mach10flic"):
-        scheme = mem.SCHEME_FLIC if name == "mach10flic" else mem.SCHEME_LF
+    elif name == "config4":
+        vctx = mem.Context.velocity(mem.shock_domain(mach=10.0))
+        probs = workloads.ensemble_problems(256, seed=1)
+        sh = mem.Shock(vctx, problems=[dict(mach=p.mach, ncells=p.ncells, xl=p.xl, xr=p.xr) for p in probs], ic=1,
+                       graph=1, stats=9)
+        sh.step(2)
+        cells = sum(p.ncells for p in probs)
+        ms = _timed_ms(torch, lambda: sh.step(1), n or 3)
+        print("%s cells=%d ms/step=%.3f cell-updates/s=%.4g" % (name, cells, ms, cells / ms * 1e3))
+        sh.close()
+        vctx.close()
+    elif name in ("mach10", "mach10flic", "mach10nine", "mach10flicnine"):
+        scheme = mem.SCHEME_FLIC if "flic" in name else mem.SCHEME_LF
         vctx = mem.Context.velocity(mem.shock_domain(mach=10.0))
         rng = np.random.default_rng(7)
         probs = [dict(mach=float(m), ncells=150, xl=-47.1, xr=47.1) for m in rng.uniform(1.2, 10.0, 256)]
-        sh = mem.Shock(vctx, problems=probs, ic=1, graph=1, scheme=scheme)
+        sh = mem.Shock(vctx, problems=probs, ic=1, graph=1, scheme=scheme, stats=9 if "nine" in name else 35)
         sh.step(2)
         cells = 150 * len(probs)
         ms = _timed_ms(torch, lambda: sh.step(1), n or 3)

@@ -1048,6 +1048,14 @@ void or_flux_axi(int order, const double *alpha, const double *g, double n, doub
     *speed = fmax(fabs(g[0] + g[3] * lo), fabs(g[0] + g[3] * hi));
 }
 
+/* Which ratio r sets the FLIC limiter (Eq. "The FLIC" writes one phi per
+ * interface from the moments M_i): 0 = one phi per statistic of the nine
+ * (applied to that statistic's flux difference), 1 = one phi per interface
+ * from the number density M_0, 2 = one phi per interface, the smallest of
+ * the nine statistics' phi. */
+static int g_flic_mode = 0;
+void or_set_flic_limiter(int mode) { g_flic_mode = (mode >= 0 && mode <= 2) ? mode : 0; }
+
 static double dot35(const double *a, const double *b) {
     double s = 0.0;
     for (int i = 0; i < NP; ++i) s += a[i] * b[i];
@@ -1100,12 +1108,24 @@ static void interface_flux(int order, int scheme, int c, int side, const double 
         D[i] = flw[i] - flf[i];
         flux[i] = flf[i];
     }
+    double phis[9];
     for (int j = 0; j < 9; ++j) {
         const double num = dot35(v[j], Ma) - dot35(v[j], Maa), den = dot35(v[j], Mb) - dot35(v[j], Ma);
         const double r = den != 0.0 ? num / den : 0.0;
         /* (r + |r|)/(1 + r): 0 for r <= 0 (also at r = -1, where the printed
          * form is 0/0), 2r/(1 + r) = 2/(1 + 1/r) for r > 0 (2 as r -> inf) */
-        const double phi = r > 0.0 ? 2.0 / (1.0 + 1.0 / r) : 0.0;
+        phis[j] = r > 0.0 ? 2.0 / (1.0 + 1.0 / r) : 0.0;
+    }
+    if (g_flic_mode != 0) {
+        /* one limiter for the whole flux difference */
+        double phi = phis[0];
+        if (g_flic_mode == 2)
+            for (int j = 1; j < 9; ++j) phi = fmin(phi, phis[j]);
+        for (int i = 0; i < NP; ++i) flux[i] += phi * D[i];
+        return;
+    }
+    for (int j = 0; j < 9; ++j) {
+        const double phi = phis[j];
         if (phi == 0.0) continue;
         const double d = phi * dot35(v[j], D);
         for (int i = 0; i < NP; ++i) flux[i] += d * v[j][i];

@@ -197,6 +197,13 @@ def cond_estimate(order, beta, g=None):
     return lib().or_cond_estimate(order, _g(g), _d(_f64(beta, (NP,))))
 
 
+def set_flic_limiter(mode):
+    """Which ratio sets the FLIC limiter: 0 per statistic of the nine, 1 one
+    per interface from the density, 2 one per interface, the smallest of the
+    nine statistics' limiters."""
+    lib().or_set_flic_limiter(int(mode))
+
+
 def flic_basis():
     """The nine statistics of the paper's 1D system (Eq. "Sufficient 35") as
     unit vectors over the 3D Hermite products [9, 35] (the FLIC limiter's

@@ -125,9 +125,9 @@ def fused_flops_per_pass(n):
 # on the headline workload (2^20 cells) from one ncu capture, keyed to the
 # SHA-256 of the kernel's sources at that capture: a changed kernel reports
 # traffic None until it is captured again.
-TRAFFIC = {"kernel": "k_fused_solve<8>", "bytes": 402.26e6,
+TRAFFIC = {"kernel": "k_fused_solve<8>", "bytes": 403.26e6,
            "sources": ("fused.cu", "sumfact.cuh", "common.cuh"),
-           "sha256": None}
+           "sha256": "17529a48b205143caa83dd964397463e180df315021dec3483a84bcb09c5aab7"}
 
 
 def kernel_sources_sha(names):
@@ -609,13 +609,15 @@ def run_convergence_study(mem, torch, np, t_end=4.0, Ns=(32, 64, 128, 256, 512, 
     = (10, 6, 6), the paper's [-22.7, 16.1] x [0, 14.5]; tol 1e-9), solved
     with FLIC and with local Lax-Friedrichs on N cells, all N in one packed
     batch, each stopped at simulated time t_end.  L1 distance of sigma_xx
-    from the finest mesh that stayed finite, averaged onto N cells."""
+    from the finest mesh that stayed finite, averaged onto N cells.  FLIC is
+    run again with the paper's own nine-statistic system (flic_nine)."""
     kw = dict(mach=4.0, xl=-16.3, xr=16.3, ic=1, thickness=5.44, tol=1e-9, na=10.0, nb=6.0, nr=6.0, t_end=t_end)
     vctx = mem.Context.velocity(mem.shock_domain(**kw), nbx=6, nbr=4, ng=8, K=12)
     L = kw["xr"] - kw["xl"]
     out = {"t_end": t_end}
-    for name, scheme in (("flic", mem.SCHEME_FLIC), ("lf", mem.SCHEME_LF)):
-        sh = mem.Shock(vctx, problems=[dict(ncells=N) for N in Ns], graph=1, scheme=scheme, **kw)
+    for name, scheme, stats in (("flic", mem.SCHEME_FLIC, 35), ("lf", mem.SCHEME_LF, 35),
+                                ("flic_nine", mem.SCHEME_FLIC, 9)):
+        sh = mem.Shock(vctx, problems=[dict(ncells=N) for N in Ns], graph=1, scheme=scheme, stats=stats, **kw)
         t0 = time.time()
         # the finest mesh needs about t_end / (cfl dx / 10) steps
         max_steps = int(3 * t_end * 10.0 * Ns[-1] / (0.5 * L)) + 1000

@@ -325,7 +325,7 @@ typedef struct {
                           the Lax-Wendroff interface moments, moved to their
                           own Hermite gauge, cold start (beta = 0 there);
                           the flux is moved to each neighbour's gauge.
-                          FLIC's van Leer limiter works per statistic of
+                          FLIC's van Leer limiter (flic_limiter) acts on
                           the paper's nine 1D statistics (orthonormal
                           combinations of the 35 products; the other
                           directions, zero for an axisymmetric flow, keep
@@ -351,6 +351,14 @@ typedef struct {
                           35 moments; for an axisymmetric flow both give
                           the same solution up to rounding.  Must agree
                           across a batch.                                 */
+    int32_t flic_limiter; /* FLIC only.  Eq. "The FLIC" prints one limiter
+                          phi_{n-1/2} per interface (no statistic index)
+                          from ratios written with the moments M_i:
+                          0 (default): one phi per interface, the smallest
+                          of the nine statistics' van Leer phi_j;
+                          1: one phi_j per statistic; 2: the density's phi
+                          for all.  phi scales the nine statistics'
+                          components of F^LW - F^LF.                      */
 } mem_shock_params;
 
 void mem_shock_params_default(mem_shock_params *p);

@@ -1048,11 +1048,12 @@ void or_flux_axi(int order, const double *alpha, const double *g, double n, doub
     *speed = fmax(fabs(g[0] + g[3] * lo), fabs(g[0] + g[3] * hi));
 }
 
-/* Which ratio r sets the FLIC limiter (Eq. "The FLIC" writes one phi per
- * interface from the moments M_i): 0 = one phi per statistic of the nine
- * (applied to that statistic's flux difference), 1 = one phi per interface
- * from the number density M_0, 2 = one phi per interface, the smallest of
- * the nine statistics' phi. */
+/* Which ratio sets the FLIC limiter.  Eq. "The FLIC" writes one limiter
+ * phi_{n-1/2} per interface (no statistic index) from a ratio r written
+ * with the moments M_i.  0 (default): one phi per interface, the smallest of
+ * the nine statistics' van Leer phi_j; 1: one phi_j per statistic; 2: one phi
+ * per interface from the number density M_0.  The limiter multiplies the
+ * nine statistics' components of F^LW - F^LF. */
 static int g_flic_mode = 0;
 void or_set_flic_limiter(int mode) { g_flic_mode = (mode >= 0 && mode <= 2) ? mode : 0; }
 
@@ -1116,13 +1117,12 @@ static void interface_flux(int order, int scheme, int c, int side, const double 
          * form is 0/0), 2r/(1 + r) = 2/(1 + 1/r) for r > 0 (2 as r -> inf) */
         phis[j] = r > 0.0 ? 2.0 / (1.0 + 1.0 / r) : 0.0;
     }
-    if (g_flic_mode != 0) {
-        /* one limiter for the whole flux difference */
+    if (g_flic_mode != 1) {
+        /* one limiter per interface */
         double phi = phis[0];
-        if (g_flic_mode == 2)
+        if (g_flic_mode == 0)
             for (int j = 1; j < 9; ++j) phi = fmin(phi, phis[j]);
-        for (int i = 0; i < NP; ++i) flux[i] += phi * D[i];
-        return;
+        for (int j = 0; j < 9; ++j) phis[j] = phi;
     }
     for (int j = 0; j < 9; ++j) {
         const double phi = phis[j];

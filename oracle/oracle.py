@@ -198,9 +198,9 @@ def cond_estimate(order, beta, g=None):
 
 
 def set_flic_limiter(mode):
-    """Which ratio sets the FLIC limiter: 0 per statistic of the nine, 1 one
-    per interface from the density, 2 one per interface, the smallest of the
-    nine statistics' limiters."""
+    """Which ratio sets the FLIC limiter: 0 one per interface, the smallest
+    of the nine statistics' limiters (default); 1 one per statistic of the
+    nine; 2 one per interface from the density."""
     lib().or_set_flic_limiter(int(mode))
 
 
@@ -213,7 +213,8 @@ def flic_basis():
     return v
 
 
-def interface_flux(order, scheme, c, side, M, F, g, speed, dtdx, tol=1e-10, maxI=500, final_step=False):
+def interface_flux(order, scheme, c, side, M, F, g, speed, dtdx, tol=1e-10, maxI=500, final_step=False,
+                   flic_limiter=0):
     """Interface flux between cells c - 1 + side and c + side, in the gauge of
     cell c (Eqs. "The lax F", "The lax W", "The FLIC"): scheme lf, lw, flic."""
     M = _f64(M).reshape(-1, NP)
@@ -222,6 +223,7 @@ def interface_flux(order, scheme, c, side, M, F, g, speed, dtdx, tol=1e-10, maxI
     speed = _f64(speed).reshape(-1)
     out = np.zeros(NP)
     opts = np.array([tol, float(maxI), float(bool(final_step))])
+    set_flic_limiter(flic_limiter)
     st = lib().or_interface_flux(order, {"lf": 0, "lw": 1, "flic": 2}[scheme], c, side, _d(M), _d(F), _d(g),
                                  _d(speed), ctypes.c_double(dtdx), _d(opts), _d(out))
     return out, st
@@ -352,10 +354,11 @@ class Shock:
 
     def __init__(self, mach, ncells, xl, xr, order=8, cfl=0.5, Pr=2.0 / 3.0, gamma=5.0 / 3.0,
                  kn=1.0, tol=1e-8, maxI=500, nthreads=0, ic="step", thickness=15.7, scheme="lf",
-                 final_step=False):
+                 final_step=False, flic_limiter=0):
         self.order, self.N, self.cfl, self.Pr = order, ncells, cfl, Pr
         # interface flux: Eq. "The lax F" (lf), "The lax W" (lw), "The FLIC" (flic)
         self.scheme = {"lf": 0, "lw": 1, "flic": 2}[scheme]
+        self.flic_limiter = flic_limiter  # see set_flic_limiter
         self.dx = (xr - xl) / ncells
         self.x = xl + (np.arange(ncells) + 0.5) * self.dx
         self.relax = kn * RELAX_KN1 / Pr
@@ -409,6 +412,7 @@ class Shock:
 
     def step(self):
         out = np.zeros(3)
+        set_flic_limiter(self.flic_limiter)
         lib().or_shock_step(self.order, self.N, ctypes.c_double(self.dx), ctypes.c_double(self.cfl),
                             ctypes.c_double(self.Pr), ctypes.c_double(self.relax), _d(self.M), _d(self.beta),
                             _d(self.g), _d(self.speed), _i(self.status), _i(self.iters), _d(self.opts),

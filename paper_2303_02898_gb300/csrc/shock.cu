@@ -297,6 +297,9 @@ __device__ __forceinline__ void add9(float *f, const float *c) {
 //   r_j = v_j . (M_a - M_{a-1}) / v_j . (M_b - M_a); r = 0 where the
 //   denominator is 0, phi = 0 for r <= 0 (also r = -1, where the printed form
 //   is 0/0), and the ghost cell standing in for the cell before the first one.
+//   The printed limiter phi_{n-1/2} carries no statistic index: by default
+//   every phi_j is the interface's smallest one (flic = 0); flic = 1 keeps
+//   one phi_j per statistic, flic = 2 takes the density's for all.
 // An interface whose Newton solve failed (IFACE_FAILED) or whose flux is not
 // finite takes F^LF.
 __global__ void __launch_bounds__(128) k_stencil2(const float *__restrict__ M, const float *__restrict__ F,
@@ -375,13 +378,17 @@ __global__ void __launch_bounds__(128) k_stencil2(const float *__restrict__ M, c
 #pragma unroll
                 for (int k = 0; k < NP; ++k) w[k] -= f[k];
                 project9(w, qd);
+                float phi[9], pmin = 2.f;
 #pragma unroll
                 for (int j = 0; j < 9; ++j) {
                     const float num = qa[j] - qaa[j], den = qb[j] - qa[j];
                     const float r = den != 0.f ? num / den : 0.f;
-                    const float phi = r > 0.f ? 2.f / (1.f + 1.f / r) : 0.f;
-                    qd[j] *= phi;
+                    phi[j] = r > 0.f ? 2.f / (1.f + 1.f / r) : 0.f;
+                    pmin = fminf(pmin, phi[j]);
                 }
+                const int mode = prm[p].flic;
+#pragma unroll
+                for (int j = 0; j < 9; ++j) qd[j] *= mode == 1 ? phi[j] : (mode == 2 ? phi[0] : pmin);
                 add9(f, qd);
             }
         }
@@ -465,7 +472,8 @@ bool shock_params_valid(const mem_shock_params &p) {
     return p.ncells >= 1 && p.xr > p.xl && p.mach >= 1.0 && p.cfl > 0 && p.Pr > 0.5 && p.gamma > 1.0 && p.kn > 0 &&
            (p.ic == 0 || p.ic == 1) && p.maxI >= 0 && (p.impl == MEM_IMPL_PLAIN || p.impl == MEM_IMPL_FUSED) &&
            p.na > 0 && p.nb > 0 && p.nr > 0 && p.scheme >= MEM_SCHEME_LF && p.scheme <= MEM_SCHEME_FLIC &&
-           (p.ic == 0 || p.thickness > 0) && p.t_end >= 0.0 && (p.stats == 35 || p.stats == 9);
+           (p.ic == 0 || p.thickness > 0) && p.t_end >= 0.0 && (p.stats == 35 || p.stats == 9) &&
+           p.flic_limiter >= 0 && p.flic_limiter <= 2;
 }
 
 // Device bytes per packed cell, the interface arrays of Lax-Wendroff / FLIC
@@ -575,7 +583,7 @@ int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **o
         pr.relax = (float)(ps[i].kn * sqrt(2.0 / 3.14159265358979323846) / ps[i].Pr);
         pr.drho = (float)(n_dn - 1.0);
         pr.scheme = ps[i].scheme;
-        pr.pad = 0;
+        pr.flic = ps[i].flic_limiter;
         pr.t_end = ps[i].t_end;
         b->second_order |= ps[i].scheme != MEM_SCHEME_LF;
         b->hprm.push_back(pr);
@@ -868,6 +876,7 @@ void mem_shock_params_default(mem_shock_params *p) {
     p->thickness = 15.7;
     p->t_end = 0.0;
     p->stats = 35;
+    p->flic_limiter = 0;
 }
 
 void mem_shock_free(mem_shock *s) {

@@ -37,7 +37,7 @@ class ShockParams(ctypes.Structure):
                 ("impl", ctypes.c_int32), ("graph", ctypes.c_int32), ("tol", ctypes.c_float),
                 ("maxI", ctypes.c_int32), ("na", ctypes.c_double), ("nb", ctypes.c_double),
                 ("nr", ctypes.c_double), ("scheme", ctypes.c_int32), ("thickness", ctypes.c_double),
-                ("t_end", ctypes.c_double), ("stats", ctypes.c_int32)]
+                ("t_end", ctypes.c_double), ("stats", ctypes.c_int32), ("flic_limiter", ctypes.c_int32)]
 
 
 SCHEME_LF, SCHEME_LW, SCHEME_FLIC = 0, 1, 2

@@ -351,13 +351,15 @@ typedef struct {
                           35 moments; for an axisymmetric flow both give
                           the same solution up to rounding.  Must agree
                           across a batch.                                 */
-    int32_t flic_limiter; /* FLIC only.  Eq. "The FLIC" prints one limiter
-                          phi_{n-1/2} per interface (no statistic index)
-                          from ratios written with the moments M_i:
-                          0 (default): one phi per interface, the smallest
-                          of the nine statistics' van Leer phi_j;
-                          1: one phi_j per statistic; 2: the density's phi
-                          for all.  phi scales the nine statistics'
+    int32_t flic_limiter; /* FLIC only.  Eq. "The FLIC" prints the limiter
+                          phi_{n-1/2} without a statistic index and its
+                          ratio with the moments M_i.  0 (default): one
+                          van Leer phi_j per statistic of the nine, ratios
+                          in the updated cell's gauge; 1: one phi per
+                          interface, the smallest phi_j, ratios in the
+                          interface's Hermite gauge (both sides share it:
+                          conservative in every moment); 2: the density's
+                          phi for all.  phi scales the nine statistics'
                           components of F^LW - F^LF.                      */
 } mem_shock_params;
 

@@ -1048,12 +1048,14 @@ void or_flux_axi(int order, const double *alpha, const double *g, double n, doub
     *speed = fmax(fabs(g[0] + g[3] * lo), fabs(g[0] + g[3] * hi));
 }
 
-/* Which ratio sets the FLIC limiter.  Eq. "The FLIC" writes one limiter
- * phi_{n-1/2} per interface (no statistic index) from a ratio r written
- * with the moments M_i.  0 (default): one phi per interface, the smallest of
- * the nine statistics' van Leer phi_j; 1: one phi_j per statistic; 2: one phi
- * per interface from the number density M_0.  The limiter multiplies the
- * nine statistics' components of F^LW - F^LF. */
+/* Which ratio sets the FLIC limiter.  Eq. "The FLIC" writes the limiter
+ * phi_{n-1/2} without a statistic index but its ratio r with the moments
+ * M_i.  0 (default): one phi_j per statistic of the nine; 1: one phi per
+ * interface, the smallest of the nine statistics' phi_j, from ratios taken
+ * in the interface's Hermite gauge (both neighbours then use the same phi,
+ * and the scheme stays conservative); 2: one phi per interface from the
+ * number density M_0.  The limiter multiplies the nine statistics'
+ * components of F^LW - F^LF. */
 static int g_flic_mode = 0;
 void or_set_flic_limiter(int mode) { g_flic_mode = (mode >= 0 && mode <= 2) ? mode : 0; }
 
@@ -1109,18 +1111,31 @@ static void interface_flux(int order, int scheme, int c, int side, const double 
         D[i] = flw[i] - flf[i];
         flux[i] = flf[i];
     }
+    /* Mode 1 (the smallest phi per interface): its ratios are taken in the
+     * interface's own Hermite gauge gI, which both neighbours share, so the
+     * two sides of the interface use the same phi and the scheme stays
+     * conservative; modes 0 and 2 take them in the updated cell's gauge
+     * g(c), as every quantity of cell c. */
+    const double *ra = Ma, *raa = Maa, *rb = Mb;
+    double MaI[NP], MaaI[NP], MbI[NP];
+    if (g_flic_mode == 1) {
+        or_gauge_T(gI, &g[6 * a], T); matvec35(T, &M[NP * a], MaI);
+        or_gauge_T(gI, &g[6 * aa], T); matvec35(T, &M[NP * aa], MaaI);
+        or_gauge_T(gI, &g[6 * b], T); matvec35(T, &M[NP * b], MbI);
+        ra = MaI; raa = MaaI; rb = MbI;
+    }
     double phis[9];
     for (int j = 0; j < 9; ++j) {
-        const double num = dot35(v[j], Ma) - dot35(v[j], Maa), den = dot35(v[j], Mb) - dot35(v[j], Ma);
+        const double num = dot35(v[j], ra) - dot35(v[j], raa), den = dot35(v[j], rb) - dot35(v[j], ra);
         const double r = den != 0.0 ? num / den : 0.0;
         /* (r + |r|)/(1 + r): 0 for r <= 0 (also at r = -1, where the printed
          * form is 0/0), 2r/(1 + r) = 2/(1 + 1/r) for r > 0 (2 as r -> inf) */
         phis[j] = r > 0.0 ? 2.0 / (1.0 + 1.0 / r) : 0.0;
     }
-    if (g_flic_mode != 1) {
+    if (g_flic_mode != 0) {
         /* one limiter per interface */
         double phi = phis[0];
-        if (g_flic_mode == 0)
+        if (g_flic_mode == 1)
             for (int j = 1; j < 9; ++j) phi = fmin(phi, phis[j]);
         for (int j = 0; j < 9; ++j) phis[j] = phi;
     }

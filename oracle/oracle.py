@@ -198,9 +198,10 @@ def cond_estimate(order, beta, g=None):
 
 
 def set_flic_limiter(mode):
-    """Which ratio sets the FLIC limiter: 0 one per interface, the smallest
-    of the nine statistics' limiters (default); 1 one per statistic of the
-    nine; 2 one per interface from the density."""
+    """Which ratio sets the FLIC limiter: 0 one per statistic of the nine
+    (default); 1 one per interface, the smallest of the nine statistics'
+    limiters, in the interface's Hermite gauge; 2 one per interface from the
+    density."""
     lib().or_set_flic_limiter(int(mode))
 
 

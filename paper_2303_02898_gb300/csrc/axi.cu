@@ -78,8 +78,8 @@ struct AxiLayout {
 __host__ __device__ inline AxiLayout axi_layout(int nx, int nrp) {
     AxiLayout L;
     int o = 0;
-    L.hx = o; o += 10 * nx;
-    L.lwx = o; o += nx;
+    L.hx = o; o += 12 * nx;  // per x node: he_0..he_9, log weight, pad (three 16-byte loads)
+    L.lwx = L.hx;
     L.Tt = o; o += 10 * nrp;
     L.Lt = o; o += 5 * nrp;
     L.mu = o; o += 52;
@@ -147,10 +147,10 @@ __device__ __forceinline__ float axi_sweep(const float (&c)[R][3], float c3, flo
 #pragma unroll
             for (int k = 0; k < 10; ++k) T[r][k] = 0.f;
         for (int i = 0; i < nx; ++i) {
-            float h[10];
-#pragma unroll
-            for (int k = 0; k < 10; ++k) h[k] = hx[k * nx + i];
-            const float lx = lwx[i];
+            const float4 *hp = reinterpret_cast<const float4 *>(hx + 12 * i);
+            const float4 q0 = hp[0], q1 = hp[1], q2 = hp[2];
+            const float h[10] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y};
+            const float lx = q2.z;
             const float cx = fmaf(h[3], c3, h[4] * c4);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -262,8 +262,9 @@ __global__ void __launch_bounds__(AW * 32) k_axi(AxiArgs A) {
             float h[10];
             hermite_vals<9>(uh, h);
 #pragma unroll
-            for (int k = 0; k < 10; ++k) hx[k * nx + i] = h[k];
-            lwx[i] = ((lhx + lgx[i]) - hs) - hl;
+            for (int k = 0; k < 10; ++k) hx[12 * i + k] = h[k];
+            hx[12 * i + 10] = ((lhx + lgx[i]) - hs) - hl;
+            hx[12 * i + 11] = 0.f;
         }
         float lwr[R], L1[R], L2[R];
 #pragma unroll

@@ -297,9 +297,11 @@ __device__ __forceinline__ void add9(float *f, const float *c) {
 //   r_j = v_j . (M_a - M_{a-1}) / v_j . (M_b - M_a); r = 0 where the
 //   denominator is 0, phi = 0 for r <= 0 (also r = -1, where the printed form
 //   is 0/0), and the ghost cell standing in for the cell before the first one.
-//   The printed limiter phi_{n-1/2} carries no statistic index: by default
-//   every phi_j is the interface's smallest one (flic = 0); flic = 1 keeps
-//   one phi_j per statistic, flic = 2 takes the density's for all.
+//   flic = 0 (default): one phi_j per statistic; flic = 1: one phi per
+//   interface, the smallest phi_j with the ratios taken in the interface's
+//   Hermite gauge (the same phi on both sides: conservative); flic = 2: the
+//   density's phi for all (the printed phi_{n-1/2} carries no statistic
+//   index, its ratio is written with the moments M_i).
 // An interface whose Newton solve failed (IFACE_FAILED) or whose flux is not
 // finite takes F^LF.
 __global__ void __launch_bounds__(128) k_stencil2(const float *__restrict__ M, const float *__restrict__ F,
@@ -378,6 +380,26 @@ __global__ void __launch_bounds__(128) k_stencil2(const float *__restrict__ M, c
 #pragma unroll
                 for (int k = 0; k < NP; ++k) w[k] -= f[k];
                 project9(w, qd);
+                const int mode = prm[p].flic;
+                if (mode == 1) {
+                    // the ratios in the interface's Hermite gauge, which both
+                    // neighbours share (one phi for both sides)
+                    float gi[6];
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) gi[k] = gI[(size_t)b * 6 + k];
+                    const int cells[3] = {aa, a, b};
+                    float *dst[3] = {qaa, qa, qb};
+#pragma unroll 1
+                    for (int t = 0; t < 3; ++t) {
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) gn[k] = g[(size_t)cells[t] * 6 + k];
+                        gauge_maps(gi, gn, T);
+#pragma unroll
+                        for (int k = 0; k < NP; ++k) x[k] = M[(size_t)cells[t] * NP + k];
+                        apply_T(T, x, y);
+                        project9(y, dst[t]);
+                    }
+                }
                 float phi[9], pmin = 2.f;
 #pragma unroll
                 for (int j = 0; j < 9; ++j) {
@@ -386,9 +408,8 @@ __global__ void __launch_bounds__(128) k_stencil2(const float *__restrict__ M, c
                     phi[j] = r > 0.f ? 2.f / (1.f + 1.f / r) : 0.f;
                     pmin = fminf(pmin, phi[j]);
                 }
-                const int mode = prm[p].flic;
 #pragma unroll
-                for (int j = 0; j < 9; ++j) qd[j] *= mode == 1 ? phi[j] : (mode == 2 ? phi[0] : pmin);
+                for (int j = 0; j < 9; ++j) qd[j] *= mode == 0 ? phi[j] : (mode == 2 ? phi[0] : pmin);
                 add9(f, qd);
             }
         }

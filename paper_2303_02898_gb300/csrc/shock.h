@@ -15,7 +15,7 @@ struct ShockProb {
     float relax;   // tau = relax / n
     float drho;    // rho_+ - rho_- (normalises the steady-state metric)
     int scheme;    // interface flux, MEM_SCHEME_*
-    int flic;      // FLIC limiter: 0 smallest of the nine, 1 per statistic, 2 density
+    int flic;      // FLIC limiter: 0 per statistic, 1 smallest of the nine (interface gauge), 2 density
     double t_end;  // > 0: simulated time at which the problem stops
 };
 

@@ -71,6 +71,22 @@ def test_shock_mach15_second_order_matches_oracle(O, mem, ctx8, scheme, impl, gr
     assert np.abs(out["M"] - so.M).max() <= 1e-3 * np.abs(so.M).max()
 
 
+@pytest.mark.parametrize("mode", [1, 2])
+def test_flic_limiter_readings_match_oracle(O, mem, ctx8, mode):
+    """The other readings of the FLIC limiter (one phi per interface: the
+    smallest of the nine statistics' in the interface's gauge, or the
+    density's), Mach 1.5, 64 cells, 20 steps, against the oracle's same
+    reading."""
+    sh = mem.Shock(ctx8, mach=1.5, ncells=64, xl=-20.0, xr=20.0, graph=1, scheme=mem.SCHEME_FLIC, flic_limiter=mode)
+    sh.step(20)
+    out = sh.get()
+    sh.close()
+    so = O.Shock(1.5, 64, -20.0, 20.0, scheme="flic", flic_limiter=mode)
+    for _ in range(20):
+        so.step()
+    _compare(out, so)
+
+
 def test_shock_mach12_lax_wendroff_paper_setup(O, mem):
     """Section 4's Mach-1.2 run (Lax-Wendroff): 25 cells on [-47.7, 47.7],
     tanh start with thickness 15.9, on a velocity-space rule of 2 x 2 blocks

@@ -29,6 +29,8 @@ class SolveTargets:
     T: np.ndarray   # [B]
     a: np.ndarray   # [B, 10]
     b: np.ndarray   # [B, 6]
+    redrawn: int = 0            # cells whose first (a, b) draw had a second mode
+    bimodal: np.ndarray = None  # redraw=False: mask of the cells with a second mode
 
 
 _CUBIC = [(3, 0, 0), (2, 1, 0), (2, 0, 1), (1, 2, 0), (1, 1, 1), (1, 0, 2), (0, 3, 0), (0, 2, 1), (0, 1, 2), (0, 0, 3)]
@@ -55,23 +57,29 @@ def _unimodal(a: np.ndarray, b: np.ndarray, dirs: np.ndarray) -> np.ndarray:
 
 
 def solve_targets(B: int, seed: int = 0, v_sigma: float = 3.0, a_sigma: float = 0.05,
-                  b_lo: float = 0.01, b_hi: float = 0.1) -> SolveTargets:
+                  b_lo: float = 0.01, b_hi: float = 0.1, redraw: bool = True) -> SolveTargets:
     """Cells whose density would have a second mode (checked along fixed
-    directions) get their (a, b) redrawn until unimodal."""
+    directions) get their (a, b) redrawn until unimodal (redraw=True; the
+    count is kept in `redrawn`); redraw=False returns the draws as they come
+    and marks the bimodal ones."""
     rng = np.random.Generator(np.random.PCG64(seed))
     v = rng.normal(0.0, v_sigma, size=(B, 3))
     T = np.exp(rng.uniform(np.log(0.5), np.log(20.0), size=B))
     a = rng.normal(0.0, a_sigma, size=(B, 10))
     b = rng.uniform(b_lo, b_hi, size=(B, 6))
     dirs = _directions()
+    first = ~_unimodal(a, b, dirs)
+    if not redraw:
+        return SolveTargets(v=v, T=T, a=a, b=b, redrawn=0, bimodal=first)
+    bad = first
     for _ in range(200):
-        bad = ~_unimodal(a, b, dirs)
         nb = int(bad.sum())
         if nb == 0:
             break
         a[bad] = rng.normal(0.0, a_sigma, size=(nb, 10))
         b[bad] = rng.uniform(b_lo, b_hi, size=(nb, 6))
-    return SolveTargets(v=v, T=T, a=a, b=b)
+        bad = ~_unimodal(a, b, dirs)
+    return SolveTargets(v=v, T=T, a=a, b=b, redrawn=int(first.sum()))
 
 
 def perturbed_hermite_moments(B: int, seed: int = 0, scale: float = 0.05) -> np.ndarray:

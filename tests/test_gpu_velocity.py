@@ -181,3 +181,29 @@ def test_velocity_shock_condition_matches_oracle(O, mem, vctx, dom):
         assert co > 10.0
         assert cg == pytest.approx(co, rel=0.1), (k, cg, co)
     sh.close()
+
+
+@pytest.mark.parametrize("scheme", ["lf", "flic"])
+@pytest.mark.parametrize("stats", [35, 9])
+def test_paper_mesh_mach10_matches_oracle(mem, scheme, stats):
+    """The paper's Mach-10 run (Section 4): 150 cells on [-47.1, 47.1], tanh
+    start, velocity-space rule on the Rankine-Hugoniot box; 100 local
+    Lax-Friedrichs steps or 60 FLIC steps against the FP64 oracle's profiles
+    (tests/golden/mach10_paper_mesh.json, written by make_mach10_paper_mesh.py
+    from the oracle only), in both statistics systems."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "mach10_paper_mesh.json")))
+    g = gold[scheme]
+    vctx = mem.Context.velocity(gold["rule"]["box"], nbx=6, nbr=4, ng=8, K=12)
+    sh = mem.Shock(vctx, mach=10.0, ncells=150, xl=-47.1, xr=47.1, ic=1, thickness=15.7, graph=1, stats=stats,
+                   scheme=mem.SCHEME_FLIC if scheme == "flic" else mem.SCHEME_LF)
+    sh.step(g["steps"])
+    out = sh.get()
+    sh.close()
+    vctx.close()
+    assert out["t"] == pytest.approx(g["t"], rel=1e-4)
+    for k, i in (("rho", 0), ("ux", 1), ("T", 2)):
+        a, b = g["up"][i], g["down"][i]
+        err = np.abs(_norm(out[k], a, b) - _norm(np.array(g[k]), a, b)).max()
+        assert err <= 1e-3, (k, err)

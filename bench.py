@@ -293,6 +293,15 @@ def run_mach10_4096(mem, torch, np, vctx, nsteps=2000, chunk=200):
     return out
 
 
+def axi_flops_per_pass(nx, nr):
+    """Algorithmic FP32 flops of one Newton pass of the nine-statistic kernel
+    for one cell (FMA = 2): one sweep over the nx x nr nodes (5 FMA of
+    exponent, 10 of x stage), the s stage (50 moments over nr nodes), the
+    linearisation terms of the 8 x 8 Hessian (about 200), the 8 x 8 Cholesky
+    and two triangular solves."""
+    return 2 * (nx * nr * 15 + 50 * nr + 200 + 8 ** 3 // 6 + 2 * 64)
+
+
 def run_ensemble_config4(mem, torch, np, nsteps=40):
     """The batched ensemble as stated: 256 problems, ncells logU[256, 16384],
     Mach U[1.2, 10] (seed 1), cell width 0.628, each problem on its own
@@ -311,7 +320,7 @@ def run_ensemble_config4(mem, torch, np, nsteps=40):
     sh.step(3)
     # launch shape of the nine-statistic kernel from the autotuner, timed on
     # the batch's own state (first 2^17 cells)
-    Md, bd, gd = sh.device_tensors()
+    Md, bd, gd = sh.device_tensors()[:3]
     nt = min(Md.shape[0], 1 << 17)
     rep = vctx.tune(mem.TUNE_AXI, Md[:nt], bd[:nt].clone(), gd[:nt], reps=2)
     bw, bb, bms = rep["candidates"][rep["best"]]
@@ -327,6 +336,13 @@ def run_ensemble_config4(mem, torch, np, nsteps=40):
     fin = np.array([bool(np.isfinite(sh.problem(i)["rho"]).all()) for i in range(len(probs))])
     mach = np.array([p.mach for p in probs])
     nc = np.array([p.ncells for p in probs])
+    # Newton passes of the last step (every cell), for the kernel's roofline
+    passes = int(sh.device_tensors()[4].sum().item())
+    rule = vctx.velocity_rule()[0]
+    nx, nr = rule[0] * rule[2], rule[1] * rule[2]
+    fpp = axi_flops_per_pass(nx, nr)
+    peak = measured_peaks(mem)["fp32_tflops"]
+    ach = passes * fpp / (dt / nsteps) / 1e12
     sh.close()
     vctx.close()
     return {"ensemble_config4": {"value": cells * nsteps / dt, "unit": "cell-updates/s", "problems": len(probs),
@@ -336,6 +352,11 @@ def run_ensemble_config4(mem, torch, np, nsteps=40):
                                  "failed": [{"mach": round(float(m), 2), "ncells": int(n)}
                                             for m, n, f in zip(mach, nc, fin) if not f],
                                  "statistics": 9, "rule": "velocity-space 6x4 blocks x 8 GL per problem box",
+                                 "roofline_k_axi": {"bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": peak,
+                                                    "frac": ach / peak, "passes_per_step": passes,
+                                                    "flops_per_pass": fpp,
+                                                    "note": "of measured FP32 FMA rate; whole step time (k_axi is "
+                                                            "95 % of it) in the denominator"},
                                  "autotune": {"kernel": "k_axi", "chosen": {"warps": bw, "blocks_per_sm": bb},
                                               "candidates": [{"warps": w, "blocks_per_sm": b, "ms": round(ms, 3)}
                                                              for w, b, ms in rep["candidates"]],

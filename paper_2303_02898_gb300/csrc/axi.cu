@@ -226,8 +226,10 @@ __device__ __forceinline__ void packed_pq(int e, int &p, int &q) {
 }
 
 // AW warps (cells) per block: the launch shape is chosen by the autotuner.
+// With one radial node per lane (R = 1) the register budget is held to
+// about 100 per thread (5 blocks of 4 warps per SM) except for 8-warp blocks.
 template <int R, int AW>
-__global__ void __launch_bounds__(AW * 32) k_axi(AxiArgs A) {
+__global__ void __launch_bounds__(AW * 32, (R == 1 && AW < 8) ? 20 / AW : 1) k_axi(AxiArgs A) {
     extern __shared__ float smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nx = A.nx, nr = A.nr, nrp = 32 * R;

@@ -377,17 +377,19 @@ class Shock:
         return [p.value for p in ptrs]
 
     def device_tensors(self):
-        """Zero-copy views (M, beta, gauge) of the packed device state, ghost
-        cells included (valid while the shock lives)."""
+        """Zero-copy views (M, beta, gauge, status, iters) of the packed device
+        state, ghost cells included (valid while the shock lives)."""
         NT = sum(p.ncells + 2 for p in self.ps)
-        M, beta, g = self.device_state()[:3]
+        M, beta, g, _, status, iters = self.device_state()
 
         class _View:
-            def __init__(self, ptr, shape):
-                self.__cuda_array_interface__ = {"shape": shape, "typestr": "<f4", "data": (ptr, False),
+            def __init__(self, ptr, shape, typestr="<f4"):
+                self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False),
                                                  "version": 2}
         dev = torch.device("cuda", torch.cuda.current_device())
-        return tuple(torch.as_tensor(_View(p, (NT, n)), device=dev) for p, n in ((M, NP), (beta, NP), (g, 6)))
+        views = [torch.as_tensor(_View(p, (NT, n)), device=dev) for p, n in ((M, NP), (beta, NP), (g, 6))]
+        views += [torch.as_tensor(_View(p, (NT,), "<i4"), device=dev) for p in (status, iters)]
+        return tuple(views)
 
     def close(self):
         if self.h:

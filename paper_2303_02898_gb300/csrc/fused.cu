@@ -193,38 +193,24 @@ __global__ void __launch_bounds__(NW * 32, (N <= 8 ? 16 : 8) / NW) k_fused_solve
                 }
             }
             __syncwarp();
-            // ---- stage y: t_ab(k) = sum_j s_a(j,k) he_b(y_j), a + b <= 8;
-            // two outputs per lane and iteration (independent chains)
-            for (int t = lane; t < C::T2; t += 64) {
-                const int u = t + 32 < C::T2 ? t + 32 : t;
-                const int ab0 = t / N, k0 = t % N, ab1 = u / N, k1 = u % N;
-                const int p0 = s_ab[ab0], a0 = p0 & 255, b0 = p0 >> 8;
-                const int p1 = s_ab[ab1], a1 = p1 & 255, b1 = p1 >> 8;
-                float c0 = 0.f, c1 = 0.f;
+            // ---- stage y: t_ab(k) = sum_j s_a(j,k) he_b(y_j), a + b <= 8
+            for (int t = lane; t < C::T2; t += 32) {
+                const int ab = t / N, k = t % N;
+                const int abp = s_ab[ab], a = abp & 255, b = abp >> 8;
+                float acc = 0.f;
 #pragma unroll
-                for (int j = 0; j < N; ++j) {
-                    c0 = fmaf(S1[a0 * C::P + j * N + k0], s_he[j * MEM_HE_STRIDE + b0], c0);
-                    c1 = fmaf(S1[a1 * C::P + j * N + k1], s_he[j * MEM_HE_STRIDE + b1], c1);
-                }
-                T2[ab0 * N + k0] = c0;
-                T2[ab1 * N + k1] = c1;
+                for (int j = 0; j < N; ++j) acc += S1[a * C::P + j * N + k] * s_he[j * MEM_HE_STRIDE + b];
+                T2[ab * N + k] = acc;
             }
             __syncwarp();
-            // ---- stage z: mu_abc = sum_k t_ab(k) he_c(z_k), two outputs per lane
-            for (int t = lane; t < 165; t += 64) {
-                const int u = t + 32 < 165 ? t + 32 : t;
-                const int e0 = s_abc[t], e1 = s_abc[u];
-                const int a0 = e0 & 255, b0 = (e0 >> 8) & 255, z0 = e0 >> 16;
-                const int a1 = e1 & 255, b1 = (e1 >> 8) & 255, z1 = e1 >> 16;
-                const int ab0 = (a0 + b0) * (a0 + b0 + 1) / 2 + b0, ab1 = (a1 + b1) * (a1 + b1 + 1) / 2 + b1;
-                float c0 = 0.f, c1 = 0.f;
+            // ---- stage z: mu_abc = sum_k t_ab(k) he_c(z_k)
+            for (int t = lane; t < 165; t += 32) {
+                const int abc = s_abc[t], a = abc & 255, b = (abc >> 8) & 255, c = abc >> 16;
+                const int ab = (a + b) * (a + b + 1) / 2 + b;
+                float acc = 0.f;
 #pragma unroll
-                for (int k = 0; k < N; ++k) {
-                    c0 = fmaf(T2[ab0 * N + k], s_he[k * MEM_HE_STRIDE + z0], c0);
-                    c1 = fmaf(T2[ab1 * N + k], s_he[k * MEM_HE_STRIDE + z1], c1);
-                }
-                smu[t] = c0;
-                smu[u] = c1;
+                for (int k = 0; k < N; ++k) acc += T2[ab * N + k] * s_he[k * MEM_HE_STRIDE + c];
+                smu[t] = acc;
             }
             __syncwarp();
             // ---- gradient and Hessian (Appendix C)
@@ -240,19 +226,14 @@ __global__ void __launch_bounds__(NW * 32, (N <= 8 ? 16 : 8) / NW) k_fused_solve
                 const int2 *sl = A.rslots;
                 for (int r = 0; r < A.n_rounds; ++r) {
                     const int T = __ldg(&A.rounds[r]);
-                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                    float a0 = 0.f, a1 = 0.f;
                     int t = 0;
-                    // four independent chains: the slot and moment loads of
-                    // four terms are in flight together
-                    for (; t + 3 < T; t += 4) {
+                    for (; t + 1 < T; t += 2) {
                         const int2 s0 = __ldg(&sl[t * 32 + lane]), s1 = __ldg(&sl[(t + 1) * 32 + lane]);
-                        const int2 s2 = __ldg(&sl[(t + 2) * 32 + lane]), s3 = __ldg(&sl[(t + 3) * 32 + lane]);
                         a0 = fmaf(__int_as_float(s0.y), smu[s0.x], a0);
                         a1 = fmaf(__int_as_float(s1.y), smu[s1.x], a1);
-                        a2 = fmaf(__int_as_float(s2.y), smu[s2.x], a2);
-                        a3 = fmaf(__int_as_float(s3.y), smu[s3.x], a3);
                     }
-                    for (; t < T; ++t) {
+                    if (t < T) {
                         const int2 s0 = __ldg(&sl[t * 32 + lane]);
                         a0 = fmaf(__int_as_float(s0.y), smu[s0.x], a0);
                     }
@@ -260,7 +241,7 @@ __global__ void __launch_bounds__(NW * 32, (N <= 8 ? 16 : 8) / NW) k_fused_solve
                     const int e = __ldg(&A.rent[r * 32 + lane]);
                     if (e >= 0) {
                         const int i = e & 255, j = e >> 8;
-                        H[i * LDH + j] = ((a0 + a1) + (a2 + a3)) - smu[i + 1] * smu[j + 1];
+                        H[i * LDH + j] = (a0 + a1) - smu[i + 1] * smu[j + 1];
                     }
                 }
             }

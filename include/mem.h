@@ -536,7 +536,10 @@ int mem_bench_peak(int kind, int64_t iters, double *seconds, double *work);
  * kind 1 BF16 operands, 2 TF32 operands, FP32 accumulation.  A_host
  * [128][64], B_host [N][64], D_host [128][N] row-major float host arrays;
  * N a multiple of 16 in 16..256.  Synchronous.  A check of the operand and
- * accumulator layouts that the tensor-core kernels rely on. */
+ * accumulator layouts that the tensor-core kernels rely on.  kind 3: TF32
+ * operands brought in by TMA tensor loads (row-major global arrays, boxes of
+ * 32 columns, 128-byte swizzle) and read through swizzled descriptors, the
+ * path of the mixed back-end's contraction. */
 int mem_tc_selftest(int kind, int N, const float *A_host, const float *B_host, float *D_host);
 
 #ifdef __cplusplus

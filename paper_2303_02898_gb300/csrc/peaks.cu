@@ -11,6 +11,7 @@
 #include "common.cuh"
 #include "ctx.h"
 #include "tc.cuh"
+#include "tmap.h"
 
 namespace {
 
@@ -199,6 +200,74 @@ __global__ void __launch_bounds__(128, 1) k_tc_selftest(const float *Ag, const f
     if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
+// D [128 x N] = A [128 x 64] . B [N x 64]^T with TF32 operands brought in
+// by TMA tensor loads (boxes of 32 columns, 128-byte swizzle) and read by
+// the MMAs through swizzled descriptors: the layout of the mixed back-end's
+// contraction.
+__global__ void __launch_bounds__(128, 1) k_tc_selftest_tma(const __grid_constant__ CUtensorMap tA,
+                                                            const __grid_constant__ CUtensorMap tB, float *Dg,
+                                                            int N, int *err) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_load, s_bar;
+    // the swizzled tiles start on a 1024-byte boundary
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    uint8_t *A = smem, *B = smem + 2 * 16384;  // two K-chunks of 32 columns each
+    if (warp == 0) {
+        tc::tmem_alloc(&s_tmem, 256);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(&s_load, 1);
+        tc::mbar_init(&s_bar, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    const uint32_t bbytes = (uint32_t)N * 128;
+    if (tid == 0) {
+        tc::mbar_expect_tx(&s_load, 2 * 16384 + 2 * bbytes);
+        for (int kc = 0; kc < 2; ++kc) {
+            tc::tma_load_2d(A + kc * 16384, &tA, 32 * kc, 0, &s_load);
+            tc::tma_load_2d(B + kc * bbytes, &tB, 32 * kc, 0, &s_load);
+        }
+        bool ok = tc::mbar_wait(&s_load, 0, kMaxPolls);
+        if (!ok) {
+            atomicExch(err, 1);
+            tc::mbar_wait(&s_load, 0, kMaxPolls);  // the copies land before the CTA may exit
+        } else {
+            const uint32_t sa = tc::smem_u32(A), sb = tc::smem_u32(B), id = tc::idesc(128, N, 2);
+            for (int kc = 0; kc < 2; ++kc)
+                for (int s = 0; s < 4; ++s)
+                    tc::mma_tf32(tmem, tc::sdesc_sw128(sa + kc * 16384 + 32 * s, 1024),
+                                 tc::sdesc_sw128(sb + kc * bbytes + 32 * s, 1024), id, (kc | s) != 0);
+        }
+        tc::mma_commit(&s_bar);
+    }
+    __syncwarp();
+    bool ok = tc::mbar_wait(&s_bar, 0, kMaxPolls);
+    if (!ok) {
+        atomicExch(err, 1);
+        tc::mbar_wait(&s_bar, 0, kMaxPolls);
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    tc::fence_after_sync();
+    if (ok) {
+        const int row = 32 * (warp & 3) + (tid & 31);
+        for (int c = 0; c < N; c += 8) {
+            float v[8];
+            tc::tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c, v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) Dg[(size_t)row * N + c + j] = v[j];
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
 int sm_count(int dev) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
@@ -266,7 +335,7 @@ int mem_bench_peak(int kind, int64_t iters, double *seconds, double *work) {
 }
 
 int mem_tc_selftest(int kind, int N, const float *A_host, const float *B_host, float *D_host) {
-    if ((kind != 1 && kind != 2) || N < 16 || N > 256 || N % 16 || !A_host || !B_host || !D_host) return MEM_EINVAL;
+    if (kind < 1 || kind > 3 || N < 16 || N > 256 || N % 16 || !A_host || !B_host || !D_host) return MEM_EINVAL;
     float *A = nullptr, *B = nullptr, *D = nullptr;
     int *err = nullptr;
     MEM_CUDA_TRY(cudaMalloc(&A, sizeof(float) * 128 * 64));
@@ -277,7 +346,18 @@ int mem_tc_selftest(int kind, int N, const float *A_host, const float *B_host, f
     MEM_CUDA_TRY(cudaMemcpy(A, A_host, sizeof(float) * 128 * 64, cudaMemcpyHostToDevice));
     MEM_CUDA_TRY(cudaMemcpy(B, B_host, sizeof(float) * N * 64, cudaMemcpyHostToDevice));
     const size_t smem = (size_t)(128 + 256) * 64 * 4;
-    if (kind == 1) {
+    if (kind == 3) {
+        CUtensorMap tA, tB;
+        int rc = mem_host::encode_tmap_2d_f32(&tA, A, 64, 128, 32, 128);
+        if (!rc) rc = mem_host::encode_tmap_2d_f32(&tB, B, 64, (uint64_t)N, 32, (uint32_t)N);
+        if (rc) {
+            cudaFree(A); cudaFree(B); cudaFree(D); cudaFree(err);
+            return rc;
+        }
+        const size_t sm3 = 2 * 16384 + 2 * (size_t)N * 128 + 1024;
+        MEM_CUDA_TRY(cudaFuncSetAttribute(k_tc_selftest_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+        k_tc_selftest_tma<<<1, 128, sm3>>>(tA, tB, D, N, err);
+    } else if (kind == 1) {
         MEM_CUDA_TRY(cudaFuncSetAttribute(k_tc_selftest<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_tc_selftest<1><<<1, 128, smem>>>(A, B, D, N, err);
     } else {

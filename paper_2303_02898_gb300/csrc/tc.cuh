@@ -38,6 +38,16 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// Shared-memory matrix descriptor for the 128-byte swizzled K-major layout
+// that a TMA tensor load with CU_TENSOR_MAP_SWIZZLE_128B writes: rows of 128
+// bytes, the 16-byte chunks of row r XOR-permuted by (r mod 8), 8-row atoms of
+// 1024 bytes SBO apart (the tile must start on a 1024-byte boundary).  One
+// MMA reads 32 bytes of K; K step s starts 32 s bytes further.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) |
+           (1ull << 46) | (2ull << 61);
+}
+
 // Byte offset of element (r, k) in the layout above (size = element bytes).
 __host__ __device__ constexpr uint32_t kmajor_off(int r, int k, int K, int size) {
     return (uint32_t)((r >> 3) * (128 * K * size / 16) + (k / (16 / size)) * 128 + (r & 7) * 16 +
@@ -133,6 +143,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src, uint32
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
             smem_u32(dst_smem)),
         "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+        : "memory");
+}
+
+// ---- tiled tensor copy global -> shared through a tensor map (2D box at
+// element coordinates (x, y), x innermost; x times the element size must be
+// a multiple of 16 bytes); completion counted on mbar.
+__device__ __forceinline__ void tma_load_2d(void *dst_smem, const void *tmap, int x, int y, uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(mbar))
         : "memory");
 }
 

@@ -17,7 +17,7 @@ def mem():
     return m
 
 
-@pytest.mark.parametrize("kind", [1, 2])
+@pytest.mark.parametrize("kind", [1, 2, 3])
 @pytest.mark.parametrize("N", [16, 64, 256])
 def test_tcgen05_layouts_exact(mem, kind, N):
     """A [128 x 64] and B [N x 64] hold values exact in BF16 (small integers)
@@ -26,6 +26,7 @@ def test_tcgen05_layouts_exact(mem, kind, N):
     A wrong descriptor offset, core-matrix order or accumulator lane would
     move entries and fail here."""
     rng = np.random.default_rng(7 + kind + N)
+    # kind 3: TF32 operands through TMA tensor loads with the 128-byte swizzle
     if kind == 1:
         A = rng.integers(-8, 9, (128, 64)).astype(np.float32)
         B = rng.integers(-8, 9, (N, 64)).astype(np.float32)

@@ -2,6 +2,7 @@
 // translation units (host side).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -54,7 +55,8 @@ struct mem_ctx {
     int *d_xlin_off = nullptr;     // [631]  flux-Jacobian terms (packed i>=j>=0)
     int2 *d_xlin_terms = nullptr;
     float xmax = 0.f;              // largest 1D node
-    float *d_tc_tab = nullptr;     // tensor-core contraction tables (mixed back-end), tiled
+    float *d_tc_tab = nullptr;     // tensor-core contraction tables (mixed back-end), [704][Q] row-major
+    CUtensorMap tm_tab48, tm_tab256;  // their tensor maps: boxes of 48 and 256 rows x 32 nodes
     double *d_phiT64 = nullptr;    // [35][Q] phi_k(ubar_q) in FP64 (residual recompute)
     double *d_logw64 = nullptr;    // [Q] log w_q in FP64
     // Velocity-space rule (mem_init_velocity): nodes fixed in the lab frame.
@@ -87,7 +89,8 @@ size_t plain_scratch_bytes(int Q);                                    // plain /
 bool tc_available(const mem_ctx *ctx);
 int build_tc_tables(mem_ctx *ctx, const std::vector<double> &phi);
 size_t tc_sigma_floats(int Q, int64_t cells);
-int tc_contract(mem_ctx *ctx, const float *a_hi, const float *a_lo, float *mom, int n, int *err, cudaStream_t st);
+int tc_contract(mem_ctx *ctx, const float *a_hi, const float *a_lo, int64_t rows, float *mom, int n, int *err,
+                cudaStream_t st);
 int residual64(mem_ctx *ctx, const float *M, const float *beta, const int32_t *status, int32_t mask, double *res,
                int32_t *status_out, double accept, int64_t B, cudaStream_t st);
 size_t flux_scratch_bytes(int Q);                                     // dense flux, one chunk

@@ -8,17 +8,23 @@
 // Hessian, which Newton's method only needs as a model, uses one TF32
 // product.
 //
-// Layout (tc.cuh, K-major, no swizzle): the line-search kernel writes sigma
-// for tile t of 128 cells and K-chunk kc of 32 nodes as one 16 KB block
-// (hi and lo in two arrays); the constant statistics tables are stored the
-// same way, ROWS_g rows (N) x 32 nodes (K) per block, in three column groups:
-//   group 0 (96 rows):  0-47 phi_hi (35 used), 48-95 phi_lo;
-//   group 1 (304 rows): Hessian entries 0-303;
-//   group 2 (304 rows): Hessian entries 304-594 (rows 291-303 zero).
-// One CTA (128 threads) computes one tile and one group: thread 0 issues the
-// bulk copies (TMA engine, double-buffered, mbarrier transaction counts) and
-// the MMAs (accumulators in TMEM); then all four warps read their 32 rows of
-// TMEM and write the moments row of each cell.  Every wait is bounded.
+// Layout: sigma (hi and lo, one array each) is row-major [cells][Q], written
+// coalesced by the line-search kernel; the constant statistics tables are
+// row-major [704][Q]:
+//   rows   0- 47: phi_hi (35 used),      rows  48- 95: phi_lo;
+//   rows  96-399: Hessian entries 0-303;  rows 400-703: entries 304-594
+//                                          (rows 695-703 zero).
+// Tensor maps (TMA descriptors) cut them into boxes of 32 nodes (128 bytes:
+// one swizzle span) x 128 cells, 48 or 256 table rows, which the TMA engine
+// writes to shared memory with the 128-byte swizzle (tc.cuh, sdesc_sw128).
+// One CTA (160 threads) computes one tile of 128 cells and one column group
+// (0: moments, 1: Hessian 0-303, 2: Hessian 304-594); the group index runs
+// fastest in the grid, so the three CTAs of a tile run together and two of
+// them read sigma from L2.  Warp 4 issues the tensor loads (three stages,
+// mbarrier transaction counts) and the MMAs (accumulators in TMEM); warps
+// 0-3 read their 32 TMEM lanes, stage the rows in shared memory and write
+// each cell's row of the moments array with coalesced stores.  Every wait is
+// bounded.
 //
 // Accumulation: the tensor cores add the products of one MMA into the FP32
 // accumulator with truncation, so a long chain of MMAs into one accumulator
@@ -43,51 +49,48 @@ using namespace mem;
 namespace {
 
 constexpr int NGRP = 3;
-constexpr int ROWS0 = 96, ROWS12 = 304;      // N rows per block of group 0 / groups 1, 2
-constexpr int HSPLIT = 304;                 // Hessian entries of group 1
-constexpr int KCH = 32;                     // nodes per K-chunk
-constexpr uint32_t A_BYTES = 128 * KCH * 4;  // 16 KB
-constexpr uint32_t SBO = KCH / 4 * 128;       // 1024: bytes between 8-row groups
-constexpr uint32_t STAGE = 2 * A_BYTES + ROWS12 * KCH * 4;
+constexpr int TROWS = 704;                    // table rows
+constexpr int HSPLIT = 304;                   // Hessian entries of group 1
+constexpr int KCH = 32;                       // nodes per K-chunk (128 bytes of FP32)
+constexpr int STAGES = 3;
+constexpr uint32_t A_BYTES = 128 * KCH * 4;   // 16 KB: one box of sigma
+constexpr uint32_t B_MAX = 304 * KCH * 4;     // 38 KB: the table rows of a Hessian group
+constexpr uint32_t STAGE = 2 * A_BYTES + B_MAX;  // 70 KB, a multiple of 1024
+constexpr uint32_t SMEM = STAGES * STAGE + 1024;  // + the 1024-byte alignment of the swizzled tiles
+constexpr int EP = 308;                       // row pitch (floats) of the staged epilogue
 constexpr uint32_t kMaxPolls = 1u << 22;
+static_assert(STAGE % 1024 == 0, "stages must keep the 1024-byte alignment of the swizzle atoms");
+static_assert(128 * EP * 4 <= STAGES * STAGE, "the epilogue staging reuses the stage buffers");
 
-__host__ __device__ constexpr int grp_rows(int g) { return g == 0 ? ROWS0 : ROWS12; }
-// first float of group g's blocks in the table (KC chunks per group)
-__host__ __device__ constexpr size_t grp_base(int g, int KC) {
-    return g == 0 ? 0 : (size_t)KC * KCH * (ROWS0 + (size_t)(g - 1) * ROWS12);
-}
-
-struct ContractArgs {
-    const float *a_hi, *a_lo;  // [tiles][KC][128 x 32] tiled sigma
-    const float *tab;          // [2][KC][352 x 32] tiled tables
-    float *mom;                // [n][630]
-    int n, KC;
-    int *err;
-};
-
-// Warps 0-3 own the 128 accumulator lanes (cells); warp 4 issues the bulk
-// copies and the MMAs.  Group 0 (the moments): each K-chunk's three split
+// Warps 0-3 own the 128 accumulator lanes (cells); warp 4 issues the tensor
+// loads and the MMAs.  Group 0 (the moments): each K-chunk's three split
 // products go into a fresh accumulator buffer (NB buffers in rotation), which
 // warps 0-3 add into FP32 registers as soon as the chunk completes, so no
 // accumulator chain is longer than one chunk.  Groups 1, 2 (the Hessian):
 // one accumulator chain over all chunks, read once at the end.
 constexpr int NB = 8;  // moment accumulator buffers (48 columns each)
 
-__global__ void __launch_bounds__(160, 1) k_tc_contract(ContractArgs A) {
-    extern __shared__ __align__(1024) uint8_t smem[];
+__global__ void __launch_bounds__(160, 1)
+    k_tc_contract(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
+                  const __grid_constant__ CUtensorMap tm_t48, const __grid_constant__ CUtensorMap tm_t256,
+                  float *__restrict__ mom, int n, int KC, int *err) {
+    extern __shared__ uint8_t smem_raw[];
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_full[2], s_empty[2], s_done, s_accf[NB], s_acce[NB];
+    __shared__ int s_fail;
+    __shared__ __align__(8) uint64_t s_full[STAGES], s_empty[STAGES], s_done, s_accf[NB], s_acce[NB];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tile = blockIdx.x, grp = blockIdx.y;
+    const int grp = blockIdx.x, tile = blockIdx.y;
     if (warp == 0) {
         tc::tmem_alloc(&s_tmem, 512);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        tc::mbar_init(&s_full[0], 1);
-        tc::mbar_init(&s_full[1], 1);
-        tc::mbar_init(&s_empty[0], 1);
-        tc::mbar_init(&s_empty[1], 1);
+        s_fail = 0;
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(&s_full[s], 1);
+            tc::mbar_init(&s_empty[s], 1);
+        }
         tc::mbar_init(&s_done, 1);
         for (int b = 0; b < NB; ++b) {
             tc::mbar_init(&s_accf[b], 1);  // the MMAs of a chunk are done
@@ -98,133 +101,153 @@ __global__ void __launch_bounds__(160, 1) k_tc_contract(ContractArgs A) {
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = s_tmem;
-    const int KC = A.KC;
+    float sum[40];  // group 0: the moment sums of this thread's cell
+#pragma unroll
+    for (int c = 0; c < 40; ++c) sum[c] = 0.f;
     if (warp == 4) {
         if (lane == 0) {
             bool failed = false;
-            int loaded = 0;  // chunks whose copies were issued
-            const uint32_t b_bytes = (uint32_t)grp_rows(grp) * KCH * 4;
+            int loaded = 0, waited = 0;  // chunks whose loads were issued / have landed
+            const int y = tile * 128;
             auto load = [&](int kc) {
-                const int s = kc & 1;
-                uint8_t *st = smem + s * STAGE;
-                const size_t ablk = ((size_t)tile * KC + kc) * (A_BYTES / 4);
-                const size_t bblk = grp_base(grp, KC) + (size_t)kc * (b_bytes / 4);
-                const uint32_t bytes = (grp == 0 ? 2 * A_BYTES : A_BYTES) + b_bytes;
-                tc::mbar_expect_tx(&s_full[s], bytes);
-                tc::bulk_g2s(st, A.a_hi + ablk, A_BYTES, &s_full[s]);
-                if (grp == 0) tc::bulk_g2s(st + A_BYTES, A.a_lo + ablk, A_BYTES, &s_full[s]);
-                tc::bulk_g2s(st + 2 * A_BYTES, A.tab + bblk, b_bytes, &s_full[s]);
+                uint8_t *st = smem + (kc % STAGES) * STAGE;
+                uint8_t *b = st + 2 * A_BYTES;
+                uint64_t *bar = &s_full[kc % STAGES];
+                const int x = kc * KCH;  // 128-byte multiple: the TMA alignment rule holds
+                if (grp == 0) {
+                    tc::mbar_expect_tx(bar, 2 * A_BYTES + 96 * 128);
+                    tc::tma_load_2d(st, &tm_hi, x, y, bar);
+                    tc::tma_load_2d(st + A_BYTES, &tm_lo, x, y, bar);
+                    tc::tma_load_2d(b, &tm_t48, x, 0, bar);
+                    tc::tma_load_2d(b + 48 * 128, &tm_t48, x, 48, bar);
+                } else {
+                    const int t0 = grp == 1 ? 96 : 96 + HSPLIT;
+                    tc::mbar_expect_tx(bar, A_BYTES + 304 * 128);
+                    tc::tma_load_2d(st, &tm_hi, x, y, bar);
+                    tc::tma_load_2d(b, &tm_t256, x, t0, bar);
+                    tc::tma_load_2d(b + 256 * 128, &tm_t48, x, t0 + 256, bar);
+                }
                 loaded = kc + 1;
             };
-            load(0);
+            for (int j = 0; j < STAGES - 1 && j < KC; ++j) load(j);
             const uint32_t id48 = tc::idesc(128, 48, 2), id256 = tc::idesc(128, 256, 2);
-            int kc = 0;
-            for (; kc < KC; ++kc) {
-                if (kc + 1 < KC) {
-                    // stage (kc+1)&1 was last read by the MMAs of chunk kc-1
-                    if (kc >= 1 && !tc::mbar_wait(&s_empty[(kc + 1) & 1], ((kc - 1) >> 1) & 1, kMaxPolls)) {
-                        failed = true;
-                        break;
-                    }
-                    load(kc + 1);
-                }
-                if (!tc::mbar_wait(&s_full[kc & 1], (kc >> 1) & 1, kMaxPolls)) {
+            for (int kc = 0; kc < KC; ++kc) {
+                const int s = kc % STAGES, bf = kc % NB;
+                if (!tc::mbar_wait(&s_full[s], (kc / STAGES) & 1, kMaxPolls)) {
                     failed = true;
                     break;
                 }
-                const int bf = kc % NB;
+                waited = kc + 1;
                 if (grp == 0 && kc >= NB && !tc::mbar_wait(&s_acce[bf], ((kc / NB) - 1) & 1, kMaxPolls)) {
                     failed = true;
                     break;
                 }
                 tc::fence_after_sync();
-                const uint32_t base = tc::smem_u32(smem + (kc & 1) * STAGE);
+                const uint32_t base = tc::smem_u32(smem + s * STAGE);
                 const uint32_t ahi = base, alo = base + A_BYTES, b = base + 2 * A_BYTES;
                 const uint32_t dacc = tmem + (uint32_t)(48 * bf);
 #pragma unroll
-                for (int s = 0; s < KCH / 8; ++s) {
-                    const uint64_t dh = tc::sdesc(ahi + 256 * s, 128, SBO);
+                for (int k = 0; k < KCH / 8; ++k) {  // one MMA consumes 8 nodes (32 bytes)
+                    const uint64_t dh = tc::sdesc_sw128(ahi + 32 * k, 1024);
                     if (grp == 0) {
-                        const uint64_t dl = tc::sdesc(alo + 256 * s, 128, SBO);
-                        const uint64_t bmh = tc::sdesc(b + 256 * s, 128, SBO);
-                        const uint64_t bml = tc::sdesc(b + 6 * SBO + 256 * s, 128, SBO);
-                        tc::mma_tf32(dacc, dl, bmh, id48, s != 0);  // lo . hi (a fresh chunk sum)
+                        const uint64_t dl = tc::sdesc_sw128(alo + 32 * k, 1024);
+                        const uint64_t bmh = tc::sdesc_sw128(b + 32 * k, 1024);
+                        const uint64_t bml = tc::sdesc_sw128(b + 48 * 128 + 32 * k, 1024);
+                        tc::mma_tf32(dacc, dl, bmh, id48, k != 0);  // lo . hi (a fresh chunk sum)
                         tc::mma_tf32(dacc, dh, bml, id48, 1);       // hi . lo
                         tc::mma_tf32(dacc, dh, bmh, id48, 1);       // hi . hi
                     } else {
-                        const uint32_t acc = (kc | s) != 0;
-                        const uint64_t b0 = tc::sdesc(b + 256 * s, 128, SBO);
-                        const uint64_t b1 = tc::sdesc(b + 32 * SBO + 256 * s, 128, SBO);
-                        tc::mma_tf32(tmem, dh, b0, id256, acc);
-                        tc::mma_tf32(tmem + 256, dh, b1, id48, acc);
+                        const uint32_t acc = (kc | k) != 0;
+                        tc::mma_tf32(tmem, dh, tc::sdesc_sw128(b + 32 * k, 1024), id256, acc);
+                        tc::mma_tf32(tmem + 256, dh, tc::sdesc_sw128(b + 256 * 128 + 32 * k, 1024), id48, acc);
                     }
                 }
-                tc::mma_commit(&s_empty[kc & 1]);
+                tc::mma_commit(&s_empty[s]);
                 if (grp == 0) tc::mma_commit(&s_accf[bf]);
+                // refill the stage of chunk kc - 1 once its MMAs are done (the
+                // MMAs of chunk kc are already queued behind them)
+                const int nxt = kc + STAGES - 1;
+                if (nxt < KC) {
+                    if (kc >= 1 && !tc::mbar_wait(&s_empty[(kc - 1) % STAGES], ((kc - 1) / STAGES) & 1, kMaxPolls)) {
+                        failed = true;
+                        break;
+                    }
+                    load(nxt);
+                }
             }
             if (failed) {
-                atomicExch(A.err, 1);
+                atomicExch(err, 1);
+                s_fail = 1;
                 // copies still in flight land in this CTA's shared memory:
                 // wait for them (bounded) before the CTA can exit
-                for (int j = kc; j < loaded; ++j) tc::mbar_wait(&s_full[j & 1], (j >> 1) & 1, kMaxPolls);
+                for (int j = waited; j < loaded; ++j) tc::mbar_wait(&s_full[j % STAGES], (j / STAGES) & 1, kMaxPolls);
             }
             tc::mma_commit(&s_done);  // every MMA issued above
         }
         __syncwarp();
-    } else {
-        const int row = 32 * warp + lane;
-        const int cell = tile * 128 + row;
-        const bool live = cell < A.n;
+    } else if (grp == 0) {
         const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
-        float *m = A.mom + (size_t)cell * MEM_NCOL_SOLVE;
         bool ok = true;
-        if (grp == 0) {
-            float sum[40];
+        for (int kc = 0; kc < KC; ++kc) {
+            const int bf = kc % NB;
+            ok = tc::mbar_wait(&s_accf[bf], (kc / NB) & 1, kMaxPolls);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            tc::fence_after_sync();
 #pragma unroll
-            for (int c = 0; c < 40; ++c) sum[c] = 0.f;
-            for (int kc = 0; kc < KC; ++kc) {
-                const int bf = kc % NB;
-                ok = tc::mbar_wait(&s_accf[bf], (kc / NB) & 1, kMaxPolls);
-                ok = __all_sync(0xffffffffu, ok);
-                if (!ok) break;
-                tc::fence_after_sync();
+            for (int c = 0; c < 40; c += 8) {
+                float v[8];
+                tc::tmem_ld8(tl + (uint32_t)(48 * bf + c), v);
 #pragma unroll
-                for (int c = 0; c < 40; c += 8) {
-                    float v[8];
-                    tc::tmem_ld8(tl + (uint32_t)(48 * bf + c), v);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) sum[c + j] += v[j];
-                }
-                tc::fence_before_sync();
-                __syncwarp();
-                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&s_acce[bf]))
-                                            : "memory");
+                for (int j = 0; j < 8; ++j) sum[c + j] += v[j];
             }
-            if (!ok) atomicExch(A.err, 1);
-            if (ok && live) {
-#pragma unroll
-                for (int c = 0; c < NP; ++c) m[c] = sum[c];
-            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&s_acce[bf]))
+                                        : "memory");
         }
-        // every MMA of the CTA is complete before its accumulators are read
-        // (groups 1, 2) or released
+        if (!ok) {
+            atomicExch(err, 1);
+            s_fail = 1;
+        }
+    }
+    __syncthreads();  // s_fail is final
+    if (warp < 4) {
+        // every MMA of the CTA is complete (and every tensor load has landed)
+        // before the accumulators are read or the stage buffers reused
         bool done = tc::mbar_wait(&s_done, 0, kMaxPolls);
         if (!done) {
-            atomicExch(A.err, 1);
+            atomicExch(err, 1);
             done = tc::mbar_wait(&s_done, 0, kMaxPolls);
         }
-        done = __all_sync(0xffffffffu, done);
+        done = __all_sync(0xffffffffu, done) && !s_fail;
         tc::fence_after_sync();
-        if (grp != 0 && done) {
-            const int off = grp == 1 ? 0 : HSPLIT, cnt = grp == 1 ? HSPLIT : NP1 * NP / 2 - HSPLIT;
-            for (int c = 0; c < 304; c += 8) {
-                float v[8];
-                tc::tmem_ld8(tl + (uint32_t)c, v);
-                if (live) {
+        if (done) {
+            // stage this warp's 32 rows in shared memory, then write each row
+            // with the whole warp (consecutive addresses)
+            float *ep = reinterpret_cast<float *>(smem) + (size_t)32 * warp * EP;
+            float *my = ep + (size_t)lane * EP;
+            const int col0 = grp == 0 ? 0 : grp == 1 ? NP : NP + HSPLIT;
+            const int cnt = grp == 0 ? NP : grp == 1 ? HSPLIT : NP1 * NP / 2 - HSPLIT;
+            if (grp == 0) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        if (c + j < cnt) m[NP + off + c + j] = v[j];
+                for (int c = 0; c < 36; c += 4)
+                    *reinterpret_cast<float4 *>(my + c) = make_float4(sum[c], sum[c + 1], sum[c + 2], sum[c + 3]);
+            } else {
+                const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
+                for (int c = 0; c < 304; c += 8) {
+                    float v[8];
+                    tc::tmem_ld8(tl + (uint32_t)c, v);
+                    *reinterpret_cast<float4 *>(my + c) = make_float4(v[0], v[1], v[2], v[3]);
+                    *reinterpret_cast<float4 *>(my + c + 4) = make_float4(v[4], v[5], v[6], v[7]);
                 }
+            }
+            __syncwarp();
+            const int cell0 = tile * 128 + 32 * warp;
+            for (int r = 0; r < 32 && cell0 + r < n; ++r) {
+                float *m = mom + (size_t)(cell0 + r) * MEM_NCOL_SOLVE + col0;
+                const float *e = ep + (size_t)r * EP;
+                for (int j = lane; j < cnt; j += 32) m[j] = e[j];
             }
         }
     }
@@ -275,58 +298,66 @@ int encode_tmap_2d_f32(CUtensorMap *out, const void *base, uint64_t cols, uint64
 
 bool tc_available(const mem_ctx *ctx) { return ctx->d_tc_tab != nullptr; }
 
-// Tiled tables of the contraction for a Gauss-Hermite context (Q a multiple
-// of 32): phi values and packed products phi_i phi_j, i >= j >= 1, at the
-// nodes in the order of the dense tables (Section 3.1 statistics).
+// Tables of the contraction for a Gauss-Hermite context (Q a multiple of
+// 32), row-major [704][Q]: phi values (TF32 hi and lo) and the products
+// phi_i phi_j, i >= j >= 1, packed in the order of the dense tables, at the
+// nodes (Section 3.1 statistics), with their tensor maps.  No tensor-core
+// path (and MEM_OK) for other orders or when the driver offers no tensor-map
+// encoder.
 int build_tc_tables(mem_ctx *ctx, const std::vector<double> &phi /*[Q][35]*/) {
     const int Q = ctx->Q;
-    if (Q % KCH) return MEM_OK;  // no tensor-core path for this order
-    const int KC = Q / KCH;
-    std::vector<float> tab(grp_base(NGRP, KC), 0.f);
-    auto put = [&](int grp, int row, int q, float v) {
-        const int kc = q / KCH, k = q % KCH;
-        const size_t blk = grp_base(grp, KC) + (size_t)kc * grp_rows(grp) * KCH;
-        const size_t off = (size_t)(row >> 3) * (SBO / 4) + (size_t)(k >> 2) * 32 + (row & 7) * 4 + (k & 3);
-        tab[blk + off] = v;
-    };
+    if (Q % KCH) return MEM_OK;
+    std::vector<float> tab((size_t)TROWS * Q, 0.f);
+    auto put = [&](int row, int q, float v) { tab[(size_t)row * Q + q] = v; };
     for (int q = 0; q < Q; ++q) {
         const double *ph = &phi[(size_t)q * NP];
         for (int k = 0; k < NP; ++k) {
             const float f = (float)ph[k], hi = tf32_host(f), lo = tf32_host(f - hi);
-            put(0, k, q, hi);
-            put(0, 48 + k, q, lo);
+            put(k, q, hi);
+            put(48 + k, q, lo);
         }
         for (int i = 1; i < NP; ++i)
             for (int j = 1; j <= i; ++j) {
                 const int p = (i - 1) * i / 2 + (j - 1);
-                const float v = tf32_host((float)(ph[i] * ph[j]));
-                if (p < HSPLIT) put(1, p, q, v);
-                else put(2, p - HSPLIT, q, v);
+                put(96 + p, q, tf32_host((float)(ph[i] * ph[j])));
             }
     }
-    if (cudaMalloc((void **)&ctx->d_tc_tab, sizeof(float) * tab.size()) != cudaSuccess) {
+    float *d = nullptr;
+    if (cudaMalloc((void **)&d, sizeof(float) * tab.size()) != cudaSuccess) {
         cudaGetLastError();
-        ctx->d_tc_tab = nullptr;
         return MEM_ENOMEM;
     }
-    if (cudaMemcpy(ctx->d_tc_tab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpy(d, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
         return MEM_ECUDA;
+    }
+    if (encode_tmap_2d_f32(&ctx->tm_tab48, d, Q, TROWS, KCH, 48) ||
+        encode_tmap_2d_f32(&ctx->tm_tab256, d, Q, TROWS, KCH, 256)) {
+        cudaFree(d);
+        return MEM_OK;  // no tensor maps: the mixed back-end is unavailable (MEM_EINVAL)
+    }
+    ctx->d_tc_tab = d;
     return MEM_OK;
 }
 
 size_t tc_sigma_floats(int Q, int64_t cells) { return (size_t)((cells + 127) / 128) * 128 * Q; }
 
-int tc_contract(mem_ctx *ctx, const float *a_hi, const float *a_lo, float *mom, int n, int *err, cudaStream_t st) {
-    if (!ctx->d_tc_tab) return MEM_EINVAL;
+// sigma hi / lo: row-major [rows][Q] (rows a multiple of 128); moment rows
+// of the first n of them go to mom.
+int tc_contract(mem_ctx *ctx, const float *a_hi, const float *a_lo, int64_t rows, float *mom, int n, int *err,
+                cudaStream_t st) {
+    if (!ctx->d_tc_tab || rows % 128 || n > rows) return MEM_EINVAL;
+    if (n <= 0) return MEM_OK;
     static bool configured = false;
-    const int smem = 2 * STAGE;
     if (!configured) {
-        MEM_CUDA_TRY(cudaFuncSetAttribute(k_tc_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        MEM_CUDA_TRY(cudaFuncSetAttribute(k_tc_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM));
         configured = true;
     }
-    ContractArgs a{a_hi, a_lo, ctx->d_tc_tab, mom, n, ctx->Q / KCH, err};
-    dim3 grid((n + 127) / 128, NGRP);
-    k_tc_contract<<<grid, 160, smem, st>>>(a);
+    CUtensorMap thi, tlo;
+    if (encode_tmap_2d_f32(&thi, a_hi, ctx->Q, rows, KCH, 128) || encode_tmap_2d_f32(&tlo, a_lo, ctx->Q, rows, KCH, 128))
+        return MEM_ECUDA;
+    dim3 grid(NGRP, (n + 127) / 128);
+    k_tc_contract<<<grid, 160, SMEM, st>>>(thi, tlo, ctx->tm_tab48, ctx->tm_tab256, mom, n, ctx->Q / KCH, err);
     MEM_CUDA_TRY(cudaGetLastError());
     return MEM_OK;
 }

@@ -58,8 +58,8 @@ __device__ __forceinline__ float block_reduce_sum(float v, float *red) {
 }
 
 struct PlainState {
-    float *sigma;  // [CHUNK][Q] (mixed back-end: hi part, tiled for the tensor cores)
-    float *sig_lo; // mixed back-end: lo part, tiled
+    float *sigma;  // [CHUNK][Q] (mixed back-end: TF32 hi part, rows padded to whole tiles of 128)
+    float *sig_lo; // mixed back-end: TF32 lo part, same layout
     float *mom;    // [CHUNK][630]
     float *db;     // [CHUNK][35]
     float *G;      // [CHUNK][35]
@@ -71,13 +71,6 @@ struct PlainState {
     int *cnt;      // [2]
     int *err;      // [1] mixed back-end: a tensor-core wait timed out
 };
-
-// Offset of sigma(slot, q) in the tensor cores' tiled layout: tiles of 128
-// cells, K-chunks of 32 nodes, core matrices of 8 cells x 4 nodes.
-__device__ __forceinline__ size_t tiled_off(int slot, int q, int KC) {
-    const int tile = slot >> 7, r = slot & 127, kc = q >> 5, k = q & 31;
-    return ((size_t)tile * KC + kc) * 4096 + (size_t)((r >> 3) * 256 + (k >> 2) * 32 + (r & 7) * 4 + (k & 3));
-}
 
 __global__ void k_init(const float *__restrict__ M, float *__restrict__ beta, int n, PlainState S,
                        int32_t *status, int32_t *iters, const unsigned char *active) {
@@ -105,8 +98,8 @@ __global__ void k_init(const float *__restrict__ M, float *__restrict__ beta, in
 
 // One block per active cell.  Nodes q = tid + 256 j.  The exponent of the
 // trial point beta + alpha dbeta is e_beta + alpha e_dbeta (both computed once).
-// TILED: sigma goes to the tensor cores' tiled layout as a TF32 hi part and
-// a TF32 lo part (sigma = hi + lo to about 2^-22).
+// TILED: sigma goes to the tensor cores as a TF32 hi part and a TF32 lo part
+// (sigma = hi + lo to about 2^-22), each row-major with rows padded to tiles.
 template <bool TILED>
 __global__ void __launch_bounds__(BLK) k_linesearch(const int *__restrict__ act, const float *__restrict__ M,
                                                     float *__restrict__ beta, PlainState S,
@@ -179,16 +172,15 @@ __global__ void __launch_bounds__(BLK) k_linesearch(const int *__restrict__ act,
     }
     const float invZ = 1.f / Z;
     if (TILED) {
-        const int KC = Q >> 5;
+        float *hi_row = S.sigma + (size_t)slot * Q, *lo_row = S.sig_lo + (size_t)slot * Q;
 #pragma unroll
         for (int j = 0; j < MAXJ; ++j) {
             const int q = tid + j * BLK;
             if (j < nj && q < Q) {
                 const float v = __expf(eb[j] + alpha * ed[j] - mx) * invZ;
                 const float hi = tc_round(v);
-                const size_t off = tiled_off(slot, q, KC);
-                S.sigma[off] = hi;
-                S.sig_lo[off] = tc_round(v - hi);
+                hi_row[q] = hi;
+                lo_row[q] = tc_round(v - hi);
             }
         }
     } else {
@@ -628,7 +620,7 @@ void sgemm(const float *A, const float *Bm, float *C, int M, int N, int K, cudaS
 namespace mem_host {
 
 static size_t plain_need(int Q, size_t CH) {
-    // sigma hi + lo (mixed: tiled, whole tiles of 128 cells), moments,
+    // sigma hi + lo (mixed: whole tiles of 128 cells), moments,
     // per-cell vectors and scalars, the FP64 residuals of failed cells
     const size_t sig = tc_sigma_floats(Q, (int64_t)CH);
     return sizeof(float) * (2 * sig + CH * ((size_t)MEM_NCOL_SOLVE + 2 * NP + 2)) + sizeof(int) * (CH * 4 + 4) +
@@ -690,7 +682,7 @@ static int solve_dense(mem_ctx *ctx, const float *M, float *beta, int32_t *statu
         for (int pass = 0; pass <= o.maxI + 1 && nact > 0; ++pass) {
             if (mixed) {
                 k_linesearch<true><<<nact, BLK, 0, st>>>(cur, Mc, bc, S, ctx->d_phiT, ctx->d_logw, Q, o);
-                rc = tc_contract(ctx, S.sigma, S.sig_lo, S.mom, nact, S.err, st);
+                rc = tc_contract(ctx, S.sigma, S.sig_lo, (int64_t)(sig / Q), S.mom, nact, S.err, st);
                 if (rc) return rc;
             } else {
                 k_linesearch<false><<<nact, BLK, 0, st>>>(cur, Mc, bc, S, ctx->d_phiT, ctx->d_logw, Q, o);

@@ -631,19 +631,27 @@ def run_convergence_study(mem, torch, np, t_end=4.0, Ns=(32, 64, 128, 256, 512, 
     with FLIC and with local Lax-Friedrichs on N cells, all N in one packed
     batch, each stopped at simulated time t_end.  L1 distance of sigma_xx
     from the finest mesh that stayed finite, averaged onto N cells.  FLIC is
-    run again with the paper's own nine-statistic system (flic_nine) and
-    with the two other readings of its limiter (one phi per interface: the
-    smallest of the nine statistics', or the density's)."""
+    run again with the paper's own nine-statistic system (flic_nine), with
+    the two other readings of its limiter (one phi per interface: the
+    smallest of the nine statistics', or the density's), and on smaller
+    velocity boxes (the mitigation the paper names for the ill-conditioning
+    of over-refined meshes: (n_a, n_b, n_r) = (8, 5, 5) and (6, 4, 4))."""
     kw = dict(mach=4.0, xl=-16.3, xr=16.3, ic=1, thickness=5.44, tol=1e-9, na=10.0, nb=6.0, nr=6.0, t_end=t_end)
     vctx = mem.Context.velocity(mem.shock_domain(**kw), nbx=6, nbr=4, ng=8, K=12)
     L = kw["xr"] - kw["xl"]
     out = {"t_end": t_end}
-    for name, scheme, stats, fl in (("flic", mem.SCHEME_FLIC, 35, 0), ("lf", mem.SCHEME_LF, 35, 0),
-                                    ("flic_nine", mem.SCHEME_FLIC, 9, 0),
-                                    ("flic_smallest_limiter", mem.SCHEME_FLIC, 9, 1),
-                                    ("flic_density_limiter", mem.SCHEME_FLIC, 9, 2)):
+    for name, scheme, stats, fl, box in (("flic", mem.SCHEME_FLIC, 35, 0, None), ("lf", mem.SCHEME_LF, 35, 0, None),
+                                         ("flic_nine", mem.SCHEME_FLIC, 9, 0, None),
+                                         ("flic_smallest_limiter", mem.SCHEME_FLIC, 9, 1, None),
+                                         ("flic_density_limiter", mem.SCHEME_FLIC, 9, 2, None),
+                                         ("flic_box_8_5_5", mem.SCHEME_FLIC, 35, 0, (8.0, 5.0, 5.0)),
+                                         ("flic_nine_box_8_5_5", mem.SCHEME_FLIC, 9, 0, (8.0, 5.0, 5.0)),
+                                         ("flic_nine_box_6_4_4", mem.SCHEME_FLIC, 9, 0, (6.0, 4.0, 4.0))):
+        pkw = dict(kw)
+        if box is not None:
+            pkw.update(na=box[0], nb=box[1], nr=box[2])
         sh = mem.Shock(vctx, problems=[dict(ncells=N) for N in Ns], graph=1, scheme=scheme, stats=stats,
-                       flic_limiter=fl, **kw)
+                       flic_limiter=fl, **pkw)
         t0 = time.time()
         # the finest mesh needs about t_end / (cfl dx / 10) steps
         max_steps = int(3 * t_end * 10.0 * Ns[-1] / (0.5 * L)) + 1000
@@ -658,6 +666,8 @@ def run_convergence_study(mem, torch, np, t_end=4.0, Ns=(32, 64, 128, 256, 512, 
         fin = [bool(np.isfinite(p["sxx"]).all()) for p in P]
         r = max(i for i in range(len(Ns)) if fin[i]) if any(fin) else None
         row = {"cells": list(Ns), "finite": fin, "steps": steps, "wall_s": round(time.time() - t0, 1)}
+        if box is not None:
+            row["box"] = {"n_a_b_r": list(box), "domain": [round(x, 3) for x in mem.shock_domain(**pkw)]}
         if r is not None and r > 0:
             ref = P[r]["sxx"].astype(np.float64)
             err = []

@@ -1048,6 +1048,48 @@ void or_flux_axi(int order, const double *alpha, const double *g, double n, doub
     *speed = fmax(fabs(g[0] + g[3] * lo), fabs(g[0] + g[3] * hi));
 }
 
+/* Which system the shock step solves (Algorithm 2 on either set of
+ * statistics): 35 (default) the Hermite products; 9 the paper's nine
+ * statistics of axisymmetric flow (Appendix B), through or_solve_axi and
+ * or_flux_axi.  The state stays the 35 moments and parameters: for an
+ * axisymmetric flow they lie in the span of the orthonormal v_j, so
+ * M9_j = v_j . M, alpha_j = v_j . beta, beta = sum_j alpha_j v_j and
+ * F = sum_j F9_j v_j; the characteristic speed is the nine-statistic one. */
+static int g_shock_stats = 35;
+void or_set_shock_stats(int stats) { g_shock_stats = stats == 9 ? 9 : 35; }
+
+static int shock_solve(int order, const double *g, const double *M, double *beta, const double *optv, int *it) {
+    if (g_shock_stats != 9) return or_solve(order, g, M, beta, optv, it, NULL, NULL);
+    double v[9][NP], M9[9], a[9];
+    flic_basis(v);
+    for (int j = 0; j < 9; ++j) {
+        M9[j] = 0.0;
+        a[j] = 0.0;
+        for (int i = 0; i < NP; ++i) { M9[j] += v[j][i] * M[i]; a[j] += v[j][i] * beta[i]; }
+    }
+    const int st = or_solve_axi(order, g, M9, a, optv, it, NULL);
+    axi_beta(v, a, beta);
+    return st;
+}
+
+static void shock_flux(int order, const double *beta, const double *g, double n, double *F, double *speed) {
+    if (g_shock_stats != 9) {
+        or_flux(order, beta, g, n, F, speed, NULL, NULL);
+        return;
+    }
+    double v[9][NP], a[9], F9[9];
+    flic_basis(v);
+    for (int j = 0; j < 9; ++j) {
+        a[j] = 0.0;
+        for (int i = 0; i < NP; ++i) a[j] += v[j][i] * beta[i];
+    }
+    or_flux_axi(order, a, g, n, F9, speed);
+    for (int i = 0; i < NP; ++i) {
+        F[i] = 0.0;
+        for (int j = 0; j < 9; ++j) F[i] += F9[j] * v[j][i];
+    }
+}
+
 /* Which ratio sets the FLIC limiter.  Eq. "The FLIC" writes the limiter
  * phi_{n-1/2} without a statistic index but its ratio r with the moments
  * M_i.  0 (default): one phi_j per statistic of the nine; 1: one phi per
@@ -1086,9 +1128,9 @@ static void interface_flux(int order, int scheme, int c, int side, const double 
     memset(bI, 0, sizeof(bI));
     bI[0] = MH[0];
     int it = 0;
-    const int sI = or_solve(order, gI, MH, bI, optv, &it, NULL, NULL);
+    const int sI = shock_solve(order, gI, MH, bI, optv, &it);
     *ist |= sI;
-    or_flux(order, bI, gI, MH[0], FI, NULL, NULL, NULL);
+    shock_flux(order, bI, gI, MH[0], FI, NULL);
     int ok = (sI & (ST_NONFINITE | ST_LAMBDA_CAP | ST_BADINPUT | ST_MAXITER)) == 0;
     for (int i = 0; i < NP; ++i) ok = ok && isfinite(FI[i]);
     if (!ok) {
@@ -1175,7 +1217,7 @@ void or_shock_step(int order, int N, double dx, double cfl, double Pr, double re
     for (int c = 1; c <= N; ++c) {
         collide(&M[NP * c], &g[6 * c], 0.5 * dt, Pr, relax_coef);
         int it = 0;
-        int st = or_solve(order, &g[6 * c], &M[NP * c], &beta[NP * c], optv, &it, NULL, NULL);
+        int st = shock_solve(order, &g[6 * c], &M[NP * c], &beta[NP * c], optv, &it);
         if (status) status[c] = st;
         if (iters) iters[c] = it;
         if (cond) cond[c] = or_cond_estimate(order, &g[6 * c], &beta[NP * c]);
@@ -1185,7 +1227,7 @@ void or_shock_step(int order, int N, double dx, double cfl, double Pr, double re
         double bb[NP];
         memcpy(bb, &beta[NP * c], sizeof(bb));
         if (c == 0 || c == N + 1) for (int i = 0; i < NP; ++i) bb[i] = 0.0;
-        or_flux(order, bb, &g[6 * c], M[NP * c], &F[NP * c], &speed[c], NULL, NULL);
+        shock_flux(order, bb, &g[6 * c], M[NP * c], &F[NP * c], &speed[c]);
     }
     #pragma omp parallel for schedule(dynamic, 1)
     for (int c = 1; c <= N; ++c) {

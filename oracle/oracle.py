@@ -205,6 +205,13 @@ def set_flic_limiter(mode):
     lib().or_set_flic_limiter(int(mode))
 
 
+def set_shock_stats(stats):
+    """Which system or_shock_step solves: 35 the Hermite products (default),
+    9 the paper's nine statistics of axisymmetric flow through or_solve_axi /
+    or_flux_axi (the state stays the 35 moments, in the span of the nine)."""
+    lib().or_set_shock_stats(int(stats))
+
+
 def flic_basis():
     """The nine statistics of the paper's 1D system (Eq. "Sufficient 35") as
     unit vectors over the 3D Hermite products [9, 35] (the FLIC limiter's
@@ -355,8 +362,13 @@ class Shock:
 
     def __init__(self, mach, ncells, xl, xr, order=8, cfl=0.5, Pr=2.0 / 3.0, gamma=5.0 / 3.0,
                  kn=1.0, tol=1e-8, maxI=500, nthreads=0, ic="step", thickness=15.7, scheme="lf",
-                 final_step=False, flic_limiter=0):
+                 final_step=False, flic_limiter=0, stats=35):
         self.order, self.N, self.cfl, self.Pr = order, ncells, cfl, Pr
+        # 35: the Hermite products; 9: the paper's nine statistics of
+        # axisymmetric flow (Appendix B), see set_shock_stats
+        if stats not in (9, 35):
+            raise ValueError("stats must be 9 or 35")
+        self.stats = stats
         # interface flux: Eq. "The lax F" (lf), "The lax W" (lw), "The FLIC" (flic)
         self.scheme = {"lf": 0, "lw": 1, "flic": 2}[scheme]
         self.flic_limiter = flic_limiter  # see set_flic_limiter
@@ -396,11 +408,19 @@ class Shock:
                 self.M[c] = transform_M(gH, g_up, Mb)
                 self.g[c] = gH
                 self.beta[c, 0] = self.M[c, 0]
-        if ic != "step":
-            b, st, it = solve_batch(order, self.M[1:-1], None, tol, maxI, nthreads, final_step=final_step,
-                                    g=self.g[1:-1])
-            self.beta[1:-1] = b
-        _, self.speed = flux_batch(order, self.M, self.beta, self.g, nthreads)
+        if stats == 9:
+            v = flic_basis()
+            if ic != "step":
+                for c in range(1, NT - 1):
+                    a, _, _, _ = solve_axi(order, v @ self.M[c], v @ self.beta[c], tol, maxI, final_step, self.g[c])
+                    self.beta[c] = a @ v
+            self.speed = np.array([flux_axi(order, v @ self.beta[c], self.g[c], self.M[c, 0])[1] for c in range(NT)])
+        else:
+            if ic != "step":
+                b, st, it = solve_batch(order, self.M[1:-1], None, tol, maxI, nthreads, final_step=final_step,
+                                        g=self.g[1:-1])
+                self.beta[1:-1] = b
+            _, self.speed = flux_batch(order, self.M, self.beta, self.g, nthreads)
         self.status = np.zeros(NT, dtype=np.int32)
         self.iters = np.zeros(NT, dtype=np.int32)
         # pivot-ratio condition estimate of each cell's last solve (Fig. 7), on request
@@ -414,6 +434,7 @@ class Shock:
     def step(self):
         out = np.zeros(3)
         set_flic_limiter(self.flic_limiter)
+        set_shock_stats(self.stats)
         lib().or_shock_step(self.order, self.N, ctypes.c_double(self.dx), ctypes.c_double(self.cfl),
                             ctypes.c_double(self.Pr), ctypes.c_double(self.relax), _d(self.M), _d(self.beta),
                             _d(self.g), _d(self.speed), _i(self.status), _i(self.iters), _d(self.opts),

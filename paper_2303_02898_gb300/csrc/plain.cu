@@ -98,9 +98,6 @@ __global__ void k_init(const float *__restrict__ M, float *__restrict__ beta, in
 
 // One block per active cell.  Nodes q = tid + 256 j.  The exponent of the
 // trial point beta + alpha dbeta is e_beta + alpha e_dbeta (both computed once).
-// TILED: sigma goes to the tensor cores as a TF32 hi part and a TF32 lo part
-// (sigma = hi + lo to about 2^-22), each row-major with rows padded to tiles.
-template <bool TILED>
 __global__ void __launch_bounds__(BLK) k_linesearch(const int *__restrict__ act, const float *__restrict__ M,
                                                     float *__restrict__ beta, PlainState S,
                                                     const float *__restrict__ phiT, const float *__restrict__ logw,
@@ -171,19 +168,7 @@ __global__ void __launch_bounds__(BLK) k_linesearch(const int *__restrict__ act,
         sat = (LD - gradD) >= -(o.atol + o.rtol * fabsf(LD));
     }
     const float invZ = 1.f / Z;
-    if (TILED) {
-        float *hi_row = S.sigma + (size_t)slot * Q, *lo_row = S.sig_lo + (size_t)slot * Q;
-#pragma unroll
-        for (int j = 0; j < MAXJ; ++j) {
-            const int q = tid + j * BLK;
-            if (j < nj && q < Q) {
-                const float v = __expf(eb[j] + alpha * ed[j] - mx) * invZ;
-                const float hi = tc_round(v);
-                hi_row[q] = hi;
-                lo_row[q] = tc_round(v - hi);
-            }
-        }
-    } else {
+    {
         float *sig = S.sigma + (size_t)slot * Q;
 #pragma unroll
         for (int j = 0; j < MAXJ; ++j) {
@@ -193,6 +178,97 @@ __global__ void __launch_bounds__(BLK) k_linesearch(const int *__restrict__ act,
     }
     if (tid >= 1 && tid < NP) bc[tid] = sb[tid] + alpha * sd[tid];
     if (tid == 0) { S.Lcur[c] = Lt; S.alpha[c] = alpha; }
+}
+
+// The line search of the mixed back-end, one warp per active cell: the same
+// steps as k_linesearch (exponents at beta and dbeta, Armijo backtracking,
+// sigma of the accepted point), with the exponents sum-factorised on the
+// tensor Gauss-Hermite grid (nodes q = i N^2 + p, lane l owning the node
+// lines p = l + 32 r: the order of the dense tables) and sigma written as a
+// TF32 hi row and a TF32 lo row (sigma = hi + lo to about 2^-22), 32
+// consecutive nodes per warp store.
+template <int N>
+__global__ void __launch_bounds__(128) k_linesearch_sf(const int *__restrict__ act, int nact,
+                                                       const float *__restrict__ M, float *__restrict__ beta,
+                                                       PlainState S, const float *__restrict__ he1d,
+                                                       const float *__restrict__ logw1d, mem_solve_opts o) {
+    using C = FusedCfg<N>;
+    constexpr int Q = N * N * N;
+    __shared__ float s_he[N * MEM_HE_STRIDE], s_lw[16];
+    __shared__ float sv[4][4][36];
+    for (int t = threadIdx.x; t < N * MEM_HE_STRIDE; t += blockDim.x) s_he[t] = he1d[t];
+    for (int t = threadIdx.x; t < N; t += blockDim.x) s_lw[t] = logw1d[t];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slot = blockIdx.x * 4 + w;
+    if (slot >= nact) return;
+    const int c = act[slot];
+    const float *Mc = M + (size_t)c * NP;
+    float *bc = beta + (size_t)c * NP;
+    float *sb = sv[w][0], *sd = sv[w][1], *sg = sv[w][2], *sm = sv[w][3];
+    const float n = Mc[0];
+    for (int k = lane; k < NP; k += 32) {
+        sb[k] = k ? bc[k] : 0.f;
+        sd[k] = k ? S.db[(size_t)c * NP + k] : 0.f;
+        sg[k] = k ? S.G[(size_t)c * NP + k] : 0.f;
+        sm[k] = k ? Mc[k] / n : 0.f;
+    }
+    __syncwarp();
+    float pg = 0.f, pb = 0.f, pd = 0.f;
+    for (int k = lane; k < NP; k += 32) {
+        pg += sg[k] * sd[k];
+        pb += sb[k] * sm[k];
+        pd += sd[k] * sm[k];
+    }
+    const float gd = warp_sum(pg), mb = warp_sum(pb), md = warp_sum(pd);
+    float eb[C::NODES], ed[C::NODES];
+    exponent<N>(sb, s_he, s_lw, lane, true, eb);
+    exponent<N>(sd, s_he, s_lw, lane, false, ed);
+    float Lcur = S.Lcur[c];
+    if (isnan(Lcur)) {  // first pass: objective at the start point
+        float m = -INFINITY;
+#pragma unroll
+        for (int q = 0; q < C::NODES; ++q) m = fmaxf(m, eb[q]);
+        const float mx0 = warp_max(m);
+        float z = 0.f;
+#pragma unroll
+        for (int q = 0; q < C::NODES; ++q) z += __expf(eb[q] - mx0);
+        Lcur = mx0 + logf(warp_sum(z)) - mb;
+    }
+    float alpha = 2.f, Lt = NAN, mx = 0.f, Z = 1.f;
+    bool sat = false;
+    for (int s = 0; !sat && s <= o.maxT; ++s) {
+        alpha *= 0.5f;
+        float m = -INFINITY;
+#pragma unroll
+        for (int q = 0; q < C::NODES; ++q) m = fmaxf(m, fmaf(alpha, ed[q], eb[q]));
+        mx = warp_max(m);
+        float z = 0.f;
+#pragma unroll
+        for (int q = 0; q < C::NODES; ++q) z += __expf(fmaf(alpha, ed[q], eb[q]) - mx);
+        Z = warp_sum(z);
+        Lt = mx + logf(Z) - (mb + alpha * md);
+        const float LD = Lcur - Lt, gradD = -o.c_armijo * alpha * gd;
+        sat = (LD - gradD) >= -(o.atol + o.rtol * fabsf(LD));
+    }
+    const float invZ = 1.f / Z;
+    float *hi_row = S.sigma + (size_t)slot * Q, *lo_row = S.sig_lo + (size_t)slot * Q;
+#pragma unroll
+    for (int r = 0; r < C::R; ++r) {
+        const int p = lane + 32 * r;
+        if (p < C::P) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const float v = __expf(fmaf(alpha, ed[r * N + i], eb[r * N + i]) - mx) * invZ;
+                const float hi = tc_round(v);
+                hi_row[i * C::P + p] = hi;
+                lo_row[i * C::P + p] = tc_round(v - hi);
+            }
+        }
+    }
+    for (int k = lane; k < NP; k += 32)
+        if (k >= 1) bc[k] = sb[k] + alpha * sd[k];
+    if (lane == 0) { S.Lcur[c] = Lt; S.alpha[c] = alpha; }
 }
 
 // C[M x N] = A[M x K] B[K x N], row-major, 64x64 tiles, 4x4 per thread.
@@ -681,11 +757,16 @@ static int solve_dense(mem_ctx *ctx, const float *M, float *beta, int32_t *statu
         int cur_cnt = 0;
         for (int pass = 0; pass <= o.maxI + 1 && nact > 0; ++pass) {
             if (mixed) {
-                k_linesearch<true><<<nact, BLK, 0, st>>>(cur, Mc, bc, S, ctx->d_phiT, ctx->d_logw, Q, o);
+                if (ctx->n1d == 8)
+                    k_linesearch_sf<8><<<(nact + 3) / 4, 128, 0, st>>>(cur, nact, Mc, bc, S, ctx->d_he1d,
+                                                                      ctx->d_logw1d, o);
+                else
+                    k_linesearch_sf<12><<<(nact + 3) / 4, 128, 0, st>>>(cur, nact, Mc, bc, S, ctx->d_he1d,
+                                                                       ctx->d_logw1d, o);
                 rc = tc_contract(ctx, S.sigma, S.sig_lo, (int64_t)(sig / Q), S.mom, nact, S.err, st);
                 if (rc) return rc;
             } else {
-                k_linesearch<false><<<nact, BLK, 0, st>>>(cur, Mc, bc, S, ctx->d_phiT, ctx->d_logw, Q, o);
+                k_linesearch<<<nact, BLK, 0, st>>>(cur, Mc, bc, S, ctx->d_phiT, ctx->d_logw, Q, o);
                 sgemm(S.sigma, ctx->d_tab_solve, S.mom, nact, MEM_NCOL_SOLVE, Q, st);
             }
             const int nxt_cnt = 1 - cur_cnt;

@@ -917,3 +917,28 @@ def test_shock_speeds_equal_nine_statistic_speeds(O):
             a[0] = M[0]
             _, sp9 = O.flux_axi(215, a, g, M[0])
             assert sp9 == pytest.approx(sp35, rel=1e-9), (mach, c)
+
+
+def test_nine_statistic_shock_equals_35(O):
+    """Algorithm 2 on the paper's nine statistics of axisymmetric flow
+    (Appendix B: or_solve_axi / or_flux_axi inside the shock step, one
+    azimuth) against Algorithm 2 on the 35 Hermite products (12 azimuths) for
+    a Mach-4 FLIC shock from the tanh start on a velocity-space rule: an
+    axisymmetric state stays in the span of the nine, both systems reach the
+    same Newton solutions and fluxes, so the two runs agree to the solver's
+    tolerance.  A dropped statistic, a wrong map between the nine and the 35
+    or a different speed would leave O(1e-3) differences."""
+    d = O.shock_domain(4.0, 10.0, 6.0, 6.0)
+    O.set_velocity_rule(214, d[0], d[1], 3, d[2], 2, 8, 1)
+    O.set_velocity_rule(215, d[0], d[1], 3, d[2], 2, 8, 12)
+    kw = dict(ic="tanh", thickness=5.44, tol=1e-10, scheme="flic")
+    s9 = O.Shock(4.0, 16, -16.3, 16.3, order=214, stats=9, **kw)
+    s35 = O.Shock(4.0, 16, -16.3, 16.3, order=215, stats=35, **kw)
+    assert np.abs(s9.speed - s35.speed).max() < 1e-9 * s35.speed.max()
+    for _ in range(3):
+        s9.step()
+        s35.step()
+    assert s9.t == pytest.approx(s35.t, rel=1e-10)
+    for a, b in zip(s9.profile(), s35.profile()):
+        assert np.isfinite(a).all()
+        assert np.abs(a - b).max() < 1e-8 * np.abs(b).max()

@@ -252,12 +252,25 @@ def run_mach10(mem, torch, np, nsteps=400):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         fin = all(np.isfinite(sh.problem(i)["rho"]).all() for i in range(0, 256, 15))
+        # Newton passes of the last step (every cell): the solve kernel's roofline
+        passes = int(sh.device_tensors()[4].sum().item())
         sh.close()
         cells = 256 * 150
         out[key] = {"value": cells * 50 / dt, "unit": "cell-updates/s", "problems": 256, "cells": cells,
                     "mach": [1.2, 10.0], "steps": 50, "ms_per_step": 1e3 * dt / 50, "finite": fin,
                     "scheme": "FLIC" if scheme == mem.SCHEME_FLIC else "local Lax-Friedrichs",
                     "statistics": stats}
+        if scheme == mem.SCHEME_LF:
+            rule = vctx.velocity_rule()[0]
+            nx, nr = rule[0] * rule[2], rule[1] * rule[2]
+            fpp = vel_flops_per_pass(nx, nr * rule[3]) if stats == 35 else axi_flops_per_pass(nx, nr)
+            peak = measured_peaks(mem)["fp32_tflops"]
+            ach = passes * fpp / (dt / 50) / 1e12
+            out[key]["roofline_" + ("k_vel" if stats == 35 else "k_axi")] = {
+                "bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": peak, "frac": ach / peak,
+                "passes_per_step": passes, "flops_per_pass": fpp,
+                "note": "of measured FP32 FMA rate; whole step time (the solve kernel is most of it, "
+                        "profiles/launches_mach10_ensemble_*.md) in the denominator"}
     out.update(run_mach10_4096(mem, torch, np, vctx))
     vctx.close()
     return out
@@ -300,6 +313,16 @@ def axi_flops_per_pass(nx, nr):
     linearisation terms of the 8 x 8 Hessian (about 200), the 8 x 8 Cholesky
     and two triangular solves."""
     return 2 * (nx * nr * 15 + 50 * nr + 200 + 8 ** 3 // 6 + 2 * 64)
+
+
+def vel_flops_per_pass(nx, npt):
+    """Algorithmic FP32 flops of one Newton pass of the 35-statistic
+    velocity-rule kernel (k_vel) for one cell (FMA = 2): on each of the
+    nx x npt nodes 5 FMA of exponent and 9 of x stage; on each of the npt
+    plane points the 35 terms of P_a and the 165 moments of degree <= 8 plus
+    about 60 products he_b(y) he_c(z); the 1670 linearisation terms of the
+    34 x 34 Hessian, its Cholesky (34^3 / 6) and two triangular solves."""
+    return 2 * (nx * npt * 14 + npt * 260 + 1670 + 34 ** 3 // 6 + 2 * 34 * 34)
 
 
 def run_ensemble_config4(mem, torch, np, nsteps=40):

@@ -95,80 +95,140 @@ __device__ __forceinline__ void esbgk_target(const float *M, const float *g, flo
     gaussian_hermite<float>(mb, K, n, Mt);
 }
 
-__global__ void k_collide(float *__restrict__ M, const float *__restrict__ g, const int *__restrict__ pid,
-                          const unsigned char *__restrict__ interior, const ShockProb *__restrict__ prm,
-                          const ShockScalars *__restrict__ sc, int NT, float frac, float *rho0) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= NT || !interior[c]) return;
-    const int p = pid[c];
-    float m[NP], gg[6], mt[NP];
+// Cells per block of the stencil-type kernels below.  Each block moves its
+// rows of the row-major state arrays between HBM and shared memory with
+// consecutive threads on consecutive floats (coalesced), and each thread
+// computes one cell from shared memory.
+constexpr int SB = 64;
+
+// Rows [r0, r0 + n) of a row-major array of w floats per row into shared
+// memory (row pitch w); rows outside [0, NT) are left unset.
+__device__ __forceinline__ void stage_in(float *dst, const float *__restrict__ src, int r0, int n, int w, int NT) {
+    const int lo = max(r0, 0), hi = min(r0 + n, NT);
+    if (hi <= lo) return;
+    const float *s = src + (size_t)lo * w;
+    float *d = dst + (lo - r0) * w;
+    const int cnt = (hi - lo) * w;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) d[t] = s[t];
+}
+
+// Rows [r0, r0 + n) back from shared memory, only those whose live flag
+// (shared memory, one per row) is set.
+__device__ __forceinline__ void stage_out(float *__restrict__ dst, const float *src, int r0, int n, int w, int NT,
+                                          const unsigned char *live) {
+    const int hi = min(r0 + n, NT);
+    if (hi <= r0) return;
+    const int cnt = (hi - r0) * w;
+    float *d = dst + (size_t)r0 * w;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x)
+        if (live[t / w]) d[t] = src[t];
+}
+
+__global__ void __launch_bounds__(SB) k_collide(float *__restrict__ M, const float *__restrict__ g,
+                                                const int *__restrict__ pid, const unsigned char *__restrict__ interior,
+                                                const ShockProb *__restrict__ prm, const ShockScalars *__restrict__ sc,
+                                                int NT, float frac, float *rho0) {
+    __shared__ float sM[SB * NP], sg[SB * 6];
+    __shared__ unsigned char sl[SB];
+    const int c0 = blockIdx.x * SB, c = c0 + threadIdx.x;
+    stage_in(sM, M, c0, SB, NP, NT);
+    stage_in(sg, g, c0, SB, 6, NT);
+    const bool live = c < NT && interior[c];
+    sl[threadIdx.x] = live;
+    __syncthreads();
+    if (live) {
+        const int p = pid[c];
+        float *row = sM + threadIdx.x * NP;
+        float m[NP], gg[6], mt[NP];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) m[k] = M[(size_t)c * NP + k];
+        for (int k = 0; k < NP; ++k) m[k] = row[k];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) gg[k] = g[(size_t)c * 6 + k];
-    if (rho0) rho0[c] = m[0];
-    esbgk_target(m, gg, prm[p].Pr, mt);
-    const float r = frac * sc[p].dt * m[0] / prm[p].relax;  // dt' / tau, tau = relax / n
+        for (int k = 0; k < 6; ++k) gg[k] = sg[threadIdx.x * 6 + k];
+        if (rho0) rho0[c] = m[0];
+        esbgk_target(m, gg, prm[p].Pr, mt);
+        const float r = frac * sc[p].dt * m[0] / prm[p].relax;  // dt' / tau, tau = relax / n
 #pragma unroll
-    for (int k = 0; k < NP; ++k) M[(size_t)c * NP + k] = (1.f - r) * m[k] + r * mt[k];
+        for (int k = 0; k < NP; ++k) row[k] = (1.f - r) * m[k] + r * mt[k];
+    }
+    __syncthreads();
+    stage_out(M, sM, c0, SB, NP, NT, sl);
 }
 
 // Local Lax-Friedrichs finite-volume update of interior cell c in its own
 // gauge: M_c += dt/dx (F^LF_{c-1/2} - F^LF_{c+1/2}), neighbours moved to g_c.
-// One compiled copy serves k_stencil and the LF problems of k_stencil2, so a
-// problem's result does not depend on the schemes of the batch it shares.
-__device__ __noinline__ void lf_update(const float *__restrict__ M, const float *__restrict__ F,
-                                       const float *__restrict__ g, const float *__restrict__ speed,
-                                       float *__restrict__ Mn, int c, float r) {
+// Arguments are the rows of cells c - 1, c, c + 1 (M, F, gauge) and their
+// speeds; out receives the updated row.  One compiled copy serves k_stencil
+// (rows in shared memory) and the LF problems of k_stencil2 (rows in HBM), so
+// a problem's result does not depend on the schemes of the batch it shares.
+__device__ __noinline__ void lf_update(const float *Ml, const float *M0, const float *Mr, const float *Fl,
+                                       const float *F0, const float *Fr, const float *gl_, const float *g0_,
+                                       const float *gr_, float sl, float s0, float sr, float *out, float r) {
     float g0[6], gl[6], gr[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        g0[k] = g[(size_t)c * 6 + k];
-        gl[k] = g[(size_t)(c - 1) * 6 + k];
-        gr[k] = g[(size_t)(c + 1) * 6 + k];
+        g0[k] = g0_[k];
+        gl[k] = gl_[k];
+        gr[k] = gr_[k];
     }
-    const float s0 = speed[c], ll = fmaxf(speed[c - 1], s0), lr = fmaxf(s0, speed[c + 1]);
+    const float ll = fmaxf(sl, s0), lr = fmaxf(s0, sr);
     float acc[NP], x[NP], y[NP];
     AxisMap T[3];
     // F^LF_{c-1/2} - F^LF_{c+1/2} = 0.5(Fl + F0) + 0.5 ll (Ml - M0) - 0.5(F0 + Fr) - 0.5 lr (M0 - Mr)
 #pragma unroll
-    for (int k = 0; k < NP; ++k) acc[k] = -0.5f * (ll + lr) * M[(size_t)c * NP + k];
+    for (int k = 0; k < NP; ++k) acc[k] = -0.5f * (ll + lr) * M0[k];
     gauge_maps(g0, gl, T);
 #pragma unroll
-    for (int k = 0; k < NP; ++k) x[k] = M[(size_t)(c - 1) * NP + k];
+    for (int k = 0; k < NP; ++k) x[k] = Ml[k];
     apply_T(T, x, y);
 #pragma unroll
     for (int k = 0; k < NP; ++k) acc[k] += 0.5f * ll * y[k];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) x[k] = F[(size_t)(c - 1) * NP + k];
+    for (int k = 0; k < NP; ++k) x[k] = Fl[k];
     apply_T(T, x, y);
 #pragma unroll
     for (int k = 0; k < NP; ++k) acc[k] += 0.5f * y[k];
     gauge_maps(g0, gr, T);
 #pragma unroll
-    for (int k = 0; k < NP; ++k) x[k] = M[(size_t)(c + 1) * NP + k];
+    for (int k = 0; k < NP; ++k) x[k] = Mr[k];
     apply_T(T, x, y);
 #pragma unroll
     for (int k = 0; k < NP; ++k) acc[k] += 0.5f * lr * y[k];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) x[k] = F[(size_t)(c + 1) * NP + k];
+    for (int k = 0; k < NP; ++k) x[k] = Fr[k];
     apply_T(T, x, y);
 #pragma unroll
     for (int k = 0; k < NP; ++k) acc[k] -= 0.5f * y[k];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) Mn[(size_t)c * NP + k] = M[(size_t)c * NP + k] + r * acc[k];
+    for (int k = 0; k < NP; ++k) out[k] = M0[k] + r * acc[k];
 }
 
-__global__ void __launch_bounds__(128) k_stencil(const float *__restrict__ M, const float *__restrict__ F,
-                                                 const float *__restrict__ g, const float *__restrict__ speed,
-                                                 float *__restrict__ Mn, const int *__restrict__ pid,
-                                                 const unsigned char *__restrict__ interior,
-                                                 const ShockProb *__restrict__ prm,
-                                                 const ShockScalars *__restrict__ sc, int NT) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= NT || !interior[c]) return;
-    const int p = pid[c];
-    lf_update(M, F, g, speed, Mn, c, sc[p].dt / prm[p].dx);
+// LF step of every interior cell: rows c0 - 1 .. c0 + SB of M, F, g and
+// speed staged in shared memory, the updated rows staged and stored back.
+__global__ void __launch_bounds__(SB) k_stencil(const float *__restrict__ M, const float *__restrict__ F,
+                                                const float *__restrict__ g, const float *__restrict__ speed,
+                                                float *__restrict__ Mn, const int *__restrict__ pid,
+                                                const unsigned char *__restrict__ interior,
+                                                const ShockProb *__restrict__ prm,
+                                                const ShockScalars *__restrict__ sc, int NT) {
+    __shared__ float sM[(SB + 2) * NP], sF[(SB + 2) * NP], sg[(SB + 2) * 6], ss[SB + 2], sO[SB * NP];
+    __shared__ unsigned char sl[SB];
+    const int c0 = blockIdx.x * SB, c = c0 + threadIdx.x;
+    stage_in(sM, M, c0 - 1, SB + 2, NP, NT);
+    stage_in(sF, F, c0 - 1, SB + 2, NP, NT);
+    stage_in(sg, g, c0 - 1, SB + 2, 6, NT);
+    stage_in(ss, speed, c0 - 1, SB + 2, 1, NT);
+    // an interior cell's neighbours are cells of its own problem (or its ghosts)
+    const bool live = c < NT && interior[c];
+    sl[threadIdx.x] = live;
+    __syncthreads();
+    if (live) {
+        const int p = pid[c], i = threadIdx.x + 1;  // row of c in the staged arrays
+        lf_update(sM + (i - 1) * NP, sM + i * NP, sM + (i + 1) * NP, sF + (i - 1) * NP, sF + i * NP,
+                  sF + (i + 1) * NP, sg + (i - 1) * 6, sg + i * 6, sg + (i + 1) * 6, ss[i - 1], ss[i], ss[i + 1],
+                  sO + threadIdx.x * NP, sc[p].dt / prm[p].dx);
+    }
+    __syncthreads();
+    stage_out(Mn, sO, c0, SB, NP, NT, sl);
 }
 
 // Status bits of an interface solve whose parameters are not used: the
@@ -317,7 +377,10 @@ __global__ void __launch_bounds__(128) k_stencil2(const float *__restrict__ M, c
     const int p = pid[c];
     const int scheme = prm[p].scheme, off = prm[p].off;
     if (scheme == MEM_SCHEME_LF) {
-        lf_update(M, F, g, speed, Mn, c, sc[p].dt / prm[p].dx);
+        lf_update(M + (size_t)(c - 1) * NP, M + (size_t)c * NP, M + (size_t)(c + 1) * NP, F + (size_t)(c - 1) * NP,
+                  F + (size_t)c * NP, F + (size_t)(c + 1) * NP, g + (size_t)(c - 1) * 6, g + (size_t)c * 6,
+                  g + (size_t)(c + 1) * 6, speed[c - 1], speed[c], speed[c + 1], Mn + (size_t)c * NP,
+                  sc[p].dt / prm[p].dx);
         return;
     }
     float g0[6];
@@ -421,27 +484,50 @@ __global__ void __launch_bounds__(128) k_stencil2(const float *__restrict__ M, c
     for (int k = 0; k < NP; ++k) Mn[(size_t)c * NP + k] = M[(size_t)c * NP + k] + r * acc[k];
 }
 
-__global__ void k_regauge(const float *__restrict__ Mn, float *__restrict__ M, float *__restrict__ beta,
-                          float *__restrict__ g, const float *__restrict__ rho0, const int *__restrict__ pid,
-                          const unsigned char *__restrict__ interior, ShockScalars *sc, int NT) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= NT || !interior[c]) return;
-    float m[NP], gg[6], gh[6], y[NP], b[NP], bo[NP];
+__global__ void __launch_bounds__(SB) k_regauge(const float *__restrict__ Mn, float *__restrict__ M,
+                                                float *__restrict__ beta, float *__restrict__ g,
+                                                const float *__restrict__ rho0, const int *__restrict__ pid,
+                                                const unsigned char *__restrict__ interior, ShockScalars *sc, int NT) {
+    __shared__ float sM[SB * NP], sB[SB * NP], sg[SB * 6];
+    __shared__ unsigned char sl[SB];
+    const int c0 = blockIdx.x * SB, c = c0 + threadIdx.x;
+    stage_in(sM, Mn, c0, SB, NP, NT);
+    stage_in(sB, beta, c0, SB, NP, NT);
+    stage_in(sg, g, c0, SB, 6, NT);
+    const bool live = c < NT && interior[c];
+    sl[threadIdx.x] = live;
+    __syncthreads();
+    unsigned dv = 0u;
+    int key = -1;
+    if (live) {
+        float *mrow = sM + threadIdx.x * NP, *brow = sB + threadIdx.x * NP, *grow = sg + threadIdx.x * 6;
+        float m[NP], gg[6], gh[6], y[NP], b[NP], bo[NP];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) { m[k] = Mn[(size_t)c * NP + k]; b[k] = beta[(size_t)c * NP + k]; }
+        for (int k = 0; k < NP; ++k) { m[k] = mrow[k]; b[k] = brow[k]; }
 #pragma unroll
-    for (int k = 0; k < 6; ++k) gg[k] = g[(size_t)c * 6 + k];
-    hermite_gauge(m, gg, 1, gh);
-    AxisMap T[3];
-    gauge_maps(gh, gg, T);
-    apply_T(T, m, y);
-    transform_beta(gh, gg, b, bo);
-    bo[0] = y[0];
+        for (int k = 0; k < 6; ++k) gg[k] = grow[k];
+        hermite_gauge(m, gg, 1, gh);
+        AxisMap T[3];
+        gauge_maps(gh, gg, T);
+        apply_T(T, m, y);
+        transform_beta(gh, gg, b, bo);
+        bo[0] = y[0];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) { M[(size_t)c * NP + k] = y[k]; beta[(size_t)c * NP + k] = bo[k]; }
+        for (int k = 0; k < NP; ++k) { mrow[k] = y[k]; brow[k] = bo[k]; }
 #pragma unroll
-    for (int k = 0; k < 6; ++k) g[(size_t)c * 6 + k] = gh[k];
-    atomicMax(&sc[pid[c]].steady_bits, __float_as_uint(fabsf(y[0] - rho0[c])));
+        for (int k = 0; k < 6; ++k) grow[k] = gh[k];
+        key = pid[c];
+        dv = __float_as_uint(fabsf(y[0] - rho0[c]));
+    }
+    // the steady metric: one atomic per problem and warp (non-negative
+    // floats order like their bit patterns)
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    dv = __reduce_max_sync(grp, dv);
+    if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicMax(&sc[key].steady_bits, dv);
+    __syncthreads();
+    stage_out(M, sM, c0, SB, NP, NT, sl);
+    stage_out(beta, sB, c0, SB, NP, NT, sl);
+    stage_out(g, sg, c0, SB, 6, NT, sl);
 }
 
 // dt_p = cfl dx_p / max speed over problem p's cells (ghosts included); one
@@ -717,9 +803,9 @@ int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **o
 
 int batch_enqueue_step(ShockBatch *b, cudaStream_t st) {
     const int NT = b->NT;
-    const unsigned nb = (unsigned)((NT + 127) / 128);
+    const unsigned nb = (unsigned)((NT + 127) / 128), nsb = (unsigned)((NT + SB - 1) / SB);
     k_dt<<<b->P, 256, 0, st>>>(b->speed, b->prm, b->sc);
-    k_collide<<<nb, 128, 0, st>>>(b->M, b->g, b->pid, b->interior, b->prm, b->sc, NT, 0.5f, b->rho0);
+    k_collide<<<nsb, SB, 0, st>>>(b->M, b->g, b->pid, b->interior, b->prm, b->sc, NT, 0.5f, b->rho0);
     const mem_shock_params &p0 = b->params[0];
     mem_solve_opts o;
     mem_solve_opts_default(&o);
@@ -776,9 +862,9 @@ int batch_enqueue_step(ShockBatch *b, cudaStream_t st) {
         k_stencil2<<<nb, 128, 0, st>>>(b->M, b->F, b->g, b->speed, b->FI, b->gI, b->statusI, b->Mn, b->pid,
                                        b->interior, b->prm, b->sc, NT);
     } else
-        k_stencil<<<nb, 128, 0, st>>>(b->M, b->F, b->g, b->speed, b->Mn, b->pid, b->interior, b->prm, b->sc, NT);
-    k_collide<<<nb, 128, 0, st>>>(b->Mn, b->g, b->pid, b->interior, b->prm, b->sc, NT, 0.5f, nullptr);
-    k_regauge<<<nb, 128, 0, st>>>(b->Mn, b->M, b->beta, b->g, b->rho0, b->pid, b->interior, b->sc, NT);
+        k_stencil<<<nsb, SB, 0, st>>>(b->M, b->F, b->g, b->speed, b->Mn, b->pid, b->interior, b->prm, b->sc, NT);
+    k_collide<<<nsb, SB, 0, st>>>(b->Mn, b->g, b->pid, b->interior, b->prm, b->sc, NT, 0.5f, nullptr);
+    k_regauge<<<nsb, SB, 0, st>>>(b->Mn, b->M, b->beta, b->g, b->rho0, b->pid, b->interior, b->sc, NT);
     MEM_CUDA_TRY(cudaGetLastError());
     return MEM_OK;
 }

@@ -489,13 +489,15 @@ int mem_init_velocity(int degree, int nbx, int nbr, int ng, int K, double ax, do
     std::vector<double> x, w;
     int rc = mem_host::gl_rule(ng, x, w);
     if (rc) { delete ctx; return rc; }
-    std::vector<double> d0 = {ax, bx, br, 0.0};
+    std::vector<float> d0(mem_host::DOM_REC);
+    mem_host::dom_record(ax, bx, br, nbx, nbr, d0.data());
     // Per-node constants of the rule: offsets in units of the block width
     // (x_i = a_x + h_x t_i; y_p = h_r t_m cos(2 pi k / K), z_p likewise with
     // sin, p = m K + k) and the log weights without the per-cell block widths.
     const int nx = nbx * ng, nr = nbr * ng;
     std::vector<double> vtd;
     std::vector<float> vtf;
+    std::vector<float2> vt2;
     const double two_pi = 6.283185307179586476925286766559;
     std::vector<double> rt(nr);
     for (int m = 0; m < nr; ++m) rt[m] = (m / ng) + 0.5 * (x[m % ng] + 1.0);
@@ -504,7 +506,11 @@ int mem_init_velocity(int degree, int nbx, int nbr, int ng, int K, double ax, do
     for (int p = 0; p < nr * K; ++p) vtd.push_back(rt[p / K] * sin(two_pi * (p % K) / K));
     for (int i = 0; i < nx; ++i) vtf.push_back((float)log(w[i % ng]));
     for (int m = 0; m < nr; ++m) vtf.push_back((float)log(w[m % ng] * rt[m] / K));
-    if (!rc) rc = upload(&ctx->d_vtd, vtd);
+    for (double t : vtd) {
+        const float hi = (float)t;
+        vt2.push_back(make_float2(hi, (float)(t - (double)hi)));
+    }
+    if (!rc) rc = upload(&ctx->d_vt2, vt2);
     if (!rc) rc = upload(&ctx->d_vtf, vtf);
     if (!rc) rc = upload(&ctx->d_dom0, d0);
     if (!rc) rc = build_slot_tables(ctx);
@@ -528,7 +534,7 @@ void mem_destroy(mem_ctx *ctx) {
     cudaDeviceSynchronize();
     void *ptrs[] = {ctx->d_phiT, ctx->d_logw, ctx->d_tab_solve, ctx->d_tab_flux, ctx->d_he1d, ctx->d_x1d,
                     ctx->d_logw1d, ctx->d_lin_off, ctx->d_lin_terms, ctx->d_hess_slots, ctx->d_hess_slots128, ctx->d_hr_slots, ctx->d_hr_rounds, ctx->d_hr_ent, ctx->d_flux_slots, ctx->d_axi_slots, ctx->d_xlin_off, ctx->d_xlin_terms,
-                    ctx->scratch, ctx->d_vtd, ctx->d_vtf, ctx->d_dom0, ctx->d_tc_tab, ctx->d_phiT64, ctx->d_logw64, ctx->d_axi_terms, ctx->d_axi_toff};
+                    ctx->scratch, ctx->d_vt2, ctx->d_vtf, ctx->d_dom0, ctx->d_tc_tab, ctx->d_phiT64, ctx->d_logw64, ctx->d_axi_terms, ctx->d_axi_toff};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (ctx->scratch_ev) cudaEventDestroy(ctx->scratch_ev);

@@ -34,6 +34,7 @@
 
 #include "common.cuh"
 #include "ctx.h"
+#include "ffloat.cuh"
 #include "linalg.cuh"
 
 using namespace mem;
@@ -59,9 +60,9 @@ struct AxiArgs {
     int32_t *status, *iters;
     float *F, *speed, *cond;
     const int *pid;
-    const double *dom;
+    const float *dom;    // [domains][DOM_REC] domain records
     const unsigned char *active;
-    const double *vtd;
+    const float2 *vt2;   // node offsets in block widths, float pairs
     const float *vtf;
     const int2 *terms;  // (mu index, coefficient bits)
     const int *toff;    // [91]: entries 0..44 E[psi_p psi_q], 45..89 E[ubar_x psi_p psi_q] (p >= q, packed)
@@ -95,25 +96,6 @@ __host__ __device__ inline AxiLayout axi_layout(int nx, int nrp) {
     o += 72;  // 35-vectors of the cell (M, beta)
     L.total = (o + 3) & ~3;
     return L;
-}
-
-// float-float node placement (as in the 35-statistic velocity kernel)
-__device__ __forceinline__ void ffa_recip(float s, float &rh, float &rl) {
-    rh = 1.f / s;
-    rl = rh * fmaf(-s, rh, 1.f);
-}
-__device__ __forceinline__ void ffa_ubar(double d, float rh, float rl, float &uh, float &ul) {
-    const float dh = (float)d, dl = (float)(d - (double)dh);
-    const float p = __fmul_rn(dh, rh);
-    const float e = fmaf(dh, rh, -p);
-    uh = p;
-    ul = e + fmaf(dh, rl, dl * rh);
-}
-__device__ __forceinline__ void ffa_half_square(float uh, float ul, float &hs, float &hl) {
-    const float q = __fmul_rn(uh, uh);
-    const float qe = fmaf(uh, uh, -q);
-    hs = 0.5f * q;
-    hl = fmaf(uh, ul, 0.5f * qe);
 }
 
 // Coefficients of the exponent on the lane's radial nodes for the parameter
@@ -248,19 +230,19 @@ __global__ void __launch_bounds__(AW * 32, (R == 1 && AW < 8) ? 20 / AW : 1) k_a
         // ---- the rule as seen from this cell (gauge (w_x, 0, 0, s_x, s_r, s_r))
         const float *gc = A.gauge + cell * 6;
         const float wx = gc[0], sx = gc[3], sr = gc[4];
-        const double *dm = A.dom + 4 * (A.pid ? A.pid[cell] : 0);
-        const double ax = dm[0], hxw = (dm[1] - dm[0]) / A.nbx, hr = dm[2] / A.nbr;
-        const float lhx = __logf(0.5f * (float)hxw), lhr2 = 2.f * __logf((float)hr);
+        const float *dr = A.dom + mem_host::DOM_REC * (A.pid ? A.pid[cell] : 0);
+        const float axh = dr[0], axl = dr[1], hxh = dr[2], hxl = dr[3], hrh = dr[4], hrl = dr[5];
+        const float lhx = dr[6], lhr2 = dr[7];
         float rxh, rxl, rrh, rrl;
-        ffa_recip(sx, rxh, rxl);
-        ffa_recip(sr, rrh, rrl);
-        const double *xt = A.vtd;
+        ff_recip(sx, rxh, rxl);
+        ff_recip(sr, rrh, rrl);
         const float *lgx = A.vtf, *lrw = A.vtf + nx;
         __syncwarp();  // the previous cell is done with the tables
         for (int i = lane; i < nx; i += 32) {
-            float uh, ul, hs, hl;
-            ffa_ubar(fma(hxw, xt[i], ax) - (double)wx, rxh, rxl, uh, ul);
-            ffa_half_square(uh, ul, hs, hl);
+            float dh, dl, uh, ul, hs, hl;
+            ff_offset(axh, axl, hxh, hxl, A.vt2[i], wx, dh, dl);
+            ff_ubar(dh, dl, rxh, rxl, uh, ul);
+            ff_half_square(uh, ul, hs, hl);
             float h[10];
             hermite_vals<9>(uh, h);
 #pragma unroll
@@ -276,9 +258,10 @@ __global__ void __launch_bounds__(AW * 32, (R == 1 && AW < 8) ? 20 / AW : 1) k_a
             lwr[r] = -INFINITY;
             if (m < nr) {
                 // the radial offset of node m is the y offset of its first azimuth
-                float uh, ul, hs, hl;
-                ffa_ubar(hr * A.vtd[nx + (size_t)m * A.K], rrh, rrl, uh, ul);
-                ffa_half_square(uh, ul, hs, hl);
+                float dh, dl, uh, ul, hs, hl;
+                ff_offset(0.f, 0.f, hrh, hrl, A.vt2[nx + (size_t)m * A.K], 0.f, dh, dl);
+                ff_ubar(dh, dl, rrh, rrl, uh, ul);
+                ff_half_square(uh, ul, hs, hl);
                 const float s = hs + hl;
                 Lk[0] = 1.f;
                 Lk[1] = 1.f - s;
@@ -475,7 +458,9 @@ __global__ void __launch_bounds__(AW * 32, (R == 1 && AW < 8) ? 20 / AW : 1) k_a
                 (e < 45 ? Sm : Xm)[p * 16 + q] = axi_entry(A, mu, e);
             }
             __syncwarp();
-            const float ulo = (float)fma(hxw, xt[0], ax), uhi = (float)fma(hxw, xt[nx - 1], ax);
+            float ulo, uhi, el;
+            ff_offset(axh, axl, hxh, hxl, A.vt2[0], 0.f, ulo, el);
+            ff_offset(axh, axl, hxh, hxl, A.vt2[nx - 1], 0.f, uhi, el);
             const float bound = fmaxf(fabsf(ulo), fabsf(uhi));
             float lo = 0.f, hi = 0.f;
             const bool ok = !bad && small_pencil_extremes(Sm, Xm, NS, al, bt, sv, lane, lo, hi);
@@ -639,14 +624,14 @@ int build_axi_tables(mem_ctx *ctx) {
 }
 
 int axi_run(mem_ctx *ctx, const float *M, float *beta, const float *g, int32_t *status, int32_t *iters, float *F,
-            float *speed, const int *pid, const double *dom, int64_t B, const mem_solve_opts &o, bool solve,
+            float *speed, const int *pid, const float *dom, int64_t B, const mem_solve_opts &o, bool solve,
             cudaStream_t st, const unsigned char *active, float *cond) {
     if (!ctx->vel || !ctx->d_axi_terms) return MEM_EINVAL;
     if (B == 0) return MEM_OK;
     AxiArgs a;
     a.M = M; a.beta = beta; a.gauge = g; a.status = status; a.iters = iters; a.F = F; a.speed = speed;
     a.cond = cond; a.pid = pid; a.dom = dom ? dom : ctx->d_dom0; a.active = active;
-    a.vtd = ctx->d_vtd; a.vtf = ctx->d_vtf;
+    a.vt2 = ctx->d_vt2; a.vtf = ctx->d_vtf;
     a.terms = ctx->d_axi_terms; a.toff = ctx->d_axi_toff;
     a.B = B;
     a.nbx = ctx->nbx; a.nbr = ctx->nbr; a.K = ctx->K; a.nx = ctx->nx; a.nr = ctx->nbr * ctx->ng;

@@ -64,9 +64,9 @@ struct mem_ctx {
     int nbx = 0, nbr = 0, ng = 0, K = 0;     // blocks in u_x, blocks in u_r, points per block, azimuths
     int nx = 0, npt = 0;                     // nodes in u_x; points of the transverse plane
     double dom[3] = {0, 0, 0};               // default domain (a_x, b_x, b_r)
-    double *d_vtd = nullptr;  // [nx] x-node offsets | [nr] r-node offsets (block widths) | [K] cos | [K] sin
+    float2 *d_vt2 = nullptr;  // [nx] x | [npt] y | [npt] z node offsets in block widths, as float pairs (hi, lo)
     float *d_vtf = nullptr;   // [nx] log w^GL of each x node | [nr] log(w^GL t_r / K) of each radial node
-    double *d_dom0 = nullptr;                // the default domain (a_x, b_x, b_r, 0) on the device
+    float *d_dom0 = nullptr;                 // the default domain as a domain record (dom_record)
     int2 *d_axi_terms = nullptr;             // nine-statistic system: linearisation terms (mu index, coef)
     int *d_axi_toff = nullptr;               // [91] term offsets of E[psi psi^T] and E[ubar_x psi psi^T]
     // Scratch owned by the context (plain solver, flux at orders without a
@@ -87,6 +87,11 @@ int scratch_begin(mem_ctx *ctx, size_t bytes, cudaStream_t st);       // with ct
 void scratch_end(mem_ctx *ctx, cudaStream_t st);                      // with ctx->mu held
 size_t plain_scratch_bytes(int Q);                                    // plain / mixed solve, one chunk
 bool tc_available(const mem_ctx *ctx);
+// Domain record of a velocity-space rule (what its kernels read per cell, all
+// FP32): a_x, the block widths h_x = (b_x - a_x) / nbx and h_r = b_r / nbr as
+// float pairs (hi, lo), then log(h_x / 2) and 2 log(h_r).
+constexpr int DOM_REC = 8;
+void dom_record(double ax, double bx, double br, int nbx, int nbr, float *rec);
 int build_tc_tables(mem_ctx *ctx, const std::vector<double> &phi);
 size_t tc_sigma_floats(int Q, int64_t cells);
 int tc_contract(mem_ctx *ctx, const float *a_hi, const float *a_lo, int64_t rows, float *mom, int n, int *err,
@@ -111,14 +116,14 @@ bool flux_fused_available(const mem_ctx *ctx);
 int flux_from_mu(mem_ctx *ctx, const float *mu, const float *M, const float *g, float *F, float *speed, int64_t B,
                  cudaStream_t st, bool axisym);
 int vel_run(mem_ctx *ctx, const float *M, float *beta, const float *g, int32_t *status, int32_t *iters, float *mu,
-            const int *pid, const double *dom, int64_t B, const mem_solve_opts &o, bool solve, cudaStream_t st,
+            const int *pid, const float *dom, int64_t B, const mem_solve_opts &o, bool solve, cudaStream_t st,
             const unsigned char *active = nullptr, float *cond = nullptr);
 size_t vel_smem_bytes(int nx, int npt);
 int build_axi_tables(mem_ctx *ctx);
 int axi_occupancy(mem_ctx *ctx, int W, int *per_sm);
 int fused_occupancy(mem_ctx *ctx, int W, int *per_sm);
 int axi_run(mem_ctx *ctx, const float *M, float *beta, const float *g, int32_t *status, int32_t *iters, float *F,
-            float *speed, const int *pid, const double *dom, int64_t B, const mem_solve_opts &o, bool solve,
+            float *speed, const int *pid, const float *dom, int64_t B, const mem_solve_opts &o, bool solve,
             cudaStream_t st, const unsigned char *active = nullptr, float *cond = nullptr);
 int gl_rule(int n, std::vector<double> &x, std::vector<double> &w);
 int gauge_hermite(mem_ctx *ctx, const float *M_in, const float *g_in, float *g_out, float *M_out,

@@ -101,27 +101,42 @@ __device__ __forceinline__ void esbgk_target(const float *M, const float *g, flo
 // computes one cell from shared memory.
 constexpr int SB = 64;
 
-// Rows [r0, r0 + n) of a row-major array of w floats per row into shared
-// memory (row pitch w); rows outside [0, NT) are left unset.
-__device__ __forceinline__ void stage_in(float *dst, const float *__restrict__ src, int r0, int n, int w, int NT) {
-    const int lo = max(r0, 0), hi = min(r0 + n, NT);
-    if (hi <= lo) return;
-    const float *s = src + (size_t)lo * w;
-    float *d = dst + (lo - r0) * w;
-    const int cnt = (hi - lo) * w;
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) d[t] = s[t];
+// Rows [r0, r0 + N) of a row-major array of W floats per row into shared
+// memory (row pitch W); rows outside [0, NT) are left unset.  Unrolled so
+// that sixteen loads per thread are in flight together.
+template <int W, int N>
+__device__ __forceinline__ void stage_in(float *dst, const float *src, int r0, int NT) {
+    constexpr int CNT = W * N, IT = (CNT + SB - 1) / SB, U = 16;
+    const int lo = (max(r0, 0) - r0) * W, hi = (min(r0 + N, NT) - r0) * W;
+    const float *s = src + (ptrdiff_t)r0 * W;
+#pragma unroll
+    for (int j0 = 0; j0 < IT; j0 += U) {
+        float v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = threadIdx.x + (j0 + u) * SB;
+            v[u] = (j0 + u < IT && t >= lo && t < hi) ? s[t] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = threadIdx.x + (j0 + u) * SB;
+            if (j0 + u < IT && t < CNT) dst[t] = v[u];
+        }
+    }
 }
 
-// Rows [r0, r0 + n) back from shared memory, only those whose live flag
-// (shared memory, one per row) is set.
-__device__ __forceinline__ void stage_out(float *__restrict__ dst, const float *src, int r0, int n, int w, int NT,
-                                          const unsigned char *live) {
-    const int hi = min(r0 + n, NT);
-    if (hi <= r0) return;
-    const int cnt = (hi - r0) * w;
-    float *d = dst + (size_t)r0 * w;
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x)
-        if (live[t / w]) d[t] = src[t];
+// Rows [r0, r0 + N) back from shared memory, only those whose live flag
+// (shared memory, one per row) is set and that lie below NT.
+template <int W, int N>
+__device__ __forceinline__ void stage_out(float *dst, const float *src, int r0, int NT, const unsigned char *live) {
+    constexpr int CNT = W * N, IT = (CNT + SB - 1) / SB;
+    const int hi = (min(r0 + N, NT) - r0) * W;
+    float *d = dst + (ptrdiff_t)r0 * W;
+#pragma unroll
+    for (int j = 0; j < IT; ++j) {
+        const int t = threadIdx.x + j * SB;
+        if (t < hi && live[t / W]) d[t] = src[t];
+    }
 }
 
 __global__ void __launch_bounds__(SB) k_collide(float *__restrict__ M, const float *__restrict__ g,
@@ -131,8 +146,8 @@ __global__ void __launch_bounds__(SB) k_collide(float *__restrict__ M, const flo
     __shared__ float sM[SB * NP], sg[SB * 6];
     __shared__ unsigned char sl[SB];
     const int c0 = blockIdx.x * SB, c = c0 + threadIdx.x;
-    stage_in(sM, M, c0, SB, NP, NT);
-    stage_in(sg, g, c0, SB, 6, NT);
+    stage_in<NP, SB>(sM, M, c0, NT);
+    stage_in<6, SB>(sg, g, c0, NT);
     const bool live = c < NT && interior[c];
     sl[threadIdx.x] = live;
     __syncthreads();
@@ -151,7 +166,7 @@ __global__ void __launch_bounds__(SB) k_collide(float *__restrict__ M, const flo
         for (int k = 0; k < NP; ++k) row[k] = (1.f - r) * m[k] + r * mt[k];
     }
     __syncthreads();
-    stage_out(M, sM, c0, SB, NP, NT, sl);
+    stage_out<NP, SB>(M, sM, c0, NT, sl);
 }
 
 // Local Lax-Friedrichs finite-volume update of interior cell c in its own
@@ -213,10 +228,10 @@ __global__ void __launch_bounds__(SB) k_stencil(const float *__restrict__ M, con
     __shared__ float sM[(SB + 2) * NP], sF[(SB + 2) * NP], sg[(SB + 2) * 6], ss[SB + 2], sO[SB * NP];
     __shared__ unsigned char sl[SB];
     const int c0 = blockIdx.x * SB, c = c0 + threadIdx.x;
-    stage_in(sM, M, c0 - 1, SB + 2, NP, NT);
-    stage_in(sF, F, c0 - 1, SB + 2, NP, NT);
-    stage_in(sg, g, c0 - 1, SB + 2, 6, NT);
-    stage_in(ss, speed, c0 - 1, SB + 2, 1, NT);
+    stage_in<NP, SB + 2>(sM, M, c0 - 1, NT);
+    stage_in<NP, SB + 2>(sF, F, c0 - 1, NT);
+    stage_in<6, SB + 2>(sg, g, c0 - 1, NT);
+    stage_in<1, SB + 2>(ss, speed, c0 - 1, NT);
     // an interior cell's neighbours are cells of its own problem (or its ghosts)
     const bool live = c < NT && interior[c];
     sl[threadIdx.x] = live;
@@ -228,7 +243,7 @@ __global__ void __launch_bounds__(SB) k_stencil(const float *__restrict__ M, con
                   sO + threadIdx.x * NP, sc[p].dt / prm[p].dx);
     }
     __syncthreads();
-    stage_out(Mn, sO, c0, SB, NP, NT, sl);
+    stage_out<NP, SB>(Mn, sO, c0, NT, sl);
 }
 
 // Status bits of an interface solve whose parameters are not used: the
@@ -491,9 +506,9 @@ __global__ void __launch_bounds__(SB) k_regauge(const float *__restrict__ Mn, fl
     __shared__ float sM[SB * NP], sB[SB * NP], sg[SB * 6];
     __shared__ unsigned char sl[SB];
     const int c0 = blockIdx.x * SB, c = c0 + threadIdx.x;
-    stage_in(sM, Mn, c0, SB, NP, NT);
-    stage_in(sB, beta, c0, SB, NP, NT);
-    stage_in(sg, g, c0, SB, 6, NT);
+    stage_in<NP, SB>(sM, Mn, c0, NT);
+    stage_in<NP, SB>(sB, beta, c0, NT);
+    stage_in<6, SB>(sg, g, c0, NT);
     const bool live = c < NT && interior[c];
     sl[threadIdx.x] = live;
     __syncthreads();
@@ -525,9 +540,9 @@ __global__ void __launch_bounds__(SB) k_regauge(const float *__restrict__ Mn, fl
     dv = __reduce_max_sync(grp, dv);
     if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicMax(&sc[key].steady_bits, dv);
     __syncthreads();
-    stage_out(M, sM, c0, SB, NP, NT, sl);
-    stage_out(beta, sB, c0, SB, NP, NT, sl);
-    stage_out(g, sg, c0, SB, 6, NT, sl);
+    stage_out<NP, SB>(M, sM, c0, NT, sl);
+    stage_out<NP, SB>(beta, sB, c0, NT, sl);
+    stage_out<6, SB>(g, sg, c0, NT, sl);
 }
 
 // dt_p = cfl dx_p / max speed over problem p's cells (ghosts included); one
@@ -703,7 +718,7 @@ int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **o
     // Flux work space: moment rows (velocity-space rule) or the plain path's
     // sigma and moment columns (Gauss-Hermite rule).
     const bool work_ok = ctx->vel ? alloc((void **)&b->mu, sizeof(float) * NT * MEM_MU_STRIDE) &&
-                                        alloc((void **)&b->dom, sizeof(double) * 4 * P) &&
+                                        alloc((void **)&b->dom, sizeof(float) * DOM_REC * P) &&
                                         alloc((void **)&b->cond, sizeof(float) * NT)
                                   : alloc((void **)&b->sigma, sizeof(float) * NT * (size_t)Q) &&
                                         alloc((void **)&b->mom, sizeof(float) * NT * (size_t)MEM_NCOL_FLUX);
@@ -757,9 +772,13 @@ int batch_create(mem_ctx *ctx, const mem_shock_params *ps, int P, ShockBatch **o
         return MEM_ECUDA;
     }
     if (ctx->vel) {
-        std::vector<double> hdom(4 * (size_t)P);
-        for (int i = 0; i < P; ++i) shock_domain(ps[i], &hdom[4 * (size_t)i]);
-        if (cudaMemcpy(b->dom, hdom.data(), sizeof(double) * hdom.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        std::vector<float> hdom(DOM_REC * (size_t)P);
+        for (int i = 0; i < P; ++i) {
+            double d[4];
+            shock_domain(ps[i], d);
+            dom_record(d[0], d[1], d[2], ctx->nbx, ctx->nbr, &hdom[DOM_REC * (size_t)i]);
+        }
+        if (cudaMemcpy(b->dom, hdom.data(), sizeof(float) * hdom.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemset(b->cond, 0, sizeof(float) * NT) != cudaSuccess) {
             batch_free(b);
             return MEM_ECUDA;

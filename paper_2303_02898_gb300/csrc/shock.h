@@ -39,7 +39,7 @@ struct ShockBatch {
     float *M = nullptr, *beta = nullptr, *g = nullptr, *speed = nullptr, *F = nullptr, *Mn = nullptr;
     float *rho0 = nullptr, *sigma = nullptr, *mom = nullptr;
     float *mu = nullptr;      // [NT][MEM_MU_STRIDE] moment rows (velocity-space rule)
-    double *dom = nullptr;    // [P][4] integration domain (a_x, b_x, b_r, 0) per problem (velocity-space rule)
+    float *dom = nullptr;     // [P][DOM_REC] integration domain record per problem (velocity-space rule)
     float *cond = nullptr;    // [NT] pivot-ratio condition estimate of each cell's last solve (velocity-space rule)
     int32_t *status = nullptr, *iters = nullptr;
     // Interfaces (Lax-Wendroff / FLIC problems only): entry c is the interface

@@ -27,6 +27,7 @@
 // warp 0 while the other warps wait at the barrier.
 #include "common.cuh"
 #include "ctx.h"
+#include "ffloat.cuh"
 #include "linalg.cuh"
 #include "sumfact.cuh"
 
@@ -46,9 +47,9 @@ struct VelArgs {
     float *mu;                    // [B][MEM_MU_STRIDE] moments of degree <= 9 at the final beta, or null
     float *cond;                  // [B] largest / smallest Cholesky pivot of the last Newton pass, or null
     const int *pid;               // per-cell domain index, or null (domain 0)
-    const double *dom;            // (a_x, b_x, b_r, 0) per domain
+    const float *dom;             // [domains][DOM_REC] domain records (dom_record)
     const unsigned char *active;  // 0: no solve for this cell (its moments are still produced)
-    const double *vtd;            // [nx] x offsets | [npt] y offsets | [npt] z offsets (in block widths)
+    const float2 *vt2;            // [nx] x | [npt] y | [npt] z offsets in block widths, float pairs
     const float *vtf;             // [nx] log w^GL of the x node | [nr] log(w^GL t_r / K) of the radial node
     const int2 *slots;            // Hessian linearisation terms over the block's 128 lanes
     int n_slots;
@@ -134,29 +135,6 @@ __device__ __forceinline__ void plane_coeffs(const float *v, const float *hy, co
             c[r][a] = acc;
         }
     }
-}
-
-// Float-float helpers (Dekker products with FMA; __fmul_rn keeps the
-// products from being contracted).  1/s as rh + rl with one Newton correction.
-__device__ __forceinline__ void ff_recip(float s, float &rh, float &rl) {
-    rh = 1.f / s;
-    rl = rh * fmaf(-s, rh, 1.f);
-}
-// ubar = d / s for d given in FP64 (the only FP64 value per coordinate):
-// d = dh + dl, ubar = uh + ul to about 2^-44 relative.
-__device__ __forceinline__ void ff_ubar(double d, float rh, float rl, float &uh, float &ul) {
-    const float dh = (float)d, dl = (float)(d - (double)dh);
-    const float p = __fmul_rn(dh, rh);
-    const float e = fmaf(dh, rh, -p);
-    uh = p;
-    ul = e + fmaf(dh, rl, dl * rh);
-}
-// ubar^2 / 2 = hs + hl.
-__device__ __forceinline__ void ff_half_square(float uh, float ul, float &hs, float &hl) {
-    const float q = __fmul_rn(uh, uh);
-    const float qe = fmaf(uh, uh, -q);
-    hs = 0.5f * q;
-    hl = fmaf(uh, ul, 0.5f * qe);
 }
 
 // Plane stage mu_o = sum_p T_a(p) he_b(y_p) he_c(z_p), o = idx3(a, b, c) < NO,
@@ -287,24 +265,24 @@ __global__ void __launch_bounds__(VT, 3) k_vel(VelArgs A) {
         const float wx = gc[0], wy = gc[1], wz = gc[2], sx_ = gc[3], sy = gc[4], sz = gc[5];
         // u - w cancels on a box tens of thermal widths wide, and the hot tail
         // of a mixed cell sits at |ubar| ~ 5-10, where plain FP32 rounding of
-        // ubar and ubar^2 / 2 moves its weights by ~1e-5.  So u - w is formed
-        // in FP64 (one FMA and one subtraction per coordinate) and split into
-        // a float pair; ubar = (u - w) / s and ubar^2 / 2 follow in error-free
-        // float-float arithmetic and the log weight is rounded once.  (FP64
-        // beyond that stalls the whole SM on this part.)
-        const double *dm = A.dom + 4 * (A.pid ? A.pid[cell] : 0);
-        const double ax = dm[0], hxw = (dm[1] - dm[0]) / A.nbx, hr = dm[2] / A.nbr;
-        const float lhx = __logf(0.5f * (float)hxw), lhr2 = 2.f * __logf((float)hr);
+        // ubar and ubar^2 / 2 moves its weights by ~1e-5.  So u - w, ubar =
+        // (u - w) / s and ubar^2 / 2 are formed in error-free float-float
+        // arithmetic from the domain record and the offsets as float pairs,
+        // and the log weight is rounded once.
+        const float *dr = A.dom + mem_host::DOM_REC * (A.pid ? A.pid[cell] : 0);
+        const float axh = dr[0], axl = dr[1], hxh = dr[2], hxl = dr[3], hrh = dr[4], hrl = dr[5];
+        const float lhx = dr[6], lhr2 = dr[7];
         float rxh, rxl, ryh, ryl, rzh, rzl;
         ff_recip(sx_, rxh, rxl);
         ff_recip(sy, ryh, ryl);
         ff_recip(sz, rzh, rzl);
-        const double *xt = A.vtd, *yt = A.vtd + nx, *zt = yt + npt;
+        const float2 *xt = A.vt2, *yt = A.vt2 + nx, *zt = yt + npt;
         const float *lgx = A.vtf, *lrw = A.vtf + nx;
         __syncthreads();  // the previous cell is done with every table
         for (int i = tid; i < nx; i += VT) {
-            float uh, ul, hs, hl;
-            ff_ubar(fma(hxw, xt[i], ax) - (double)wx, rxh, rxl, uh, ul);
+            float dh, dl, uh, ul, hs, hl;
+            ff_offset(axh, axl, hxh, hxl, xt[i], wx, dh, dl);
+            ff_ubar(dh, dl, rxh, rxl, uh, ul);
             ff_half_square(uh, ul, hs, hl);
             float h[10];
             hermite_vals<9>(uh, h);
@@ -313,9 +291,11 @@ __global__ void __launch_bounds__(VT, 3) k_vel(VelArgs A) {
             s_lwx[i] = ((lhx + lgx[i]) - hs) - hl;
         }
         for (int p = tid; p < npt; p += VT) {
-            float yh, yl, zh, zl, ys, yls, zs, zls;
-            ff_ubar(fma(hr, yt[p], -(double)wy), ryh, ryl, yh, yl);
-            ff_ubar(fma(hr, zt[p], -(double)wz), rzh, rzl, zh, zl);
+            float dh, dl, yh, yl, zh, zl, ys, yls, zs, zls;
+            ff_offset(0.f, 0.f, hrh, hrl, yt[p], wy, dh, dl);
+            ff_ubar(dh, dl, ryh, ryl, yh, yl);
+            ff_offset(0.f, 0.f, hrh, hrl, zt[p], wz, dh, dl);
+            ff_ubar(dh, dl, rzh, rzl, zh, zl);
             ff_half_square(yh, yl, ys, yls);
             ff_half_square(zh, zl, zs, zls);
             float h[10];
@@ -486,8 +466,9 @@ __global__ void __launch_bounds__(VT, 3) k_vel(VelArgs A) {
             if (tid == 0) {
                 // u_x range of the nodes: the speed bound when the pencil has
                 // no reliable spectrum
-                out[220] = (float)fma(hxw, xt[0], ax);
-                out[221] = (float)fma(hxw, xt[nx - 1], ax);
+                float el;
+                ff_offset(axh, axl, hxh, hxl, xt[0], 0.f, out[220], el);
+                ff_offset(axh, axl, hxh, hxl, xt[nx - 1], 0.f, out[221], el);
             }
         }
     }
@@ -512,17 +493,30 @@ int launch_vel(mem_ctx *ctx, const VelArgs &a, cudaStream_t st) {
 
 namespace mem_host {
 
+void dom_record(double ax, double bx, double br, int nbx, int nbr, float *rec) {
+    auto split = [](double v, float *hl) {
+        hl[0] = (float)v;
+        hl[1] = (float)(v - (double)hl[0]);
+    };
+    const double hx = (bx - ax) / nbx, hr = br / nbr;
+    split(ax, rec);
+    split(hx, rec + 2);
+    split(hr, rec + 4);
+    rec[6] = (float)log(0.5 * hx);
+    rec[7] = (float)(2.0 * log(hr));
+}
+
 size_t vel_smem_bytes(int nx, int npt) { return sizeof(float) * (size_t)vel_layout(nx, npt).total; }
 
 int vel_run(mem_ctx *ctx, const float *M, float *beta, const float *g, int32_t *status, int32_t *iters, float *mu,
-            const int *pid, const double *dom, int64_t B, const mem_solve_opts &o, bool solve, cudaStream_t st,
+            const int *pid, const float *dom, int64_t B, const mem_solve_opts &o, bool solve, cudaStream_t st,
             const unsigned char *active, float *cond) {
     if (!ctx->vel) return MEM_EINVAL;
     if (B == 0) return MEM_OK;
     VelArgs a;
     a.M = M; a.beta = beta; a.gauge = g; a.status = status; a.iters = iters; a.mu = mu; a.cond = cond;
     a.pid = pid; a.dom = dom ? dom : ctx->d_dom0; a.active = active;
-    a.vtd = ctx->d_vtd; a.vtf = ctx->d_vtf;
+    a.vt2 = ctx->d_vt2; a.vtf = ctx->d_vtf;
     a.slots = ctx->d_hess_slots128; a.n_slots = ctx->n_hess_slots128;
     a.B = B;
     a.nbx = ctx->nbx; a.nbr = ctx->nbr; a.ng = ctx->ng; a.K = ctx->K;

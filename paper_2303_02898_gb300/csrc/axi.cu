@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(AW * 32, (R == 1 && AW < 8) ? 20 / AW : 1) k_a
         const float wx = gc[0], sx = gc[3], sr = gc[4];
         const float *dr = A.dom + mem_host::DOM_REC * (A.pid ? A.pid[cell] : 0);
         const float axh = dr[0], axl = dr[1], hxh = dr[2], hxl = dr[3], hrh = dr[4], hrl = dr[5];
-        const float lhx = dr[6], lhr2 = dr[7];
+        const float lhx = __logf(0.5f * hxh), lhr2 = 2.f * __logf(hrh);
         float rxh, rxl, rrh, rrl;
         ff_recip(sx, rxh, rxl);
         ff_recip(sr, rrh, rrl);

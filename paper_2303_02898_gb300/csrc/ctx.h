@@ -89,7 +89,7 @@ size_t plain_scratch_bytes(int Q);                                    // plain /
 bool tc_available(const mem_ctx *ctx);
 // Domain record of a velocity-space rule (what its kernels read per cell, all
 // FP32): a_x, the block widths h_x = (b_x - a_x) / nbx and h_r = b_r / nbr as
-// float pairs (hi, lo), then log(h_x / 2) and 2 log(h_r).
+// float pairs (hi, lo); two unused slots.
 constexpr int DOM_REC = 8;
 void dom_record(double ax, double bx, double br, int nbx, int nbr, float *rec);
 int build_tc_tables(mem_ctx *ctx, const std::vector<double> &phi);

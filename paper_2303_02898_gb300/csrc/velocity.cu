@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(VT, 3) k_vel(VelArgs A) {
         // and the log weight is rounded once.
         const float *dr = A.dom + mem_host::DOM_REC * (A.pid ? A.pid[cell] : 0);
         const float axh = dr[0], axl = dr[1], hxh = dr[2], hxl = dr[3], hrh = dr[4], hrl = dr[5];
-        const float lhx = dr[6], lhr2 = dr[7];
+        const float lhx = __logf(0.5f * hxh), lhr2 = 2.f * __logf(hrh);
         float rxh, rxl, ryh, ryl, rzh, rzl;
         ff_recip(sx_, rxh, rxl);
         ff_recip(sy, ryh, ryl);
@@ -502,8 +502,7 @@ void dom_record(double ax, double bx, double br, int nbx, int nbr, float *rec) {
     split(ax, rec);
     split(hx, rec + 2);
     split(hr, rec + 4);
-    rec[6] = (float)log(0.5 * hx);
-    rec[7] = (float)(2.0 * log(hr));
+    rec[6] = rec[7] = 0.f;
 }
 
 size_t vel_smem_bytes(int nx, int npt) { return sizeof(float) * (size_t)vel_layout(nx, npt).total; }

@@ -175,6 +175,25 @@ int mem_quad_order(const mem_ctx *ctx);
 int mem_solve(mem_ctx *ctx, const float *M, float *beta, int32_t *status, int32_t *iters,
               int64_t B, const mem_solve_opts *opts, void *stream);
 
+/* mem_solve (Algorithm 1, Section 3.2) on arrays in host memory, for a batch
+ * that starts and ends on the host:
+ *   M_host      host [B][35] moments (pinned memory lets the copies overlap).
+ *   beta_host   host [B][35] out: solution, beta[0] = n; in: warm start when
+ *               warm != 0 (warm = 0 starts every cell from beta = 0, the
+ *               Maxwellian of its gauge, without reading beta_host).
+ *   status_host, iters_host  host [B] int32, or NULL.
+ * The batch streams through the device in chunks of 262,144 cells staged in
+ * the context's scratch: while the fused kernel solves one chunk on
+ * `stream`, a copy stream owned by the call brings in the next and takes out
+ * the previous one.  Results equal mem_solve's bit for bit.  Asynchronous:
+ * the host arrays are complete once `stream` reaches the point of the call
+ * (synchronise it before reading them, and keep them alive until then).
+ * The fused back-end only (opts->impl MEM_IMPL_FUSED, quad_order 8 or 12);
+ * MEM_EINVAL otherwise, on a velocity-space context, for NULL M_host /
+ * beta_host, or when `stream` is being captured. */
+int mem_solve_host(mem_ctx *ctx, const float *M_host, float *beta_host, int32_t *status_host,
+                   int32_t *iters_host, int64_t B, int warm, const mem_solve_opts *opts, void *stream);
+
 /* The paper's own system for axisymmetric flow on a velocity-space context
  * (Appendix B: the nine statistics psi_j of (u_x, u_r) of Eq. "Sufficient
  * 35" in orthonormal form, which are orthonormal combinations v_j of the 35

@@ -77,6 +77,8 @@ def lib():
                      "mem_serve_progress", "mem_serve_poll", "mem_serve_stats"):
             getattr(L, name).restype = ctypes.c_int
         L.mem_solve.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(SolveOpts), _P]
+        L.mem_solve_host.restype = ctypes.c_int
+        L.mem_solve_host.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(SolveOpts), _P]
         L.mem_solve_gauge.restype = ctypes.c_int
         L.mem_solve_gauge.argtypes = [_P, _P, _P, _P, _P, _P, ctypes.c_int64, ctypes.POINTER(SolveOpts), _P]
         L.mem_init_velocity.restype = ctypes.c_int
@@ -127,6 +129,17 @@ def declared_functions():
     txt = open(HEADER).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(mem_[a-z_0-9]+)\s*\(", txt)))
+
+
+def _hptr(t):
+    """Address of a contiguous CPU tensor (host buffers of mem_solve_host)."""
+    if t is None:
+        return None
+    if t.is_cuda:
+        raise ValueError("expected a host tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _ptr(t):
@@ -204,6 +217,16 @@ class Context:
         rc = lib().mem_solve(self.h, _ptr(M), _ptr(beta), _ptr(status), _ptr(iters), B, ctypes.byref(o),
                              _stream(stream))
         _check(rc, "mem_solve")
+
+    def solve_host(self, M, beta, status=None, iters=None, warm=False, opts=None, stream=None, **kw):
+        """mem_solve_host: Algorithm 1 on host (CPU, ideally pinned) tensors,
+        streamed through the device in chunks with the copies overlapped.
+        Asynchronous on `stream`: synchronise before reading beta / status."""
+        B = M.shape[0]
+        o = opts if opts is not None else default_opts(**kw)
+        rc = lib().mem_solve_host(self.h, _hptr(M), _hptr(beta), _hptr(status), _hptr(iters), B, int(bool(warm)),
+                                  ctypes.byref(o), _stream(stream))
+        _check(rc, "mem_solve_host")
 
     def solve_gauge(self, M, beta, gauge, status=None, iters=None, opts=None, stream=None, **kw):
         """mem_solve_gauge: Algorithm 1 with the cells' gauges (velocity-space rules)."""

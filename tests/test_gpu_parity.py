@@ -409,6 +409,51 @@ def test_full_size_solve_sampled(O, mem, ctx8, dev):
     assert res[ok].max() <= RES_TOL, res.max()
 
 
+@pytest.mark.parametrize("order", [8, 12])
+def test_solve_host_matches_device(O, mem, dev, order, ctx8, ctx12):
+    """mem_solve_host streams host arrays through the device in chunks of
+    262,144 cells with the copies overlapped: more than one chunk and a
+    ragged tail here.  Same kernel per cell, so beta, status and iters equal
+    mem_solve's bit for bit, cold (beta from 0) and warm (beta_host read);
+    a sample meets the oracle's residual bar."""
+    from paper_2303_02898_gb300 import workloads
+    ctx = ctx8 if order == 8 else ctx12
+    B = 300_001 if order == 8 else 270_000
+    t = workloads.solve_targets(B, seed=5)
+    Mg = torch.zeros(B, 35, device=dev)
+    gg = torch.zeros(B, 6, device=dev)
+    ctx.targets(T32(t.v, dev), T32(t.T, dev), T32(t.a, dev), T32(t.b, dev), Mg, gg, gen_order=24)
+    beta_d = torch.zeros_like(Mg)
+    st_d = torch.zeros(B, dtype=torch.int32, device=dev)
+    it_d = torch.zeros(B, dtype=torch.int32, device=dev)
+    ctx.solve(Mg, beta_d, st_d, it_d, **EXT)
+    M_h = Mg.cpu().pin_memory()
+    beta_h = torch.full((B, 35), float("nan")).pin_memory()   # cold start: never read
+    st_h = torch.zeros(B, dtype=torch.int32).pin_memory()
+    it_h = torch.zeros(B, dtype=torch.int32).pin_memory()
+    ctx.solve_host(M_h, beta_h, st_h, it_h, warm=False, **EXT)
+    torch.cuda.synchronize()
+    assert torch.equal(beta_h, beta_d.cpu())
+    assert torch.equal(st_h, st_d.cpu()) and torch.equal(it_h, it_d.cpu())
+    # warm start from a perturbed solution, against mem_solve from the same start
+    start = beta_d.clone()
+    start[:, 1:] *= 0.9
+    beta_w = start.clone()
+    ctx.solve(Mg, beta_w, st_d, it_d, **EXT)
+    beta_hw = start.cpu().pin_memory()
+    ctx.solve_host(M_h, beta_hw, st_h, it_h, warm=True, **EXT)
+    torch.cuda.synchronize()
+    assert torch.equal(beta_hw, beta_w.cpu())
+    assert torch.equal(st_h, st_d.cpu()) and torch.equal(it_h, it_d.cpu())
+    idx = np.concatenate([np.random.default_rng(1).choice(B, 48, replace=False), [0, B - 1]])
+    conv = (st_h.numpy()[idx] & mem.ST_CONVERGED) != 0
+    res = O.residual_batch(order, beta_h[idx].double().numpy(), M_h[idx].double().numpy())
+    assert conv.all() and res.max() <= RES_TOL, res.max()
+    # the plain back-end uses the scratch itself: refused
+    with pytest.raises(RuntimeError):
+        ctx.solve_host(M_h[:8], beta_h[:8], impl=mem.IMPL_PLAIN)
+
+
 def test_context_scratch_ordered_across_streams(O, mem, dev):
     """The dense flux path (and the plain back-end) share the context's
     scratch.  Calls made on two streams of one context are ordered on the GPU

@@ -449,7 +449,12 @@ def test_solve_host_matches_device(O, mem, dev, order, ctx8, ctx12):
     conv = (st_h.numpy()[idx] & mem.ST_CONVERGED) != 0
     res = O.residual_batch(order, beta_h[idx].double().numpy(), M_h[idx].double().numpy())
     assert conv.all() and res.max() <= RES_TOL, res.max()
-    # the plain back-end uses the scratch itself: refused
+    # a single cell (one chunk of one), and the plain back-end, which uses the
+    # scratch itself: refused
+    b1 = torch.zeros(1, 35).pin_memory()
+    ctx.solve_host(M_h[:1].clone().pin_memory(), b1, **EXT)
+    torch.cuda.synchronize()
+    assert torch.equal(b1, beta_h[:1])
     with pytest.raises(RuntimeError):
         ctx.solve_host(M_h[:8], beta_h[:8], impl=mem.IMPL_PLAIN)
 

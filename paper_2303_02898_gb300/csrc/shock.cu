@@ -465,18 +465,18 @@ __global__ void __launch_bounds__(128) k_stencil2(const float *__restrict__ M, c
                     float gi[6];
 #pragma unroll
                     for (int k = 0; k < 6; ++k) gi[k] = gI[(size_t)b * 6 + k];
-                    const int cells[3] = {aa, a, b};
-                    float *dst[3] = {qaa, qa, qb};
-#pragma unroll 1
-                    for (int t = 0; t < 3; ++t) {
+                    auto in_gi = [&](int cc, float *q) {
 #pragma unroll
-                        for (int k = 0; k < 6; ++k) gn[k] = g[(size_t)cells[t] * 6 + k];
+                        for (int k = 0; k < 6; ++k) gn[k] = g[(size_t)cc * 6 + k];
                         gauge_maps(gi, gn, T);
 #pragma unroll
-                        for (int k = 0; k < NP; ++k) x[k] = M[(size_t)cells[t] * NP + k];
+                        for (int k = 0; k < NP; ++k) x[k] = M[(size_t)cc * NP + k];
                         apply_T(T, x, y);
-                        project9(y, dst[t]);
-                    }
+                        project9(y, q);
+                    };
+                    in_gi(aa, qaa);
+                    in_gi(a, qa);
+                    in_gi(b, qb);
                 }
                 float phi[9], pmin = 2.f;
 #pragma unroll

@@ -482,6 +482,49 @@ def run_serving_mach10(mem, torch, np, nreq=32, max_steps=100, chunk=10):
                                "all_finite": bool(all(np.isfinite(r["rho"]).all() for r, _ in res))}}
 
 
+def run_serving_steady(mem, torch, np, nreq=32, max_steps=40000, chunk=200):
+    """Requests served to steady state: the Poisson trace of serving_mach10
+    (200 req/s, Mach U[1.5, 10], the paper's Mach-10 cell width, ncells
+    logU[128, 160]) with the nine-statistic system, each request running
+    until max |d rho| / (rho_+ - rho_-) < 1e-6 per step (or max_steps);
+    continuous batching with graph-captured batch steps.  p50 / p99 latency
+    from arrival to completion, and how many requests reached the metric."""
+    from paper_2303_02898_gb300 import workloads
+    t_arr, probs = workloads.serving_trace(nreq, seed=3, lo=128, hi=160, mach_lo=1.5, mach_hi=10.0)
+    vctx = mem.Context.velocity(mem.shock_domain(mach=10.0))
+    sv = mem.Server(vctx, hbm_budget_bytes=8 << 30, max_cells=1 << 16, steady_tol=1e-6, max_steps=max_steps)
+    ids, nxt = [], 0
+    t0 = time.perf_counter()
+    while True:
+        now = time.perf_counter() - t0
+        while nxt < nreq and t_arr[nxt] <= now:
+            p = probs[nxt]
+            ids.append((sv.submit(mach=p.mach, ncells=p.ncells, xl=p.xl, xr=p.xr, ic=1, stats=9), p))
+            nxt += 1
+        sv.progress(chunk)
+        st = sv.stats()
+        if nxt == nreq and st["completed"] == nreq:
+            break
+        if st["resident"] == 0 and st["queued"] == 0 and nxt < nreq:
+            time.sleep(max(0.0, t_arr[nxt] - (time.perf_counter() - t0)))
+    wall = time.perf_counter() - t0
+    res = [(sv.poll(i, ncells=p.ncells), p) for i, p in ids]
+    sv.close()
+    vctx.close()
+    lat = np.array([r["latency_s"] for r, _ in res])
+    steps = np.array([r["steps"] for r, _ in res])
+    upd = sum(r["steps"] * p.ncells for r, p in res)
+    return {"serving_steady_mach10_nine": {
+        "requests": nreq, "rate_per_s": 200.0, "mach": [1.5, 10.0], "ncells": [128, 160],
+        "max_steps": max_steps, "steady_tol": 1e-6, "statistics": 9,
+        "steady_requests": int(sum(r["steady"] for r, _ in res)),
+        "steps_to_steady": {"min": int(steps.min()), "median": float(np.median(steps)), "max": int(steps.max())},
+        "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+        "throughput": upd / wall, "unit": "cell-updates/s", "wall_s": wall,
+        "all_finite": bool(all(np.isfinite(r["rho"]).all() for r, _ in res)),
+        "graph": "each packed batch's step captured once and replayed"}}
+
+
 def run_condition_study(mem, torch, np, steps=200, every=10):
     """Section 4, Fig. 7 analogue: the largest pivot-ratio estimate of
     cond(H) met over a run, against the number of cells, at Mach 4 (domain
@@ -1179,6 +1222,7 @@ def main():
         extras.update(run_serving_mach10(mem, torch, np))
         extras.update(run_ensemble_config4(mem, torch, np))
         extras.update(run_serving_config5(mem, torch, np))
+        extras.update(run_serving_steady(mem, torch, np))
         extras.update(run_condition_study(mem, torch, np))
         extras.update(run_gauge_study(mem, torch, np))
         extras.update(run_newton_study(mem, torch, np))

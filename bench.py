@@ -482,17 +482,19 @@ def run_serving_mach10(mem, torch, np, nreq=32, max_steps=100, chunk=10):
                                "all_finite": bool(all(np.isfinite(r["rho"]).all() for r, _ in res))}}
 
 
-def run_serving_steady(mem, torch, np, nreq=32, max_steps=40000, chunk=200):
+def run_serving_steady(mem, torch, np, nreq=32, max_steps=40000, chunk=200, steady_tol=2e-5):
     """Requests served to steady state: the Poisson trace of serving_mach10
     (200 req/s, Mach U[1.5, 10], the paper's Mach-10 cell width, ncells
     logU[128, 160]) with the nine-statistic system, each request running
-    until max |d rho| / (rho_+ - rho_-) < 1e-6 per step (or max_steps);
-    continuous batching with graph-captured batch steps.  p50 / p99 latency
-    from arrival to completion, and how many requests reached the metric."""
+    until max |d rho| / (rho_+ - rho_-) < steady_tol per step (or
+    max_steps); continuous batching with graph-captured batch steps.  The
+    tolerance sits above the FP32 noise of that metric (the paper's 150-cell
+    Mach-10 mesh settles at 1e-5 - 7e-5 per step, never 1e-6).  p50 / p99
+    latency from arrival to completion, and how many requests reached it."""
     from paper_2303_02898_gb300 import workloads
     t_arr, probs = workloads.serving_trace(nreq, seed=3, lo=128, hi=160, mach_lo=1.5, mach_hi=10.0)
     vctx = mem.Context.velocity(mem.shock_domain(mach=10.0))
-    sv = mem.Server(vctx, hbm_budget_bytes=8 << 30, max_cells=1 << 16, steady_tol=1e-6, max_steps=max_steps)
+    sv = mem.Server(vctx, hbm_budget_bytes=8 << 30, max_cells=1 << 16, steady_tol=steady_tol, max_steps=max_steps)
     ids, nxt = [], 0
     t0 = time.perf_counter()
     while True:
@@ -516,7 +518,7 @@ def run_serving_steady(mem, torch, np, nreq=32, max_steps=40000, chunk=200):
     upd = sum(r["steps"] * p.ncells for r, p in res)
     return {"serving_steady_mach10_nine": {
         "requests": nreq, "rate_per_s": 200.0, "mach": [1.5, 10.0], "ncells": [128, 160],
-        "max_steps": max_steps, "steady_tol": 1e-6, "statistics": 9,
+        "max_steps": max_steps, "steady_tol": steady_tol, "statistics": 9,
         "steady_requests": int(sum(r["steady"] for r, _ in res)),
         "steps_to_steady": {"min": int(steps.min()), "median": float(np.median(steps)), "max": int(steps.max())},
         "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),

@@ -406,7 +406,9 @@ __global__ void __launch_bounds__(128) k_newton(const int *__restrict__ act, int
 // Cholesky of the fused back-end (reg_chol_solve34: lane j holds column j,
 // pivot columns broadcast through shared memory, both triangular solves
 // fused) in place of the shared-memory factorisation.  Same results up to
-// rounding order, same lambda I retries and status bits.
+// rounding order, same lambda I retries and status bits.  Persistent: a grid
+// of resident blocks whose warps loop over the active cells; the packed
+// Hessian index of each entry comes from a per-block table.
 __global__ void __launch_bounds__(128) k_newton_reg(const int *__restrict__ act, int nact, const float *__restrict__ M,
                                                     float *__restrict__ beta, PlainState S, int *__restrict__ act_next,
                                                     int *__restrict__ cnt_next, mem_solve_opts o, int32_t *status,
@@ -414,74 +416,80 @@ __global__ void __launch_bounds__(128) k_newton_reg(const int *__restrict__ act,
     __shared__ float sA[4][NP1 * LDH];
     __shared__ float sv[4][2][36];
     __shared__ __align__(16) float sbc[4][36];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int slot = blockIdx.x * 4 + w;
-    if (slot >= nact) return;
-    const int c = act[slot];
-    float *A = sA[w], *m = sv[w][0], *G = sv[w][1];
-    const float *mom = S.mom + (size_t)slot * MEM_NCOL_SOLVE;
-    const float *Mc = M + (size_t)c * NP;
-    const float n = Mc[0];
-    for (int k = lane; k < NP; k += 32) m[k] = mom[k];
-    __syncwarp();
-    for (int k = lane; k < NP; k += 32) {
-        G[k] = k ? m[k] - Mc[k] / n : 0.f;
-        S.G[(size_t)c * NP + k] = G[k];
-    }
-    for (int p = lane; p < NP1 * (NP1 + 1) / 2; p += 32) {
-        int i = (int)((sqrtf(8.f * p + 1.f) - 1.f) * 0.5f);
-        while (i * (i + 1) / 2 > p) --i;
+    __shared__ int s_pij[NP1 * (NP1 + 1) / 2];  // packed entry p -> i | j << 8
+    for (int p = threadIdx.x; p < NP1 * (NP1 + 1) / 2; p += blockDim.x) {
+        int i = 0;
         while ((i + 1) * (i + 2) / 2 <= p) ++i;
-        const int j = p - i * (i + 1) / 2;
-        A[i * LDH + j] = mom[NP + p] - m[i + 1] * m[j + 1];
+        s_pij[p] = i | ((p - i * (i + 1) / 2) << 8);
     }
-    __syncwarp();
-    int st = S.st[c];
-    const float g_l = G[lane + 1], g32 = G[33], g33 = G[34];
-    float x = 0.f, x32 = 0.f, x33 = 0.f, lam = 0.f;
-    bool ok = false;
-    for (int t = 0; t <= o.max_lambda; ++t) {
-        ok = reg_chol_solve34<true>(A, lam, lane, -g_l, -g32, -g33, x, x32, x33, sbc[w]);
-        if (ok) break;
-        st |= MEM_ST_LAMBDA;
-        lam = (t == 0) ? o.lambda0 : lam * o.lambda_mul;
-    }
-    const int it = S.it[c] + 1;
-    bool done = false;
-    if (!ok) {
-        st |= MEM_ST_LAMBDA_CAP | MEM_ST_NONFINITE;
-        done = true;
-    } else {
-        const float res = 0.5f * fabsf(warp_sum(x * g_l) + x32 * g32 + x33 * g33);
-        float *db = S.db + (size_t)c * NP;
-        db[lane + 1] = x;
-        if (lane == 0) { db[0] = 0.f; db[33] = x32; db[34] = x33; }
-        if (!isfinite(res)) {
-            st |= MEM_ST_NONFINITE;
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // persistent: each warp takes active cells gridDim.x * 4 apart
+    for (int slot = blockIdx.x * 4 + w; slot < nact; slot += gridDim.x * 4) {
+        const int c = act[slot];
+        float *A = sA[w], *m = sv[w][0], *G = sv[w][1];
+        const float *mom = S.mom + (size_t)slot * MEM_NCOL_SOLVE;
+        const float *Mc = M + (size_t)c * NP;
+        const float n = Mc[0];
+        for (int k = lane; k < NP; k += 32) m[k] = mom[k];
+        __syncwarp();
+        for (int k = lane; k < NP; k += 32) {
+            G[k] = k ? m[k] - Mc[k] / n : 0.f;
+            S.G[(size_t)c * NP + k] = G[k];
+        }
+        for (int p = lane; p < NP1 * (NP1 + 1) / 2; p += 32) {
+            const int ij = s_pij[p], i = ij & 255, j = ij >> 8;
+            A[i * LDH + j] = mom[NP + p] - m[i + 1] * m[j + 1];
+        }
+        __syncwarp();
+        int st = S.st[c];
+        const float g_l = G[lane + 1], g32 = G[33], g33 = G[34];
+        float x = 0.f, x32 = 0.f, x33 = 0.f, lam = 0.f;
+        bool ok = false;
+        for (int t = 0; t <= o.max_lambda; ++t) {
+            ok = reg_chol_solve34<true>(A, lam, lane, -g_l, -g32, -g33, x, x32, x33, sbc[w]);
+            if (ok) break;
+            st |= MEM_ST_LAMBDA;
+            lam = (t == 0) ? o.lambda0 : lam * o.lambda_mul;
+        }
+        const int it = S.it[c] + 1;
+        bool done = false;
+        if (!ok) {
+            st |= MEM_ST_LAMBDA_CAP | MEM_ST_NONFINITE;
             done = true;
         } else {
-            const float alpha = S.alpha[c];
-            const bool conv_res = res <= o.tol, conv_a = alpha <= o.alpha_min;
-            if (conv_res) st |= MEM_ST_CONVERGED;
-            if (conv_a) st |= MEM_ST_STAGNATED;
-            if (conv_res || conv_a) done = true;
-            else if (it > o.maxI) { st |= MEM_ST_MAXITER; done = true; }
-            if (done && conv_res && o.final_step) {
-                float *bc = beta + (size_t)c * NP;
-                bc[lane + 1] += x;
-                if (lane == 0) { bc[33] += x32; bc[34] += x33; }
+            const float res = 0.5f * fabsf(warp_sum(x * g_l) + x32 * g32 + x33 * g33);
+            float *db = S.db + (size_t)c * NP;
+            db[lane + 1] = x;
+            if (lane == 0) { db[0] = 0.f; db[33] = x32; db[34] = x33; }
+            if (!isfinite(res)) {
+                st |= MEM_ST_NONFINITE;
+                done = true;
+            } else {
+                const float alpha = S.alpha[c];
+                const bool conv_res = res <= o.tol, conv_a = alpha <= o.alpha_min;
+                if (conv_res) st |= MEM_ST_CONVERGED;
+                if (conv_a) st |= MEM_ST_STAGNATED;
+                if (conv_res || conv_a) done = true;
+                else if (it > o.maxI) { st |= MEM_ST_MAXITER; done = true; }
+                if (done && conv_res && o.final_step) {
+                    float *bc = beta + (size_t)c * NP;
+                    bc[lane + 1] += x;
+                    if (lane == 0) { bc[33] += x32; bc[34] += x33; }
+                }
             }
         }
-    }
-    if (lane == 0) {
-        S.it[c] = it;
-        S.st[c] = st;
-        if (done) {
-            if (status) status[c] = st;
-            if (iters) iters[c] = it;
-        } else {
-            act_next[atomicAdd(cnt_next, 1)] = c;
+        if (lane == 0) {
+            S.it[c] = it;
+            S.st[c] = st;
+            if (done) {
+                if (status) status[c] = st;
+                if (iters) iters[c] = it;
+            } else {
+                act_next[atomicAdd(cnt_next, 1)] = c;
+            }
         }
+        __syncwarp();  // the warp's buffers are free for its next cell
     }
 }
 
@@ -695,6 +703,19 @@ void sgemm(const float *A, const float *Bm, float *C, int M, int N, int K, cudaS
 
 namespace mem_host {
 
+// Resident blocks of the mixed back-end's persistent Newton kernel.
+static int newton_reg_grid(mem_ctx *ctx) {
+    static int grid = 0;
+    if (!grid) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_newton_reg, 128, 0);
+        cudaGetLastError();
+        grid = std::max(1, sms * std::max(1, per_sm));
+    }
+    return grid;
+}
+
 static size_t plain_need(int Q, size_t CH) {
     // sigma hi + lo (mixed: whole tiles of 128 cells), moments,
     // per-cell vectors and scalars, the FP64 residuals of failed cells
@@ -772,7 +793,8 @@ static int solve_dense(mem_ctx *ctx, const float *M, float *beta, int32_t *statu
             const int nxt_cnt = 1 - cur_cnt;
             MEM_CUDA_TRY(cudaMemsetAsync(S.cnt + nxt_cnt, 0, sizeof(int), st));
             if (mixed)
-                k_newton_reg<<<(nact + 3) / 4, 128, 0, st>>>(cur, nact, Mc, bc, S, nxt, S.cnt + nxt_cnt, o, stc, itc);
+                k_newton_reg<<<std::min((nact + 3) / 4, newton_reg_grid(ctx)), 128, 0, st>>>(cur, nact, Mc, bc, S, nxt,
+                                                                                          S.cnt + nxt_cnt, o, stc, itc);
             else
                 k_newton<<<(nact + 3) / 4, 128, 0, st>>>(cur, nact, Mc, bc, S, nxt, S.cnt + nxt_cnt, o, stc, itc);
             MEM_CUDA_TRY(cudaMemcpyAsync(&hc[0], S.cnt + nxt_cnt, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -482,15 +482,14 @@ def run_serving_mach10(mem, torch, np, nreq=32, max_steps=100, chunk=10):
                                "all_finite": bool(all(np.isfinite(r["rho"]).all() for r, _ in res))}}
 
 
-def run_serving_steady(mem, torch, np, nreq=32, max_steps=40000, chunk=200, steady_tol=2e-5):
+def _serving_steady(mem, torch, np, nreq, max_steps, chunk, steady_tol):
     """Requests served to steady state: the Poisson trace of serving_mach10
     (200 req/s, Mach U[1.5, 10], the paper's Mach-10 cell width, ncells
     logU[128, 160]) with the nine-statistic system, each request running
     until max |d rho| / (rho_+ - rho_-) < steady_tol per step (or
-    max_steps); continuous batching with graph-captured batch steps.  The
-    tolerance sits above the FP32 noise of that metric (the paper's 150-cell
-    Mach-10 mesh settles at 1e-5 - 7e-5 per step, never 1e-6).  p50 / p99
-    latency from arrival to completion, and how many requests reached it."""
+    max_steps); continuous batching with graph-captured batch steps.  p50 /
+    p99 latency from arrival to completion, and how many requests reached
+    the tolerance."""
     from paper_2303_02898_gb300 import workloads
     t_arr, probs = workloads.serving_trace(nreq, seed=3, lo=128, hi=160, mach_lo=1.5, mach_hi=10.0)
     vctx = mem.Context.velocity(mem.shock_domain(mach=10.0))
@@ -516,7 +515,7 @@ def run_serving_steady(mem, torch, np, nreq=32, max_steps=40000, chunk=200, stea
     lat = np.array([r["latency_s"] for r, _ in res])
     steps = np.array([r["steps"] for r, _ in res])
     upd = sum(r["steps"] * p.ncells for r, p in res)
-    return {"serving_steady_mach10_nine": {
+    return {
         "requests": nreq, "rate_per_s": 200.0, "mach": [1.5, 10.0], "ncells": [128, 160],
         "max_steps": max_steps, "steady_tol": steady_tol, "statistics": 9,
         "steady_requests": int(sum(r["steady"] for r, _ in res)),
@@ -524,7 +523,15 @@ def run_serving_steady(mem, torch, np, nreq=32, max_steps=40000, chunk=200, stea
         "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
         "throughput": upd / wall, "unit": "cell-updates/s", "wall_s": wall,
         "all_finite": bool(all(np.isfinite(r["rho"]).all() for r, _ in res)),
-        "graph": "each packed batch's step captured once and replayed"}}
+        "graph": "each packed batch's step captured once and replayed"}
+
+
+def run_serving_steady(mem, torch, np, nreq=32, max_steps=40000, chunk=200):
+    """The steady-state serving trace at the stated tolerance (1e-6) and at
+    2e-5: in FP32 the metric levels off between 1e-5 and 7e-5 per step on the
+    paper's Mach-10 mesh, so few requests reach 1e-6."""
+    return {"serving_steady_mach10_nine": {"tol_1e-06": _serving_steady(mem, torch, np, nreq, max_steps, chunk, 1e-6),
+                                           "tol_2e-05": _serving_steady(mem, torch, np, nreq, max_steps, chunk, 2e-5)}}
 
 
 def run_condition_study(mem, torch, np, steps=200, every=10):

@@ -56,7 +56,7 @@ struct mem_ctx {
     int2 *d_xlin_terms = nullptr;
     float xmax = 0.f;              // largest 1D node
     float *d_tc_tab = nullptr;     // tensor-core contraction tables (mixed back-end), [704][Q] row-major
-    CUtensorMap tm_tab48, tm_tab256;  // their tensor maps: boxes of 48 and 256 rows x 32 nodes
+    CUtensorMap tm_tab48, tm_tab208, tm_tab192;  // their tensor maps: boxes of 48, 208, 192 rows x 32 nodes
     double *d_phiT64 = nullptr;    // [35][Q] phi_k(ubar_q) in FP64 (residual recompute)
     double *d_logw64 = nullptr;    // [Q] log w_q in FP64
     // Velocity-space rule (mem_init_velocity): nodes fixed in the lab frame.

@@ -12,19 +12,18 @@
 // coalesced by the line-search kernel; the constant statistics tables are
 // row-major [704][Q]:
 //   rows   0- 47: phi_hi (35 used),      rows  48- 95: phi_lo;
-//   rows  96-399: Hessian entries 0-303;  rows 400-703: entries 304-594
-//                                          (rows 695-703 zero).
+//   rows 96 + p:  Hessian entry p, p = 0 .. 594 (rows 691-703 zero).
 // Tensor maps (TMA descriptors) cut them into boxes of 32 nodes (128 bytes:
-// one swizzle span) x 128 cells, 48 or 256 table rows, which the TMA engine
-// writes to shared memory with the 128-byte swizzle (tc.cuh, sdesc_sw128).
-// One CTA (160 threads) computes one tile of 128 cells and one column group
-// (0: moments, 1: Hessian 0-303, 2: Hessian 304-594); the group index runs
-// fastest in the grid, so the three CTAs of a tile run together and two of
-// them read sigma from L2.  Warp 4 issues the tensor loads (three stages,
-// mbarrier transaction counts) and the MMAs (accumulators in TMEM); warps
-// 0-3 read their 32 TMEM lanes, stage the rows in shared memory and write
-// each cell's row of the moments array with coalesced stores.  Every wait is
-// bounded.
+// one swizzle span) x 128 cells, or 48, 208 or 192 table rows, which the TMA
+// engine writes to shared memory with the 128-byte swizzle (tc.cuh,
+// sdesc_sw128).  One CTA (160 threads) computes one tile of 128 cells and
+// one column group (0: moments; 1, 2, 3: Hessian entries 0-207, 208-415,
+// 416-594); the group index runs fastest in the grid, so the four CTAs of a
+// tile run together and three of them read sigma from L2.  Warp 4 issues the
+// tensor loads (two stages, mbarrier transaction counts) and the MMAs
+// (accumulators in TMEM); warps 0-3 read their 32 TMEM lanes, stage the rows
+// in shared memory and write each cell's row of the moments array with
+// coalesced stores.  Every wait is bounded.
 //
 // Accumulation: the tensor cores add the products of one MMA into the FP32
 // accumulator with truncation, so a long chain of MMAs into one accumulator
@@ -48,31 +47,41 @@ using namespace mem;
 
 namespace {
 
-constexpr int NGRP = 3;
+constexpr int NGRP = 4;
 constexpr int TROWS = 704;                    // table rows
-constexpr int HSPLIT = 304;                   // Hessian entries of group 1
+constexpr int HN = 208;                       // Hessian entries of groups 1 and 2 (group 3: 179 of 192)
 constexpr int KCH = 32;                       // nodes per K-chunk (128 bytes of FP32)
-constexpr int STAGES = 3;
+constexpr int STAGES = 2;
 constexpr uint32_t A_BYTES = 128 * KCH * 4;   // 16 KB: one box of sigma
-constexpr uint32_t B_MAX = 304 * KCH * 4;     // 38 KB: the table rows of a Hessian group
-constexpr uint32_t STAGE = 2 * A_BYTES + B_MAX;  // 70 KB, a multiple of 1024
+constexpr uint32_t STAGE = 2 * A_BYTES + 96 * KCH * 4;  // 44 KB: sigma hi + lo + 96 table rows (moments)
 constexpr uint32_t SMEM = STAGES * STAGE + 1024;  // + the 1024-byte alignment of the swizzled tiles
-constexpr int EP = 308;                       // row pitch (floats) of the staged epilogue
+constexpr int EPC = 104;                      // columns per epilogue round
+constexpr int EP = 108;                       // row pitch (floats) of the staged epilogue
+constexpr uint32_t TMEM_COLS = 256;           // two CTAs share an SM's 512 TMEM columns
 constexpr uint32_t kMaxPolls = 1u << 22;
 static_assert(STAGE % 1024 == 0, "stages must keep the 1024-byte alignment of the swizzle atoms");
+static_assert(A_BYTES + HN * KCH * 4 <= STAGE, "a Hessian group's operands fit a stage");
 static_assert(128 * EP * 4 <= STAGES * STAGE, "the epilogue staging reuses the stage buffers");
+static_assert(2 * (SMEM + 1024) <= 227 * 1024, "two CTAs per SM");
+
+__host__ __device__ constexpr int hess_first(int g) { return (g - 1) * HN; }             // first entry of group g
+__host__ __device__ constexpr int hess_cols(int g) { return g == 3 ? 192 : HN; }          // MMA N of group g
+__host__ __device__ constexpr int hess_count(int g) { return g == 3 ? NP1 * NP / 2 - 2 * HN : HN; }
 
 // Warps 0-3 own the 128 accumulator lanes (cells); warp 4 issues the tensor
 // loads and the MMAs.  Group 0 (the moments): each K-chunk's three split
 // products go into a fresh accumulator buffer (NB buffers in rotation), which
 // warps 0-3 add into FP32 registers as soon as the chunk completes, so no
-// accumulator chain is longer than one chunk.  Groups 1, 2 (the Hessian):
-// one accumulator chain over all chunks, read once at the end.
-constexpr int NB = 8;  // moment accumulator buffers (48 columns each)
+// accumulator chain is longer than one chunk.  Groups 1-3 (the Hessian):
+// one accumulator chain over all chunks, read once at the end.  Each CTA
+// holds 256 TMEM columns and 89 KB of shared memory, so two run on an SM
+// and one's epilogue overlaps the other's loads and MMAs.
+constexpr int NB = 5;  // moment accumulator buffers (48 columns each)
 
-__global__ void __launch_bounds__(160, 1)
+__global__ void __launch_bounds__(160, 2)
     k_tc_contract(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
-                  const __grid_constant__ CUtensorMap tm_t48, const __grid_constant__ CUtensorMap tm_t256,
+                  const __grid_constant__ CUtensorMap tm_t48, const __grid_constant__ CUtensorMap tm_t208,
+                  const __grid_constant__ CUtensorMap tm_t192,
                   float *__restrict__ mom, int n, int KC, int *err) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint32_t s_tmem;
@@ -82,7 +91,7 @@ __global__ void __launch_bounds__(160, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int grp = blockIdx.x, tile = blockIdx.y;
     if (warp == 0) {
-        tc::tmem_alloc(&s_tmem, 512);
+        tc::tmem_alloc(&s_tmem, TMEM_COLS);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
@@ -121,16 +130,16 @@ __global__ void __launch_bounds__(160, 1)
                     tc::tma_load_2d(b, &tm_t48, x, 0, bar);
                     tc::tma_load_2d(b + 48 * 128, &tm_t48, x, 48, bar);
                 } else {
-                    const int t0 = grp == 1 ? 96 : 96 + HSPLIT;
-                    tc::mbar_expect_tx(bar, A_BYTES + 304 * 128);
+                    // the table rows follow sigma hi directly (16 KB: the 1024-byte alignment holds)
+                    const int t0 = 96 + hess_first(grp);
+                    tc::mbar_expect_tx(bar, A_BYTES + hess_cols(grp) * 128);
                     tc::tma_load_2d(st, &tm_hi, x, y, bar);
-                    tc::tma_load_2d(b, &tm_t256, x, t0, bar);
-                    tc::tma_load_2d(b + 256 * 128, &tm_t48, x, t0 + 256, bar);
+                    tc::tma_load_2d(st + A_BYTES, grp == 3 ? &tm_t192 : &tm_t208, x, t0, bar);
                 }
                 loaded = kc + 1;
             };
             for (int j = 0; j < STAGES - 1 && j < KC; ++j) load(j);
-            const uint32_t id48 = tc::idesc(128, 48, 2), id256 = tc::idesc(128, 256, 2);
+            const uint32_t id48 = tc::idesc(128, 48, 2), idh = tc::idesc(128, hess_cols(grp), 2);
             for (int kc = 0; kc < KC; ++kc) {
                 const int s = kc % STAGES, bf = kc % NB;
                 if (!tc::mbar_wait(&s_full[s], (kc / STAGES) & 1, kMaxPolls)) {
@@ -158,8 +167,7 @@ __global__ void __launch_bounds__(160, 1)
                         tc::mma_tf32(dacc, dh, bmh, id48, 1);       // hi . hi
                     } else {
                         const uint32_t acc = (kc | k) != 0;
-                        tc::mma_tf32(tmem, dh, tc::sdesc_sw128(b + 32 * k, 1024), id256, acc);
-                        tc::mma_tf32(tmem + 256, dh, tc::sdesc_sw128(b + 256 * 128 + 32 * k, 1024), id48, acc);
+                        tc::mma_tf32(tmem, dh, tc::sdesc_sw128(ahi + A_BYTES + 32 * k, 1024), idh, acc);  // rows after sigma hi
                     }
                 }
                 tc::mma_commit(&s_empty[s]);
@@ -223,37 +231,42 @@ __global__ void __launch_bounds__(160, 1)
         done = __all_sync(0xffffffffu, done) && !s_fail;
         tc::fence_after_sync();
         if (done) {
-            // stage this warp's 32 rows in shared memory, then write each row
-            // with the whole warp (consecutive addresses)
+            // stage this warp's 32 rows in shared memory, EPC columns at a
+            // time, then write each row with the whole warp (consecutive
+            // addresses)
             float *ep = reinterpret_cast<float *>(smem) + (size_t)32 * warp * EP;
             float *my = ep + (size_t)lane * EP;
-            const int col0 = grp == 0 ? 0 : grp == 1 ? NP : NP + HSPLIT;
-            const int cnt = grp == 0 ? NP : grp == 1 ? HSPLIT : NP1 * NP / 2 - HSPLIT;
-            if (grp == 0) {
-#pragma unroll
-                for (int c = 0; c < 36; c += 4)
-                    *reinterpret_cast<float4 *>(my + c) = make_float4(sum[c], sum[c + 1], sum[c + 2], sum[c + 3]);
-            } else {
-                const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
-                for (int c = 0; c < 304; c += 8) {
-                    float v[8];
-                    tc::tmem_ld8(tl + (uint32_t)c, v);
-                    *reinterpret_cast<float4 *>(my + c) = make_float4(v[0], v[1], v[2], v[3]);
-                    *reinterpret_cast<float4 *>(my + c + 4) = make_float4(v[4], v[5], v[6], v[7]);
-                }
-            }
-            __syncwarp();
+            const int col0 = grp == 0 ? 0 : NP + hess_first(grp);
+            const int cnt = grp == 0 ? NP : hess_count(grp);
+            const uint32_t tl = tmem + ((uint32_t)(32 * warp) << 16);
             const int cell0 = tile * 128 + 32 * warp;
-            for (int r = 0; r < 32 && cell0 + r < n; ++r) {
-                float *m = mom + (size_t)(cell0 + r) * MEM_NCOL_SOLVE + col0;
-                const float *e = ep + (size_t)r * EP;
-                for (int j = lane; j < cnt; j += 32) m[j] = e[j];
+            for (int c0 = 0; c0 < cnt; c0 += EPC) {
+                if (grp == 0) {
+#pragma unroll
+                    for (int c = 0; c < 36; c += 4)
+                        *reinterpret_cast<float4 *>(my + c) = make_float4(sum[c], sum[c + 1], sum[c + 2], sum[c + 3]);
+                } else {
+                    for (int c = 0; c < EPC && c0 + c < hess_cols(grp); c += 8) {
+                        float v[8];
+                        tc::tmem_ld8(tl + (uint32_t)(c0 + c), v);
+                        *reinterpret_cast<float4 *>(my + c) = make_float4(v[0], v[1], v[2], v[3]);
+                        *reinterpret_cast<float4 *>(my + c + 4) = make_float4(v[4], v[5], v[6], v[7]);
+                    }
+                }
+                __syncwarp();
+                const int w = min(EPC, cnt - c0);
+                for (int r = 0; r < 32 && cell0 + r < n; ++r) {
+                    float *m = mom + (size_t)(cell0 + r) * MEM_NCOL_SOLVE + col0 + c0;
+                    const float *e = ep + (size_t)r * EP;
+                    for (int j = lane; j < w; j += 32) m[j] = e[j];
+                }
+                __syncwarp();  // the staging rows are free for the next round
             }
         }
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
 }
 
 // Host round to TF32 (nearest, ties away from zero: the rounding of
@@ -332,7 +345,8 @@ int build_tc_tables(mem_ctx *ctx, const std::vector<double> &phi /*[Q][35]*/) {
         return MEM_ECUDA;
     }
     if (encode_tmap_2d_f32(&ctx->tm_tab48, d, Q, TROWS, KCH, 48) ||
-        encode_tmap_2d_f32(&ctx->tm_tab256, d, Q, TROWS, KCH, 256)) {
+        encode_tmap_2d_f32(&ctx->tm_tab208, d, Q, TROWS, KCH, 208) ||
+        encode_tmap_2d_f32(&ctx->tm_tab192, d, Q, TROWS, KCH, 192)) {
         cudaFree(d);
         return MEM_OK;  // no tensor maps: the mixed back-end is unavailable (MEM_EINVAL)
     }
@@ -357,7 +371,8 @@ int tc_contract(mem_ctx *ctx, const float *a_hi, const float *a_lo, int64_t rows
     if (encode_tmap_2d_f32(&thi, a_hi, ctx->Q, rows, KCH, 128) || encode_tmap_2d_f32(&tlo, a_lo, ctx->Q, rows, KCH, 128))
         return MEM_ECUDA;
     dim3 grid(NGRP, (n + 127) / 128);
-    k_tc_contract<<<grid, 160, SMEM, st>>>(thi, tlo, ctx->tm_tab48, ctx->tm_tab256, mom, n, ctx->Q / KCH, err);
+    k_tc_contract<<<grid, 160, SMEM, st>>>(thi, tlo, ctx->tm_tab48, ctx->tm_tab208, ctx->tm_tab192, mom, n,
+                                           ctx->Q / KCH, err);
     MEM_CUDA_TRY(cudaGetLastError());
     return MEM_OK;
 }

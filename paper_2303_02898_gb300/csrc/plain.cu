@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(BLK) k_linesearch(const int *__restrict__ act,
 // tensor Gauss-Hermite grid (nodes q = i N^2 + p, lane l owning the node
 // lines p = l + 32 r: the order of the dense tables) and sigma written as a
 // TF32 hi row and a TF32 lo row (sigma = hi + lo to about 2^-22), 32
-// consecutive nodes per warp store.
+// consecutive nodes per warp store.  Persistent: resident blocks whose warps
+// loop over the active cells.
 template <int N>
 __global__ void __launch_bounds__(128) k_linesearch_sf(const int *__restrict__ act, int nact,
                                                        const float *__restrict__ M, float *__restrict__ beta,
@@ -200,75 +201,77 @@ __global__ void __launch_bounds__(128) k_linesearch_sf(const int *__restrict__ a
     for (int t = threadIdx.x; t < N; t += blockDim.x) s_lw[t] = logw1d[t];
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int slot = blockIdx.x * 4 + w;
-    if (slot >= nact) return;
-    const int c = act[slot];
-    const float *Mc = M + (size_t)c * NP;
-    float *bc = beta + (size_t)c * NP;
-    float *sb = sv[w][0], *sd = sv[w][1], *sg = sv[w][2], *sm = sv[w][3];
-    const float n = Mc[0];
-    for (int k = lane; k < NP; k += 32) {
-        sb[k] = k ? bc[k] : 0.f;
-        sd[k] = k ? S.db[(size_t)c * NP + k] : 0.f;
-        sg[k] = k ? S.G[(size_t)c * NP + k] : 0.f;
-        sm[k] = k ? Mc[k] / n : 0.f;
-    }
-    __syncwarp();
-    float pg = 0.f, pb = 0.f, pd = 0.f;
-    for (int k = lane; k < NP; k += 32) {
-        pg += sg[k] * sd[k];
-        pb += sb[k] * sm[k];
-        pd += sd[k] * sm[k];
-    }
-    const float gd = warp_sum(pg), mb = warp_sum(pb), md = warp_sum(pd);
-    float eb[C::NODES], ed[C::NODES];
-    exponent<N>(sb, s_he, s_lw, lane, true, eb);
-    exponent<N>(sd, s_he, s_lw, lane, false, ed);
-    float Lcur = S.Lcur[c];
-    if (isnan(Lcur)) {  // first pass: objective at the start point
-        float m = -INFINITY;
+    // persistent: each warp takes active cells gridDim.x * 4 apart
+    for (int slot = blockIdx.x * 4 + w; slot < nact; slot += gridDim.x * 4) {
+        const int c = act[slot];
+        const float *Mc = M + (size_t)c * NP;
+        float *bc = beta + (size_t)c * NP;
+        float *sb = sv[w][0], *sd = sv[w][1], *sg = sv[w][2], *sm = sv[w][3];
+        const float n = Mc[0];
+        for (int k = lane; k < NP; k += 32) {
+            sb[k] = k ? bc[k] : 0.f;
+            sd[k] = k ? S.db[(size_t)c * NP + k] : 0.f;
+            sg[k] = k ? S.G[(size_t)c * NP + k] : 0.f;
+            sm[k] = k ? Mc[k] / n : 0.f;
+        }
+        __syncwarp();
+        float pg = 0.f, pb = 0.f, pd = 0.f;
+        for (int k = lane; k < NP; k += 32) {
+            pg += sg[k] * sd[k];
+            pb += sb[k] * sm[k];
+            pd += sd[k] * sm[k];
+        }
+        const float gd = warp_sum(pg), mb = warp_sum(pb), md = warp_sum(pd);
+        float eb[C::NODES], ed[C::NODES];
+        exponent<N>(sb, s_he, s_lw, lane, true, eb);
+        exponent<N>(sd, s_he, s_lw, lane, false, ed);
+        float Lcur = S.Lcur[c];
+        if (isnan(Lcur)) {  // first pass: objective at the start point
+            float m = -INFINITY;
 #pragma unroll
-        for (int q = 0; q < C::NODES; ++q) m = fmaxf(m, eb[q]);
-        const float mx0 = warp_max(m);
-        float z = 0.f;
+            for (int q = 0; q < C::NODES; ++q) m = fmaxf(m, eb[q]);
+            const float mx0 = warp_max(m);
+            float z = 0.f;
 #pragma unroll
-        for (int q = 0; q < C::NODES; ++q) z += __expf(eb[q] - mx0);
-        Lcur = mx0 + logf(warp_sum(z)) - mb;
-    }
-    float alpha = 2.f, Lt = NAN, mx = 0.f, Z = 1.f;
-    bool sat = false;
-    for (int s = 0; !sat && s <= o.maxT; ++s) {
-        alpha *= 0.5f;
-        float m = -INFINITY;
+            for (int q = 0; q < C::NODES; ++q) z += __expf(eb[q] - mx0);
+            Lcur = mx0 + logf(warp_sum(z)) - mb;
+        }
+        float alpha = 2.f, Lt = NAN, mx = 0.f, Z = 1.f;
+        bool sat = false;
+        for (int s = 0; !sat && s <= o.maxT; ++s) {
+            alpha *= 0.5f;
+            float m = -INFINITY;
 #pragma unroll
-        for (int q = 0; q < C::NODES; ++q) m = fmaxf(m, fmaf(alpha, ed[q], eb[q]));
-        mx = warp_max(m);
-        float z = 0.f;
+            for (int q = 0; q < C::NODES; ++q) m = fmaxf(m, fmaf(alpha, ed[q], eb[q]));
+            mx = warp_max(m);
+            float z = 0.f;
 #pragma unroll
-        for (int q = 0; q < C::NODES; ++q) z += __expf(fmaf(alpha, ed[q], eb[q]) - mx);
-        Z = warp_sum(z);
-        Lt = mx + logf(Z) - (mb + alpha * md);
-        const float LD = Lcur - Lt, gradD = -o.c_armijo * alpha * gd;
-        sat = (LD - gradD) >= -(o.atol + o.rtol * fabsf(LD));
-    }
-    const float invZ = 1.f / Z;
-    float *hi_row = S.sigma + (size_t)slot * Q, *lo_row = S.sig_lo + (size_t)slot * Q;
+            for (int q = 0; q < C::NODES; ++q) z += __expf(fmaf(alpha, ed[q], eb[q]) - mx);
+            Z = warp_sum(z);
+            Lt = mx + logf(Z) - (mb + alpha * md);
+            const float LD = Lcur - Lt, gradD = -o.c_armijo * alpha * gd;
+            sat = (LD - gradD) >= -(o.atol + o.rtol * fabsf(LD));
+        }
+        const float invZ = 1.f / Z;
+        float *hi_row = S.sigma + (size_t)slot * Q, *lo_row = S.sig_lo + (size_t)slot * Q;
 #pragma unroll
-    for (int r = 0; r < C::R; ++r) {
-        const int p = lane + 32 * r;
-        if (p < C::P) {
+        for (int r = 0; r < C::R; ++r) {
+            const int p = lane + 32 * r;
+            if (p < C::P) {
 #pragma unroll
-            for (int i = 0; i < N; ++i) {
-                const float v = __expf(fmaf(alpha, ed[r * N + i], eb[r * N + i]) - mx) * invZ;
-                const float hi = tc_round(v);
-                hi_row[i * C::P + p] = hi;
-                lo_row[i * C::P + p] = tc_round(v - hi);
+                for (int i = 0; i < N; ++i) {
+                    const float v = __expf(fmaf(alpha, ed[r * N + i], eb[r * N + i]) - mx) * invZ;
+                    const float hi = tc_round(v);
+                    hi_row[i * C::P + p] = hi;
+                    lo_row[i * C::P + p] = tc_round(v - hi);
+                }
             }
         }
+        for (int k = lane; k < NP; k += 32)
+            if (k >= 1) bc[k] = sb[k] + alpha * sd[k];
+        if (lane == 0) { S.Lcur[c] = Lt; S.alpha[c] = alpha; }
+        __syncwarp();  // the warp's vectors are free for its next cell
     }
-    for (int k = lane; k < NP; k += 32)
-        if (k >= 1) bc[k] = sb[k] + alpha * sd[k];
-    if (lane == 0) { S.Lcur[c] = Lt; S.alpha[c] = alpha; }
 }
 
 // C[M x N] = A[M x K] B[K x N], row-major, 64x64 tiles, 4x4 per thread.
@@ -703,6 +706,20 @@ void sgemm(const float *A, const float *Bm, float *C, int M, int N, int K, cudaS
 
 namespace mem_host {
 
+// Resident blocks of the mixed back-end's persistent line-search kernel.
+template <int N>
+static int linesearch_sf_grid(mem_ctx *ctx) {
+    static int grid = 0;
+    if (!grid) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_linesearch_sf<N>, 128, 0);
+        cudaGetLastError();
+        grid = std::max(1, sms * std::max(1, per_sm));
+    }
+    return grid;
+}
+
 // Resident blocks of the mixed back-end's persistent Newton kernel.
 static int newton_reg_grid(mem_ctx *ctx) {
     static int grid = 0;
@@ -779,10 +796,10 @@ static int solve_dense(mem_ctx *ctx, const float *M, float *beta, int32_t *statu
         for (int pass = 0; pass <= o.maxI + 1 && nact > 0; ++pass) {
             if (mixed) {
                 if (ctx->n1d == 8)
-                    k_linesearch_sf<8><<<(nact + 3) / 4, 128, 0, st>>>(cur, nact, Mc, bc, S, ctx->d_he1d,
+                    k_linesearch_sf<8><<<std::min((nact + 3) / 4, linesearch_sf_grid<8>(ctx)), 128, 0, st>>>(cur, nact, Mc, bc, S, ctx->d_he1d,
                                                                       ctx->d_logw1d, o);
                 else
-                    k_linesearch_sf<12><<<(nact + 3) / 4, 128, 0, st>>>(cur, nact, Mc, bc, S, ctx->d_he1d,
+                    k_linesearch_sf<12><<<std::min((nact + 3) / 4, linesearch_sf_grid<12>(ctx)), 128, 0, st>>>(cur, nact, Mc, bc, S, ctx->d_he1d,
                                                                        ctx->d_logw1d, o);
                 rc = tc_contract(ctx, S.sigma, S.sig_lo, (int64_t)(sig / Q), S.mom, nact, S.err, st);
                 if (rc) return rc;

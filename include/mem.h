@@ -536,6 +536,20 @@ int mem_tune(mem_ctx *ctx, int kernel, const float *M, const float *beta0, const
 int mem_set_launch(mem_ctx *ctx, int kernel, int warps, int blocks_per_sm);
 int mem_get_launch(const mem_ctx *ctx, int kernel, int32_t *warps, int32_t *blocks_per_sm);
 
+/* The tuning table on disk, a text file of lines
+ *   device-name<TAB>rule<TAB>kernel<TAB>warps<TAB>blocks_per_sm
+ * keyed by the GPU's name, the context's rule ("gh8", "gh12", or
+ * "vel<nbx>x<nbr>x<ng>x<K>") and the kernel (MEM_TUNE_FUSED on Gauss-Hermite
+ * contexts, MEM_TUNE_AXI on velocity-space ones).  mem_tune_save writes the
+ * context's current shape for its kernel, replacing the line with the same
+ * key (the file is rewritten through a temporary and a rename; MEM_EINVAL if
+ * it cannot be written).  mem_tune_load applies the matching line
+ * (MEM_ENOTFOUND if none, MEM_EINVAL if the file cannot be read).
+ * mem_init and mem_init_velocity load the table named by the environment
+ * variable MEM_TUNE_TABLE, when it is set, into every new context. */
+int mem_tune_save(const mem_ctx *ctx, const char *path);
+int mem_tune_load(mem_ctx *ctx, const char *path);
+
 /* ---------------------------------------------------------------------- */
 /* Measurement services (no counterpart in the paper): the rates the
  * roofline fractions of the library's kernels are quoted against. */

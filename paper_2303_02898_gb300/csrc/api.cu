@@ -466,6 +466,7 @@ int mem_init(int degree, int quad_order, mem_ctx **out) {
             ctx, std::max(mem_host::plain_scratch_bytes(Q), mem_host::flux_scratch_bytes(Q)));
     if (rc) { mem_destroy(ctx); return rc; }
     if (cudaDeviceSynchronize() != cudaSuccess) { mem_destroy(ctx); return MEM_ECUDA; }
+    if (const char *table = getenv("MEM_TUNE_TABLE")) mem_tune_load(ctx, table);  // a missing entry keeps the defaults
     *out = ctx;
     return MEM_OK;
 }
@@ -518,6 +519,7 @@ int mem_init_velocity(int degree, int nbx, int nbr, int ng, int K, double ax, do
     if (!rc) rc = mem_host::reserve_scratch(ctx, sizeof(float) * (size_t)VEL_FLUX_CHUNK * MEM_MU_STRIDE);
     if (rc) { mem_destroy(ctx); return rc; }
     if (cudaDeviceSynchronize() != cudaSuccess) { mem_destroy(ctx); return MEM_ECUDA; }
+    if (const char *table = getenv("MEM_TUNE_TABLE")) mem_tune_load(ctx, table);  // a missing entry keeps the defaults
     *out = ctx;
     return MEM_OK;
 }

@@ -109,3 +109,85 @@ int mem_tune(mem_ctx *ctx, int kernel, const float *M, const float *beta0, const
 }
 
 }  // extern "C"
+
+// ---- the tuning table on disk: one line per (device, rule, kernel),
+// "device<TAB>rule<TAB>kernel<TAB>warps<TAB>blocks_per_sm".
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+namespace {
+
+std::string rule_key(const mem_ctx *ctx) {
+    char b[96];
+    if (ctx->vel) snprintf(b, sizeof b, "vel%dx%dx%dx%d", ctx->nbx, ctx->nbr, ctx->ng, ctx->K);
+    else snprintf(b, sizeof b, "gh%d", ctx->n1d);
+    return b;
+}
+
+std::string device_key(const mem_ctx *ctx) {
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, ctx->device) != cudaSuccess) {
+        cudaGetLastError();
+        return "unknown";
+    }
+    std::string s(p.name);
+    for (char &ch : s)
+        if (ch == '\t' || ch == '\n') ch = ' ';
+    return s;
+}
+
+int tuned_kernel(const mem_ctx *ctx) { return ctx->vel ? MEM_TUNE_AXI : MEM_TUNE_FUSED; }
+
+}  // namespace
+
+extern "C" {
+
+int mem_tune_save(const mem_ctx *ctx, const char *path) {
+    if (!ctx || !path) return MEM_EINVAL;
+    const std::string dev = device_key(ctx), rule = rule_key(ctx);
+    const int kernel = tuned_kernel(ctx);
+    const mem_launch_cfg &c = ctx->vel ? ctx->cfg_axi : ctx->cfg_fused;
+    std::vector<std::string> keep;
+    if (FILE *f = fopen(path, "r")) {
+        char line[512];
+        while (fgets(line, sizeof line, f)) {
+            char d[256] = {0}, r[96] = {0};
+            int k = -1, w = 0, b = 0;
+            const bool same = sscanf(line, "%255[^\t]\t%95[^\t]\t%d\t%d\t%d", d, r, &k, &w, &b) == 5 && dev == d &&
+                              rule == r && k == kernel;
+            if (!same && strchr(line, '\t')) keep.push_back(line);
+        }
+        fclose(f);
+    }
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return MEM_EINVAL;
+    for (const std::string &l : keep) fputs(l.c_str(), f);
+    fprintf(f, "%s\t%s\t%d\t%d\t%d\n", dev.c_str(), rule.c_str(), kernel, c.warps, c.blocks_per_sm);
+    const bool ok = fclose(f) == 0 && rename(tmp.c_str(), path) == 0;
+    return ok ? MEM_OK : MEM_EINVAL;
+}
+
+int mem_tune_load(mem_ctx *ctx, const char *path) {
+    if (!ctx || !path) return MEM_EINVAL;
+    FILE *f = fopen(path, "r");
+    if (!f) return MEM_EINVAL;
+    const std::string dev = device_key(ctx), rule = rule_key(ctx);
+    const int kernel = tuned_kernel(ctx);
+    int found = 0;
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        char d[256] = {0}, r[96] = {0};
+        int k = -1, w = 0, b = 0;
+        if (sscanf(line, "%255[^\t]\t%95[^\t]\t%d\t%d\t%d", d, r, &k, &w, &b) == 5 && dev == d && rule == r &&
+            k == kernel && mem_set_launch(ctx, kernel, w, b) == MEM_OK)
+            found = 1;  // the last matching line wins
+    }
+    fclose(f);
+    return found ? MEM_OK : MEM_ENOTFOUND;
+}
+
+}  // extern "C"

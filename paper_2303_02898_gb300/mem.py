@@ -113,6 +113,10 @@ def lib():
         L.mem_set_launch.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.mem_get_launch.restype = ctypes.c_int
         L.mem_get_launch.argtypes = [_P, ctypes.c_int, _P, _P]
+        L.mem_tune_save.restype = ctypes.c_int
+        L.mem_tune_save.argtypes = [_P, ctypes.c_char_p]
+        L.mem_tune_load.restype = ctypes.c_int
+        L.mem_tune_load.argtypes = [_P, ctypes.c_char_p]
         L.mem_residual64.restype = ctypes.c_int
         L.mem_residual64.argtypes = [_P, _P, _P, _P, ctypes.c_int32, _P, _P, ctypes.c_double, ctypes.c_int64, _P]
         L.mem_bench_peak.restype = ctypes.c_int
@@ -262,6 +266,19 @@ class Context:
         w, b = ctypes.c_int32(), ctypes.c_int32()
         _check(lib().mem_get_launch(self.h, kernel, ctypes.byref(w), ctypes.byref(b)), "mem_get_launch")
         return w.value, b.value
+
+    def tune_save(self, path):
+        """mem_tune_save: write this context's launch shape to the tuning table."""
+        _check(lib().mem_tune_save(self.h, os.fsencode(path)), "mem_tune_save")
+
+    def tune_load(self, path):
+        """mem_tune_load: apply the table's entry for this GPU, rule and kernel;
+        False when the table has none."""
+        rc = lib().mem_tune_load(self.h, os.fsencode(path))
+        if rc == MEM_ENOTFOUND:
+            return False
+        _check(rc, "mem_tune_load")
+        return True
 
     def residual64(self, M, beta, res, status=None, mask=0, status_out=None, accept=1e-5, stream=None):
         """mem_residual64: FP64 relative moment residual per cell (res: float64

@@ -74,3 +74,36 @@ def test_tune_nine_statistic_solve(O, mem):
         vctx.solve_axi(M, b, g)
         assert torch.equal(b, b_def), (cw, cb)
     vctx.close()
+
+
+def test_tuning_table_round_trip(mem, tmp_path, monkeypatch):
+    """mem_tune_save / mem_tune_load: the shape kept for this GPU, rule and
+    kernel comes back in a new context, also through MEM_TUNE_TABLE at
+    context creation; other rules and kernels keep their defaults."""
+    path = str(tmp_path / "tune.tsv")
+    c8 = mem.Context(8)
+    c8.set_launch(mem.TUNE_FUSED, 8, 2)
+    c8.tune_save(path)
+    c8.set_launch(mem.TUNE_FUSED, 2, 6)
+    c8.tune_save(path)                      # replaces the line with the same key
+    c8.close()
+    lines = open(path).read().strip().splitlines()
+    assert len(lines) == 1 and lines[0].split("\t")[2:] == ["0", "2", "6"]
+    v = mem.Context.velocity(mem.shock_domain(mach=10.0))
+    v.set_launch(mem.TUNE_AXI, 2, 10)
+    v.tune_save(path)
+    v.close()
+    assert len(open(path).read().strip().splitlines()) == 2
+    n8 = mem.Context(8)
+    assert n8.get_launch(mem.TUNE_FUSED) == (4, 0)
+    assert n8.tune_load(path) and n8.get_launch(mem.TUNE_FUSED) == (2, 6)
+    n8.close()
+    n12 = mem.Context(12)
+    assert not n12.tune_load(path) and n12.get_launch(mem.TUNE_FUSED) == (4, 0)
+    n12.close()
+    monkeypatch.setenv("MEM_TUNE_TABLE", path)
+    a8 = mem.Context(8)
+    av = mem.Context.velocity(mem.shock_domain(mach=10.0))
+    assert a8.get_launch(mem.TUNE_FUSED) == (2, 6) and av.get_launch(mem.TUNE_AXI) == (2, 10)
+    a8.close()
+    av.close()

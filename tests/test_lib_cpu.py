@@ -45,6 +45,8 @@ def test_invalid_arguments_rejected_without_gpu():
     assert L.mem_init(4, 40, ctypes.byref(h)) == mem.MEM_EINVAL
     assert L.mem_solve(None, None, None, None, None, 0, None, None) == mem.MEM_EINVAL
     assert L.mem_solve_host(None, None, None, None, None, 0, 0, None, None) == mem.MEM_EINVAL
+    assert L.mem_tune_save(None, None) == mem.MEM_EINVAL
+    assert L.mem_tune_load(None, b"/nonexistent") == mem.MEM_EINVAL
 
 
 def test_oracle_and_library_share_no_code():
